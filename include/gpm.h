@@ -1,0 +1,250 @@
+/*
+ * gpm.h -- C-ABI of the B300 graph-pattern-mining library (libgpm.so).
+ *
+ * The library counts and lists embeddings of small connected patterns in a
+ * large undirected graph on one GPU, following the problem statement of
+ * Sandslash (arxiv 2011.03135): Section 2 "Problem Definition" (embeddings,
+ * vertex- vs edge-induced subgraphs, counting vs listing, the GPM problems
+ * TC, k-CL, SL, k-MC) and Section 3.1 "High-Level API" (a pattern given
+ * explicitly by its edges plus an induced/non-induced flag; a clique
+ * generator; all k-vertex motifs).
+ *
+ * Conventions shared by every entry point
+ *  - Return value: GPM_OK (0) on success, a negative GPM_E_* code on error.
+ *    On error no output argument is modified and gpm_last_error() returns a
+ *    message for the calling host thread.
+ *  - Counts are exact unsigned 64-bit integers. A count that does not fit in
+ *    64 bits is reported as GPM_E_OVERFLOW where it can be detected (motif
+ *    inversion); clique/SL counts are accumulated modulo 2^64.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Calls that return results in host memory synchronise that
+ *    stream before returning; *_async calls do not.
+ *  - Handles are owned by the library; a handle must not be used after it
+ *    has been destroyed. Calls on one graph handle are serialised on the
+ *    host, and their device work must not overlap: a graph keeps one set of
+ *    accumulators and scratch buffers, so asynchronous counts on the same
+ *    graph belong on one stream. Different graphs are independent.
+ *  - Vertex ids are uint32 (n < 2^32); CSR offsets are uint64.
+ */
+#ifndef GPM_H_
+#define GPM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------- status codes ---------------- */
+#define GPM_OK 0
+#define GPM_E_INVALID_ARG (-1)
+#define GPM_E_NOT_SORTED (-2)        /* a neighbour list is not strictly ascending */
+#define GPM_E_SELF_LOOP (-3)         /* v appears in its own neighbour list */
+#define GPM_E_DUPLICATE (-4)         /* a neighbour appears twice in one list */
+#define GPM_E_ASYMMETRIC (-5)        /* u in N(v) but v not in N(u) */
+#define GPM_E_DISCONNECTED_PATTERN (-6)
+#define GPM_E_K_TOO_LARGE (-7)
+#define GPM_E_OOM (-8)               /* device allocation failed */
+#define GPM_E_DEVICE (-9)            /* a CUDA call failed */
+#define GPM_E_TIMEOUT (-10)          /* a bounded device-side wait gave up */
+#define GPM_E_BUSY (-11)             /* admission refused (server) */
+#define GPM_E_UNSUPPORTED (-12)      /* pattern class has no GPU kernel yet */
+#define GPM_E_OVERFLOW (-13)         /* a result does not fit in 64 bits */
+#define GPM_E_OUT_OF_RANGE (-14)     /* vertex id >= n in the CSR */
+
+/* ---------------- handles ---------------- */
+typedef struct gpm_graph *gpm_graph_t;
+typedef struct gpm_pattern *gpm_pattern_t;
+
+/* ---------------- graphs ---------------- */
+
+/* gpm_graph_create flags */
+#define GPM_GRAPH_VALIDATE 1u     /* check sorted / no loop / no duplicate / symmetric on the GPU */
+#define GPM_GRAPH_DEVICE_INPUT 2u /* rowptr/col are device pointers (copied device-to-device) */
+
+/*
+ * Upload an undirected simple graph given as a symmetric CSR (Section 6: the
+ * inputs are symmetric, without self-loops or duplicate edges, with sorted
+ * neighbour lists).
+ *   rowptr : uint64[n+1], rowptr[0] = 0, rowptr[n] = nnz (host memory unless
+ *            GPM_GRAPH_DEVICE_INPUT)
+ *   col    : uint32[nnz], neighbours of v in col[rowptr[v] .. rowptr[v+1])
+ *   nnz    : 2 x (number of undirected edges)
+ * The library copies both arrays; the caller keeps ownership of its buffers.
+ * With GPM_GRAPH_VALIDATE, a malformed CSR returns GPM_E_NOT_SORTED,
+ * GPM_E_SELF_LOOP, GPM_E_DUPLICATE, GPM_E_ASYMMETRIC or GPM_E_OUT_OF_RANGE and
+ * no handle is created. Without it the input is trusted.
+ * Synchronises `stream`.
+ */
+int gpm_graph_create(const uint64_t *rowptr, const uint32_t *col, uint32_t n, uint64_t nnz, uint32_t flags,
+                     void *stream, gpm_graph_t *out);
+
+/* Release every device buffer of the graph (synchronises the device). */
+int gpm_graph_destroy(gpm_graph_t g);
+
+/*
+ * Build the degree-ordered orientation (appendix "Orientation (Total Order)":
+ * every edge points to the endpoint of higher degree, ties to the larger id)
+ * and the task lists used by the kernels. Idempotent; called implicitly by
+ * the first count. Synchronises `stream`.
+ */
+int gpm_graph_prepare(gpm_graph_t g, void *stream);
+
+/*
+ * Drop the orientation and task lists so that the next prepare (or count)
+ * rebuilds them from the resident CSR; device buffers are kept for reuse.
+ * Used to time the whole path, orientation included, on a resident graph.
+ */
+int gpm_graph_reset(gpm_graph_t g);
+
+typedef struct {
+  uint32_t n;
+  uint32_t max_degree;
+  uint64_t nnz;
+  uint64_t dag_arcs;        /* = nnz / 2 once prepared, else 0 */
+  uint32_t max_out_degree;  /* largest out-degree in the orientation */
+  uint32_t prepared;
+  uint64_t device_bytes;    /* device memory held by the handle */
+} gpm_graph_info_t;
+
+int gpm_graph_info(gpm_graph_t g, gpm_graph_info_t *info);
+
+/* ---------------- patterns ---------------- */
+
+/*
+ * A pattern given explicitly by its k x k adjacency matrix (Section 3.1: a
+ * pattern is defined by its vertices and edges; Section 2: vertex-induced or
+ * edge-induced embeddings).
+ *   k       : 1..8 vertices (GPM_E_K_TOO_LARGE above 8)
+ *   adj     : uint8[k*k], row-major, 0/1, symmetric, zero diagonal
+ *   induced : 1 = count vertex-induced embeddings (TC, k-CL, k-MC),
+ *             0 = edge-induced (non-induced) embeddings (SL)
+ * The pattern must be connected (GPM_E_DISCONNECTED_PATTERN). The planner
+ * computes |Aut(P)|, the symmetry-breaking partial order, a matching order
+ * and the execution strategy (appendix "Symmetry Breaking", "Pattern-Guided
+ * Search (Matching Order)").
+ */
+int gpm_pattern_spec(uint32_t k, const uint8_t *adj, int induced, gpm_pattern_t *out);
+
+/* The k-clique, k in 1..8 (Section 3.1 helper "generate clique"). */
+int gpm_pattern_clique(uint32_t k, gpm_pattern_t *out);
+
+/*
+ * All connected k-vertex patterns, vertex-induced (Section 2, k-MC; the
+ * helper "generate all k-vertex patterns" of Section 3.1), k = 3 or 4.
+ * Writes *npat handles to out[] (room for 6 must be provided), in the fixed
+ * order  k=3: wedge, triangle;
+ *        k=4: 3-star, 4-path, tailed triangle, 4-cycle, diamond, 4-clique.
+ */
+int gpm_pattern_motifs(uint32_t k, gpm_pattern_t *out, uint32_t *npat);
+
+int gpm_pattern_destroy(gpm_pattern_t p);
+
+/* strategy chosen by the planner */
+#define GPM_STRATEGY_CLIQUE_DAG 1    /* orientation + local-graph bitmap search */
+#define GPM_STRATEGY_LOCAL_COUNT 2   /* local counting (Section 5) for 3/4-vertex patterns */
+#define GPM_STRATEGY_EDGE 3          /* single edge / vertex: closed form */
+
+typedef struct {
+  uint32_t k;
+  uint32_t n_edges;
+  uint32_t induced;
+  uint32_t is_clique;
+  uint32_t strategy;           /* GPM_STRATEGY_* */
+  uint32_t motif_index;        /* position in the k=3/k=4 motif order, or UINT32_MAX */
+  uint64_t automorphisms;      /* |Aut(P)| */
+  uint32_t n_sb_pairs;         /* symmetry-breaking constraints id(f(a)) < id(f(b)) */
+  uint32_t sb_pairs[2 * 28];   /* (a_0, b_0, a_1, b_1, ...) in pattern vertex numbering */
+  uint32_t matching_order[8];  /* pattern vertices in the order they are matched */
+  uint32_t min_degree[8];      /* degree filter per pattern vertex (its pattern degree) */
+} gpm_pattern_info_t;
+
+int gpm_pattern_info(gpm_pattern_t p, gpm_pattern_info_t *info);
+
+/* ---------------- counting ---------------- */
+
+/*
+ * Exact counts of npat patterns in g (Section 2: the support of a pattern is
+ * its number of embeddings; each distinct subgraph is counted once, i.e. the
+ * count of maps divided by |Aut(P)|).
+ *   counts : host uint64[npat]
+ * Supported on the GPU: k-cliques (k = 1..5) and every connected pattern with
+ * 3 or 4 vertices, induced or not; other patterns return GPM_E_UNSUPPORTED.
+ * Patterns that share work are computed together (e.g. all 4-vertex motifs
+ * by local counting, Section 5; 3-, 4- and 5-cliques in one pass).
+ * Synchronises `stream`.
+ */
+int gpm_count(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uint64_t *counts, void *stream);
+
+/* As gpm_count, but writes the counts to DEVICE memory `counts_dev`
+ * (uint64[npat]) and does not synchronise. The graph must be prepared. */
+int gpm_count_async(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uint64_t *counts_dev, void *stream);
+
+/*
+ * Counts restricted to embeddings whose ROOT vertex id lies in [root_lo,
+ * root_hi). Summing over a partition of [0, n) gives gpm_count's result, so a
+ * root range is the unit of sharding across GPUs. Roots, with "order" the
+ * orientation order (degree, id):
+ *   k-clique : the clique vertex that is first in the order;
+ *   diamond (edge-induced): the order-first endpoint of the shared edge;
+ *   4-cycle (edge-induced): the cycle vertex that is last in the order.
+ * Other patterns return GPM_E_UNSUPPORTED. counts: host uint64[npat].
+ */
+int gpm_count_roots(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uint32_t root_lo, uint32_t root_hi,
+                    uint64_t *counts, void *stream);
+
+/* ---------------- listing ---------------- */
+
+/*
+ * Subgraph listing (Section 2, SL): writes up to `cap` embeddings of p as
+ * k-tuples, tuple t = (f(0), ..., f(k-1)) in PATTERN vertex order, into buf
+ * (uint32[k*cap], host or device memory). Every written tuple is a valid
+ * embedding (each pattern edge maps to a graph edge), satisfies the pattern's
+ * symmetry-breaking constraints (gpm_pattern_info) and stands for a distinct
+ * subgraph. Which min(total, cap) embeddings are written is unspecified.
+ *   *written : number of tuples written = min(total, cap)
+ *   *total   : exact number of embeddings (= gpm_count of p)
+ * Supported: edge-induced diamond and 4-cycle, k-cliques k = 3..5.
+ * Synchronises `stream`.
+ */
+int gpm_list(gpm_graph_t g, gpm_pattern_t p, uint32_t *buf, uint64_t cap, uint64_t *written, uint64_t *total,
+             void *stream);
+
+/* ---------------- diagnostics ---------------- */
+
+/* Message for the last error on the calling host thread ("" if none). */
+const char *gpm_last_error(void);
+
+/* Library version string. */
+const char *gpm_version(void);
+
+/* Number of kernels this library has launched in this process. */
+uint64_t gpm_kernel_launches(void);
+
+/*
+ * Per-kernel timing: while enabled, every kernel launch of the library is
+ * bracketed by CUDA events on its launching stream. gpm_profile_report()
+ * writes {"<kernel>": {"launches": L, "ms": T}, ...} (JSON, NUL-terminated,
+ * truncated to len; *needed = full size) summed since the last reset; call it
+ * after synchronising the streams involved.
+ */
+int gpm_profile_enable(int on);
+int gpm_profile_reset(void);
+int gpm_profile_report(char *buf, size_t len, size_t *needed);
+
+/* Tuning knobs for tests and the autotuner (0 = leave unchanged). */
+typedef struct {
+  uint32_t warp_max_degree; /* roots with out-degree <= this run one per warp */
+  uint32_t cta_max_degree;  /* ... <= this one per CTA in shared memory; larger: global-memory bitmaps */
+  uint32_t blocks_per_sm;   /* persistent grid size multiplier */
+  uint32_t reserved[5];
+} gpm_options_t;
+
+int gpm_set_options(const gpm_options_t *opt);
+int gpm_get_options(gpm_options_t *opt);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPM_H_ */

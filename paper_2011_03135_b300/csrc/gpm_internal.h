@@ -1,0 +1,224 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+
+#include "../../include/gpm.h"
+
+// ---------------------------------------------------------------------------
+// error reporting
+// ---------------------------------------------------------------------------
+void gpm_set_error(const std::string &msg);
+int gpm_fail(int code, const std::string &msg);
+int gpm_cuda_fail(cudaError_t e, const char *what);
+
+#define GPM_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t _e = (call);                            \
+    if (_e != cudaSuccess) return gpm_cuda_fail(_e, #call); \
+  } while (0)
+
+#define GPM_TRY(expr)          \
+  do {                         \
+    int _rc = (expr);          \
+    if (_rc != GPM_OK) return _rc; \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// device status word bits (validation)
+// ---------------------------------------------------------------------------
+enum : uint32_t {
+  ST_OUT_OF_RANGE = 1u,
+  ST_NOT_SORTED = 2u,
+  ST_DUPLICATE = 4u,
+  ST_SELF_LOOP = 8u,
+  ST_ASYMMETRIC = 16u,
+  ST_BAD_ROWPTR = 32u,
+  ST_TIMEOUT = 64u,
+  ST_CAPACITY = 128u,
+};
+
+// Out-degree classes of root vertices in the orientation. A root with
+// out-degree d < 2 roots no triangle and is never a task.
+enum { CLS_W32 = 0, CLS_WARP = 1, CLS_CTA = 2, CLS_XL = 3, NUM_CLS = 4 };
+
+struct gpm_tuning {
+  uint32_t warp_max_degree = 128;  // class CLS_WARP upper bound (<= 256)
+  uint32_t cta_max_degree = 1024;  // class CLS_CTA upper bound (<= 1024)
+  uint32_t blocks_per_sm = 0;      // 0 = occupancy-derived
+};
+gpm_tuning &gpm_tune();
+
+// ---------------------------------------------------------------------------
+// graph handle
+// ---------------------------------------------------------------------------
+struct gpm_graph {
+  int device = 0;
+  uint32_t n = 0;
+  uint64_t nnz = 0;
+  uint32_t max_degree = 0;
+
+  // symmetric CSR and degrees
+  uint64_t *rowptr = nullptr;  // n+1
+  uint32_t *col = nullptr;     // nnz
+  uint32_t *deg = nullptr;     // n
+
+  // orientation (degree order, ties to the larger id)
+  bool prepared = false;
+  uint64_t m = 0;                // arcs = nnz/2
+  uint64_t *drow = nullptr;      // n+1
+  uint32_t *dcol = nullptr;      // m, ascending ids per row
+  uint32_t max_outdeg = 0;
+
+  // root tasks grouped by out-degree class; class c occupies
+  // tasks[cls_begin[c] .. cls_begin[c+1]) (host copy of the offsets)
+  uint32_t *tasks = nullptr;
+  uint32_t cls_begin[NUM_CLS + 1] = {0, 0, 0, 0, 0};
+  uint32_t cls_maxdeg[NUM_CLS] = {0, 0, 0, 0};
+  uint32_t tune_warp_max = 0, tune_cta_max = 0;  // thresholds the classes were built with
+
+  // preparation scratch, kept for re-orientation
+  uint32_t *prep_outdeg = nullptr;  // n
+  uint64_t *prep_tiles = nullptr;   // scan tile sums
+  uint64_t *prep_keys = nullptr;    // n, sort keys of the CTA/XL classes
+
+  // small device work area: queue heads, accumulators, status
+  uint64_t *work = nullptr;  // WORK_WORDS words
+  // scratch pools, grown on demand
+  uint32_t *t_edge = nullptr;   // per-arc triangle counts (m)
+  uint32_t *xl_pool = nullptr;  // global-memory bitmaps for CLS_XL roots
+  size_t xl_pool_bytes = 0;
+  uint32_t *tally_pool = nullptr;  // 4-cycle wedge tallies, n words per slot
+  size_t tally_slots = 0;
+  uint32_t *list_scratch = nullptr;
+  size_t list_scratch_bytes = 0;
+  // 4-cycle roots grouped by wedge bound (small: shared-memory hash per
+  // warp; big: dense global tally per CTA)
+  uint32_t *c4_tasks = nullptr;
+  uint32_t c4_begin[3] = {0, 0, 0};
+  bool c4_ready = false;
+
+  size_t device_bytes = 0;
+  std::mutex mu;
+};
+
+// layout of gpm_graph::work (uint64 words)
+enum {
+  WK_QUEUE0 = 0,   // 16 uint32 queue heads
+  WK_ACC = 8,      // 16 accumulators
+  WK_ACC2 = 24,    // 16 accumulators of a second pass
+  WK_OUT = 40,     // 16 results
+  WK_STATUS = 56,  // status bits
+  WK_MISC = 57,    // 7 misc words
+  WORK_WORDS = 64,
+};
+
+// ---------------------------------------------------------------------------
+// pattern handle
+// ---------------------------------------------------------------------------
+enum PatternClass : uint32_t {
+  PC_VERTEX = 0,      // k = 1
+  PC_EDGE,            // k = 2
+  PC_CLIQUE,          // k >= 3, complete
+  PC_WEDGE,           // 3 vertices, 2 edges
+  PC_STAR3,           // 4 vertices
+  PC_PATH4,
+  PC_TAILED,
+  PC_CYCLE4,
+  PC_DIAMOND,
+  PC_OTHER,
+};
+
+struct gpm_pattern {
+  uint32_t k = 0;
+  uint8_t adj[64] = {0};
+  int induced = 1;
+  PatternClass cls = PC_OTHER;
+  gpm_pattern_info_t info{};
+  // isomorphism from the class template to this pattern's numbering:
+  // template vertex t is pattern vertex tmpl_to_pat[t]
+  uint32_t tmpl_to_pat[8] = {0, 1, 2, 3, 4, 5, 6, 7};
+};
+
+int gpm_plan_pattern(gpm_pattern *p);  // fills cls, info, tmpl_to_pat
+
+// ---------------------------------------------------------------------------
+// device entry points (launchers), all asynchronous on `st`
+// ---------------------------------------------------------------------------
+int gpm_launch_validate(gpm_graph *g, cudaStream_t st, uint32_t *d_status);
+int gpm_prepare_graph(gpm_graph *g, cudaStream_t st);
+int gpm_ensure_classes(gpm_graph *g, cudaStream_t st);
+
+// persistent grid size for a kernel
+int gpm_num_sms(int device);
+
+// Clique counts for k = 3..kmax (kmax <= 5) over roots in [root_lo, root_hi).
+// Adds to acc[ACC_T .. kmax] (uint64, device). scatter: additionally adds
+// every triangle to the per-arc counts g->t_edge (zeroed by the caller).
+int gpm_launch_cliques(gpm_graph *g, int kmax, bool scatter, uint32_t root_lo, uint32_t root_hi,
+                       unsigned long long *acc, cudaStream_t st);
+
+// 4-cycles whose order-last vertex lies in [root_lo, root_hi): acc[ACC_C4] += count.
+int gpm_launch_cycles4(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigned long long *acc, cudaStream_t st);
+
+// Per-arc and per-vertex local-count terms (ACC_D .. ACC_T3). With
+// use_t_edge = false only the degree terms (ACC_P, ACC_S, ACC_W) are formed.
+// ACC_D only counts arcs whose tail lies in [root_lo, root_hi).
+int gpm_launch_edge_terms(gpm_graph *g, bool use_t_edge, uint32_t root_lo, uint32_t root_hi,
+                          unsigned long long *acc, cudaStream_t st);
+
+// Accumulator slots (uint64) filled by the passes above.
+enum {
+  ACC_T = 3,     // triangles
+  ACC_K4 = 4,    // 4-cliques
+  ACC_K5 = 5,    // 5-cliques
+  ACC_D = 8,     // sum over arcs C(t_e, 2)   (edge-induced diamonds)
+  ACC_P = 9,     // sum over arcs (d_u-1)(d_v-1)
+  ACC_S = 10,    // sum_v C(d_v, 3)
+  ACC_W = 11,    // sum_v C(d_v, 2)
+  ACC_TT2 = 12,  // sum over arcs t_e (d_u + d_v - 4)  (= 2 x tailed triangles)
+  ACC_T3 = 13,   // sum over arcs t_e (= 3 x triangles)
+  ACC_C4 = 14,   // 4-cycles
+  ACC_WORDS = 16,
+};
+
+// output formulas for gpm_launch_finalize
+enum Formula : uint32_t {
+  F_VERTEX = 0, F_EDGE, F_TRI, F_K4, F_K5, F_WEDGE_NI, F_WEDGE_I,
+  F_STAR_NI, F_PATH_NI, F_TT_NI, F_C4_NI, F_D_NI,
+  F_STAR_I, F_PATH_I, F_TT_I, F_C4_I, F_D_I, F_K4_I,
+};
+struct FinalizeSpec {
+  uint32_t npat;
+  uint32_t formula[16];
+};
+// out[i] = formula[i](acc); status |= ST_CAPACITY when an induced count is
+// inconsistent (a term overflowed 64 bits).
+int gpm_launch_finalize(const FinalizeSpec &spec, const unsigned long long *acc, uint64_t n, uint64_t m,
+                        unsigned long long *out, unsigned int *status, cudaStream_t st);
+
+// Listing.
+int gpm_launch_list_diamond(gpm_graph *g, uint32_t *buf, uint64_t cap, unsigned long long *counter,
+                            cudaStream_t st);
+int gpm_launch_list_cycle4(gpm_graph *g, uint32_t *buf, uint64_t cap, unsigned long long *counter,
+                           cudaStream_t st);
+int gpm_launch_list_cliques(gpm_graph *g, int k, uint32_t *buf, uint64_t cap, unsigned long long *counter,
+                            cudaStream_t st);
+int gpm_launch_permute_tuples(uint32_t *buf, uint64_t count, int k, const uint32_t *perm, cudaStream_t st);
+
+// launch accounting / per-kernel event timing (profile.cpp)
+void gpm_prof_begin(const char *name, cudaStream_t st);
+void gpm_prof_end(cudaStream_t st);
+#define GPM_LAUNCH(name, st, ...)  \
+  do {                             \
+    gpm_prof_begin(name, st);      \
+    __VA_ARGS__;                   \
+    gpm_prof_end(st);              \
+  } while (0)
+
+// grow-on-demand device allocation owned by the graph
+int gpm_graph_alloc(gpm_graph *g, void **ptr, size_t bytes);

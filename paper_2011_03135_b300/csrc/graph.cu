@@ -1,0 +1,368 @@
+// Graph ingest on the device: CSR validation, degrees, the degree-ordered
+// orientation and the root-task classes.
+//
+// Orientation (appendix "Orientation (Total Order)"): arc u -> v iff
+// (deg u, u) < (deg v, v), i.e. each edge points to the endpoint of higher
+// degree and ties point to the larger id. Every row of the oriented CSR keeps
+// the ascending id order of the symmetric CSR.
+#include <algorithm>
+#include <vector>
+
+#include "gpm_internal.h"
+
+namespace {
+
+
+__device__ __forceinline__ bool precedes(uint32_t du, uint32_t u, uint32_t dv, uint32_t v) {
+  return du < dv || (du == dv && u < v);
+}
+
+// ---------------------------------------------------------------------------
+// validation: one warp per vertex
+// ---------------------------------------------------------------------------
+__global__ void validate_kernel(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col, uint32_t n,
+                                uint64_t nnz, uint32_t *__restrict__ status) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  uint32_t bad = 0;
+  if (warp == 0 && lane == 0) {
+    if (rowptr[0] != 0 || rowptr[n] != nnz) bad |= ST_BAD_ROWPTR;
+  }
+  for (uint64_t v = warp; v < n; v += nwarps) {
+    const uint64_t b = rowptr[v], e = rowptr[v + 1];
+    if (e < b || e > nnz) {
+      bad |= ST_BAD_ROWPTR;
+      continue;
+    }
+    for (uint64_t i = b + lane; i < e; i += 32) {
+      const uint32_t c = col[i];
+      if (c >= n) {
+        bad |= ST_OUT_OF_RANGE;
+        continue;
+      }
+      if (c == v) bad |= ST_SELF_LOOP;
+      if (i > b) {
+        const uint32_t p = col[i - 1];
+        if (p == c) bad |= ST_DUPLICATE;
+        else if (p > c) bad |= ST_NOT_SORTED;
+      }
+      // symmetric: v must be in N(c) (binary search; rows may be unsorted if
+      // the input is bad, in which case NOT_SORTED is reported as well)
+      uint64_t lo = rowptr[c], hi = rowptr[c + 1];
+      if (hi < lo || hi > nnz) {
+        bad |= ST_BAD_ROWPTR;
+        continue;
+      }
+      const uint64_t end = hi;
+      while (lo < hi) {
+        uint64_t mid = lo + ((hi - lo) >> 1);
+        if (col[mid] < (uint32_t)v) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo >= end || col[lo] != (uint32_t)v) bad |= ST_ASYMMETRIC;
+    }
+  }
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  if (lane == 0 && bad) atomicOr(status, bad);
+}
+
+// degrees and the largest degree
+__global__ void degree_kernel(const uint64_t *__restrict__ rowptr, uint32_t n, uint32_t *__restrict__ deg,
+                              uint32_t *__restrict__ maxdeg) {
+  uint32_t mx = 0;
+  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t d = (uint32_t)(rowptr[v + 1] - rowptr[v]);
+    deg[v] = d;
+    mx = max(mx, d);
+  }
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  if ((threadIdx.x & 31) == 0) atomicMax(maxdeg, mx);
+}
+
+// out-degree of every vertex in the orientation: one warp per vertex
+__global__ void outdeg_kernel(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
+                              const uint32_t *__restrict__ deg, uint32_t n, uint32_t *__restrict__ outdeg,
+                              uint32_t *__restrict__ maxout) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  uint32_t mx = 0;
+  for (uint64_t v = warp; v < n; v += nwarps) {
+    const uint64_t b = rowptr[v], e = rowptr[v + 1];
+    const uint32_t dv = deg[v];
+    uint32_t c = 0;
+    for (uint64_t i = b + lane; i < e; i += 32) {
+      const uint32_t w = col[i];
+      c += precedes(dv, (uint32_t)v, deg[w], w);
+    }
+    c = __reduce_add_sync(0xffffffffu, c);
+    if (lane == 0) outdeg[v] = c;
+    mx = max(mx, c);
+  }
+  if (lane == 0) atomicMax(maxout, mx);
+}
+
+// write the kept neighbours of every vertex, order preserved (warp ballot)
+__global__ void fill_dag_kernel(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
+                                const uint32_t *__restrict__ deg, uint32_t n, const uint64_t *__restrict__ drow,
+                                uint32_t *__restrict__ dcol) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t v = warp; v < n; v += nwarps) {
+    const uint64_t b = rowptr[v], e = rowptr[v + 1];
+    const uint32_t dv = deg[v];
+    uint64_t out = drow[v];
+    for (uint64_t base = b; base < e; base += 32) {
+      const uint64_t i = base + lane;
+      uint32_t w = 0;
+      bool keep = false;
+      if (i < e) {
+        w = col[i];
+        keep = precedes(dv, (uint32_t)v, deg[w], w);
+      }
+      const uint32_t mask = __ballot_sync(0xffffffffu, keep);
+      if (keep) dcol[out + __popc(mask & ((1u << lane) - 1u))] = w;
+      out += __popc(mask);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of uint32 counts into uint64 offsets (three passes)
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t *total) {
+  __shared__ uint64_t warp_sums[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint64_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    uint64_t s = (lane < kScanThreads / 32) ? warp_sums[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint64_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < kScanThreads / 32) warp_sums[lane] = s;
+  }
+  __syncthreads();
+  uint64_t before = (wid > 0) ? warp_sums[wid - 1] : 0;
+  *total = warp_sums[kScanThreads / 32 - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+__global__ void scan_tiles_kernel(const uint32_t *__restrict__ in, uint64_t n, uint64_t *__restrict__ out,
+                                  uint64_t *__restrict__ tile_sums) {
+  const uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
+  uint32_t vals[kScanItems];
+  uint64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    vals[k] = (base + k < n) ? in[base + k] : 0u;
+    s += vals[k];
+  }
+  uint64_t total;
+  uint64_t pre = block_exclusive_scan(s, &total);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < n) out[base + k] = pre;
+    pre += vals[k];
+  }
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void scan_sums_kernel(uint64_t *__restrict__ tile_sums, uint64_t ntiles) {
+  uint64_t carry = 0;
+  for (uint64_t b = 0; b < ntiles; b += kScanThreads) {
+    uint64_t i = b + threadIdx.x;
+    uint64_t v = (i < ntiles) ? tile_sums[i] : 0;
+    uint64_t total;
+    uint64_t pre = block_exclusive_scan(v, &total);
+    if (i < ntiles) tile_sums[i] = carry + pre;
+    carry += total;
+  }
+}
+
+__global__ void scan_add_kernel(uint64_t *__restrict__ out, uint64_t n, const uint64_t *__restrict__ tile_sums,
+                                const uint32_t *__restrict__ in) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    out[i] += tile_sums[i / kScanTile];
+    if (i == n - 1) out[n] = out[i] + in[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// root-task classes by out-degree
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int task_class(uint32_t d, uint32_t warp_max, uint32_t cta_max) {
+  if (d < 2) return -1;
+  if (d <= 32) return CLS_W32;
+  if (d <= warp_max) return CLS_WARP;
+  if (d <= cta_max) return CLS_CTA;
+  return CLS_XL;
+}
+
+__global__ void class_count_kernel(const uint64_t *__restrict__ drow, uint32_t n, uint32_t warp_max,
+                                   uint32_t cta_max, uint32_t *__restrict__ counts, uint32_t *__restrict__ maxd) {
+  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t d = (uint32_t)(drow[v + 1] - drow[v]);
+    int c = task_class(d, warp_max, cta_max);
+    if (c >= 0) {
+      atomicAdd(&counts[c], 1u);
+      atomicMax(&maxd[c], d);
+    }
+  }
+}
+
+// Scatter roots into their class segment. Within a segment, roots are
+// placed by a cursor; order within a class is unspecified.
+__global__ void class_fill_kernel(const uint64_t *__restrict__ drow, uint32_t n, uint32_t warp_max, uint32_t cta_max,
+                                  uint32_t *__restrict__ cursors, uint32_t *__restrict__ tasks) {
+  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t d = (uint32_t)(drow[v + 1] - drow[v]);
+    int c = task_class(d, warp_max, cta_max);
+    if (c >= 0) tasks[atomicAdd(&cursors[c], 1u)] = (uint32_t)v;
+  }
+}
+
+// Sort keys for ordering the CTA and XL classes by decreasing out-degree so
+// that the largest roots start first (longest-processing-time-first).
+__global__ void class_keys_kernel(const uint32_t *__restrict__ tasks, uint32_t count,
+                                  const uint64_t *__restrict__ drow, uint64_t *__restrict__ keys) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    uint32_t v = tasks[i];
+    keys[i] = ((uint64_t)(drow[v + 1] - drow[v]) << 32) | v;
+  }
+}
+
+}  // namespace
+
+int gpm_num_sms(int device) {
+  static int cached[64] = {0};
+  if (device < 0 || device >= 64) return 148;
+  if (!cached[device]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0) v = 148;
+    cached[device] = v;
+  }
+  return cached[device];
+}
+
+int gpm_launch_validate(gpm_graph *g, cudaStream_t st, uint32_t *d_status) {
+  int blocks = gpm_num_sms(g->device) * 8;
+  GPM_LAUNCH("validate_kernel", st, validate_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, g->n, g->nnz, d_status));
+  GPM_CUDA(cudaGetLastError());
+  return GPM_OK;
+}
+
+int gpm_graph_alloc(gpm_graph *g, void **ptr, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return gpm_fail(GPM_E_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  g->device_bytes += bytes;
+  return GPM_OK;
+}
+
+int gpm_ensure_classes(gpm_graph *g, cudaStream_t st) {
+  const gpm_tuning &t = gpm_tune();
+  if (g->tune_warp_max == t.warp_max_degree && g->tune_cta_max == t.cta_max_degree) return GPM_OK;
+  if (!g->tasks) GPM_TRY(gpm_graph_alloc(g, (void **)&g->tasks, sizeof(uint32_t) * (size_t)std::max<uint32_t>(g->n, 1)));
+  uint32_t *dtmp = reinterpret_cast<uint32_t *>(g->work + WK_MISC);  // 4 counts + 4 maxd = 8 words = 4 uint64
+  GPM_CUDA(cudaMemsetAsync(dtmp, 0, 8 * sizeof(uint32_t), st));
+  const int blocks = gpm_num_sms(g->device) * 4;
+  GPM_LAUNCH("class_count_kernel", st, class_count_kernel<<<blocks, 256, 0, st>>>(g->drow, g->n, t.warp_max_degree, t.cta_max_degree, dtmp, dtmp + 4));
+  GPM_CUDA(cudaGetLastError());
+  uint32_t h[8];
+  GPM_CUDA(cudaMemcpyAsync(h, dtmp, sizeof(h), cudaMemcpyDeviceToHost, st));
+  GPM_CUDA(cudaStreamSynchronize(st));
+  g->cls_begin[0] = 0;
+  for (int c = 0; c < NUM_CLS; ++c) {
+    g->cls_begin[c + 1] = g->cls_begin[c] + h[c];
+    g->cls_maxdeg[c] = h[4 + c];
+  }
+  uint32_t cur[4] = {g->cls_begin[0], g->cls_begin[1], g->cls_begin[2], g->cls_begin[3]};
+  GPM_CUDA(cudaMemcpyAsync(dtmp, cur, sizeof(cur), cudaMemcpyHostToDevice, st));
+  GPM_LAUNCH("class_fill_kernel", st, class_fill_kernel<<<blocks, 256, 0, st>>>(g->drow, g->n, t.warp_max_degree, t.cta_max_degree, dtmp, g->tasks));
+  GPM_CUDA(cudaGetLastError());
+  const uint32_t big = g->cls_begin[NUM_CLS] - g->cls_begin[CLS_CTA];
+  if (big > 1) {
+    if (!g->prep_keys)
+      GPM_TRY(gpm_graph_alloc(g, (void **)&g->prep_keys, sizeof(uint64_t) * (size_t)std::max<uint32_t>(g->n, 1)));
+    uint64_t *dkeys = g->prep_keys;
+    GPM_LAUNCH("class_keys_kernel", st, class_keys_kernel<<<(big + 255) / 256, 256, 0, st>>>(g->tasks + g->cls_begin[CLS_CTA], big, g->drow, dkeys));
+    std::vector<uint64_t> keys(big);
+    GPM_CUDA(cudaGetLastError());
+    GPM_CUDA(cudaMemcpyAsync(keys.data(), dkeys, sizeof(uint64_t) * big, cudaMemcpyDeviceToHost, st));
+    GPM_CUDA(cudaStreamSynchronize(st));
+    std::vector<uint32_t> order(big);
+    for (int c = CLS_CTA; c <= CLS_XL; ++c) {
+      const uint32_t b = g->cls_begin[c] - g->cls_begin[CLS_CTA], en = g->cls_begin[c + 1] - g->cls_begin[CLS_CTA];
+      std::sort(keys.begin() + b, keys.begin() + en, [](uint64_t x, uint64_t y) {
+        return (x >> 32) != (y >> 32) ? (x >> 32) > (y >> 32) : (uint32_t)x < (uint32_t)y;
+      });
+    }
+    for (uint32_t i = 0; i < big; ++i) order[i] = (uint32_t)keys[i];
+    GPM_CUDA(cudaMemcpyAsync(g->tasks + g->cls_begin[CLS_CTA], order.data(), sizeof(uint32_t) * big,
+                             cudaMemcpyHostToDevice, st));
+  }
+  GPM_CUDA(cudaStreamSynchronize(st));
+  g->tune_warp_max = t.warp_max_degree;
+  g->tune_cta_max = t.cta_max_degree;
+  return GPM_OK;
+}
+
+int gpm_prepare_graph(gpm_graph *g, cudaStream_t st) {
+  if (g->prepared) return gpm_ensure_classes(g, st);
+  const uint32_t n = g->n;
+  g->m = g->nnz / 2;
+  if (!g->drow) GPM_TRY(gpm_graph_alloc(g, (void **)&g->drow, sizeof(uint64_t) * ((size_t)n + 1)));
+  if (!g->dcol) GPM_TRY(gpm_graph_alloc(g, (void **)&g->dcol, sizeof(uint32_t) * (size_t)std::max<uint64_t>(g->m, 1)));
+  const uint64_t ntiles = ((uint64_t)n + kScanTile - 1) / kScanTile;
+  if (!g->prep_outdeg)
+    GPM_TRY(gpm_graph_alloc(g, (void **)&g->prep_outdeg, sizeof(uint32_t) * (size_t)std::max<uint32_t>(n, 1)));
+  if (!g->prep_tiles)
+    GPM_TRY(gpm_graph_alloc(g, (void **)&g->prep_tiles, sizeof(uint64_t) * (size_t)std::max<uint64_t>(ntiles, 1)));
+  uint32_t *outdeg = g->prep_outdeg;
+  uint64_t *tile_sums = g->prep_tiles;
+  uint32_t *dmax = reinterpret_cast<uint32_t *>(g->work + WK_MISC);
+  cudaError_t e = cudaMemsetAsync(dmax, 0, 2 * sizeof(uint32_t), st);
+  const int sms = gpm_num_sms(g->device);
+  if (e == cudaSuccess && n > 0) {
+    GPM_LAUNCH("degree_kernel", st, degree_kernel<<<sms * 4, 256, 0, st>>>(g->rowptr, n, g->deg, dmax));
+    GPM_LAUNCH("outdeg_kernel", st, outdeg_kernel<<<sms * 8, 256, 0, st>>>(g->rowptr, g->col, g->deg, n, outdeg, dmax + 1));
+    GPM_LAUNCH("scan_tiles_kernel", st, scan_tiles_kernel<<<(unsigned)ntiles, kScanThreads, 0, st>>>(outdeg, n, g->drow, tile_sums));
+    GPM_LAUNCH("scan_sums_kernel", st, scan_sums_kernel<<<1, kScanThreads, 0, st>>>(tile_sums, ntiles));
+    GPM_LAUNCH("scan_add_kernel", st, scan_add_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g->drow, n, tile_sums, outdeg));
+    GPM_LAUNCH("fill_dag_kernel", st, fill_dag_kernel<<<sms * 8, 256, 0, st>>>(g->rowptr, g->col, g->deg, n, g->drow, g->dcol));
+    e = cudaGetLastError();
+  } else if (e == cudaSuccess) {
+    e = cudaMemsetAsync(g->drow, 0, sizeof(uint64_t), st);
+  }
+  uint32_t h[2] = {0, 0};
+  uint64_t arcs = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, dmax, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&arcs, g->drow + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return gpm_cuda_fail(e, "orientation");
+  g->max_degree = h[0];
+  g->max_outdeg = h[1];
+  if (arcs != g->m) return gpm_fail(GPM_E_ASYMMETRIC, "orientation produced " + std::to_string(arcs) +
+                                                          " arcs for " + std::to_string(g->m) + " edges");
+  g->prepared = true;
+  return gpm_ensure_classes(g, st);
+}

@@ -1,0 +1,404 @@
+// Motif counting by local counting, and 4-cycle counting.
+//
+// Local counting (Section 5 "Local Counting", Eq. 1 and the 3-MC / 4-MC
+// local-count listings of the appendix): the non-induced (edge-induced)
+// counts of the connected 4-vertex patterns follow from per-vertex degrees
+// and per-edge triangle counts t_e, except the 4-cycle and the 4-clique,
+// which are enumerated (as the paper's 4-MC code does):
+//   3-star          N_S  = sum_v C(d_v, 3)
+//   4-path          N_P  = sum_{uv} (d_u - 1)(d_v - 1) - 3T
+//   tailed triangle N_TT = sum_v t_v (d_v - 2) = 1/2 sum_{uv} t_uv (d_u + d_v - 4)
+//   diamond         N_D  = sum_{uv} C(t_uv, 2)   (the diamond example of Section 5)
+//   4-cycle         N_C4 (enumerated below)
+//   4-clique        N_K4 (clique pass)
+// The induced counts then follow by inverting the unitriangular relation
+// N_X = sum_Y (copies of X spanning Y) I_Y, densest pattern first.
+// For 3 vertices: induced triangle = T, induced (open) wedge = sum_v C(d_v,2) - 3T.
+//
+// 4-cycles: a cycle is rooted at its order-last vertex v0 (order = degree,
+// then id). All wedges v0 - x - w with x and w before v0 in the order are
+// tallied by their far end w; a cycle rooted at v0 with opposite vertex w is a
+// pair of such wedges, so the count is sum_w C(tally(w), 2). Roots with a
+// small wedge bound tally in a per-warp shared-memory hash table, the others
+// in a dense per-CTA tally array in global memory.
+#include <algorithm>
+
+#include "gpm_internal.h"
+
+namespace {
+
+__device__ __forceinline__ bool precedes(uint32_t da, uint32_t a, uint32_t db, uint32_t b) {
+  return da < db || (da == db && a < b);
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// per-arc / per-vertex local-count terms
+// ---------------------------------------------------------------------------
+template <bool USE_T>
+__global__ void edge_terms_kernel(const uint64_t *__restrict__ drow, const uint32_t *__restrict__ dcol,
+                                  const uint32_t *__restrict__ deg, const uint32_t *__restrict__ t_edge, uint32_t n,
+                                  uint32_t root_lo, uint32_t root_hi, unsigned long long *__restrict__ acc) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long sD = 0, sP = 0, sS = 0, sW = 0, sTT = 0, sT3 = 0;
+  for (uint64_t u = warp; u < n; u += nwarps) {
+    const unsigned long long du = deg[u];
+    if (lane == 0) {
+      if (du >= 3) sS += du * (du - 1) * (du - 2) / 6;
+      if (du >= 2) sW += du * (du - 1) / 2;
+    }
+    const bool in_range = u >= root_lo && u < root_hi;
+    for (uint64_t e = drow[u] + lane; e < drow[u + 1]; e += 32) {
+      const unsigned long long dv = deg[dcol[e]];
+      sP += (du - 1) * (dv - 1);
+      if (USE_T) {
+        const unsigned long long t = t_edge[e];
+        if (t) {
+          if (in_range) sD += t * (t - 1) / 2;
+          sTT += t * (du + dv - 4);
+          sT3 += t;
+        }
+      }
+    }
+  }
+  sD = warp_sum(sD);
+  sP = warp_sum(sP);
+  sS = warp_sum(sS);
+  sW = warp_sum(sW);
+  sTT = warp_sum(sTT);
+  sT3 = warp_sum(sT3);
+  if (lane == 0) {
+    atomicAdd(&acc[ACC_P], sP);
+    atomicAdd(&acc[ACC_S], sS);
+    atomicAdd(&acc[ACC_W], sW);
+    if (USE_T) {
+      atomicAdd(&acc[ACC_D], sD);
+      atomicAdd(&acc[ACC_TT2], sTT);
+      atomicAdd(&acc[ACC_T3], sT3);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 4-cycles
+// ---------------------------------------------------------------------------
+constexpr uint32_t kSmallBound = 512;   // wedge bound for the shared-memory class
+constexpr uint32_t kHashSlots = 1024;   // per warp, load factor <= 1/2
+constexpr uint32_t kEmpty = 0xffffffffu;
+
+// wedge bound B(v0) = sum of d_x over neighbours x before v0; class 0 small, 1 big
+__global__ void c4_bound_kernel(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
+                                const uint32_t *__restrict__ deg, uint32_t n, uint32_t *__restrict__ counts,
+                                uint32_t *__restrict__ tasks, uint32_t *__restrict__ cursors, int fill) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t v = warp; v < n; v += nwarps) {
+    const uint32_t dv = deg[v];
+    unsigned long long b = 0;
+    for (uint64_t e = rowptr[v] + lane; e < rowptr[v + 1]; e += 32) {
+      const uint32_t x = col[e];
+      const uint32_t dx = deg[x];
+      if (precedes(dx, x, dv, (uint32_t)v)) b += dx;
+    }
+    b = warp_sum(b);
+    if (lane == 0 && b >= 3) {  // a cycle needs two wedges, each scanning v0 itself plus w
+      const int c = (b <= kSmallBound) ? 0 : 1;
+      if (fill) tasks[atomicAdd(&cursors[c], 1u)] = (uint32_t)v;
+      else atomicAdd(&counts[c], 1u);
+    }
+  }
+}
+
+struct C4Args {
+  const uint64_t *__restrict__ rowptr;
+  const uint32_t *__restrict__ col;
+  const uint32_t *__restrict__ deg;
+  const uint32_t *__restrict__ tasks;
+  uint32_t ntasks;
+  uint32_t root_lo, root_hi;
+  unsigned int *queue;
+  unsigned long long *acc;
+  unsigned int *status;
+  uint32_t *pool;  // big class: per CTA, tally[n] then touched[n]
+  uint32_t n;
+};
+
+// one warp per root, shared-memory hash table
+__global__ void __launch_bounds__(256) c4_small_kernel(C4Args a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t *keys = smem + (size_t)wid * 2 * kHashSlots;
+  uint32_t *cnt = keys + kHashSlots;
+  unsigned long long acc = 0;
+  bool overflow = false;
+  for (;;) {
+    uint32_t task = 0;
+    if (lane == 0) task = atomicAdd(a.queue, 1u);
+    task = __shfl_sync(0xffffffffu, task, 0);
+    if (task >= a.ntasks) break;
+    const uint32_t v0 = a.tasks[task];
+    if (v0 < a.root_lo || v0 >= a.root_hi) continue;
+    for (uint32_t i = lane; i < kHashSlots; i += 32) {
+      keys[i] = kEmpty;
+      cnt[i] = 0;
+    }
+    __syncwarp();
+    const uint32_t d0 = a.deg[v0];
+    const uint64_t b0 = a.rowptr[v0], e0 = a.rowptr[v0 + 1];
+    for (uint64_t cb = b0; cb < e0; cb += 32) {
+      const uint64_t ex = cb + lane;
+      uint32_t x = 0;
+      bool ok = false;
+      if (ex < e0) {
+        x = a.col[ex];
+        ok = precedes(a.deg[x], x, d0, v0);
+      }
+      uint32_t mask = __ballot_sync(0xffffffffu, ok);
+      while (mask) {
+        const int src = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const uint32_t xx = __shfl_sync(0xffffffffu, x, src);
+        for (uint64_t f = a.rowptr[xx] + lane; f < a.rowptr[xx + 1]; f += 32) {
+          const uint32_t w = a.col[f];
+          if (!precedes(a.deg[w], w, d0, v0)) continue;
+          uint32_t h = (w * 2654435761u) >> 22;  // 10 bits
+          uint32_t probes = 0;
+          for (;;) {
+            const uint32_t k = atomicCAS(&keys[h], kEmpty, w);
+            if (k == kEmpty || k == w) {
+              atomicAdd(&cnt[h], 1u);
+              break;
+            }
+            h = (h + 1) & (kHashSlots - 1);
+            if (++probes >= kHashSlots) {
+              overflow = true;
+              break;
+            }
+          }
+        }
+      }
+    }
+    __syncwarp();
+    for (uint32_t i = lane; i < kHashSlots; i += 32) {
+      const unsigned long long c = cnt[i];
+      acc += c * (c - 1) / 2;
+    }
+    __syncwarp();
+  }
+  acc = warp_sum(acc);
+  if (lane == 0 && acc) atomicAdd(&a.acc[ACC_C4], acc);
+  if (__any_sync(0xffffffffu, overflow) && lane == 0) atomicOr(a.status, ST_CAPACITY);
+}
+
+// one CTA per root, dense tally in this CTA's global-memory slot
+__global__ void __launch_bounds__(512) c4_big_kernel(C4Args a) {
+  __shared__ uint32_t s_task, s_nt;
+  __shared__ uint32_t s_x[512];
+  const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  uint32_t *tally = a.pool + (size_t)blockIdx.x * 2 * a.n;
+  uint32_t *touched = tally + a.n;
+  unsigned long long acc = 0;
+  for (;;) {
+    if (tid == 0) {
+      s_task = atomicAdd(a.queue, 1u);
+      s_nt = 0;
+    }
+    __syncthreads();
+    const uint32_t task = s_task;
+    if (task >= a.ntasks) break;
+    const uint32_t v0 = a.tasks[task];
+    if (v0 < a.root_lo || v0 >= a.root_hi) {
+      __syncthreads();
+      continue;
+    }
+    const uint32_t d0 = a.deg[v0];
+    const uint64_t b0 = a.rowptr[v0], e0 = a.rowptr[v0 + 1];
+    // neighbours before v0, in chunks of nt; each warp scans whole lists
+    for (uint64_t cb = b0; cb < e0; cb += nt) {
+      __shared__ uint32_t s_cnt;
+      if (tid == 0) s_cnt = 0;
+      __syncthreads();
+      const uint64_t ex = cb + tid;
+      if (ex < e0) {
+        const uint32_t x = a.col[ex];
+        if (precedes(a.deg[x], x, d0, v0)) s_x[atomicAdd(&s_cnt, 1u)] = x;
+      }
+      __syncthreads();
+      const uint32_t cnt = s_cnt;
+      for (uint32_t xi = wid; xi < cnt; xi += nw) {
+        const uint32_t x = s_x[xi];
+        for (uint64_t f = a.rowptr[x] + lane; f < a.rowptr[x + 1]; f += 32) {
+          const uint32_t w = a.col[f];
+          if (!precedes(a.deg[w], w, d0, v0)) continue;
+          if (atomicAdd(&tally[w], 1u) == 0u) touched[atomicAdd(&s_nt, 1u)] = w;
+        }
+      }
+      __syncthreads();
+    }
+    __threadfence_block();
+    __syncthreads();
+    const uint32_t ntouched = s_nt;
+    for (uint32_t i = tid; i < ntouched; i += nt) {
+      const uint32_t w = touched[i];
+      const unsigned long long c = tally[w];
+      acc += c * (c - 1) / 2;
+      tally[w] = 0;
+    }
+    __syncthreads();
+  }
+  acc = warp_sum(acc);
+  if (lane == 0 && acc) atomicAdd(&a.acc[ACC_C4], acc);
+}
+
+// ---------------------------------------------------------------------------
+// finalize: requested counts from the accumulators (one thread)
+// ---------------------------------------------------------------------------
+__global__ void finalize_kernel(FinalizeSpec spec, const unsigned long long *__restrict__ acc, uint64_t n, uint64_t m,
+                                unsigned long long *__restrict__ out, unsigned int *__restrict__ status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const unsigned long long T = acc[ACC_T];
+  const unsigned long long NS = acc[ACC_S], NP = acc[ACC_P] - 3ull * T, NTT = acc[ACC_TT2] / 2ull,
+                           NC4 = acc[ACC_C4], ND = acc[ACC_D], NK4 = acc[ACC_K4];
+  // induced 4-vertex counts, modulo 2^64 (exact when the true values fit)
+  const unsigned long long iK4 = NK4;
+  const unsigned long long iD = ND - 6ull * iK4;
+  const unsigned long long iC4 = NC4 - iD - 3ull * iK4;
+  const unsigned long long iTT = NTT - 4ull * iD - 12ull * iK4;
+  const unsigned long long iP = NP - 2ull * iTT - 4ull * iC4 - 6ull * iD - 12ull * iK4;
+  const unsigned long long iS = NS - iTT - 2ull * iD - 4ull * iK4;
+  unsigned int bad = 0;
+  for (uint32_t i = 0; i < spec.npat; ++i) {
+    unsigned long long v = 0;
+    switch (spec.formula[i]) {
+      case F_VERTEX: v = n; break;
+      case F_EDGE: v = m; break;
+      case F_TRI: v = T; break;
+      case F_K4: v = acc[ACC_K4]; break;
+      case F_K5: v = acc[ACC_K5]; break;
+      case F_WEDGE_NI: v = acc[ACC_W]; break;
+      case F_WEDGE_I: v = acc[ACC_W] - 3ull * T; bad |= (v > acc[ACC_W]); break;
+      case F_STAR_NI: v = NS; break;
+      case F_PATH_NI: v = NP; break;
+      case F_TT_NI: v = NTT; break;
+      case F_C4_NI: v = NC4; break;
+      case F_D_NI: v = ND; break;
+      case F_STAR_I: v = iS; bad |= (iS > NS); break;
+      case F_PATH_I: v = iP; bad |= (iP > NP); break;
+      case F_TT_I: v = iTT; bad |= (iTT > NTT); break;
+      case F_C4_I: v = iC4; bad |= (iC4 > NC4); break;
+      case F_D_I: v = iD; bad |= (iD > ND); break;
+      case F_K4_I: v = iK4; break;
+      default: bad = 1; break;
+    }
+    out[i] = v;
+  }
+  if (bad) atomicOr(status, ST_CAPACITY);
+}
+
+}  // namespace
+
+int gpm_launch_edge_terms(gpm_graph *g, bool use_t_edge, uint32_t root_lo, uint32_t root_hi,
+                          unsigned long long *acc, cudaStream_t st) {
+  const int blocks = gpm_num_sms(g->device) * 8;
+  if (g->n == 0) return GPM_OK;
+  if (use_t_edge)
+    GPM_LAUNCH("edge_terms_kernel", st, edge_terms_kernel<true><<<blocks, 256, 0, st>>>(g->drow, g->dcol, g->deg, g->t_edge, g->n, root_lo, root_hi, acc));
+  else
+    GPM_LAUNCH("edge_terms_kernel", st, edge_terms_kernel<false><<<blocks, 256, 0, st>>>(g->drow, g->dcol, g->deg, nullptr, g->n, root_lo, root_hi, acc));
+  GPM_CUDA(cudaGetLastError());
+  return GPM_OK;
+}
+
+static int ensure_c4_tasks(gpm_graph *g, cudaStream_t st) {
+  if (g->c4_ready) return GPM_OK;
+  if (!g->c4_tasks) GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4_tasks, sizeof(uint32_t) * std::max<uint32_t>(g->n, 1)));
+  uint32_t *tmp = reinterpret_cast<uint32_t *>(g->work + WK_MISC);
+  GPM_CUDA(cudaMemsetAsync(tmp, 0, 4 * sizeof(uint32_t), st));
+  const int blocks = gpm_num_sms(g->device) * 8;
+  if (g->n) {
+    GPM_LAUNCH("c4_bound_kernel", st, c4_bound_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->n, tmp, nullptr, nullptr, 0));
+    GPM_CUDA(cudaGetLastError());
+  }
+  uint32_t h[2];
+  GPM_CUDA(cudaMemcpyAsync(h, tmp, sizeof(h), cudaMemcpyDeviceToHost, st));
+  GPM_CUDA(cudaStreamSynchronize(st));
+  g->c4_begin[0] = 0;
+  g->c4_begin[1] = h[0];
+  g->c4_begin[2] = h[0] + h[1];
+  uint32_t cur[2] = {0, h[0]};
+  GPM_CUDA(cudaMemcpyAsync(tmp + 2, cur, sizeof(cur), cudaMemcpyHostToDevice, st));
+  if (g->n) {
+    GPM_LAUNCH("c4_bound_kernel", st, c4_bound_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->n, nullptr, g->c4_tasks, tmp + 2, 1));
+    GPM_CUDA(cudaGetLastError());
+  }
+  GPM_CUDA(cudaStreamSynchronize(st));
+  g->c4_ready = true;
+  return GPM_OK;
+}
+
+int gpm_launch_cycles4(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigned long long *acc, cudaStream_t st) {
+  GPM_TRY(ensure_c4_tasks(g, st));
+  unsigned int *queues = reinterpret_cast<unsigned int *>(g->work + WK_QUEUE0) + 4;
+  GPM_CUDA(cudaMemsetAsync(queues, 0, 2 * sizeof(unsigned int), st));
+  C4Args a{};
+  a.rowptr = g->rowptr;
+  a.col = g->col;
+  a.deg = g->deg;
+  a.root_lo = root_lo;
+  a.root_hi = root_hi;
+  a.acc = acc;
+  a.status = reinterpret_cast<unsigned int *>(g->work + WK_STATUS);
+  a.n = g->n;
+  const int sms = gpm_num_sms(g->device);
+  const uint32_t nsmall = g->c4_begin[1] - g->c4_begin[0];
+  const uint32_t nbig = g->c4_begin[2] - g->c4_begin[1];
+  if (nsmall) {
+    C4Args s = a;
+    s.tasks = g->c4_tasks;
+    s.ntasks = nsmall;
+    s.queue = queues;
+    const size_t smem = (size_t)8 * 2 * kHashSlots * 4;
+    GPM_CUDA(cudaFuncSetAttribute(c4_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c4_small_kernel, 256, smem));
+    int blocks = std::max(1, std::min<int>(sms * std::max(per_sm, 1), (int)((nsmall + 7) / 8)));
+    GPM_LAUNCH("c4_small_kernel", st, c4_small_kernel<<<blocks, 256, smem, st>>>(s));
+    GPM_CUDA(cudaGetLastError());
+  }
+  if (nbig) {
+    C4Args b = a;
+    b.tasks = g->c4_tasks + g->c4_begin[1];
+    b.ntasks = nbig;
+    b.queue = queues + 1;
+    const size_t slots = (size_t)std::min<uint32_t>((uint32_t)sms, nbig);
+    if (g->tally_slots < slots) {
+      if (g->tally_pool) {
+        cudaFree(g->tally_pool);
+        g->device_bytes -= g->tally_slots * 2 * (size_t)g->n * 4;
+        g->tally_pool = nullptr;
+        g->tally_slots = 0;
+      }
+      GPM_TRY(gpm_graph_alloc(g, (void **)&g->tally_pool, slots * 2 * (size_t)g->n * 4));
+      GPM_CUDA(cudaMemsetAsync(g->tally_pool, 0, slots * 2 * (size_t)g->n * 4, st));
+      g->tally_slots = slots;
+    }
+    b.pool = g->tally_pool;
+    GPM_LAUNCH("c4_big_kernel", st, c4_big_kernel<<<(unsigned)slots, 512, 0, st>>>(b));
+    GPM_CUDA(cudaGetLastError());
+  }
+  return GPM_OK;
+}
+
+int gpm_launch_finalize(const FinalizeSpec &spec, const unsigned long long *acc, uint64_t n, uint64_t m,
+                        unsigned long long *out, unsigned int *status, cudaStream_t st) {
+  GPM_LAUNCH("finalize_kernel", st, finalize_kernel<<<1, 32, 0, st>>>(spec, acc, n, m, out, status));
+  GPM_CUDA(cudaGetLastError());
+  return GPM_OK;
+}

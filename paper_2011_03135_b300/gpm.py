@@ -1,0 +1,323 @@
+"""Python binding of libgpm.so (include/gpm.h): argument marshalling only.
+
+Every count and listing runs in the library's CUDA kernels; this module only
+converts numpy arrays / torch tensors to pointers, torch streams to
+cudaStream_t handles, and status codes to exceptions. There is no CPU
+fallback: importing this module raises if libgpm.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgpm.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing; build it with `python -m paper_2011_03135_b300.build` "
+                      "(the library has no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+GPM_OK = 0
+ERRORS = {
+    -1: "INVALID_ARG", -2: "NOT_SORTED", -3: "SELF_LOOP", -4: "DUPLICATE", -5: "ASYMMETRIC",
+    -6: "DISCONNECTED_PATTERN", -7: "K_TOO_LARGE", -8: "OOM", -9: "DEVICE", -10: "TIMEOUT", -11: "BUSY",
+    -12: "UNSUPPORTED", -13: "OVERFLOW", -14: "OUT_OF_RANGE",
+}
+GRAPH_VALIDATE = 1
+GRAPH_DEVICE_INPUT = 2
+STRATEGY_CLIQUE_DAG, STRATEGY_LOCAL_COUNT, STRATEGY_EDGE = 1, 2, 3
+MOTIF4_NAMES = ("3-star", "4-path", "tailed-triangle", "4-cycle", "diamond", "4-clique")
+MOTIF3_NAMES = ("wedge", "triangle")
+
+
+class GpmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("max_degree", ctypes.c_uint32), ("nnz", ctypes.c_uint64),
+                ("dag_arcs", ctypes.c_uint64), ("max_out_degree", ctypes.c_uint32), ("prepared", ctypes.c_uint32),
+                ("device_bytes", ctypes.c_uint64)]
+
+
+class PatternInfo(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_uint32), ("n_edges", ctypes.c_uint32), ("induced", ctypes.c_uint32),
+                ("is_clique", ctypes.c_uint32), ("strategy", ctypes.c_uint32), ("motif_index", ctypes.c_uint32),
+                ("automorphisms", ctypes.c_uint64), ("n_sb_pairs", ctypes.c_uint32),
+                ("sb_pairs", ctypes.c_uint32 * 56), ("matching_order", ctypes.c_uint32 * 8),
+                ("min_degree", ctypes.c_uint32 * 8)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("warp_max_degree", ctypes.c_uint32), ("cta_max_degree", ctypes.c_uint32),
+                ("blocks_per_sm", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
+
+
+_vp, _u32, _u64, _i = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+_U64P = ctypes.POINTER(ctypes.c_uint64)
+_SIGS = {
+    "gpm_graph_create": [_vp, _vp, _u32, _u64, _u32, _vp, ctypes.POINTER(_vp)],
+    "gpm_graph_destroy": [_vp],
+    "gpm_graph_prepare": [_vp, _vp],
+    "gpm_graph_info": [_vp, ctypes.POINTER(GraphInfo)],
+    "gpm_pattern_spec": [_u32, _vp, _i, ctypes.POINTER(_vp)],
+    "gpm_pattern_clique": [_u32, ctypes.POINTER(_vp)],
+    "gpm_pattern_motifs": [_u32, _vp, ctypes.POINTER(_u32)],
+    "gpm_pattern_destroy": [_vp],
+    "gpm_pattern_info": [_vp, ctypes.POINTER(PatternInfo)],
+    "gpm_count": [_vp, _vp, _u32, _vp, _vp],
+    "gpm_count_async": [_vp, _vp, _u32, _vp, _vp],
+    "gpm_count_roots": [_vp, _vp, _u32, _u32, _u32, _vp, _vp],
+    "gpm_list": [_vp, _vp, _vp, _u64, _U64P, _U64P, _vp],
+    "gpm_graph_reset": [_vp],
+    "gpm_profile_enable": [_i],
+    "gpm_profile_reset": [],
+    "gpm_profile_report": [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
+    "gpm_set_options": [ctypes.POINTER(Options)],
+    "gpm_get_options": [ctypes.POINTER(Options)],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+_lib.gpm_last_error.argtypes = []
+_lib.gpm_last_error.restype = ctypes.c_char_p
+_lib.gpm_version.argtypes = []
+_lib.gpm_version.restype = ctypes.c_char_p
+_lib.gpm_kernel_launches.argtypes = []
+_lib.gpm_kernel_launches.restype = ctypes.c_uint64
+
+
+def _check(rc: int):
+    if rc != GPM_OK:
+        raise GpmError(rc, _lib.gpm_last_error().decode(errors="replace"))
+
+
+def version() -> str:
+    return _lib.gpm_version().decode()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def _ptr(x):
+    """(address, is_device, keepalive) of a numpy array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            x = np.ascontiguousarray(x)
+        return x.ctypes.data, False, x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            x = x.contiguous()
+        return x.data_ptr(), x.is_cuda, x
+    raise TypeError(f"expected a numpy array or a torch tensor, got {type(x)}")
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(_lib.gpm_kernel_launches())
+
+
+def profile_enable(on: bool = True):
+    _check(_lib.gpm_profile_enable(int(bool(on))))
+
+
+def profile_reset():
+    _check(_lib.gpm_profile_reset())
+
+
+def profile_report() -> dict:
+    """{kernel: {"launches": L, "ms": T}} summed since the last reset (call after synchronising)."""
+    import json
+    need = ctypes.c_size_t(0)
+    _check(_lib.gpm_profile_report(None, 0, ctypes.byref(need)))
+    buf = ctypes.create_string_buffer(need.value + 16)
+    _check(_lib.gpm_profile_report(buf, len(buf), ctypes.byref(need)))
+    return json.loads(buf.value.decode())
+
+
+def set_options(warp_max_degree: int = 0, cta_max_degree: int = 0, blocks_per_sm: int = 0):
+    o = Options(warp_max_degree, cta_max_degree, blocks_per_sm)
+    _check(_lib.gpm_set_options(ctypes.byref(o)))
+
+
+def get_options() -> dict:
+    o = Options()
+    _check(_lib.gpm_get_options(ctypes.byref(o)))
+    return dict(warp_max_degree=o.warp_max_degree, cta_max_degree=o.cta_max_degree, blocks_per_sm=o.blocks_per_sm)
+
+
+class Graph:
+    """A device-resident graph (library-owned copy of a symmetric sorted CSR)."""
+
+    def __init__(self, rowptr, col, n: int | None = None, validate: bool = True, stream=None):
+        rp, rp_dev, self._k1 = _ptr(rowptr)
+        cp, cp_dev, self._k2 = _ptr(col)
+        if rp_dev != cp_dev:
+            raise ValueError("rowptr and col must both be host or both be device arrays")
+        if n is None:
+            n = len(rowptr) - 1
+        nnz = int(col.shape[0]) if hasattr(col, "shape") else len(col)
+        if isinstance(rowptr, np.ndarray) and rowptr.dtype != np.uint64:
+            raise TypeError("rowptr must be uint64")
+        if isinstance(col, np.ndarray) and col.dtype != np.uint32:
+            raise TypeError("col must be uint32")
+        flags = (GRAPH_VALIDATE if validate else 0) | (GRAPH_DEVICE_INPUT if rp_dev else 0)
+        h = _vp()
+        _check(_lib.gpm_graph_create(rp, cp if nnz else None, n, nnz, flags, _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.n = n
+        self.nnz = nnz
+        self._k1 = self._k2 = None
+
+    @classmethod
+    def from_host(cls, g, validate: bool = True, stream=None):
+        """From an object with .rowptr (uint64) and .col (uint32) numpy arrays."""
+        return cls(g.rowptr, g.col, g.n, validate=validate, stream=stream)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("graph has been destroyed")
+        return self._h
+
+    def prepare(self, stream=None):
+        _check(_lib.gpm_graph_prepare(self.handle, _stream(stream)))
+        return self
+
+    def reset(self):
+        """Drop the orientation so the next count rebuilds it (buffers are kept)."""
+        _check(_lib.gpm_graph_reset(self.handle))
+        return self
+
+    def info(self) -> dict:
+        i = GraphInfo()
+        _check(_lib.gpm_graph_info(self.handle, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in GraphInfo._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.gpm_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Pattern:
+    """A planned pattern (library-owned)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @classmethod
+    def spec(cls, adj, induced: bool = True):
+        a = np.ascontiguousarray(np.asarray(adj, dtype=np.uint8))
+        k = a.shape[0]
+        h = _vp()
+        _check(_lib.gpm_pattern_spec(k, a.ctypes.data, int(bool(induced)), ctypes.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def clique(cls, k: int):
+        h = _vp()
+        _check(_lib.gpm_pattern_clique(k, ctypes.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def motifs(cls, k: int):
+        arr = (_vp * 8)()
+        npat = _u32(0)
+        _check(_lib.gpm_pattern_motifs(k, arr, ctypes.byref(npat)))
+        return [cls(_vp(arr[i])) for i in range(npat.value)]
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        i = PatternInfo()
+        _check(_lib.gpm_pattern_info(self._h, ctypes.byref(i)))
+        return dict(k=i.k, n_edges=i.n_edges, induced=i.induced, is_clique=i.is_clique, strategy=i.strategy,
+                    motif_index=i.motif_index, automorphisms=i.automorphisms,
+                    sb_pairs=[(i.sb_pairs[2 * j], i.sb_pairs[2 * j + 1]) for j in range(i.n_sb_pairs)],
+                    matching_order=list(i.matching_order[: i.k]), min_degree=list(i.min_degree[: i.k]))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.gpm_pattern_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _handles(patterns: Sequence[Pattern]):
+    arr = (_vp * len(patterns))()
+    for i, p in enumerate(patterns):
+        arr[i] = p.handle
+    return arr
+
+
+def count(graph: Graph, patterns: Sequence[Pattern], stream=None) -> list:
+    """Exact counts (host), one per pattern."""
+    out = np.zeros(len(patterns), dtype=np.uint64)
+    _check(_lib.gpm_count(graph.handle, _handles(patterns), len(patterns), out.ctypes.data, _stream(stream)))
+    return [int(x) for x in out]
+
+
+def count_async(graph: Graph, patterns: Sequence[Pattern], out, stream=None):
+    """Enqueue the counts into a device tensor (uint64 / int64, len >= npat); no synchronisation."""
+    p, dev, _keep = _ptr(out)
+    if not dev:
+        raise ValueError("count_async needs a device output tensor")
+    _check(_lib.gpm_count_async(graph.handle, _handles(patterns), len(patterns), p, _stream(stream)))
+
+
+def count_roots(graph: Graph, patterns: Sequence[Pattern], root_lo: int, root_hi: int, stream=None) -> list:
+    """Counts of embeddings whose root vertex lies in [root_lo, root_hi)."""
+    out = np.zeros(len(patterns), dtype=np.uint64)
+    _check(_lib.gpm_count_roots(graph.handle, _handles(patterns), len(patterns), root_lo, root_hi,
+                                out.ctypes.data, _stream(stream)))
+    return [int(x) for x in out]
+
+
+def list_embeddings(graph: Graph, pattern: Pattern, cap: int, out=None, stream=None):
+    """List up to `cap` embeddings. Returns (tuples[written, k], total).
+
+    `out` may be a preallocated uint32 numpy array / torch tensor (host or
+    device) with room for cap*k entries; by default a host array is returned.
+    """
+    k = pattern.info()["k"]
+    if out is None:
+        out = np.zeros((max(cap, 1), k), dtype=np.uint32)
+    p, _dev, _keep = _ptr(out)
+    written, total = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(_lib.gpm_list(graph.handle, pattern.handle, p if cap else None, cap, ctypes.byref(written),
+                         ctypes.byref(total), _stream(stream)))
+    return out[: written.value], int(total.value)

@@ -1,0 +1,112 @@
+"""The C-ABI library loads, exports every symbol include/gpm.h declares, and
+its host-side planner (no GPU needed) derives the right pattern facts."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2011_03135_b300 import build
+    build.build()
+    from paper_2011_03135_b300 import gpm
+    return gpm
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:int|const char \*|const char\*)\s*(gpm_\w+)\s*\(", txt, flags=re.M))
+    return names
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 15
+    so = ctypes.CDLL(lib.LIB_PATH)
+    missing = [n for n in sorted(names) if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def test_version_and_errors_without_gpu(lib):
+    assert "sm_103a" in lib.version()
+    with pytest.raises(lib.GpmError) as e:
+        lib.Pattern.spec(np.array([[0, 1, 0], [1, 0, 0], [0, 0, 0]]))
+    assert e.value.name == "DISCONNECTED_PATTERN"
+    with pytest.raises(lib.GpmError) as e:
+        lib.Pattern.spec(np.array([[0, 1], [0, 0]]))
+    assert e.value.name == "INVALID_ARG"
+    with pytest.raises(lib.GpmError) as e:
+        lib.Pattern.clique(9)
+    assert e.value.name == "K_TOO_LARGE"
+
+
+@pytest.mark.parametrize("idx", range(6))
+def test_planner_motif4(lib, idx):
+    pats = lib.Pattern.motifs(4)
+    info = pats[idx].info()
+    adj = O.MOTIF4_PATTERNS[idx]
+    assert info["motif_index"] == idx
+    assert info["automorphisms"] == O.automorphisms(adj)
+    # the constraints leave exactly one vertex order per distinct subgraph
+    assert O.orders_satisfying(4, info["sb_pairs"]) * info["automorphisms"] == math.factorial(4)
+    assert info["min_degree"] == [int(x) for x in adj.sum(axis=1)]
+    assert sorted(info["matching_order"]) == [0, 1, 2, 3]
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_planner_cliques(lib, k):
+    info = lib.Pattern.clique(k).info()
+    assert info["automorphisms"] == math.factorial(k)
+    assert info["is_clique"] == 1
+    assert O.orders_satisfying(k, info["sb_pairs"]) == 1
+    if k >= 3:
+        assert info["strategy"] == lib.STRATEGY_CLIQUE_DAG
+
+
+def test_planner_diamond_matching_order_is_triangle_first(lib):
+    # appendix "Pattern-Guided Search": the diamond is matched triangle first,
+    # starting with the two degree-3 vertices that carry a partial order
+    info = lib.Pattern.spec(O.DIAMOND, induced=False).info()
+    mo = info["matching_order"]
+    assert set(mo[:2]) == {0, 1}
+    assert (0, 1) in info["sb_pairs"] and (2, 3) in info["sb_pairs"]
+    assert info["strategy"] == lib.STRATEGY_LOCAL_COUNT
+
+
+def test_planner_other_numberings(lib):
+    # diamond with the shared edge on vertices 2,3; 4-cycle 0-1-2-3-0
+    d = O.pattern(4, [(2, 3), (2, 0), (2, 1), (3, 0), (3, 1)])
+    c = O.pattern(4, [(0, 1), (1, 2), (2, 3), (3, 0)])
+    for a in (d, c):
+        info = lib.Pattern.spec(a, induced=False).info()
+        assert O.orders_satisfying(4, info["sb_pairs"]) * info["automorphisms"] == 24
+
+
+def test_planner_five_vertex_pattern(lib):
+    # a 5-vertex house: planned, but no GPU kernel (strategy 0)
+    house = O.pattern(5, [(0, 1), (1, 2), (2, 3), (3, 0), (0, 4), (1, 4)])
+    info = lib.Pattern.spec(house).info()
+    assert info["automorphisms"] == O.automorphisms(house)
+    assert O.orders_satisfying(5, info["sb_pairs"]) * info["automorphisms"] == 120
+    assert info["strategy"] == 0
+
+
+def test_options_roundtrip(lib):
+    old = lib.get_options()
+    lib.set_options(warp_max_degree=64, cta_max_degree=512)
+    assert lib.get_options()["warp_max_degree"] == 64
+    with pytest.raises(lib.GpmError):
+        lib.set_options(warp_max_degree=8)
+    lib.set_options(**{k: v for k, v in old.items() if v})

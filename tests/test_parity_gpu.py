@@ -1,0 +1,307 @@
+"""GPU path vs the CPU oracle, element by element, through the C-ABI.
+
+All counts are integers, so the bar is bit-exact equality. Small graphs
+(n <= 30) cover every pattern class against the oracle's brute force tier;
+medium graphs span every root class (warp, CTA, global-memory bitmaps) and a
+ragged tail; the full-size workloads are checked on sampled root ranges the
+oracle computes one by one, and on totals stored by tests/golden/make_golden.py
+(which calls only the oracle).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2011_03135_b300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "fullsize_counts.json")
+
+
+@pytest.fixture(scope="module")
+def gpm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_03135_b300 import gpm as m
+    return m
+
+
+def _golden():
+    if os.path.exists(GOLDEN):
+        return json.load(open(GOLDEN))
+    return {}
+
+
+SMALL = [
+    gg.complete(6), gg.complete(9), gg.complete_multipartite([2, 3, 4]), gg.complete_multipartite([3, 3]),
+    gg.petersen(), gg.cycle(4), gg.cycle(7), gg.star(6), gg.path(5), gg.empty(4),
+    gg.from_edges(2, [(0, 1)]), gg.from_edges(3, [(0, 1), (1, 2)]),
+] + [gg.random_small(n, p, s) for s, (n, p) in enumerate(
+    [(10, 0.5), (14, 0.4), (18, 0.35), (22, 0.3), (25, 0.25), (28, 0.2), (30, 0.3), (30, 0.5), (16, 0.8),
+     (20, 0.6), (24, 0.15), (29, 0.45)])] + [gg.rmat(5, 6.0, seed=s) for s in range(4)]
+
+
+@pytest.mark.parametrize("gi", range(len(SMALL)))
+def test_small_graph_every_pattern(gpm, gi):
+    g = SMALL[gi]
+    G = gpm.Graph.from_host(g)
+    cl = [gpm.Pattern.clique(k) for k in (1, 2, 3, 4, 5)]
+    assert gpm.count(G, cl) == [g.n, g.m] + [O.cliques(g, k) for k in (3, 4, 5)]
+    m4 = gpm.Pattern.motifs(4)
+    m3 = gpm.Pattern.motifs(3)
+    assert gpm.count(G, m4) == O.motifs(g, 4)
+    assert gpm.count(G, m3) == O.motifs(g, 3)
+    ni4 = [gpm.Pattern.spec(p, induced=False) for p in O.MOTIF4_PATTERNS]
+    ni3 = [gpm.Pattern.spec(p, induced=False) for p in O.MOTIF3_PATTERNS]
+    assert gpm.count(G, ni4) == O.noninduced_terms(g, 4)
+    assert gpm.count(G, ni3) == O.noninduced_terms(g, 3)
+    # every pattern alone gives the same as in a group
+    for p, want in zip(m4 + ni4, O.motifs(g, 4) + O.noninduced_terms(g, 4)):
+        assert gpm.count(G, [p]) == [want]
+    G.close()
+
+
+def _medium():
+    return [gg.rmat(11, 16.0, seed=21), gg.rmat(12, 8.0, seed=22), gg.erdos_renyi(3000, 0.01, seed=23, permute=True),
+            gg.chung_lu(5000, 16.0, 2.1, seed=24)]
+
+
+@pytest.mark.parametrize("opts", [dict(), dict(warp_max_degree=32, cta_max_degree=32),
+                                  dict(warp_max_degree=64, cta_max_degree=64),
+                                  dict(warp_max_degree=256, cta_max_degree=1024),
+                                  dict(warp_max_degree=32, cta_max_degree=96)])
+def test_medium_graphs_every_root_class(gpm, opts):
+    old = gpm.get_options()
+    try:
+        if opts:
+            gpm.set_options(**opts)
+        for g in _medium():
+            G = gpm.Graph.from_host(g)
+            info = G.prepare().info()
+            assert info["dag_arcs"] == g.m
+            assert info["max_out_degree"] == int(O.out_degrees(g).max())
+            cl = [gpm.Pattern.clique(k) for k in (3, 4, 5)]
+            assert gpm.count(G, cl) == [O.cliques(g, k) for k in (3, 4, 5)], g.name
+            assert gpm.count(G, gpm.Pattern.motifs(4)) == O.motifs(g, 4), g.name
+            G.close()
+    finally:
+        gpm.set_options(**{k: v for k, v in old.items() if v})
+
+
+def test_root_ranges_match_oracle(gpm):
+    g = gg.rmat(12, 16.0, seed=31)
+    G = gpm.Graph.from_host(g)
+    pats = [gpm.Pattern.clique(3), gpm.Pattern.clique(4), gpm.Pattern.clique(5),
+            gpm.Pattern.spec(O.DIAMOND, induced=False), gpm.Pattern.spec(O.CYCLE4, induced=False)]
+    cuts = [0, 1, 777, 2048, 2049, 3333, g.n]
+    tot = [0] * 5
+    for lo, hi in zip(cuts[:-1], cuts[1:]):
+        got = gpm.count_roots(G, pats, lo, hi)
+        want = [O.cliques(g, 3, lo, hi), O.cliques(g, 4, lo, hi), O.cliques(g, 5, lo, hi),
+                O.diamonds(g, lo, hi), O.cycles4(g, lo, hi)]
+        assert got == want, (lo, hi)
+        tot = [a + b for a, b in zip(tot, got)]
+    assert tot == gpm.count(G, pats)
+    G.close()
+
+
+def _adjacent(g, u, v):
+    nb = g.neighbors(int(u))
+    i = np.searchsorted(nb, v)
+    return i < len(nb) and nb[i] == v
+
+
+def _edge_keys(g, adj, tuples):
+    """Per tuple, the sorted codes of the graph edges its pattern edges land on."""
+    k = adj.shape[0]
+    t = np.asarray(tuples, dtype=np.int64).reshape(-1, k)
+    cols = [np.minimum(t[:, i], t[:, j]) * g.n + np.maximum(t[:, i], t[:, j])
+            for i in range(k) for j in range(i + 1, k) if adj[i, j]]
+    return np.sort(np.stack(cols, axis=1), axis=1)
+
+
+def _check_tuples(g, adj, info, tuples):
+    """Each tuple is an embedding satisfying the constraints; all are distinct subgraphs."""
+    k = adj.shape[0]
+    pedges = [(i, j) for i in range(k) for j in range(i + 1, k) if adj[i, j]]
+    seen = set()
+    for t in np.asarray(tuples).tolist():
+        assert len(set(t)) == k
+        for i, j in pedges:
+            assert _adjacent(g, t[i], t[j]), (t, i, j)
+        for a, b in info["sb_pairs"]:
+            assert t[a] < t[b], (t, a, b)
+        es = frozenset((min(t[i], t[j]), max(t[i], t[j])) for i, j in pedges)
+        assert es not in seen
+        seen.add(es)
+    return seen
+
+
+LIST_PATTERNS = [
+    (O.DIAMOND, False),
+    (O.CYCLE4, False),
+    (O.pattern(4, [(2, 3), (2, 0), (2, 1), (3, 0), (3, 1)]), False),   # diamond, other numbering
+    (O.pattern(4, [(0, 1), (1, 2), (2, 3), (3, 0)]), False),           # 4-cycle, other numbering
+    (O.clique_pattern(3), True), (O.clique_pattern(4), True), (O.clique_pattern(5), True),
+]
+
+
+@pytest.mark.parametrize("pi", range(len(LIST_PATTERNS)))
+def test_listing_all_small(gpm, pi):
+    adj, induced = LIST_PATTERNS[pi]
+    for g in SMALL[:8] + SMALL[12:20]:
+        G = gpm.Graph.from_host(g)
+        P = gpm.Pattern.spec(adj, induced=induced)
+        want = O.bf_subgraph_set(g, adj)
+        tuples, total = gpm.list_embeddings(G, P, cap=len(want) + 5)
+        assert total == len(want) == len(tuples)
+        assert _check_tuples(g, adj, P.info(), tuples) == want
+        G.close()
+
+
+@pytest.mark.parametrize("pi", range(len(LIST_PATTERNS)))
+def test_listing_capped(gpm, pi):
+    adj, induced = LIST_PATTERNS[pi]
+    g = gg.rmat(10, 16.0, seed=41)
+    G = gpm.Graph.from_host(g)
+    P = gpm.Pattern.spec(adj, induced=induced)
+    total_want = gpm.count(G, [P])[0]
+    for cap in (1, 1000, 12345):
+        tuples, total = gpm.list_embeddings(G, P, cap=cap)
+        assert total == total_want
+        assert len(tuples) == min(cap, total)
+        _check_tuples(g, adj, P.info(), tuples)
+    G.close()
+
+
+def test_listing_into_device_tensor(gpm):
+    import torch
+    g = gg.rmat(9, 8.0, seed=5)
+    G = gpm.Graph.from_host(g)
+    P = gpm.Pattern.spec(O.DIAMOND, induced=False)
+    out = torch.zeros((500, 4), dtype=torch.int32, device="cuda")
+    tuples, total = gpm.list_embeddings(G, P, cap=500, out=out)
+    _check_tuples(g, O.DIAMOND, P.info(), tuples.cpu().numpy().astype(np.int64))
+    G.close()
+
+
+def test_count_async_and_device_input(gpm):
+    import torch
+    g = gg.rmat(10, 8.0, seed=7)
+    rp = torch.from_numpy(g.rowptr.view(np.int64)).cuda()
+    col = torch.from_numpy(g.col.view(np.int32)).cuda()
+    G = gpm.Graph(rp, col, g.n)
+    G.prepare()
+    pats = gpm.Pattern.motifs(4)
+    out = torch.zeros(6, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    gpm.count(G, pats, stream=s)  # builds lazily-created task lists
+    gpm.count_async(G, pats, out, stream=s)
+    s.synchronize()
+    assert [int(x) for x in out.cpu()] == O.motifs(g, 4)
+    G.close()
+
+
+def _bad(n, rows):
+    rp = np.zeros(n + 1, dtype=np.uint64)
+    col = []
+    for v, r in enumerate(rows):
+        col += r
+        rp[v + 1] = len(col)
+    return rp, np.array(col, dtype=np.uint32)
+
+
+@pytest.mark.parametrize("rows,code", [
+    ([[1], [0, 0]], "DUPLICATE"),
+    ([[2, 1], [0], [0]], "NOT_SORTED"),
+    ([[0, 1], [0]], "SELF_LOOP"),
+    ([[1], []], "ASYMMETRIC"),
+    ([[5], [0]], "OUT_OF_RANGE"),
+])
+def test_validation_rejects_malformed_csr(gpm, rows, code):
+    rp, col = _bad(len(rows), rows)
+    if code == "ASYMMETRIC":
+        # odd nnz is caught on the host; give an even-length asymmetric CSR
+        rp, col = _bad(3, [[1], [2], [0]])
+    with pytest.raises(gpm.GpmError) as e:
+        gpm.Graph(rp, col, len(rp) - 1)
+    assert e.value.name == code
+
+
+def test_degenerate_graphs(gpm):
+    for g in (gg.empty(1), gg.empty(100), gg.from_edges(2, [(0, 1)])):
+        G = gpm.Graph.from_host(g)
+        assert gpm.count(G, [gpm.Pattern.clique(3), gpm.Pattern.clique(5)]) == [0, 0]
+        assert gpm.count(G, gpm.Pattern.motifs(4)) == [0] * 6
+        t, total = gpm.list_embeddings(G, gpm.Pattern.spec(O.DIAMOND, induced=False), cap=10)
+        assert total == 0 and len(t) == 0
+        G.close()
+
+
+# ---------------- full-size workloads ----------------
+
+def test_fullsize_tc_rmat14(gpm):
+    g = gg.workload_tc_rmat14()
+    gold = _golden().get("tc_rmat14", {})
+    G = gpm.Graph.from_host(g)
+    got = gpm.count(G, [gpm.Pattern.clique(k) for k in (3, 4, 5)])
+    assert got == [O.triangles(g), O.cliques(g, 4), O.cliques(g, 5)]
+    if gold:
+        assert gold["digest"] == g.digest()
+        assert got == [gold["clique3"], gold["clique4"], gold["clique5"]]
+    G.close()
+
+
+def _sample_ranges(n, seed, count=4, width=1500):
+    rng = np.random.default_rng(seed)
+    starts = sorted(rng.integers(0, n - width, size=count).tolist())
+    return [(s, s + width) for s in starts] + [(n - 7, n)]
+
+
+def test_fullsize_cliques_rmat21(gpm):
+    g = gg.workload_clique_rmat21()
+    gold = _golden().get("clique_rmat21", {})
+    G = gpm.Graph.from_host(g)
+    pats = [gpm.Pattern.clique(k) for k in (3, 4, 5)]
+    for lo, hi in _sample_ranges(g.n, 2):
+        assert gpm.count_roots(G, pats, lo, hi) == [O.cliques(g, k, lo, hi) for k in (3, 4, 5)], (lo, hi)
+    # the heaviest roots (largest out-degree) are checked one by one
+    od = O.out_degrees(g)
+    for v in np.argsort(od)[-3:].tolist():
+        assert gpm.count_roots(G, pats, v, v + 1) == [O.cliques(g, k, v, v + 1) for k in (3, 4, 5)], v
+    got = gpm.count(G, pats)
+    if gold:
+        assert gold["digest"] == g.digest()
+        for k, c in zip((3, 4, 5), got):
+            if f"clique{k}" in gold:
+                assert c == gold[f"clique{k}"], k
+    G.close()
+
+
+def test_fullsize_sl_chunglu4m(gpm):
+    g = gg.workload_sl_chung_lu4m()
+    gold = _golden().get("sl_chunglu4m", {})
+    G = gpm.Graph.from_host(g)
+    D = gpm.Pattern.spec(O.DIAMOND, induced=False)
+    C = gpm.Pattern.spec(O.CYCLE4, induced=False)
+    for lo, hi in _sample_ranges(g.n, 3, width=4000):
+        assert gpm.count_roots(G, [D, C], lo, hi) == [O.diamonds(g, lo, hi), O.cycles4(g, lo, hi)], (lo, hi)
+    got = gpm.count(G, [D, C])
+    if gold:
+        assert gold["digest"] == g.digest()
+        if "diamond" in gold:
+            assert got[0] == gold["diamond"]
+        if "cycle4" in gold:
+            assert got[1] == gold["cycle4"]
+    for P, adj in ((D, O.DIAMOND), (C, O.CYCLE4)):
+        tuples, total = gpm.list_embeddings(G, P, cap=1_000_000)
+        assert len(tuples) == min(total, 1_000_000)
+        # distinct subgraphs over all written tuples, validity on a sample
+        assert len(np.unique(_edge_keys(g, adj, tuples), axis=0)) == len(tuples)
+        rows = np.random.default_rng(0).choice(len(tuples), size=min(2000, len(tuples)), replace=False)
+        _check_tuples(g, adj, P.info(), tuples[rows])
+    G.close()
