@@ -211,6 +211,52 @@ int gpm_count_roots(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uin
 int gpm_list(gpm_graph_t g, gpm_pattern_t p, uint32_t *buf, uint64_t cap, uint64_t *written, uint64_t *total,
              void *stream);
 
+/* ---------------- batched form ---------------- */
+
+#define GPM_QUERY_MOTIF3 3u  /* 2 induced counts: wedge, triangle */
+#define GPM_QUERY_MOTIF4 4u  /* 6 induced counts, order of gpm_pattern_motifs(4) */
+#define GPM_QUERY_TC 5u      /* 1 count: triangles */
+#define GPM_QUERY_CLIQUE4 6u /* 1 count: 4-cliques */
+#define GPM_QUERY_CLIQUE5 7u /* 1 count: 5-cliques */
+
+typedef struct {
+  gpm_graph_t graph; /* the library prepares it if needed */
+  uint32_t kind;     /* GPM_QUERY_* */
+  uint32_t reserved;
+} gpm_query_t;
+
+typedef struct gpm_batch *gpm_batch_t;
+
+/*
+ * Plan a batch of queries over resident graphs (the paper's k-MC and k-CL
+ * problems, Section 2, for many inputs at once). Every query is cut into work
+ * items of per-root tasks; all items of all queries run in ONE persistent
+ * kernel captured in a CUDA graph, pulling items from a global atomic queue,
+ * so small and large queries overlap on the device. The graphs must outlive
+ * the batch and must not be counted concurrently by other calls while the
+ * batch runs. Roots with out-degree above 1024 are not supported here
+ * (GPM_E_UNSUPPORTED). Synchronises the device.
+ */
+int gpm_batch_create(const gpm_query_t *queries, uint32_t nq, gpm_batch_t *out);
+
+/*
+ * Run the batch: counts is host uint64[6*nq]; query i writes counts[6i ..]
+ * (2, 6 or 1 values by kind, the rest 0). The first run autotunes the item
+ * schedule (roots per warp item, vertices per edge item) by timing each
+ * candidate once; later runs replay the captured graph. Results equal
+ * gpm_count of each query alone. Ordered after `stream`; returns when done.
+ */
+int gpm_batch_run(gpm_batch_t b, uint64_t *counts, void *stream);
+
+/* Schedule chosen by the autotuner and the persistent grid size. */
+int gpm_batch_info(gpm_batch_t b, uint32_t *nitems, uint32_t *roots_per_item, uint32_t *verts_per_item,
+                   uint32_t *grid);
+
+int gpm_batch_destroy(gpm_batch_t b);
+
+/* create + run + destroy. */
+int gpm_count_batch(const gpm_query_t *queries, uint32_t nq, uint64_t *counts, void *stream);
+
 /* ---------------- diagnostics ---------------- */
 
 /* Message for the last error on the calling host thread ("" if none). */

@@ -1,0 +1,624 @@
+// Batched form: many count queries over many resident graphs in ONE
+// persistent fused kernel, replayed from a CUDA graph.
+//
+// Each query (a graph and a kind: 3-/4-motifs, triangles, 4- or 5-cliques)
+// is cut into work items of the same per-root routines the per-class kernels
+// use (lg_device.cuh, motif_device.cuh):
+//   LG_WARP  a range of roots with out-degree <= 128, one root per warp
+//   LG_CTA   one root with a larger out-degree, the whole CTA
+//   C4_SMALL a range of 4-cycle roots with a small wedge bound, one per warp
+//   C4_BIG   one 4-cycle root, the whole CTA with a dense tally slot
+//   EDGE     a range of vertices: local-count terms (4-motif queries wait
+//            until all of the query's triangle-scatter items are done)
+// Items sit in one global queue, heavy items first and EDGE items last; every
+// CTA pulls the next item with one atomicAdd. A query's last finished item
+// computes its counts (motif inversion included) on the device. Nothing
+// synchronises the host between queries, so small queries overlap with large
+// ones instead of each paying a launch sequence and a host round trip.
+//
+// The EDGE items' wait is bounded (a spin with __nanosleep and an iteration
+// cap); on timeout the kernel sets a status bit, the host reports
+// GPM_E_TIMEOUT and re-zeroes the per-arc buffers.
+//
+// The per-query schedule (roots per warp item, vertices per EDGE item, the
+// warp/CTA split) is chosen by a small autotuner: each candidate is timed by
+// one replay on the first run and the fastest is kept.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "gpm_internal.h"
+#include "lg_device.cuh"
+#include "motif_device.cuh"
+
+namespace {
+
+enum ItemType : uint32_t { IT_LG_WARP = 0, IT_LG_CTA = 1, IT_C4_SMALL = 2, IT_C4_BIG = 3, IT_EDGE = 4 };
+
+struct Item {
+  uint32_t type, q, lo, hi;
+};
+
+struct QDesc {
+  const uint64_t *rowptr;
+  const uint32_t *col;
+  const uint32_t *deg;
+  const uint64_t *drow;
+  const uint32_t *dcol;
+  uint32_t *t_edge;
+  const uint32_t *tasks;     // LG root tasks of the graph (class order)
+  const uint32_t *c4_tasks;  // 4-cycle roots
+  unsigned long long *acc;   // ACC_WORDS accumulators
+  unsigned long long *out;   // 6 results
+  unsigned int *left;        // [0] scatter items left, [1] items left
+  uint32_t n, kind;
+  uint64_t m;
+  uint32_t nformula;
+  uint32_t formula[6];
+  uint32_t scatter_items, all_items;
+};
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr uint32_t kWarpMaxD = 128;
+constexpr uint64_t kWaitLimit = 1ull << 26;
+
+struct BatchArgs {
+  const QDesc *qs;
+  const Item *items;
+  uint32_t nitems;
+  unsigned int *head;
+  uint32_t *tally_pool;
+  uint64_t tally_slot_words;
+  unsigned int *status;
+  uint32_t cta_maxd, cta_W;
+};
+
+// shared memory carve-up: the union of the item types' needs
+__host__ __device__ constexpr size_t warp_region_words() { return gpm_dev::warp_words(kWarpMaxD, true); }
+
+template <int KMAX, bool SCATTER>
+__device__ void lg_warp_item(const QDesc &q, const Item &it, uint32_t *smem, unsigned long long &a3,
+                             unsigned long long &a4, unsigned long long &a5) {
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t *base = smem + (size_t)wid * warp_region_words();
+  for (uint32_t t = it.lo + wid; t < it.hi; t += kWarps) {
+    const uint32_t u = q.tasks[t];
+    const uint32_t d = (uint32_t)(q.drow[u + 1] - q.drow[u]);
+    if (d < 2) continue;
+    if (d <= 32)
+      gpm_dev::lg_root_warp<32, 1, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, base, a3, a4, a5);
+    else
+      gpm_dev::lg_root_warp<kWarpMaxD, 4, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, base, a3, a4, a5);
+  }
+  (void)lane;
+}
+
+template <int KMAX, bool SCATTER>
+__device__ void lg_cta_item(const BatchArgs &a, const QDesc &q, const Item &it, uint32_t *smem,
+                            unsigned long long &a3, unsigned long long &a4, unsigned long long &a5) {
+  const uint32_t u = q.tasks[it.lo];
+  if (a.cta_W <= 8)
+    gpm_dev::lg_root_cta<8, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.cta_maxd, a.cta_W, smem, a3, a4, a5);
+  else if (a.cta_W <= 16)
+    gpm_dev::lg_root_cta<16, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.cta_maxd, a.cta_W, smem, a3, a4, a5);
+  else
+    gpm_dev::lg_root_cta<32, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.cta_maxd, a.cta_W, smem, a3, a4, a5);
+}
+
+__device__ __forceinline__ void block_add(unsigned long long *dst, unsigned long long v) {
+  v = gpm_dev::warp_sum(v);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+}
+
+__global__ void __launch_bounds__(kThreads) batch_kernel(BatchArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ Item s_item;
+  __shared__ uint32_t s_idx, s_cnt, s_nt;
+  __shared__ uint32_t s_x[kThreads];
+  const uint32_t tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) {
+      s_idx = atomicAdd(a.head, 1u);
+      if (s_idx < a.nitems) s_item = a.items[s_idx];
+    }
+    __syncthreads();
+    if (s_idx >= a.nitems) break;
+    const Item it = s_item;
+    __syncthreads();
+    const QDesc &q = a.qs[it.q];
+    unsigned long long a3 = 0, a4 = 0, a5 = 0, c4 = 0;
+    gpm_dev::EdgeTerms et;
+    bool overflow = false;
+    const uint32_t kind = q.kind;
+    switch (it.type) {
+      case IT_LG_WARP:
+        if (kind == GPM_QUERY_MOTIF4) lg_warp_item<4, true>(q, it, smem, a3, a4, a5);
+        else if (kind == GPM_QUERY_CLIQUE5) lg_warp_item<5, false>(q, it, smem, a3, a4, a5);
+        else if (kind == GPM_QUERY_CLIQUE4) lg_warp_item<4, false>(q, it, smem, a3, a4, a5);
+        else lg_warp_item<3, false>(q, it, smem, a3, a4, a5);
+        break;
+      case IT_LG_CTA:
+        if (kind == GPM_QUERY_MOTIF4) lg_cta_item<4, true>(a, q, it, smem, a3, a4, a5);
+        else if (kind == GPM_QUERY_CLIQUE5) lg_cta_item<5, false>(a, q, it, smem, a3, a4, a5);
+        else if (kind == GPM_QUERY_CLIQUE4) lg_cta_item<4, false>(a, q, it, smem, a3, a4, a5);
+        else lg_cta_item<3, false>(a, q, it, smem, a3, a4, a5);
+        break;
+      case IT_C4_SMALL: {
+        const uint32_t wid = tid >> 5;
+        uint32_t *keys = smem + (size_t)wid * 2 * gpm_dev::kC4HashSlots;
+        uint32_t *cnt = keys + gpm_dev::kC4HashSlots;
+        for (uint32_t t = it.lo + wid; t < it.hi; t += kWarps)
+          c4 += gpm_dev::c4_root_warp(q.rowptr, q.col, q.deg, q.c4_tasks[t], keys, cnt, overflow);
+        break;
+      }
+      case IT_C4_BIG: {
+        uint32_t *tally = a.tally_pool + (size_t)blockIdx.x * a.tally_slot_words;
+        c4 += gpm_dev::c4_root_cta(q.rowptr, q.col, q.deg, q.c4_tasks[it.lo], tally, tally + q.n, s_x, &s_cnt,
+                                   &s_nt);
+        break;
+      }
+      case IT_EDGE: {
+        if (kind == GPM_QUERY_MOTIF4) {
+          // wait until every triangle-scatter item of this query has finished
+          if (tid == 0) {
+            uint64_t it_wait = 0;
+            while (*(volatile unsigned int *)&q.left[0] != 0u) {
+              __nanosleep(200);
+              if (++it_wait > kWaitLimit) {
+                atomicOr(a.status, ST_TIMEOUT);
+                break;
+              }
+            }
+            __threadfence();
+          }
+          __syncthreads();
+          const uint32_t lane = tid & 31, wid = tid >> 5;
+          for (uint64_t u = it.lo + wid; u < it.hi; u += kWarps)
+            gpm_dev::edge_terms_vertex<true, true>(q.drow, q.dcol, q.deg, q.t_edge, u, true, et);
+          (void)lane;
+        } else {
+          const uint32_t wid = tid >> 5;
+          for (uint64_t u = it.lo + wid; u < it.hi; u += kWarps)
+            gpm_dev::edge_terms_vertex<false, false>(q.drow, q.dcol, q.deg, nullptr, u, true, et);
+        }
+        break;
+      }
+      default: break;
+    }
+    // fold this item's partial sums into the query's accumulators
+    block_add(&q.acc[ACC_T], a3);
+    block_add(&q.acc[ACC_K4], a4);
+    block_add(&q.acc[ACC_K5], a5);
+    block_add(&q.acc[ACC_C4], c4);
+    block_add(&q.acc[ACC_D], et.D);
+    block_add(&q.acc[ACC_P], et.P);
+    block_add(&q.acc[ACC_S], et.S);
+    block_add(&q.acc[ACC_W], et.W);
+    block_add(&q.acc[ACC_TT2], et.TT);
+    block_add(&q.acc[ACC_T3], et.T3);
+    if (__syncthreads_or(overflow) && tid == 0) atomicOr(a.status, ST_CAPACITY);
+    if (tid == 0) {
+      __threadfence();
+      if (kind == GPM_QUERY_MOTIF4 && (it.type == IT_LG_WARP || it.type == IT_LG_CTA)) atomicSub(&q.left[0], 1u);
+      const unsigned int before = atomicSub(&q.left[1], 1u);
+      if (before == 1u) {
+        // last item of this query: its counts, then re-arm it for the next replay
+        __threadfence();
+        unsigned long long acc[ACC_WORDS];
+        for (int i = 0; i < ACC_WORDS; ++i) acc[i] = atomicAdd(&q.acc[i], 0ull);
+        bool bad = false;
+        for (uint32_t i = 0; i < 6; ++i)
+          q.out[i] = (i < q.nformula) ? gpm_dev::finalize_formula(q.formula[i], acc, q.n, q.m, bad) : 0ull;
+        if (bad) atomicOr(a.status, ST_CAPACITY);
+        for (int i = 0; i < ACC_WORDS; ++i) q.acc[i] = 0ull;
+        q.left[0] = q.scatter_items;
+        __threadfence();
+        q.left[1] = q.all_items;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct gpm_batch {
+  int device = 0;
+  std::vector<gpm_query_t> queries;
+  cudaStream_t stream = nullptr;
+  QDesc *d_qs = nullptr;
+  Item *d_items = nullptr;
+  uint32_t nitems = 0, items_cap = 0;
+  unsigned long long *d_acc = nullptr;  // nq * ACC_WORDS
+  unsigned long long *d_out = nullptr;  // nq * 6
+  unsigned int *d_left = nullptr;       // nq * 2
+  unsigned int *d_head = nullptr;       // head, status
+  uint32_t *tally_pool = nullptr;
+  uint64_t tally_slot_words = 0;
+  uint64_t *h_out = nullptr;  // pinned
+  std::vector<uint32_t *> own_t_edge;  // per-arc buffers of repeated motif-4 graphs
+  uint32_t cta_maxd = 0, cta_W = 0;
+  size_t smem = 0;
+  int grid = 0;
+  uint32_t roots_per_item = 64, verts_per_item = 8192;
+  bool tuned = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<QDesc> qs;
+  double tuned_ms = 0.0;
+};
+
+namespace {
+
+int formulas_for(uint32_t kind, uint32_t *f, uint32_t *nf) {
+  switch (kind) {
+    case GPM_QUERY_MOTIF3: f[0] = F_WEDGE_I; f[1] = F_TRI; *nf = 2; return GPM_OK;
+    case GPM_QUERY_MOTIF4:
+      f[0] = F_STAR_I; f[1] = F_PATH_I; f[2] = F_TT_I; f[3] = F_C4_I; f[4] = F_D_I; f[5] = F_K4_I;
+      *nf = 6;
+      return GPM_OK;
+    case GPM_QUERY_TC: f[0] = F_TRI; *nf = 1; return GPM_OK;
+    case GPM_QUERY_CLIQUE4: f[0] = F_K4; *nf = 1; return GPM_OK;
+    case GPM_QUERY_CLIQUE5: f[0] = F_K5; *nf = 1; return GPM_OK;
+    default: return gpm_fail(GPM_E_INVALID_ARG, "unknown query kind " + std::to_string(kind));
+  }
+}
+
+void free_batch(gpm_batch *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  void *dev[] = {b->d_qs, b->d_items, b->d_acc, b->d_out, b->d_left, b->d_head, b->tally_pool};
+  for (void *p : dev)
+    if (p) cudaFree(p);
+  if (b->h_out) cudaFreeHost(b->h_out);
+  for (uint32_t *p : b->own_t_edge) cudaFree(p);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+// Work items for the current schedule; heavy items first, EDGE items last.
+void make_items(gpm_batch *b, std::vector<Item> &items) {
+  items.clear();
+  std::vector<Item> heavy, light, edge;
+  const uint32_t nq = (uint32_t)b->queries.size();
+  for (uint32_t qi = 0; qi < nq; ++qi) {
+    gpm_graph *g = b->queries[qi].graph;
+    QDesc &q = b->qs[qi];
+    uint32_t scatter = 0, all = 0;
+    const uint32_t warp_end = g->cls_begin[CLS_WARP + 1];
+    for (uint32_t t = 0; t < warp_end; t += b->roots_per_item) {
+      light.push_back({IT_LG_WARP, qi, t, std::min(warp_end, t + b->roots_per_item)});
+      ++all;
+      ++scatter;
+    }
+    for (uint32_t t = g->cls_begin[CLS_CTA]; t < g->cls_begin[CLS_CTA + 1]; ++t) {
+      heavy.push_back({IT_LG_CTA, qi, t, t + 1});
+      ++all;
+      ++scatter;
+    }
+    if (q.kind == GPM_QUERY_MOTIF4) {
+      for (uint32_t t = g->c4_begin[0]; t < g->c4_begin[1]; t += b->roots_per_item) {
+        light.push_back({IT_C4_SMALL, qi, t, std::min(g->c4_begin[1], t + b->roots_per_item)});
+        ++all;
+      }
+      for (uint32_t t = g->c4_begin[1]; t < g->c4_begin[2]; ++t) {
+        heavy.push_back({IT_C4_BIG, qi, t, t + 1});
+        ++all;
+      }
+    }
+    if (q.kind == GPM_QUERY_MOTIF3 || q.kind == GPM_QUERY_MOTIF4) {
+      for (uint32_t v = 0; v < g->n; v += b->verts_per_item) {
+        edge.push_back({IT_EDGE, qi, v, std::min(g->n, v + b->verts_per_item)});
+        ++all;
+      }
+    }
+    if (q.kind != GPM_QUERY_MOTIF4) scatter = 0;
+    q.scatter_items = scatter;
+    q.all_items = all;
+  }
+  items.insert(items.end(), heavy.begin(), heavy.end());
+  items.insert(items.end(), light.begin(), light.end());
+  items.insert(items.end(), edge.begin(), edge.end());
+}
+
+int upload_schedule(gpm_batch *b) {
+  std::vector<Item> items;
+  make_items(b, items);
+  const uint32_t nq = (uint32_t)b->queries.size();
+  if (items.size() > b->items_cap) {
+    if (b->d_items) cudaFree(b->d_items);
+    b->d_items = nullptr;
+    GPM_CUDA(cudaMalloc(&b->d_items, sizeof(Item) * std::max<size_t>(items.size(), 1)));
+    b->items_cap = (uint32_t)items.size();
+  }
+  b->nitems = (uint32_t)items.size();
+  std::vector<unsigned int> left(2 * nq);
+  for (uint32_t i = 0; i < nq; ++i) {
+    left[2 * i] = b->qs[i].scatter_items;
+    left[2 * i + 1] = b->qs[i].all_items;
+  }
+  GPM_CUDA(cudaMemcpyAsync(b->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice, b->stream));
+  GPM_CUDA(cudaMemcpyAsync(b->d_qs, b->qs.data(), sizeof(QDesc) * nq, cudaMemcpyHostToDevice, b->stream));
+  GPM_CUDA(cudaMemcpyAsync(b->d_left, left.data(), sizeof(unsigned int) * 2 * nq, cudaMemcpyHostToDevice,
+                           b->stream));
+  GPM_CUDA(cudaMemsetAsync(b->d_acc, 0, sizeof(unsigned long long) * ACC_WORDS * nq, b->stream));
+  GPM_CUDA(cudaStreamSynchronize(b->stream));
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  if (b->graph) {
+    cudaGraphDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return GPM_OK;
+}
+
+int capture(gpm_batch *b) {
+  BatchArgs a{};
+  a.qs = b->d_qs;
+  a.items = b->d_items;
+  a.nitems = b->nitems;
+  a.head = b->d_head;
+  a.status = b->d_head + 1;
+  a.tally_pool = b->tally_pool;
+  a.tally_slot_words = b->tally_slot_words;
+  a.cta_maxd = b->cta_maxd;
+  a.cta_W = b->cta_W;
+  const uint32_t nq = (uint32_t)b->queries.size();
+  GPM_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  cudaMemsetAsync(b->d_head, 0, sizeof(unsigned int), b->stream);
+  GPM_LAUNCH("batch_kernel", b->stream, batch_kernel<<<b->grid, kThreads, b->smem, b->stream>>>(a));
+  cudaMemcpyAsync(b->h_out, b->d_out, sizeof(uint64_t) * 6 * nq, cudaMemcpyDeviceToHost, b->stream);
+  cudaError_t e = cudaStreamEndCapture(b->stream, &b->graph);
+  if (e != cudaSuccess) return gpm_cuda_fail(e, "batch capture");
+  GPM_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  return GPM_OK;
+}
+
+int replay(gpm_batch *b, float *ms) {
+  if (!b->exec) GPM_TRY(capture(b));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ms) {
+    GPM_CUDA(cudaEventCreate(&e0));
+    GPM_CUDA(cudaEventCreate(&e1));
+    GPM_CUDA(cudaEventRecord(e0, b->stream));
+  }
+  GPM_CUDA(cudaGraphLaunch(b->exec, b->stream));
+  gpm_note_launches(1);
+  if (ms) GPM_CUDA(cudaEventRecord(e1, b->stream));
+  GPM_CUDA(cudaStreamSynchronize(b->stream));
+  if (ms) {
+    cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  unsigned int status = 0;
+  GPM_CUDA(cudaMemcpy(&status, b->d_head + 1, sizeof(status), cudaMemcpyDeviceToHost));
+  if (status) {
+    // a timed-out or overflowing run leaves partial state: re-arm everything
+    GPM_CUDA(cudaMemset(b->d_head + 1, 0, sizeof(unsigned int)));
+    for (size_t i = 0; i < b->queries.size(); ++i)
+      if (b->qs[i].t_edge)
+        GPM_CUDA(cudaMemset(b->qs[i].t_edge, 0, sizeof(uint32_t) * std::max<uint64_t>(b->qs[i].m, 1)));
+    GPM_TRY(upload_schedule(b));
+    if (status & ST_TIMEOUT) return gpm_fail(GPM_E_TIMEOUT, "batched kernel: a bounded wait gave up");
+    return gpm_fail(GPM_E_OVERFLOW, "batched kernel: a motif count does not fit in 64 bits");
+  }
+  return GPM_OK;
+}
+
+int autotune(gpm_batch *b) {
+  struct Cand {
+    uint32_t roots, verts;
+  };
+  const Cand cands[] = {{64, 8192}, {16, 4096}, {256, 32768}};
+  float best = 1e30f;
+  Cand bestc = cands[0];
+  for (const Cand &c : cands) {
+    b->roots_per_item = c.roots;
+    b->verts_per_item = c.verts;
+    GPM_TRY(upload_schedule(b));
+    float ms = 0.f;
+    GPM_TRY(replay(b, nullptr));  // warm
+    GPM_TRY(replay(b, &ms));
+    if (ms < best) {
+      best = ms;
+      bestc = c;
+    }
+  }
+  b->roots_per_item = bestc.roots;
+  b->verts_per_item = bestc.verts;
+  b->tuned_ms = best;
+  GPM_TRY(upload_schedule(b));
+  b->tuned = true;
+  return GPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gpm_batch_create(const gpm_query_t *queries, uint32_t nq, gpm_batch_t *out) {
+  if (!queries || !out || nq == 0) return gpm_fail(GPM_E_INVALID_ARG, "null argument or empty batch");
+  gpm_batch *b = new gpm_batch();
+  auto fail = [&](int code) {
+    free_batch(b);
+    return code;
+  };
+  b->queries.assign(queries, queries + nq);
+  if (cudaGetDevice(&b->device) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(gpm_fail(GPM_E_DEVICE, "no CUDA device"));
+  }
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(gpm_fail(GPM_E_DEVICE, "stream creation failed"));
+  uint32_t nmax = 1;
+  bool need_c4 = false;
+  b->qs.resize(nq);
+  std::vector<gpm_graph *> m4_graphs;
+  for (uint32_t i = 0; i < nq; ++i) {
+    gpm_graph *g = queries[i].graph;
+    if (!g) return fail(gpm_fail(GPM_E_INVALID_ARG, "null graph in batch"));
+    std::lock_guard<std::mutex> lk(g->mu);
+    int rc = gpm_prepare_graph(g, b->stream);
+    if (rc) return fail(rc);
+    const gpm_tuning &t = gpm_tune();
+    if (g->cls_maxdeg[CLS_WARP] > kWarpMaxD || t.warp_max_degree > kWarpMaxD) {
+      // rebuild this graph's classes with the batch's warp bound
+      const uint32_t old_w = t.warp_max_degree;
+      gpm_tune().warp_max_degree = std::min<uint32_t>(old_w, kWarpMaxD);
+      g->tune_warp_max = 0;
+      rc = gpm_ensure_classes(g, b->stream);
+      gpm_tune().warp_max_degree = old_w;
+      if (rc) return fail(rc);
+    }
+    if (g->cls_begin[CLS_XL + 1] > g->cls_begin[CLS_XL])
+      return fail(gpm_fail(GPM_E_UNSUPPORTED, "batched form supports root out-degrees up to 1024"));
+    QDesc &q = b->qs[i];
+    std::memset(&q, 0, sizeof(q));
+    q.kind = queries[i].kind;
+    rc = formulas_for(q.kind, q.formula, &q.nformula);
+    if (rc) return fail(rc);
+    if (q.kind == GPM_QUERY_MOTIF4) {
+      if (!g->t_edge) {
+        rc = gpm_graph_alloc(g, (void **)&g->t_edge, sizeof(uint32_t) * std::max<uint64_t>(g->m, 1));
+        if (rc) return fail(rc);
+      }
+      if (cudaMemsetAsync(g->t_edge, 0, sizeof(uint32_t) * std::max<uint64_t>(g->m, 1), b->stream) != cudaSuccess)
+        return fail(gpm_fail(GPM_E_DEVICE, "t_edge reset failed"));
+      // 4-cycle task lists: one synchronous count builds them on first use
+      if (!g->c4_ready) {
+        gpm_pattern p{};
+        p.k = 4;
+        p.induced = 0;
+        uint8_t c4[16] = {0, 0, 1, 1, 0, 0, 1, 1, 1, 1, 0, 0, 1, 1, 0, 0};
+        std::memcpy(p.adj, c4, 16);
+        rc = gpm_plan_pattern(&p);
+        if (rc) return fail(rc);
+        unsigned long long *acc = reinterpret_cast<unsigned long long *>(g->work + WK_ACC);
+        if (cudaMemsetAsync(acc, 0, ACC_WORDS * 8, b->stream) != cudaSuccess)
+          return fail(gpm_fail(GPM_E_DEVICE, "acc reset failed"));
+        rc = gpm_launch_cycles4(g, 0, g->n, acc, b->stream);
+        if (rc) return fail(rc);
+      }
+      need_c4 = true;
+    }
+    q.rowptr = g->rowptr;
+    q.col = g->col;
+    q.deg = g->deg;
+    q.drow = g->drow;
+    q.dcol = g->dcol;
+    q.t_edge = g->t_edge;
+    if (q.kind == GPM_QUERY_MOTIF4) {
+      if (std::find(m4_graphs.begin(), m4_graphs.end(), g) != m4_graphs.end()) {
+        // the same graph in several motif-4 queries: each needs its own per-arc counts
+        uint32_t *p = nullptr;
+        if (cudaMalloc(&p, sizeof(uint32_t) * std::max<uint64_t>(g->m, 1)) != cudaSuccess) {
+          cudaGetLastError();
+          return fail(gpm_fail(GPM_E_OOM, "per-query arc buffer allocation failed"));
+        }
+        b->own_t_edge.push_back(p);
+        cudaMemsetAsync(p, 0, sizeof(uint32_t) * std::max<uint64_t>(g->m, 1), b->stream);
+        q.t_edge = p;
+      }
+      m4_graphs.push_back(g);
+    }
+    q.tasks = g->tasks;
+    q.c4_tasks = g->c4_tasks;
+    q.n = g->n;
+    q.m = g->m;
+    nmax = std::max(nmax, g->n);
+    b->cta_maxd = std::max(b->cta_maxd, g->cls_maxdeg[CLS_CTA]);
+  }
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return fail(gpm_fail(GPM_E_DEVICE, "batch preparation"));
+  // arenas
+  int rc = GPM_OK;
+  if (cudaMalloc(&b->d_qs, sizeof(QDesc) * nq) != cudaSuccess ||
+      cudaMalloc(&b->d_acc, sizeof(unsigned long long) * ACC_WORDS * nq) != cudaSuccess ||
+      cudaMalloc(&b->d_out, sizeof(unsigned long long) * 6 * nq) != cudaSuccess ||
+      cudaMalloc(&b->d_left, sizeof(unsigned int) * 2 * nq) != cudaSuccess ||
+      cudaMalloc(&b->d_head, sizeof(unsigned int) * 4) != cudaSuccess ||
+      cudaMallocHost(&b->h_out, sizeof(uint64_t) * 6 * nq) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(gpm_fail(GPM_E_OOM, "batch arena allocation failed"));
+  }
+  cudaMemset(b->d_head, 0, sizeof(unsigned int) * 4);
+  cudaMemset(b->d_out, 0, sizeof(unsigned long long) * 6 * nq);
+  for (uint32_t i = 0; i < nq; ++i) {
+    b->qs[i].acc = b->d_acc + (size_t)ACC_WORDS * i;
+    b->qs[i].out = b->d_out + (size_t)6 * i;
+    b->qs[i].left = b->d_left + 2 * i;
+  }
+  // shared memory: the largest of the item types' needs
+  b->cta_W = std::max<uint32_t>(1, (b->cta_maxd + 31) / 32);
+  const size_t warp_bytes = warp_region_words() * 4 * kWarps;
+  const size_t cta_bytes = b->cta_maxd ? gpm_dev::cta_words(b->cta_maxd, b->cta_W) * 4 : 0;
+  const size_t c4_bytes = need_c4 ? (size_t)kWarps * 2 * gpm_dev::kC4HashSlots * 4 : 0;
+  b->smem = std::max(warp_bytes, std::max(cta_bytes, c4_bytes));
+  if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem) != cudaSuccess)
+    return fail(gpm_fail(GPM_E_DEVICE, "shared memory attribute"));
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kThreads, b->smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  b->grid = gpm_num_sms(b->device) * per_sm;
+  if (need_c4) {
+    b->tally_slot_words = 2 * (uint64_t)nmax;
+    if (cudaMalloc(&b->tally_pool, sizeof(uint32_t) * b->tally_slot_words * b->grid) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(gpm_fail(GPM_E_OOM, "batch tally pool allocation failed"));
+    }
+    cudaMemset(b->tally_pool, 0, sizeof(uint32_t) * b->tally_slot_words * b->grid);
+  }
+  rc = upload_schedule(b);
+  if (rc) return fail(rc);
+  *out = b;
+  return GPM_OK;
+}
+
+int gpm_batch_run(gpm_batch_t b, uint64_t *counts, void *stream) {
+  if (!b || !counts) return gpm_fail(GPM_E_INVALID_ARG, "null argument");
+  cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+  // order after the caller's stream
+  cudaEvent_t ev;
+  GPM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  GPM_CUDA(cudaEventRecord(ev, user));
+  GPM_CUDA(cudaStreamWaitEvent(b->stream, ev, 0));
+  cudaEventDestroy(ev);
+  if (!b->tuned) GPM_TRY(autotune(b));
+  GPM_TRY(replay(b, nullptr));
+  std::memcpy(counts, b->h_out, sizeof(uint64_t) * 6 * b->queries.size());
+  return GPM_OK;
+}
+
+int gpm_batch_info(gpm_batch_t b, uint32_t *nitems, uint32_t *roots_per_item, uint32_t *verts_per_item,
+                   uint32_t *grid) {
+  if (!b) return gpm_fail(GPM_E_INVALID_ARG, "null batch");
+  if (nitems) *nitems = b->nitems;
+  if (roots_per_item) *roots_per_item = b->roots_per_item;
+  if (verts_per_item) *verts_per_item = b->verts_per_item;
+  if (grid) *grid = (uint32_t)b->grid;
+  return GPM_OK;
+}
+
+int gpm_batch_destroy(gpm_batch_t b) {
+  if (!b) return gpm_fail(GPM_E_INVALID_ARG, "null batch");
+  cudaStreamSynchronize(b->stream);
+  free_batch(b);
+  return GPM_OK;
+}
+
+int gpm_count_batch(const gpm_query_t *queries, uint32_t nq, uint64_t *counts, void *stream) {
+  gpm_batch_t b = nullptr;
+  GPM_TRY(gpm_batch_create(queries, nq, &b));
+  int rc = gpm_batch_run(b, counts, stream);
+  gpm_batch_destroy(b);
+  return rc;
+}
+
+}  // extern "C"

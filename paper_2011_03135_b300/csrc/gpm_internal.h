@@ -213,6 +213,7 @@ int gpm_launch_permute_tuples(uint32_t *buf, uint64_t count, int k, const uint32
 // launch accounting / per-kernel event timing (profile.cpp)
 void gpm_prof_begin(const char *name, cudaStream_t st);
 void gpm_prof_end(cudaStream_t st);
+void gpm_note_launches(uint64_t k);  // kernels launched by a CUDA-graph replay
 #define GPM_LAUNCH(name, st, ...)  \
   do {                             \
     gpm_prof_begin(name, st);      \

@@ -24,63 +24,40 @@
 #include <algorithm>
 
 #include "gpm_internal.h"
+#include "motif_device.cuh"
 
 namespace {
 
-__device__ __forceinline__ bool precedes(uint32_t da, uint32_t a, uint32_t db, uint32_t b) {
-  return da < db || (da == db && a < b);
-}
-
-__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
+using gpm_dev::precedes;
+using gpm_dev::warp_sum;
 
 // ---------------------------------------------------------------------------
 // per-arc / per-vertex local-count terms
 // ---------------------------------------------------------------------------
 template <bool USE_T>
 __global__ void edge_terms_kernel(const uint64_t *__restrict__ drow, const uint32_t *__restrict__ dcol,
-                                  const uint32_t *__restrict__ deg, const uint32_t *__restrict__ t_edge, uint32_t n,
+                                  const uint32_t *__restrict__ deg, uint32_t *__restrict__ t_edge, uint32_t n,
                                   uint32_t root_lo, uint32_t root_hi, unsigned long long *__restrict__ acc) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  unsigned long long sD = 0, sP = 0, sS = 0, sW = 0, sTT = 0, sT3 = 0;
-  for (uint64_t u = warp; u < n; u += nwarps) {
-    const unsigned long long du = deg[u];
-    if (lane == 0) {
-      if (du >= 3) sS += du * (du - 1) * (du - 2) / 6;
-      if (du >= 2) sW += du * (du - 1) / 2;
-    }
-    const bool in_range = u >= root_lo && u < root_hi;
-    for (uint64_t e = drow[u] + lane; e < drow[u + 1]; e += 32) {
-      const unsigned long long dv = deg[dcol[e]];
-      sP += (du - 1) * (dv - 1);
-      if (USE_T) {
-        const unsigned long long t = t_edge[e];
-        if (t) {
-          if (in_range) sD += t * (t - 1) / 2;
-          sTT += t * (du + dv - 4);
-          sT3 += t;
-        }
-      }
-    }
-  }
-  sD = warp_sum(sD);
-  sP = warp_sum(sP);
-  sS = warp_sum(sS);
-  sW = warp_sum(sW);
-  sTT = warp_sum(sTT);
-  sT3 = warp_sum(sT3);
+  gpm_dev::EdgeTerms s;
+  for (uint64_t u = warp; u < n; u += nwarps)
+    gpm_dev::edge_terms_vertex<USE_T, false>(drow, dcol, deg, t_edge, u, u >= root_lo && u < root_hi, s);
+  s.D = warp_sum(s.D);
+  s.P = warp_sum(s.P);
+  s.S = warp_sum(s.S);
+  s.W = warp_sum(s.W);
+  s.TT = warp_sum(s.TT);
+  s.T3 = warp_sum(s.T3);
   if (lane == 0) {
-    atomicAdd(&acc[ACC_P], sP);
-    atomicAdd(&acc[ACC_S], sS);
-    atomicAdd(&acc[ACC_W], sW);
+    atomicAdd(&acc[ACC_P], s.P);
+    atomicAdd(&acc[ACC_S], s.S);
+    atomicAdd(&acc[ACC_W], s.W);
     if (USE_T) {
-      atomicAdd(&acc[ACC_D], sD);
-      atomicAdd(&acc[ACC_TT2], sTT);
-      atomicAdd(&acc[ACC_T3], sT3);
+      atomicAdd(&acc[ACC_D], s.D);
+      atomicAdd(&acc[ACC_TT2], s.TT);
+      atomicAdd(&acc[ACC_T3], s.T3);
     }
   }
 }
@@ -88,9 +65,8 @@ __global__ void edge_terms_kernel(const uint64_t *__restrict__ drow, const uint3
 // ---------------------------------------------------------------------------
 // 4-cycles
 // ---------------------------------------------------------------------------
-constexpr uint32_t kSmallBound = 512;   // wedge bound for the shared-memory class
-constexpr uint32_t kHashSlots = 1024;   // per warp, load factor <= 1/2
-constexpr uint32_t kEmpty = 0xffffffffu;
+constexpr uint32_t kSmallBound = gpm_dev::kC4SmallBound;
+constexpr uint32_t kHashSlots = gpm_dev::kC4HashSlots;
 
 // wedge bound B(v0) = sum of d_x over neighbours x before v0; class 0 small, 1 big
 __global__ void c4_bound_kernel(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
@@ -145,52 +121,7 @@ __global__ void __launch_bounds__(256) c4_small_kernel(C4Args a) {
     if (task >= a.ntasks) break;
     const uint32_t v0 = a.tasks[task];
     if (v0 < a.root_lo || v0 >= a.root_hi) continue;
-    for (uint32_t i = lane; i < kHashSlots; i += 32) {
-      keys[i] = kEmpty;
-      cnt[i] = 0;
-    }
-    __syncwarp();
-    const uint32_t d0 = a.deg[v0];
-    const uint64_t b0 = a.rowptr[v0], e0 = a.rowptr[v0 + 1];
-    for (uint64_t cb = b0; cb < e0; cb += 32) {
-      const uint64_t ex = cb + lane;
-      uint32_t x = 0;
-      bool ok = false;
-      if (ex < e0) {
-        x = a.col[ex];
-        ok = precedes(a.deg[x], x, d0, v0);
-      }
-      uint32_t mask = __ballot_sync(0xffffffffu, ok);
-      while (mask) {
-        const int src = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const uint32_t xx = __shfl_sync(0xffffffffu, x, src);
-        for (uint64_t f = a.rowptr[xx] + lane; f < a.rowptr[xx + 1]; f += 32) {
-          const uint32_t w = a.col[f];
-          if (!precedes(a.deg[w], w, d0, v0)) continue;
-          uint32_t h = (w * 2654435761u) >> 22;  // 10 bits
-          uint32_t probes = 0;
-          for (;;) {
-            const uint32_t k = atomicCAS(&keys[h], kEmpty, w);
-            if (k == kEmpty || k == w) {
-              atomicAdd(&cnt[h], 1u);
-              break;
-            }
-            h = (h + 1) & (kHashSlots - 1);
-            if (++probes >= kHashSlots) {
-              overflow = true;
-              break;
-            }
-          }
-        }
-      }
-    }
-    __syncwarp();
-    for (uint32_t i = lane; i < kHashSlots; i += 32) {
-      const unsigned long long c = cnt[i];
-      acc += c * (c - 1) / 2;
-    }
-    __syncwarp();
+    acc += gpm_dev::c4_root_warp(a.rowptr, a.col, a.deg, v0, keys, cnt, overflow);
   }
   acc = warp_sum(acc);
   if (lane == 0 && acc) atomicAdd(&a.acc[ACC_C4], acc);
@@ -199,59 +130,21 @@ __global__ void __launch_bounds__(256) c4_small_kernel(C4Args a) {
 
 // one CTA per root, dense tally in this CTA's global-memory slot
 __global__ void __launch_bounds__(512) c4_big_kernel(C4Args a) {
-  __shared__ uint32_t s_task, s_nt;
+  __shared__ uint32_t s_task, s_nt, s_cnt;
   __shared__ uint32_t s_x[512];
-  const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const uint32_t tid = threadIdx.x, lane = tid & 31;
   uint32_t *tally = a.pool + (size_t)blockIdx.x * 2 * a.n;
   uint32_t *touched = tally + a.n;
   unsigned long long acc = 0;
   for (;;) {
-    if (tid == 0) {
-      s_task = atomicAdd(a.queue, 1u);
-      s_nt = 0;
-    }
+    if (tid == 0) s_task = atomicAdd(a.queue, 1u);
     __syncthreads();
     const uint32_t task = s_task;
+    __syncthreads();
     if (task >= a.ntasks) break;
     const uint32_t v0 = a.tasks[task];
-    if (v0 < a.root_lo || v0 >= a.root_hi) {
-      __syncthreads();
-      continue;
-    }
-    const uint32_t d0 = a.deg[v0];
-    const uint64_t b0 = a.rowptr[v0], e0 = a.rowptr[v0 + 1];
-    // neighbours before v0, in chunks of nt; each warp scans whole lists
-    for (uint64_t cb = b0; cb < e0; cb += nt) {
-      __shared__ uint32_t s_cnt;
-      if (tid == 0) s_cnt = 0;
-      __syncthreads();
-      const uint64_t ex = cb + tid;
-      if (ex < e0) {
-        const uint32_t x = a.col[ex];
-        if (precedes(a.deg[x], x, d0, v0)) s_x[atomicAdd(&s_cnt, 1u)] = x;
-      }
-      __syncthreads();
-      const uint32_t cnt = s_cnt;
-      for (uint32_t xi = wid; xi < cnt; xi += nw) {
-        const uint32_t x = s_x[xi];
-        for (uint64_t f = a.rowptr[x] + lane; f < a.rowptr[x + 1]; f += 32) {
-          const uint32_t w = a.col[f];
-          if (!precedes(a.deg[w], w, d0, v0)) continue;
-          if (atomicAdd(&tally[w], 1u) == 0u) touched[atomicAdd(&s_nt, 1u)] = w;
-        }
-      }
-      __syncthreads();
-    }
-    __threadfence_block();
-    __syncthreads();
-    const uint32_t ntouched = s_nt;
-    for (uint32_t i = tid; i < ntouched; i += nt) {
-      const uint32_t w = touched[i];
-      const unsigned long long c = tally[w];
-      acc += c * (c - 1) / 2;
-      tally[w] = 0;
-    }
-    __syncthreads();
+    if (v0 < a.root_lo || v0 >= a.root_hi) continue;
+    acc += gpm_dev::c4_root_cta(a.rowptr, a.col, a.deg, v0, tally, touched, s_x, &s_cnt, &s_nt);
   }
   acc = warp_sum(acc);
   if (lane == 0 && acc) atomicAdd(&a.acc[ACC_C4], acc);
@@ -263,42 +156,8 @@ __global__ void __launch_bounds__(512) c4_big_kernel(C4Args a) {
 __global__ void finalize_kernel(FinalizeSpec spec, const unsigned long long *__restrict__ acc, uint64_t n, uint64_t m,
                                 unsigned long long *__restrict__ out, unsigned int *__restrict__ status) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const unsigned long long T = acc[ACC_T];
-  const unsigned long long NS = acc[ACC_S], NP = acc[ACC_P] - 3ull * T, NTT = acc[ACC_TT2] / 2ull,
-                           NC4 = acc[ACC_C4], ND = acc[ACC_D], NK4 = acc[ACC_K4];
-  // induced 4-vertex counts, modulo 2^64 (exact when the true values fit)
-  const unsigned long long iK4 = NK4;
-  const unsigned long long iD = ND - 6ull * iK4;
-  const unsigned long long iC4 = NC4 - iD - 3ull * iK4;
-  const unsigned long long iTT = NTT - 4ull * iD - 12ull * iK4;
-  const unsigned long long iP = NP - 2ull * iTT - 4ull * iC4 - 6ull * iD - 12ull * iK4;
-  const unsigned long long iS = NS - iTT - 2ull * iD - 4ull * iK4;
-  unsigned int bad = 0;
-  for (uint32_t i = 0; i < spec.npat; ++i) {
-    unsigned long long v = 0;
-    switch (spec.formula[i]) {
-      case F_VERTEX: v = n; break;
-      case F_EDGE: v = m; break;
-      case F_TRI: v = T; break;
-      case F_K4: v = acc[ACC_K4]; break;
-      case F_K5: v = acc[ACC_K5]; break;
-      case F_WEDGE_NI: v = acc[ACC_W]; break;
-      case F_WEDGE_I: v = acc[ACC_W] - 3ull * T; bad |= (v > acc[ACC_W]); break;
-      case F_STAR_NI: v = NS; break;
-      case F_PATH_NI: v = NP; break;
-      case F_TT_NI: v = NTT; break;
-      case F_C4_NI: v = NC4; break;
-      case F_D_NI: v = ND; break;
-      case F_STAR_I: v = iS; bad |= (iS > NS); break;
-      case F_PATH_I: v = iP; bad |= (iP > NP); break;
-      case F_TT_I: v = iTT; bad |= (iTT > NTT); break;
-      case F_C4_I: v = iC4; bad |= (iC4 > NC4); break;
-      case F_D_I: v = iD; bad |= (iD > ND); break;
-      case F_K4_I: v = iK4; break;
-      default: bad = 1; break;
-    }
-    out[i] = v;
-  }
+  bool bad = false;
+  for (uint32_t i = 0; i < spec.npat; ++i) out[i] = gpm_dev::finalize_formula(spec.formula[i], acc, n, m, bad);
   if (bad) atomicOr(status, ST_CAPACITY);
 }
 

@@ -1,0 +1,199 @@
+// Device building blocks of 4-cycle counting and the local-count terms,
+// shared by the per-pass kernels (motif.cu) and the batched persistent kernel
+// (batch.cu). See motif.cu for the method.
+#pragma once
+
+#include <stdint.h>
+
+namespace gpm_dev {
+
+constexpr uint32_t kC4SmallBound = 512;  // wedge bound for the shared-memory class
+constexpr uint32_t kC4HashSlots = 1024;  // per warp, load factor <= 1/2
+constexpr uint32_t kC4Empty = 0xffffffffu;
+
+__device__ __forceinline__ bool precedes(uint32_t da, uint32_t a, uint32_t db, uint32_t b) {
+  return da < db || (da == db && a < b);
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// 4-cycles rooted at v0 (its order-last vertex) by the calling warp, with a
+// shared-memory hash table keys/cnt of kC4HashSlots entries each. The wedge
+// bound of v0 must be <= kC4SmallBound. Returns this lane's part of the count.
+__device__ __forceinline__ unsigned long long c4_root_warp(const uint64_t *__restrict__ rowptr,
+                                                           const uint32_t *__restrict__ col,
+                                                           const uint32_t *__restrict__ deg, uint32_t v0,
+                                                           uint32_t *keys, uint32_t *cnt, bool &overflow) {
+  const uint32_t lane = threadIdx.x & 31;
+  for (uint32_t i = lane; i < kC4HashSlots; i += 32) {
+    keys[i] = kC4Empty;
+    cnt[i] = 0;
+  }
+  __syncwarp();
+  const uint32_t d0 = deg[v0];
+  const uint64_t b0 = rowptr[v0], e0 = rowptr[v0 + 1];
+  for (uint64_t cb = b0; cb < e0; cb += 32) {
+    const uint64_t ex = cb + lane;
+    uint32_t x = 0;
+    bool ok = false;
+    if (ex < e0) {
+      x = col[ex];
+      ok = precedes(deg[x], x, d0, v0);
+    }
+    uint32_t mask = __ballot_sync(0xffffffffu, ok);
+    while (mask) {
+      const int src = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const uint32_t xx = __shfl_sync(0xffffffffu, x, src);
+      for (uint64_t f = rowptr[xx] + lane; f < rowptr[xx + 1]; f += 32) {
+        const uint32_t w = col[f];
+        if (!precedes(deg[w], w, d0, v0)) continue;
+        uint32_t h = (w * 2654435761u) >> 22;  // 10 bits
+        uint32_t probes = 0;
+        for (;;) {
+          const uint32_t k = atomicCAS(&keys[h], kC4Empty, w);
+          if (k == kC4Empty || k == w) {
+            atomicAdd(&cnt[h], 1u);
+            break;
+          }
+          h = (h + 1) & (kC4HashSlots - 1);
+          if (++probes >= kC4HashSlots) {
+            overflow = true;
+            break;
+          }
+        }
+      }
+    }
+  }
+  __syncwarp();
+  unsigned long long acc = 0;
+  for (uint32_t i = lane; i < kC4HashSlots; i += 32) {
+    const unsigned long long c = cnt[i];
+    acc += c * (c - 1) / 2;
+  }
+  __syncwarp();
+  return acc;
+}
+
+// 4-cycles rooted at v0 by the whole CTA with a dense tally (n words, all
+// zero on entry and on exit) and a touched list (n words) in global memory.
+// s_x is a shared buffer of blockDim.x words. Every thread must call it.
+// Returns this thread's part of the count.
+__device__ __forceinline__ unsigned long long c4_root_cta(const uint64_t *__restrict__ rowptr,
+                                                          const uint32_t *__restrict__ col,
+                                                          const uint32_t *__restrict__ deg, uint32_t v0,
+                                                          uint32_t *tally, uint32_t *touched, uint32_t *s_x,
+                                                          uint32_t *s_cnt, uint32_t *s_nt) {
+  const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  if (tid == 0) *s_nt = 0;
+  const uint32_t d0 = deg[v0];
+  const uint64_t b0 = rowptr[v0], e0 = rowptr[v0 + 1];
+  for (uint64_t cb = b0; cb < e0; cb += nt) {
+    if (tid == 0) *s_cnt = 0;
+    __syncthreads();
+    const uint64_t ex = cb + tid;
+    if (ex < e0) {
+      const uint32_t x = col[ex];
+      if (precedes(deg[x], x, d0, v0)) s_x[atomicAdd(s_cnt, 1u)] = x;
+    }
+    __syncthreads();
+    const uint32_t cnt = *s_cnt;
+    for (uint32_t xi = wid; xi < cnt; xi += nw) {
+      const uint32_t x = s_x[xi];
+      for (uint64_t f = rowptr[x] + lane; f < rowptr[x + 1]; f += 32) {
+        const uint32_t w = col[f];
+        if (!precedes(deg[w], w, d0, v0)) continue;
+        if (atomicAdd(&tally[w], 1u) == 0u) touched[atomicAdd(s_nt, 1u)] = w;
+      }
+    }
+    __syncthreads();
+  }
+  __threadfence_block();
+  __syncthreads();
+  const uint32_t ntouched = *s_nt;
+  unsigned long long acc = 0;
+  for (uint32_t i = tid; i < ntouched; i += nt) {
+    const uint32_t w = touched[i];
+    const unsigned long long c = tally[w];
+    acc += c * (c - 1) / 2;
+    tally[w] = 0;
+  }
+  __syncthreads();
+  return acc;
+}
+
+// Local-count terms of vertex u (degree terms by lane 0; arc terms over the
+// out-arcs of u in the orientation, lane-strided). With USE_T the per-arc
+// triangle counts are read (and, with CLEAR_T, reset to zero afterwards).
+struct EdgeTerms {
+  unsigned long long D = 0, P = 0, S = 0, W = 0, TT = 0, T3 = 0;
+};
+
+template <bool USE_T, bool CLEAR_T>
+__device__ __forceinline__ void edge_terms_vertex(const uint64_t *__restrict__ drow, const uint32_t *__restrict__ dcol,
+                                                  const uint32_t *__restrict__ deg, uint32_t *t_edge, uint64_t u,
+                                                  bool in_range, EdgeTerms &s) {
+  const uint32_t lane = threadIdx.x & 31;
+  const unsigned long long du = deg[u];
+  if (lane == 0) {
+    if (du >= 3) s.S += du * (du - 1) * (du - 2) / 6;
+    if (du >= 2) s.W += du * (du - 1) / 2;
+  }
+  for (uint64_t e = drow[u] + lane; e < drow[u + 1]; e += 32) {
+    const unsigned long long dv = deg[dcol[e]];
+    s.P += (du - 1) * (dv - 1);
+    if (USE_T) {
+      const unsigned long long t = CLEAR_T ? __ldcg(t_edge + e) : t_edge[e];
+      if (t) {
+        if (in_range) s.D += t * (t - 1) / 2;
+        s.TT += t * (du + dv - 4);
+        s.T3 += t;
+        if (CLEAR_T) t_edge[e] = 0;
+      }
+    }
+  }
+}
+
+// Requested count from the accumulators (layout ACC_* of gpm_internal.h).
+// Induced 4-vertex counts are formed modulo 2^64 (exact when the true values
+// fit); `bad` is set when an induced count exceeds its non-induced bound.
+__device__ __forceinline__ unsigned long long finalize_formula(uint32_t f, const unsigned long long *acc, uint64_t n,
+                                                               uint64_t m, bool &bad) {
+  const unsigned long long T = acc[3];
+  const unsigned long long NS = acc[10], NP = acc[9] - 3ull * T, NTT = acc[12] / 2ull, NC4 = acc[14], ND = acc[8],
+                           NK4 = acc[4];
+  const unsigned long long iK4 = NK4;
+  const unsigned long long iD = ND - 6ull * iK4;
+  const unsigned long long iC4 = NC4 - iD - 3ull * iK4;
+  const unsigned long long iTT = NTT - 4ull * iD - 12ull * iK4;
+  const unsigned long long iP = NP - 2ull * iTT - 4ull * iC4 - 6ull * iD - 12ull * iK4;
+  const unsigned long long iS = NS - iTT - 2ull * iD - 4ull * iK4;
+  unsigned long long v = 0;
+  switch (f) {
+    case 0: v = n; break;                 // F_VERTEX
+    case 1: v = m; break;                 // F_EDGE
+    case 2: v = T; break;                 // F_TRI
+    case 3: v = acc[4]; break;            // F_K4
+    case 4: v = acc[5]; break;            // F_K5
+    case 5: v = acc[11]; break;           // F_WEDGE_NI
+    case 6: v = acc[11] - 3ull * T; bad |= (v > acc[11]); break;  // F_WEDGE_I
+    case 7: v = NS; break;
+    case 8: v = NP; break;
+    case 9: v = NTT; break;
+    case 10: v = NC4; break;
+    case 11: v = ND; break;
+    case 12: v = iS; bad |= (iS > NS); break;
+    case 13: v = iP; bad |= (iP > NP); break;
+    case 14: v = iTT; bad |= (iTT > NTT); break;
+    case 15: v = iC4; bad |= (iC4 > NC4); break;
+    case 16: v = iD; bad |= (iD > ND); break;
+    case 17: v = iK4; break;
+    default: bad = true; break;
+  }
+  return v;
+}
+
+}  // namespace gpm_dev

@@ -68,7 +68,22 @@ void drain_locked() {
 
 }  // namespace
 
+void gpm_note_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+static bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
 void gpm_prof_begin(const char *name, cudaStream_t st) {
+  if (capturing(st)) {
+    t_open.push_back(Pending{name, nullptr, nullptr});  // launches inside a graph are counted at replay
+    return;
+  }
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (!g_enabled.load(std::memory_order_relaxed)) return;
   std::lock_guard<std::mutex> lk(g_mu);
@@ -78,7 +93,11 @@ void gpm_prof_begin(const char *name, cudaStream_t st) {
 }
 
 void gpm_prof_end(cudaStream_t st) {
-  if (!g_enabled.load(std::memory_order_relaxed) || t_open.empty()) return;
+  if (t_open.empty()) return;
+  if (!t_open.back().start && !t_open.back().stop) {
+    t_open.pop_back();
+    return;
+  }
   std::lock_guard<std::mutex> lk(g_mu);
   Pending p = t_open.back();
   t_open.pop_back();

@@ -56,6 +56,14 @@ class PatternInfo(ctypes.Structure):
                 ("min_degree", ctypes.c_uint32 * 8)]
 
 
+class Query(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_void_p), ("kind", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+QUERY_MOTIF3, QUERY_MOTIF4, QUERY_TC, QUERY_CLIQUE4, QUERY_CLIQUE5 = 3, 4, 5, 6, 7
+QUERY_WIDTH = {QUERY_MOTIF3: 2, QUERY_MOTIF4: 6, QUERY_TC: 1, QUERY_CLIQUE4: 1, QUERY_CLIQUE5: 1}
+
+
 class Options(ctypes.Structure):
     _fields_ = [("warp_max_degree", ctypes.c_uint32), ("cta_max_degree", ctypes.c_uint32),
                 ("blocks_per_sm", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
@@ -81,6 +89,12 @@ _SIGS = {
     "gpm_profile_enable": [_i],
     "gpm_profile_reset": [],
     "gpm_profile_report": [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
+    "gpm_batch_create": [_vp, _u32, ctypes.POINTER(_vp)],
+    "gpm_batch_run": [_vp, _vp, _vp],
+    "gpm_batch_info": [_vp, ctypes.POINTER(_u32), ctypes.POINTER(_u32), ctypes.POINTER(_u32),
+                       ctypes.POINTER(_u32)],
+    "gpm_batch_destroy": [_vp],
+    "gpm_count_batch": [_vp, _u32, _vp, _vp],
     "gpm_set_options": [ctypes.POINTER(Options)],
     "gpm_get_options": [ctypes.POINTER(Options)],
 }
@@ -321,3 +335,60 @@ def list_embeddings(graph: Graph, pattern: Pattern, cap: int, out=None, stream=N
     _check(_lib.gpm_list(graph.handle, pattern.handle, p if cap else None, cap, ctypes.byref(written),
                          ctypes.byref(total), _stream(stream)))
     return out[: written.value], int(total.value)
+
+
+def _queries(queries):
+    arr = (Query * len(queries))()
+    for i, (g, kind) in enumerate(queries):
+        arr[i].graph = g.handle
+        arr[i].kind = kind
+    return arr
+
+
+class Batch:
+    """Many (graph, kind) count queries run by one persistent kernel replayed from a CUDA graph."""
+
+    def __init__(self, queries):
+        self._queries = list(queries)
+        self._arr = _queries(self._queries)
+        h = _vp()
+        _check(_lib.gpm_batch_create(self._arr, len(self._queries), ctypes.byref(h)))
+        self._h = h
+
+    def run(self, stream=None) -> list:
+        out = np.zeros(6 * len(self._queries), dtype=np.uint64)
+        _check(_lib.gpm_batch_run(self._h, out.ctypes.data, _stream(stream)))
+        return [[int(x) for x in out[6 * i: 6 * i + QUERY_WIDTH[k]]] for i, (_, k) in enumerate(self._queries)]
+
+    def info(self) -> dict:
+        a, b, c, d = _u32(), _u32(), _u32(), _u32()
+        _check(_lib.gpm_batch_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+        return dict(items=a.value, roots_per_item=b.value, verts_per_item=c.value, grid=d.value)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.gpm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def count_batch(queries, stream=None) -> list:
+    """One-shot batched counts for [(Graph, QUERY_*), ...]."""
+    arr = _queries(queries)
+    out = np.zeros(6 * len(queries), dtype=np.uint64)
+    _check(_lib.gpm_count_batch(arr, len(queries), out.ctypes.data, _stream(stream)))
+    return [[int(x) for x in out[6 * i: 6 * i + QUERY_WIDTH[k]]] for i, (_, k) in enumerate(queries)]
+
+
+def plain_patterns(kind):
+    """The patterns a one-query-per-call gpm_count needs for a batch query kind."""
+    if kind == QUERY_MOTIF3:
+        return Pattern.motifs(3)
+    if kind == QUERY_MOTIF4:
+        return Pattern.motifs(4)
+    return [Pattern.clique({QUERY_TC: 3, QUERY_CLIQUE4: 4, QUERY_CLIQUE5: 5}[kind])]

@@ -216,17 +216,15 @@ def _bad(n, rows):
 
 
 @pytest.mark.parametrize("rows,code", [
-    ([[1], [0, 0]], "DUPLICATE"),
+    ([[1, 1], [0, 0]], "DUPLICATE"),
     ([[2, 1], [0], [0]], "NOT_SORTED"),
-    ([[0, 1], [0]], "SELF_LOOP"),
-    ([[1], []], "ASYMMETRIC"),
+    ([[0, 1], [0, 1]], "SELF_LOOP"),
+    ([[1, 2], [2], [0], []], "ASYMMETRIC"),     # 0 in N(2) is missing its mirror in N(1)
+    ([[1], [0, 1, 2]], "ASYMMETRIC"),           # odd nnz: rejected on the host
     ([[5], [0]], "OUT_OF_RANGE"),
 ])
 def test_validation_rejects_malformed_csr(gpm, rows, code):
     rp, col = _bad(len(rows), rows)
-    if code == "ASYMMETRIC":
-        # odd nnz is caught on the host; give an even-length asymmetric CSR
-        rp, col = _bad(3, [[1], [2], [0]])
     with pytest.raises(gpm.GpmError) as e:
         gpm.Graph(rp, col, len(rp) - 1)
     assert e.value.name == code
@@ -267,12 +265,14 @@ def test_fullsize_cliques_rmat21(gpm):
     gold = _golden().get("clique_rmat21", {})
     G = gpm.Graph.from_host(g)
     pats = [gpm.Pattern.clique(k) for k in (3, 4, 5)]
-    for lo, hi in _sample_ranges(g.n, 2):
+    for lo, hi in _sample_ranges(g.n, 2, count=3, width=600):
         assert gpm.count_roots(G, pats, lo, hi) == [O.cliques(g, k, lo, hi) for k in (3, 4, 5)], (lo, hi)
-    # the heaviest roots (largest out-degree) are checked one by one
+    # the heaviest roots (largest out-degree, CTA class) are checked one by one
     od = O.out_degrees(g)
     for v in np.argsort(od)[-3:].tolist():
-        assert gpm.count_roots(G, pats, v, v + 1) == [O.cliques(g, k, v, v + 1) for k in (3, 4, 5)], v
+        assert gpm.count_roots(G, pats[:2], v, v + 1) == [O.cliques(g, k, v, v + 1) for k in (3, 4)], v
+    v = int(np.argmax(od))
+    assert gpm.count_roots(G, pats[2:], v, v + 1) == [O.cliques(g, 5, v, v + 1)], v
     got = gpm.count(G, pats)
     if gold:
         assert gold["digest"] == g.digest()
