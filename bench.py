@@ -151,6 +151,165 @@ def cpu_baseline(g, seconds_target=15.0):
                       f"4-CL + 5-CL single-threaded, {dt:.1f} s, counts {c4} + {c5}"}
 
 
+BATCH_WORKLOAD = ("batched 3-/4-motif counting: 512 queries, each on its own seeded graph, Erdos-Renyi (mean degree "
+                  "8-64) or R-MAT (edge factor 4-32), 1K-1M vertices log-uniform")
+
+
+def run_batched(args, graphs=None):
+    """Batched form vs the plain one-query-per-call path on the same resident graphs (same GPU)."""
+    import torch
+    from paper_2011_03135_b300 import gpm
+    from paper_2011_03135_b300 import graphgen as gg
+    specs = gg.batch_query_specs(args.batch_queries)
+    if graphs is None:
+        graphs = gg.generate_many(specs)
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    Gs = [gpm.Graph.from_host(g, validate=False) for g in graphs]
+    for G in Gs:
+        G.prepare()
+    setup_s = time.perf_counter() - t0
+    kinds = [gpm.QUERY_MOTIF3 if s["k"] == 3 else gpm.QUERY_MOTIF4 for s in specs]
+    pats = {k: gpm.plain_patterns(k) for k in set(kinds)}
+
+    def plain():
+        return [gpm.count(G, pats[k]) for G, k in zip(Gs, kinds)]
+
+    want = plain()  # warm-up; also builds the lazily created task lists
+    torch.cuda.synchronize()
+    plain_t = []
+    for _ in range(max(1, args.batch_steps)):
+        t0 = time.perf_counter()
+        got = plain()
+        plain_t.append(time.perf_counter() - t0)
+        assert got == want
+    B = gpm.Batch(list(zip(Gs, kinds)))
+    t0 = time.perf_counter()
+    first = B.run()  # autotunes the item schedule
+    tune_s = time.perf_counter() - t0
+    assert first == want, "batched counts differ from the plain path"
+    batch_t = []
+    for _ in range(max(1, args.batch_steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        got = B.run()
+        batch_t.append(time.perf_counter() - t0)
+        assert got == want
+    info = B.info()
+    B.close()
+    nq = len(specs)
+    pq = nq / (sum(plain_t) / len(plain_t))
+    bq = nq / (sum(batch_t) / len(batch_t))
+    for G in Gs:
+        G.close()
+    return {"workload": BATCH_WORKLOAD, "queries": nq, "edges_total": int(sum(g.m for g in graphs)),
+            "plain_queries_per_s": pq, "batched_queries_per_s": bq, "speedup": bq / pq,
+            "plain_s": plain_t, "batched_s": batch_t, "autotune_s": tune_s, "setup_s": setup_s,
+            "schedule": info, "equal_counts": True}
+
+
+SERVED_WORKLOAD = ("served: 64 resident R-MAT graphs (scale 12+(i mod 11), edge factor 8/16/32 by seeded draw, "
+                   "seed 100+i), Poisson arrivals at 2000 queries/s (seed 5), query kind uniform over "
+                   "{triangles, 4-cliques, 5-cliques, 4-motifs}, graph uniform over the 64")
+
+
+def served_specs():
+    specs = []
+    for i in range(64):
+        r = np.random.default_rng(100 + i)
+        scale = 12 + (i % 11)
+        specs.append(dict(kind="rmat", k=4, scale=scale, n=1 << scale, edge_factor=float([8, 16, 32][r.integers(3)]),
+                          seed=100 + i))
+    return specs
+
+
+def served_trace(rate, seconds, ngraphs, seed=5):
+    r = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += r.exponential(1.0 / rate)
+        if t > seconds:
+            return out
+        out.append((t, int(r.integers(ngraphs)), int(r.integers(4))))
+
+
+def _pct(xs, q):
+    return float(np.percentile(np.array(xs), q)) if xs else None
+
+
+def run_served(args):
+    """Continuous-batching server vs plain serial serving of the same arrival trace (same GPU)."""
+    import torch
+    from paper_2011_03135_b300 import gpm
+    from paper_2011_03135_b300 import graphgen as gg
+    specs = served_specs()
+    graphs = gg.generate_many(specs)
+    torch.cuda.set_device(0)
+    Gs = [gpm.Graph.from_host(g, validate=False) for g in graphs]
+    kinds = [gpm.QUERY_TC, gpm.QUERY_CLIQUE4, gpm.QUERY_CLIQUE5, gpm.QUERY_MOTIF4]
+    trace = served_trace(args.serve_rate, args.serve_seconds, len(Gs))
+    horizon = args.serve_seconds + args.serve_grace
+    t0 = time.perf_counter()
+    S = gpm.Server(Gs, max_inflight=512)
+    start_s = time.perf_counter() - t0
+    # served
+    done, lat = {}, []
+    i = 0
+    t0 = time.perf_counter()
+    while True:
+        now = time.perf_counter() - t0
+        while i < len(trace) and trace[i][0] <= now:
+            _, gi, ki = trace[i]
+            S.submit(gi, kinds[ki], i)
+            i += 1
+        for tag, gi, kind, status, counts in S.poll():
+            assert status == 0
+            done[tag] = counts
+            lat.append(time.perf_counter() - t0 - trace[tag][0])
+        if (i == len(trace) and len(done) == len(trace)) or now > horizon:
+            break
+        time.sleep(0.0002)
+    served_elapsed = min(time.perf_counter() - t0, horizon)
+    S.stop()
+    # plain serial serving of the same trace: one query at a time, each after its arrival
+    pats = {k: gpm.plain_patterns(k) for k in kinds}
+    plain_done, plain_lat = {}, []
+    t0 = time.perf_counter()
+    for tag, (ta, gi, ki) in enumerate(trace):
+        now = time.perf_counter() - t0
+        if now > horizon:
+            break
+        if ta > now:
+            time.sleep(ta - now)
+        c = gpm.count(Gs[gi], pats[kinds[ki]])
+        plain_done[tag] = c
+        plain_lat.append(time.perf_counter() - t0 - ta)
+    plain_elapsed = min(time.perf_counter() - t0, horizon)
+    mismatches = sum(1 for t, c in done.items() if t in plain_done and plain_done[t] != c)
+    # sampled oracle check on the smallest graphs
+    import oracle as O
+    checked = 0
+    for tag, counts in sorted(done.items())[:2000]:
+        _, gi, ki = trace[tag]
+        if graphs[gi].n > (1 << 12) or checked >= 8:
+            continue
+        g = graphs[gi]
+        want = ([O.triangles(g)] if ki == 0 else [O.cliques(g, 4)] if ki == 1 else [O.cliques(g, 5)] if ki == 2
+                else O.motifs(g, 4))
+        assert counts == want, (tag, gi, ki)
+        checked += 1
+    for G in Gs:
+        G.close()
+    return {"workload": SERVED_WORKLOAD, "offered_per_s": args.serve_rate, "window_s": args.serve_seconds,
+            "horizon_s": horizon, "offered": len(trace), "server_start_s": start_s,
+            "served": {"completed": len(done), "queries_per_s": len(done) / served_elapsed,
+                       "p50_s": _pct(lat, 50), "p99_s": _pct(lat, 99), "backlog": len(trace) - len(done)},
+            "plain": {"completed": len(plain_done), "queries_per_s": len(plain_done) / plain_elapsed,
+                      "p50_s": _pct(plain_lat, 50), "p99_s": _pct(plain_lat, 99),
+                      "backlog": len(trace) - len(plain_done)},
+            "mismatches_vs_plain": mismatches, "oracle_checked": checked}
+
+
 def run_reference(args):
     rank, world, _ = _dist()
     if rank != 0:
@@ -301,9 +460,21 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["cliques", "batched", "served"], default="cliques")
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-grace", type=float, default=10.0)
+    ap.add_argument("--batch-queries", type=int, default=512)
+    ap.add_argument("--batch-steps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        print(json.dumps(run_batched(args)), flush=True)
+        return 0
+    if args.workload == "served":
+        print(json.dumps(run_served(args)), flush=True)
+        return 0
     return run_ours(args)
 
 

@@ -257,6 +257,57 @@ int gpm_batch_destroy(gpm_batch_t b);
 /* create + run + destroy. */
 int gpm_count_batch(const gpm_query_t *queries, uint32_t nq, uint64_t *counts, void *stream);
 
+/* ---------------- served form ---------------- */
+
+typedef struct gpm_server *gpm_server_t;
+
+typedef struct {
+  uint32_t max_inflight;  /* request slots running at once (default 256) */
+  uint32_t reserved0;
+  uint64_t arena_bytes;   /* device arena for per-request buffers (default 4 GiB) */
+  uint64_t ring_items;    /* capacity of the device work-item ring (default 8 Mi items) */
+  uint64_t reserved[4];
+} gpm_server_opts_t;
+
+typedef struct {
+  uint64_t tag;        /* the tag given to gpm_server_submit */
+  uint32_t graph;      /* index into the server's graph list */
+  uint32_t kind;       /* GPM_QUERY_* */
+  int32_t status;      /* GPM_OK, GPM_E_TIMEOUT or GPM_E_OVERFLOW */
+  uint32_t ncounts;    /* 1, 2 or 6 */
+  uint64_t counts[6];  /* as gpm_count_batch */
+} gpm_completion_t;
+
+/*
+ * Start a request loop over resident graphs (the GPM problems of Section 2
+ * served continuously). A persistent kernel pulls per-root work items of all
+ * admitted requests from a device ring that the host appends to while it
+ * runs, so requests that arrive while others are on the GPU overlap with
+ * them (continuous batching). A request is admitted when a request slot, room
+ * in the item ring and, for 4-motif queries, 4 bytes per edge of the device
+ * arena are free; otherwise it waits in a host FIFO. Every device-side wait is
+ * bounded; the kernel exits after ~20 ms without work and is relaunched by
+ * the next submit or poll. The graphs must outlive the server and must not be
+ * used by other calls while it runs. Synchronises the device.
+ */
+int gpm_server_start(const gpm_graph_t *graphs, uint32_t ngraphs, const gpm_server_opts_t *opts,
+                     gpm_server_t *out);
+
+/* Queue a count request (kind GPM_QUERY_*) on graph index `graph`; it is
+ * admitted at once when resources allow. GPM_E_BUSY: the host FIFO is full. */
+int gpm_server_submit(gpm_server_t s, uint32_t graph, uint32_t kind, uint64_t tag);
+
+/* Collect up to max finished requests (non-blocking), admit waiting requests
+ * whose resources have been freed, and keep the serving kernel running while
+ * work is outstanding. *n = number written to out. */
+int gpm_server_poll(gpm_server_t s, gpm_completion_t *out, uint32_t max, uint32_t *n);
+
+/* Requests in flight on the device and waiting in the host FIFO. */
+int gpm_server_stats(gpm_server_t s, uint32_t *inflight, uint32_t *pending);
+
+/* Stop the serving kernel (bounded) and release the server. */
+int gpm_server_stop(gpm_server_t s);
+
 /* ---------------- diagnostics ---------------- */
 
 /* Message for the last error on the calling host thread ("" if none). */

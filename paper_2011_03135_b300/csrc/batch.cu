@@ -27,89 +27,19 @@
 #include <cstring>
 #include <vector>
 
-#include "gpm_internal.h"
-#include "lg_device.cuh"
-#include "motif_device.cuh"
+#include "batch_device.cuh"
+
+using namespace gpm_item;
 
 namespace {
-
-enum ItemType : uint32_t { IT_LG_WARP = 0, IT_LG_CTA = 1, IT_C4_SMALL = 2, IT_C4_BIG = 3, IT_EDGE = 4 };
-
-struct Item {
-  uint32_t type, q, lo, hi;
-};
-
-struct QDesc {
-  const uint64_t *rowptr;
-  const uint32_t *col;
-  const uint32_t *deg;
-  const uint64_t *drow;
-  const uint32_t *dcol;
-  uint32_t *t_edge;
-  const uint32_t *tasks;     // LG root tasks of the graph (class order)
-  const uint32_t *c4_tasks;  // 4-cycle roots
-  unsigned long long *acc;   // ACC_WORDS accumulators
-  unsigned long long *out;   // 6 results
-  unsigned int *left;        // [0] scatter items left, [1] items left
-  uint32_t n, kind;
-  uint64_t m;
-  uint32_t nformula;
-  uint32_t formula[6];
-  uint32_t scatter_items, all_items;
-};
-
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-constexpr uint32_t kWarpMaxD = 128;
-constexpr uint64_t kWaitLimit = 1ull << 26;
 
 struct BatchArgs {
   const QDesc *qs;
   const Item *items;
   uint32_t nitems;
   unsigned int *head;
-  uint32_t *tally_pool;
-  uint64_t tally_slot_words;
-  unsigned int *status;
-  uint32_t cta_maxd, cta_W;
+  ItemEnv env;
 };
-
-// shared memory carve-up: the union of the item types' needs
-__host__ __device__ constexpr size_t warp_region_words() { return gpm_dev::warp_words(kWarpMaxD, true); }
-
-template <int KMAX, bool SCATTER>
-__device__ void lg_warp_item(const QDesc &q, const Item &it, uint32_t *smem, unsigned long long &a3,
-                             unsigned long long &a4, unsigned long long &a5) {
-  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t *base = smem + (size_t)wid * warp_region_words();
-  for (uint32_t t = it.lo + wid; t < it.hi; t += kWarps) {
-    const uint32_t u = q.tasks[t];
-    const uint32_t d = (uint32_t)(q.drow[u + 1] - q.drow[u]);
-    if (d < 2) continue;
-    if (d <= 32)
-      gpm_dev::lg_root_warp<32, 1, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, base, a3, a4, a5);
-    else
-      gpm_dev::lg_root_warp<kWarpMaxD, 4, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, base, a3, a4, a5);
-  }
-  (void)lane;
-}
-
-template <int KMAX, bool SCATTER>
-__device__ void lg_cta_item(const BatchArgs &a, const QDesc &q, const Item &it, uint32_t *smem,
-                            unsigned long long &a3, unsigned long long &a4, unsigned long long &a5) {
-  const uint32_t u = q.tasks[it.lo];
-  if (a.cta_W <= 8)
-    gpm_dev::lg_root_cta<8, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.cta_maxd, a.cta_W, smem, a3, a4, a5);
-  else if (a.cta_W <= 16)
-    gpm_dev::lg_root_cta<16, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.cta_maxd, a.cta_W, smem, a3, a4, a5);
-  else
-    gpm_dev::lg_root_cta<32, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.cta_maxd, a.cta_W, smem, a3, a4, a5);
-}
-
-__device__ __forceinline__ void block_add(unsigned long long *dst, unsigned long long v) {
-  v = gpm_dev::warp_sum(v);
-  if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
-}
 
 __global__ void __launch_bounds__(kThreads) batch_kernel(BatchArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -127,95 +57,15 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(BatchArgs a) {
     const Item it = s_item;
     __syncthreads();
     const QDesc &q = a.qs[it.q];
-    unsigned long long a3 = 0, a4 = 0, a5 = 0, c4 = 0;
-    gpm_dev::EdgeTerms et;
-    bool overflow = false;
-    const uint32_t kind = q.kind;
-    switch (it.type) {
-      case IT_LG_WARP:
-        if (kind == GPM_QUERY_MOTIF4) lg_warp_item<4, true>(q, it, smem, a3, a4, a5);
-        else if (kind == GPM_QUERY_CLIQUE5) lg_warp_item<5, false>(q, it, smem, a3, a4, a5);
-        else if (kind == GPM_QUERY_CLIQUE4) lg_warp_item<4, false>(q, it, smem, a3, a4, a5);
-        else lg_warp_item<3, false>(q, it, smem, a3, a4, a5);
-        break;
-      case IT_LG_CTA:
-        if (kind == GPM_QUERY_MOTIF4) lg_cta_item<4, true>(a, q, it, smem, a3, a4, a5);
-        else if (kind == GPM_QUERY_CLIQUE5) lg_cta_item<5, false>(a, q, it, smem, a3, a4, a5);
-        else if (kind == GPM_QUERY_CLIQUE4) lg_cta_item<4, false>(a, q, it, smem, a3, a4, a5);
-        else lg_cta_item<3, false>(a, q, it, smem, a3, a4, a5);
-        break;
-      case IT_C4_SMALL: {
-        const uint32_t wid = tid >> 5;
-        uint32_t *keys = smem + (size_t)wid * 2 * gpm_dev::kC4HashSlots;
-        uint32_t *cnt = keys + gpm_dev::kC4HashSlots;
-        for (uint32_t t = it.lo + wid; t < it.hi; t += kWarps)
-          c4 += gpm_dev::c4_root_warp(q.rowptr, q.col, q.deg, q.c4_tasks[t], keys, cnt, overflow);
-        break;
-      }
-      case IT_C4_BIG: {
-        uint32_t *tally = a.tally_pool + (size_t)blockIdx.x * a.tally_slot_words;
-        c4 += gpm_dev::c4_root_cta(q.rowptr, q.col, q.deg, q.c4_tasks[it.lo], tally, tally + q.n, s_x, &s_cnt,
-                                   &s_nt);
-        break;
-      }
-      case IT_EDGE: {
-        if (kind == GPM_QUERY_MOTIF4) {
-          // wait until every triangle-scatter item of this query has finished
-          if (tid == 0) {
-            uint64_t it_wait = 0;
-            while (*(volatile unsigned int *)&q.left[0] != 0u) {
-              __nanosleep(200);
-              if (++it_wait > kWaitLimit) {
-                atomicOr(a.status, ST_TIMEOUT);
-                break;
-              }
-            }
-            __threadfence();
-          }
-          __syncthreads();
-          const uint32_t lane = tid & 31, wid = tid >> 5;
-          for (uint64_t u = it.lo + wid; u < it.hi; u += kWarps)
-            gpm_dev::edge_terms_vertex<true, true>(q.drow, q.dcol, q.deg, q.t_edge, u, true, et);
-          (void)lane;
-        } else {
-          const uint32_t wid = tid >> 5;
-          for (uint64_t u = it.lo + wid; u < it.hi; u += kWarps)
-            gpm_dev::edge_terms_vertex<false, false>(q.drow, q.dcol, q.deg, nullptr, u, true, et);
-        }
-        break;
-      }
-      default: break;
-    }
-    // fold this item's partial sums into the query's accumulators
-    block_add(&q.acc[ACC_T], a3);
-    block_add(&q.acc[ACC_K4], a4);
-    block_add(&q.acc[ACC_K5], a5);
-    block_add(&q.acc[ACC_C4], c4);
-    block_add(&q.acc[ACC_D], et.D);
-    block_add(&q.acc[ACC_P], et.P);
-    block_add(&q.acc[ACC_S], et.S);
-    block_add(&q.acc[ACC_W], et.W);
-    block_add(&q.acc[ACC_TT2], et.TT);
-    block_add(&q.acc[ACC_T3], et.T3);
-    if (__syncthreads_or(overflow) && tid == 0) atomicOr(a.status, ST_CAPACITY);
-    if (tid == 0) {
+    run_item(a.env, q, it, smem, s_x, &s_cnt, &s_nt);
+    if (tid == 0 && item_done(q, it)) {
+      // last item of this query: its counts, then re-arm it for the next replay
+      const unsigned int bad = finalize_query(q, q.out);
+      if (bad) atomicOr(a.env.status, bad);
+      for (int i = 0; i < ACC_WORDS; ++i) q.acc[i] = 0ull;
+      q.left[0] = q.scatter_items;
       __threadfence();
-      if (kind == GPM_QUERY_MOTIF4 && (it.type == IT_LG_WARP || it.type == IT_LG_CTA)) atomicSub(&q.left[0], 1u);
-      const unsigned int before = atomicSub(&q.left[1], 1u);
-      if (before == 1u) {
-        // last item of this query: its counts, then re-arm it for the next replay
-        __threadfence();
-        unsigned long long acc[ACC_WORDS];
-        for (int i = 0; i < ACC_WORDS; ++i) acc[i] = atomicAdd(&q.acc[i], 0ull);
-        bool bad = false;
-        for (uint32_t i = 0; i < 6; ++i)
-          q.out[i] = (i < q.nformula) ? gpm_dev::finalize_formula(q.formula[i], acc, q.n, q.m, bad) : 0ull;
-        if (bad) atomicOr(a.status, ST_CAPACITY);
-        for (int i = 0; i < ACC_WORDS; ++i) q.acc[i] = 0ull;
-        q.left[0] = q.scatter_items;
-        __threadfence();
-        q.left[1] = q.all_items;
-      }
+      q.left[1] = q.all_items;
     }
     __syncthreads();
   }
@@ -254,20 +104,6 @@ struct gpm_batch {
 
 namespace {
 
-int formulas_for(uint32_t kind, uint32_t *f, uint32_t *nf) {
-  switch (kind) {
-    case GPM_QUERY_MOTIF3: f[0] = F_WEDGE_I; f[1] = F_TRI; *nf = 2; return GPM_OK;
-    case GPM_QUERY_MOTIF4:
-      f[0] = F_STAR_I; f[1] = F_PATH_I; f[2] = F_TT_I; f[3] = F_C4_I; f[4] = F_D_I; f[5] = F_K4_I;
-      *nf = 6;
-      return GPM_OK;
-    case GPM_QUERY_TC: f[0] = F_TRI; *nf = 1; return GPM_OK;
-    case GPM_QUERY_CLIQUE4: f[0] = F_K4; *nf = 1; return GPM_OK;
-    case GPM_QUERY_CLIQUE5: f[0] = F_K5; *nf = 1; return GPM_OK;
-    default: return gpm_fail(GPM_E_INVALID_ARG, "unknown query kind " + std::to_string(kind));
-  }
-}
-
 void free_batch(gpm_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
@@ -286,39 +122,9 @@ void make_items(gpm_batch *b, std::vector<Item> &items) {
   std::vector<Item> heavy, light, edge;
   const uint32_t nq = (uint32_t)b->queries.size();
   for (uint32_t qi = 0; qi < nq; ++qi) {
-    gpm_graph *g = b->queries[qi].graph;
     QDesc &q = b->qs[qi];
-    uint32_t scatter = 0, all = 0;
-    const uint32_t warp_end = g->cls_begin[CLS_WARP + 1];
-    for (uint32_t t = 0; t < warp_end; t += b->roots_per_item) {
-      light.push_back({IT_LG_WARP, qi, t, std::min(warp_end, t + b->roots_per_item)});
-      ++all;
-      ++scatter;
-    }
-    for (uint32_t t = g->cls_begin[CLS_CTA]; t < g->cls_begin[CLS_CTA + 1]; ++t) {
-      heavy.push_back({IT_LG_CTA, qi, t, t + 1});
-      ++all;
-      ++scatter;
-    }
-    if (q.kind == GPM_QUERY_MOTIF4) {
-      for (uint32_t t = g->c4_begin[0]; t < g->c4_begin[1]; t += b->roots_per_item) {
-        light.push_back({IT_C4_SMALL, qi, t, std::min(g->c4_begin[1], t + b->roots_per_item)});
-        ++all;
-      }
-      for (uint32_t t = g->c4_begin[1]; t < g->c4_begin[2]; ++t) {
-        heavy.push_back({IT_C4_BIG, qi, t, t + 1});
-        ++all;
-      }
-    }
-    if (q.kind == GPM_QUERY_MOTIF3 || q.kind == GPM_QUERY_MOTIF4) {
-      for (uint32_t v = 0; v < g->n; v += b->verts_per_item) {
-        edge.push_back({IT_EDGE, qi, v, std::min(g->n, v + b->verts_per_item)});
-        ++all;
-      }
-    }
-    if (q.kind != GPM_QUERY_MOTIF4) scatter = 0;
-    q.scatter_items = scatter;
-    q.all_items = all;
+    append_query_items(b->queries[qi].graph, q.kind, qi, b->roots_per_item, b->verts_per_item, heavy, light, edge,
+                       &q.scatter_items, &q.all_items);
   }
   items.insert(items.end(), heavy.begin(), heavy.end());
   items.insert(items.end(), light.begin(), light.end());
@@ -364,11 +170,11 @@ int capture(gpm_batch *b) {
   a.items = b->d_items;
   a.nitems = b->nitems;
   a.head = b->d_head;
-  a.status = b->d_head + 1;
-  a.tally_pool = b->tally_pool;
-  a.tally_slot_words = b->tally_slot_words;
-  a.cta_maxd = b->cta_maxd;
-  a.cta_W = b->cta_W;
+  a.env.status = b->d_head + 1;
+  a.env.tally_pool = b->tally_pool;
+  a.env.tally_slot_words = b->tally_slot_words;
+  a.env.cta_maxd = b->cta_maxd;
+  a.env.cta_W = b->cta_W;
   const uint32_t nq = (uint32_t)b->queries.size();
   GPM_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
   cudaMemsetAsync(b->d_head, 0, sizeof(unsigned int), b->stream);
@@ -465,20 +271,8 @@ int gpm_batch_create(const gpm_query_t *queries, uint32_t nq, gpm_batch_t *out) 
     gpm_graph *g = queries[i].graph;
     if (!g) return fail(gpm_fail(GPM_E_INVALID_ARG, "null graph in batch"));
     std::lock_guard<std::mutex> lk(g->mu);
-    int rc = gpm_prepare_graph(g, b->stream);
+    int rc = prepare_for_items(g, queries[i].kind == GPM_QUERY_MOTIF4, b->stream);
     if (rc) return fail(rc);
-    const gpm_tuning &t = gpm_tune();
-    if (g->cls_maxdeg[CLS_WARP] > kWarpMaxD || t.warp_max_degree > kWarpMaxD) {
-      // rebuild this graph's classes with the batch's warp bound
-      const uint32_t old_w = t.warp_max_degree;
-      gpm_tune().warp_max_degree = std::min<uint32_t>(old_w, kWarpMaxD);
-      g->tune_warp_max = 0;
-      rc = gpm_ensure_classes(g, b->stream);
-      gpm_tune().warp_max_degree = old_w;
-      if (rc) return fail(rc);
-    }
-    if (g->cls_begin[CLS_XL + 1] > g->cls_begin[CLS_XL])
-      return fail(gpm_fail(GPM_E_UNSUPPORTED, "batched form supports root out-degrees up to 1024"));
     QDesc &q = b->qs[i];
     std::memset(&q, 0, sizeof(q));
     q.kind = queries[i].kind;
@@ -491,21 +285,6 @@ int gpm_batch_create(const gpm_query_t *queries, uint32_t nq, gpm_batch_t *out) 
       }
       if (cudaMemsetAsync(g->t_edge, 0, sizeof(uint32_t) * std::max<uint64_t>(g->m, 1), b->stream) != cudaSuccess)
         return fail(gpm_fail(GPM_E_DEVICE, "t_edge reset failed"));
-      // 4-cycle task lists: one synchronous count builds them on first use
-      if (!g->c4_ready) {
-        gpm_pattern p{};
-        p.k = 4;
-        p.induced = 0;
-        uint8_t c4[16] = {0, 0, 1, 1, 0, 0, 1, 1, 1, 1, 0, 0, 1, 1, 0, 0};
-        std::memcpy(p.adj, c4, 16);
-        rc = gpm_plan_pattern(&p);
-        if (rc) return fail(rc);
-        unsigned long long *acc = reinterpret_cast<unsigned long long *>(g->work + WK_ACC);
-        if (cudaMemsetAsync(acc, 0, ACC_WORDS * 8, b->stream) != cudaSuccess)
-          return fail(gpm_fail(GPM_E_DEVICE, "acc reset failed"));
-        rc = gpm_launch_cycles4(g, 0, g->n, acc, b->stream);
-        if (rc) return fail(rc);
-      }
       need_c4 = true;
     }
     q.rowptr = g->rowptr;

@@ -1,0 +1,269 @@
+// Work items of the batched and served forms: per-root tasks of many
+// queries over many graphs, processed by one CTA each in a persistent kernel.
+// See batch.cu for the method.
+#pragma once
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "gpm_internal.h"
+#include "lg_device.cuh"
+#include "motif_device.cuh"
+
+namespace gpm_item {
+
+enum ItemType : uint32_t { IT_LG_WARP = 0, IT_LG_CTA = 1, IT_C4_SMALL = 2, IT_C4_BIG = 3, IT_EDGE = 4 };
+
+struct Item {
+  uint32_t type, q, lo, hi;
+};
+
+struct QDesc {
+  uint64_t tag;              // caller's request tag (served form)
+  const uint64_t *rowptr;
+  const uint32_t *col;
+  const uint32_t *deg;
+  const uint64_t *drow;
+  const uint32_t *dcol;
+  uint32_t *t_edge;
+  const uint32_t *tasks;     // LG root tasks of the graph (class order)
+  const uint32_t *c4_tasks;  // 4-cycle roots
+  unsigned long long *acc;   // ACC_WORDS accumulators
+  unsigned long long *out;   // 6 results
+  unsigned int *left;        // [0] scatter items left, [1] items left
+  uint32_t n, kind;
+  uint64_t m;
+  uint32_t nformula;
+  uint32_t formula[6];
+  uint32_t scatter_items, all_items;
+};
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr uint32_t kWarpMaxD = 128;
+constexpr uint64_t kWaitLimit = 1ull << 26;
+
+struct ItemEnv {
+  uint32_t *tally_pool;
+  uint64_t tally_slot_words;
+  unsigned int *status;
+  uint32_t cta_maxd, cta_W;
+};
+
+// shared memory carve-up: the union of the item types' needs
+__host__ __device__ constexpr size_t warp_region_words() { return gpm_dev::warp_words(kWarpMaxD, true); }
+
+template <int KMAX, bool SCATTER>
+__device__ void lg_warp_item(const QDesc &q, const Item &it, uint32_t *smem, unsigned long long &a3,
+                             unsigned long long &a4, unsigned long long &a5) {
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t *base = smem + (size_t)wid * warp_region_words();
+  for (uint32_t t = it.lo + wid; t < it.hi; t += kWarps) {
+    const uint32_t u = q.tasks[t];
+    const uint32_t d = (uint32_t)(q.drow[u + 1] - q.drow[u]);
+    if (d < 2) continue;
+    if (d <= 32)
+      gpm_dev::lg_root_warp<32, 1, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, base, a3, a4, a5);
+    else
+      gpm_dev::lg_root_warp<kWarpMaxD, 4, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, base, a3, a4, a5);
+  }
+  (void)lane;
+}
+
+template <int KMAX, bool SCATTER>
+__device__ void lg_cta_item(const ItemEnv &a, const QDesc &q, const Item &it, uint32_t *smem,
+                            unsigned long long &a3, unsigned long long &a4, unsigned long long &a5) {
+  const uint32_t u = q.tasks[it.lo];
+  if (a.cta_W <= 8)
+    gpm_dev::lg_root_cta<8, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.cta_maxd, a.cta_W, smem, a3, a4, a5);
+  else if (a.cta_W <= 16)
+    gpm_dev::lg_root_cta<16, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.cta_maxd, a.cta_W, smem, a3, a4, a5);
+  else
+    gpm_dev::lg_root_cta<32, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.cta_maxd, a.cta_W, smem, a3, a4, a5);
+}
+
+__device__ __forceinline__ void block_add(unsigned long long *dst, unsigned long long v) {
+  v = gpm_dev::warp_sum(v);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+}
+
+
+// Process one item with the whole CTA and fold its partial sums into the
+// query's accumulators. q must be readable by every thread (shared memory).
+__device__ __forceinline__ void run_item(const ItemEnv &a, const QDesc &q, const Item &it, uint32_t *smem,
+                                         uint32_t *s_x, uint32_t *s_cnt, uint32_t *s_nt) {
+  const uint32_t tid = threadIdx.x;
+  unsigned long long a3 = 0, a4 = 0, a5 = 0, c4 = 0;
+  gpm_dev::EdgeTerms et;
+  bool overflow = false;
+  const uint32_t kind = q.kind;
+  switch (it.type) {
+    case IT_LG_WARP:
+      if (kind == GPM_QUERY_MOTIF4) lg_warp_item<4, true>(q, it, smem, a3, a4, a5);
+      else if (kind == GPM_QUERY_CLIQUE5) lg_warp_item<5, false>(q, it, smem, a3, a4, a5);
+      else if (kind == GPM_QUERY_CLIQUE4) lg_warp_item<4, false>(q, it, smem, a3, a4, a5);
+      else lg_warp_item<3, false>(q, it, smem, a3, a4, a5);
+      break;
+    case IT_LG_CTA:
+      if (kind == GPM_QUERY_MOTIF4) lg_cta_item<4, true>(a, q, it, smem, a3, a4, a5);
+      else if (kind == GPM_QUERY_CLIQUE5) lg_cta_item<5, false>(a, q, it, smem, a3, a4, a5);
+      else if (kind == GPM_QUERY_CLIQUE4) lg_cta_item<4, false>(a, q, it, smem, a3, a4, a5);
+      else lg_cta_item<3, false>(a, q, it, smem, a3, a4, a5);
+      break;
+    case IT_C4_SMALL: {
+      const uint32_t wid = tid >> 5;
+      uint32_t *keys = smem + (size_t)wid * 2 * gpm_dev::kC4HashSlots;
+      uint32_t *cnt = keys + gpm_dev::kC4HashSlots;
+      for (uint32_t t = it.lo + wid; t < it.hi; t += kWarps)
+        c4 += gpm_dev::c4_root_warp(q.rowptr, q.col, q.deg, q.c4_tasks[t], keys, cnt, overflow);
+      break;
+    }
+    case IT_C4_BIG: {
+      uint32_t *tally = a.tally_pool + (size_t)blockIdx.x * a.tally_slot_words;
+      c4 += gpm_dev::c4_root_cta(q.rowptr, q.col, q.deg, q.c4_tasks[it.lo], tally, tally + q.n, s_x, s_cnt, s_nt);
+      break;
+    }
+    case IT_EDGE: {
+      const uint32_t wid = tid >> 5;
+      if (kind == GPM_QUERY_MOTIF4) {
+        // wait until every triangle-scatter item of this query has finished
+        if (tid == 0) {
+          uint64_t it_wait = 0;
+          while (*(volatile unsigned int *)&q.left[0] != 0u) {
+            __nanosleep(200);
+            if (++it_wait > kWaitLimit) {
+              atomicOr(a.status, ST_TIMEOUT);
+              break;
+            }
+          }
+          __threadfence();
+        }
+        __syncthreads();
+        for (uint64_t u = it.lo + wid; u < it.hi; u += kWarps)
+          gpm_dev::edge_terms_vertex<true, true>(q.drow, q.dcol, q.deg, q.t_edge, u, true, et);
+      } else {
+        for (uint64_t u = it.lo + wid; u < it.hi; u += kWarps)
+          gpm_dev::edge_terms_vertex<false, false>(q.drow, q.dcol, q.deg, nullptr, u, true, et);
+      }
+      break;
+    }
+    default: break;
+  }
+  block_add(&q.acc[ACC_T], a3);
+  block_add(&q.acc[ACC_K4], a4);
+  block_add(&q.acc[ACC_K5], a5);
+  block_add(&q.acc[ACC_C4], c4);
+  block_add(&q.acc[ACC_D], et.D);
+  block_add(&q.acc[ACC_P], et.P);
+  block_add(&q.acc[ACC_S], et.S);
+  block_add(&q.acc[ACC_W], et.W);
+  block_add(&q.acc[ACC_TT2], et.TT);
+  block_add(&q.acc[ACC_T3], et.T3);
+  // Every thread's atomics (partial sums, per-arc triangle counts) must be
+  // performed device-wide before thread 0 counts this item as done: another
+  // CTA may read them as soon as the counter drops.
+  __threadfence();
+  if (__syncthreads_or(overflow) && tid == 0) atomicOr(a.status, ST_CAPACITY);
+}
+
+// Called by thread 0 after run_item: counts the item as done; returns true
+// when it was the query's last item.
+__device__ __forceinline__ bool item_done(const QDesc &q, const Item &it) {
+  __threadfence();
+  if (q.kind == GPM_QUERY_MOTIF4 && (it.type == IT_LG_WARP || it.type == IT_LG_CTA)) atomicSub(&q.left[0], 1u);
+  const unsigned int before = atomicSub(&q.left[1], 1u);
+  if (before != 1u) return false;
+  __threadfence();
+  return true;
+}
+
+// The query's counts from its accumulators (thread 0, after its last item).
+__device__ __forceinline__ unsigned int finalize_query(const QDesc &q, unsigned long long *out6) {
+  unsigned long long acc[ACC_WORDS];
+  for (int i = 0; i < ACC_WORDS; ++i) acc[i] = atomicAdd(&q.acc[i], 0ull);
+  bool bad = false;
+  for (uint32_t i = 0; i < 6; ++i)
+    out6[i] = (i < q.nformula) ? gpm_dev::finalize_formula(q.formula[i], acc, q.n, q.m, bad) : 0ull;
+  return bad ? ST_CAPACITY : 0u;
+}
+
+// Host side: cut one query (graph g, kind) into items for query slot qi.
+// Heavy items (one CTA root each) go to `heavy`, ranges of warp roots to
+// `light`, vertex ranges of local-count terms to `edge`. Returns the number
+// of items and of triangle-scatter items through *all and *scatter.
+inline void append_query_items(const gpm_graph *g, uint32_t kind, uint32_t qi, uint32_t roots_per_item,
+                               uint32_t verts_per_item, std::vector<Item> &heavy, std::vector<Item> &light,
+                               std::vector<Item> &edge, uint32_t *scatter, uint32_t *all) {
+  uint32_t sc = 0, al = 0;
+  const uint32_t warp_end = g->cls_begin[CLS_WARP + 1];
+  for (uint32_t t = 0; t < warp_end; t += roots_per_item) {
+    light.push_back({IT_LG_WARP, qi, t, std::min(warp_end, t + roots_per_item)});
+    ++al;
+    ++sc;
+  }
+  for (uint32_t t = g->cls_begin[CLS_CTA]; t < g->cls_begin[CLS_CTA + 1]; ++t) {
+    heavy.push_back({IT_LG_CTA, qi, t, t + 1});
+    ++al;
+    ++sc;
+  }
+  if (kind == GPM_QUERY_MOTIF4) {
+    for (uint32_t t = g->c4_begin[0]; t < g->c4_begin[1]; t += roots_per_item) {
+      light.push_back({IT_C4_SMALL, qi, t, std::min(g->c4_begin[1], t + roots_per_item)});
+      ++al;
+    }
+    for (uint32_t t = g->c4_begin[1]; t < g->c4_begin[2]; ++t) {
+      heavy.push_back({IT_C4_BIG, qi, t, t + 1});
+      ++al;
+    }
+  }
+  if (kind == GPM_QUERY_MOTIF3 || kind == GPM_QUERY_MOTIF4) {
+    for (uint32_t v = 0; v < g->n; v += verts_per_item) {
+      edge.push_back({IT_EDGE, qi, v, std::min(g->n, v + verts_per_item)});
+      ++al;
+    }
+  }
+  *scatter = (kind == GPM_QUERY_MOTIF4) ? sc : 0u;
+  *all = al;
+}
+
+inline int formulas_for(uint32_t kind, uint32_t *f, uint32_t *nf) {
+  switch (kind) {
+    case GPM_QUERY_MOTIF3: f[0] = F_WEDGE_I; f[1] = F_TRI; *nf = 2; return GPM_OK;
+    case GPM_QUERY_MOTIF4:
+      f[0] = F_STAR_I; f[1] = F_PATH_I; f[2] = F_TT_I; f[3] = F_C4_I; f[4] = F_D_I; f[5] = F_K4_I;
+      *nf = 6;
+      return GPM_OK;
+    case GPM_QUERY_TC: f[0] = F_TRI; *nf = 1; return GPM_OK;
+    case GPM_QUERY_CLIQUE4: f[0] = F_K4; *nf = 1; return GPM_OK;
+    case GPM_QUERY_CLIQUE5: f[0] = F_K5; *nf = 1; return GPM_OK;
+    default: return gpm_fail(GPM_E_INVALID_ARG, "unknown query kind " + std::to_string(kind));
+  }
+}
+
+// Prepare a graph for item processing: orientation, root classes with the
+// item bound on warp roots, and (for 4-motif queries) the 4-cycle root lists.
+inline int prepare_for_items(gpm_graph *g, bool need_c4, cudaStream_t st) {
+  int rc = gpm_prepare_graph(g, st);
+  if (rc) return rc;
+  const gpm_tuning &t = gpm_tune();
+  if (g->cls_maxdeg[CLS_WARP] > kWarpMaxD || t.warp_max_degree > kWarpMaxD) {
+    const uint32_t old_w = t.warp_max_degree;
+    gpm_tune().warp_max_degree = std::min<uint32_t>(old_w, kWarpMaxD);
+    g->tune_warp_max = 0;
+    rc = gpm_ensure_classes(g, st);
+    gpm_tune().warp_max_degree = old_w;
+    if (rc) return rc;
+  }
+  if (g->cls_begin[CLS_XL + 1] > g->cls_begin[CLS_XL])
+    return gpm_fail(GPM_E_UNSUPPORTED, "batched and served forms support root out-degrees up to 1024");
+  if (need_c4 && !g->c4_ready) {
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(g->work + WK_ACC);
+    if (cudaMemsetAsync(acc, 0, ACC_WORDS * 8, st) != cudaSuccess) return gpm_fail(GPM_E_DEVICE, "acc reset");
+    rc = gpm_launch_cycles4(g, 0, g->n, acc, st);  // builds the 4-cycle root lists
+    if (rc) return rc;
+  }
+  return GPM_OK;
+}
+
+}  // namespace gpm_item

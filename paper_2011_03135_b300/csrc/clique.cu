@@ -95,10 +95,12 @@ __global__ void __launch_bounds__(256) lg_warp_kernel(LGArgs a) {
 // CTA's global-memory slot (GLOBAL = true)
 // ---------------------------------------------------------------------------
 template <int G, int KMAX, bool SCATTER, bool GLOBAL>
-__global__ void __launch_bounds__(512) lg_cta_kernel(LGArgs a, uint32_t maxd) {
+__global__ void __launch_bounds__(512) lg_cta_kernel(LGArgs a, uint32_t maxd, uint32_t big_cap) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint32_t s_task;
   uint32_t *base = GLOBAL ? a.pool + (size_t)blockIdx.x * a.slot_words : smem;
+  // nested local graphs for the 5-clique level live after the bitmap (shared memory only)
+  uint32_t *nest = (!GLOBAL && KMAX >= 5 && big_cap) ? smem + gpm_dev::cta_words(maxd, a.W) : nullptr;
   unsigned long long a3 = 0, a4 = 0, a5 = 0;
   for (;;) {
     if (threadIdx.x == 0) s_task = atomicAdd(a.queue, 1u);
@@ -110,7 +112,7 @@ __global__ void __launch_bounds__(512) lg_cta_kernel(LGArgs a, uint32_t maxd) {
     if (u < a.root_lo || u >= a.root_hi) continue;
     const uint32_t d = (uint32_t)(a.drow[u + 1] - a.drow[u]);
     if (d < 2 || d > maxd) continue;
-    gpm_dev::lg_root_cta<G, KMAX, SCATTER>(a.drow, a.dcol, a.t_edge, u, maxd, a.W, base, a3, a4, a5);
+    gpm_dev::lg_root_cta<G, KMAX, SCATTER>(a.drow, a.dcol, a.t_edge, u, maxd, a.W, base, a3, a4, a5, nest, big_cap);
   }
   flush_acc(a, a3, a4, a5, KMAX);
 }
@@ -136,10 +138,34 @@ int launch_warp(const LGArgs &a, int device, cudaStream_t st) {
   return GPM_OK;
 }
 
+int max_smem_optin(int device) {
+  static int cached[64] = {0};
+  if (device < 0 || device >= 64) return 227 * 1024;
+  if (!cached[device]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      v = 227 * 1024;
+    }
+    cached[device] = v;
+  }
+  return cached[device];
+}
+
 template <int G, int KMAX, bool SCATTER, bool GLOBAL>
 int launch_cta(const LGArgs &a, uint32_t maxd, int blocks_cap, int device, cudaStream_t st) {
   constexpr int kThreads = 512;
-  const size_t smem = GLOBAL ? 0 : (size_t)cta_words(maxd, a.W) * 4;
+  size_t smem = GLOBAL ? 0 : (size_t)cta_words(maxd, a.W) * 4;
+  uint32_t big_cap = 0;
+  if (!GLOBAL && KMAX >= 5) {
+    // room left after the bitmap and the per-warp nested buffers goes to the CTA-wide nested buffer
+    const size_t fixed = smem + (size_t)gpm_dev::nest_words(maxd, kThreads / 32, 0) * 4 + 2048;
+    const size_t limit = (size_t)max_smem_optin(device);
+    if (fixed + 4 * 1024 <= limit) {
+      big_cap = (uint32_t)std::min<size_t>((limit - fixed) / 4, 32768);
+      smem += (size_t)gpm_dev::nest_words(maxd, kThreads / 32, big_cap) * 4;
+    }
+  }
   auto kern = lg_cta_kernel<G, KMAX, SCATTER, GLOBAL>;
   if (!GLOBAL) GPM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
@@ -148,7 +174,7 @@ int launch_cta(const LGArgs &a, uint32_t maxd, int blocks_cap, int device, cudaS
   int blocks = gpm_num_sms(device) * per_sm;
   blocks = std::max(1, std::min<int>(blocks, (int)a.ntasks));
   if (blocks_cap > 0) blocks = std::min(blocks, blocks_cap);
-  GPM_LAUNCH(GLOBAL ? "lg_cta_global" : "lg_cta", st, kern<<<blocks, kThreads, smem, st>>>(a, maxd));
+  GPM_LAUNCH(GLOBAL ? "lg_cta_global" : "lg_cta", st, kern<<<blocks, kThreads, smem, st>>>(a, maxd, big_cap));
   GPM_CUDA(cudaGetLastError());
   return GPM_OK;
 }

@@ -93,7 +93,7 @@ __device__ __forceinline__ void enumerate_rows(const uint32_t *R, uint32_t d, ui
 
 // Same for W > 32 (global-memory class): lane gl holds words gl, gl+G, ...
 template <int KMAX>
-__device__ void enumerate_rows_wide(const uint32_t *R, uint32_t d, uint32_t W, uint32_t row0, uint32_t row_step,
+__device__ inline void enumerate_rows_wide(const uint32_t *R, uint32_t d, uint32_t W, uint32_t row0, uint32_t row_step,
                                     uint32_t gl, unsigned long long &a4, unsigned long long &a5) {
   constexpr uint32_t G = 32;
   for (uint32_t i = row0; i < d; i += row_step) {
@@ -121,6 +121,184 @@ __device__ void enumerate_rows_wide(const uint32_t *R, uint32_t d, uint32_t W, u
   }
 }
 
+
+
+// ---------------------------------------------------------------------------
+// Nested local graph for the 5-clique level (CTA roots).
+//
+// For row i of the root's local graph, the candidates of the next level are
+// S = R_i (c vertices). Compacting every row R_j, j in S, to the positions of
+// S (a bit-gather) gives the local graph of the next level, C (c rows of
+// W' = ceil(c/32) words), on which
+//   4-cliques through (u, L[i]) = sum_a |C_a|
+//   5-cliques through (u, L[i]) = sum_a sum_{b in C_a} |C_a & C_b|
+// -- the paper's shrinking local graph, one more level down. A row of width
+// W' is far narrower than W for most i, so the last level costs W' words per
+// visited 4-clique instead of W, and one thread walks one compacted row.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kNestWarpC = 128;  // rows with c <= this are nested by one warp
+constexpr uint32_t kNestWarpWp = 4;   // = kNestWarpC / 32
+constexpr uint32_t kNestWarpWords = kNestWarpC + 32 + kNestWarpC * kNestWarpWp;
+
+__host__ __device__ constexpr uint64_t nest_words(uint32_t maxd, uint32_t nwarps, uint32_t big_cap) {
+  // per warp: S[128] pref[32] C[128*4]; CTA: big-row list[maxd], S[maxd], pref[32], C[big_cap], 4 counters
+  return (uint64_t)nwarps * kNestWarpWords + 2ull * maxd + 32 + big_cap + 4;
+}
+
+// Number of set bits of row ri (W <= 32 words); when it is at most cap, their
+// positions go to S (ascending) and per-word prefix counts to pref. Called by
+// one whole warp.
+__device__ __forceinline__ uint32_t list_bits_warp(const uint32_t *ri, uint32_t W, uint32_t *S, uint32_t *pref,
+                                                   uint32_t cap) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t x = (lane < W) ? ri[lane] : 0u;
+  const uint32_t cnt = __popc(x);
+  uint32_t incl = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= (uint32_t)o) incl += y;
+  }
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  if (total > cap) return total;
+  uint32_t k = incl - cnt;
+  if (lane < W) pref[lane] = k;
+  while (x) {
+    const uint32_t p = __ffs(x) - 1;
+    x &= x - 1;
+    S[k++] = lane * 32 + p;
+  }
+  __syncwarp();
+  return total;
+}
+
+// compact row R_j (j = S[a]) onto the positions of ri into crow (Wp words, zeroed here)
+__device__ __forceinline__ uint32_t compact_row(const uint32_t *rj, const uint32_t *ri, const uint32_t *pref, uint32_t W,
+                                                uint32_t *crow, uint32_t Wp) {
+  for (uint32_t k = 0; k < Wp; ++k) crow[k] = 0u;
+  uint32_t bits = 0;
+  for (uint32_t w = 0; w < W; ++w) {
+    const uint32_t riw = ri[w];
+    uint32_t x = rj[w] & riw;
+    if (!x) continue;
+    const uint32_t base = pref[w];
+    bits += __popc(x);
+    while (x) {
+      const uint32_t p = __ffs(x) - 1;
+      x &= x - 1;
+      const uint32_t b = base + __popc(riw & ((1u << p) - 1u));
+      crow[b >> 5] |= 1u << (b & 31);
+    }
+  }
+  return bits;
+}
+
+// sum over set bits b of row a of |C_a & C_b| (rows of Wp words, stride Wp)
+__device__ __forceinline__ unsigned long long nested_pairs(const uint32_t *C, uint32_t a, uint32_t Wp) {
+  const uint32_t *ca = C + (size_t)a * Wp;
+  unsigned long long s = 0;
+  for (uint32_t k = 0; k < Wp; ++k) {
+    uint32_t bits = ca[k];
+    while (bits) {
+      const uint32_t b = k * 32 + __ffs(bits) - 1;
+      bits &= bits - 1;
+      const uint32_t *cb = C + (size_t)b * Wp;
+      for (uint32_t k2 = 0; k2 < Wp; ++k2) s += __popc(ca[k2] & cb[k2]);
+    }
+  }
+  return s;
+}
+
+// Row i by a group of lanes without nesting (fallback for rows too wide to
+// compact): the group takes every `ng`-th bit j of R_i.
+__device__ __forceinline__ void row_k45_groups(const uint32_t *R, uint32_t W, uint32_t i, uint32_t g, uint32_t ng,
+                                               uint32_t gl, uint32_t G, unsigned long long &a4,
+                                               unsigned long long &a5) {
+  const uint32_t *ri = R + (size_t)i * W;
+  uint32_t seen = 0;
+  for (uint32_t t = 0; t < W; ++t) {
+    uint32_t bits = ri[t];
+    while (bits) {
+      const uint32_t j = t * 32 + __ffs(bits) - 1;
+      bits &= bits - 1;
+      if ((seen++ % ng) != g) continue;
+      const uint32_t *rj = R + (size_t)j * W;
+      for (uint32_t w = gl; w < W; w += G) {
+        const uint32_t mw = ri[w] & rj[w];
+        a4 += __popc(mw);
+      }
+      for (uint32_t t2 = 0; t2 < W; ++t2) {
+        uint32_t b2 = ri[t2] & rj[t2];
+        while (b2) {
+          const uint32_t l = t2 * 32 + __ffs(b2) - 1;
+          b2 &= b2 - 1;
+          const uint32_t *rl = R + (size_t)l * W;
+          for (uint32_t w = gl; w < W; w += G) a5 += __popc(ri[w] & rj[w] & rl[w]);
+        }
+      }
+    }
+  }
+}
+
+// 4- and 5-cliques of one root's local graph R (d rows, W <= 32 words) by the
+// whole CTA with nesting. nest: nest_words(maxd, blockDim/32, big_cap) words.
+__device__ inline void enumerate_nested_cta(const uint32_t *R, uint32_t d, uint32_t W, uint32_t *nest, uint32_t maxd,
+                                     uint32_t big_cap, unsigned long long &a4, unsigned long long &a5) {
+  const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  uint32_t *wbuf = nest + (size_t)wid * kNestWarpWords;
+  uint32_t *S = wbuf, *pref = wbuf + kNestWarpC, *C = wbuf + kNestWarpC + 32;
+  uint32_t *big_list = nest + (size_t)nw * kNestWarpWords;
+  uint32_t *Sb = big_list + maxd, *prefb = Sb + maxd, *Cb = prefb + 32;
+  uint32_t *ctr = Cb + big_cap;  // [0] next row, [1] big rows, [2] c of the current big row
+  if (tid == 0) {
+    ctr[0] = 0;
+    ctr[1] = 0;
+  }
+  __syncthreads();
+  // rows with c <= kNestWarpC: one warp each, pulled dynamically
+  for (;;) {
+    uint32_t i = 0;
+    if (lane == 0) i = atomicAdd(&ctr[0], 1u);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (i >= d) break;
+    const uint32_t *ri = R + (size_t)i * W;
+    const uint32_t c = list_bits_warp(ri, W, S, pref, kNestWarpC);
+    if (c < 2) continue;
+    if (c > kNestWarpC) {
+      if (lane == 0) big_list[atomicAdd(&ctr[1], 1u)] = i;
+      continue;
+    }
+    const uint32_t Wp = (c + 31) / 32;
+    for (uint32_t a = lane; a < c; a += 32) {
+      const uint32_t bits = compact_row(R + (size_t)S[a] * W, ri, pref, W, C + (size_t)a * Wp, Wp);
+      a4 += bits;
+    }
+    __syncwarp();
+    for (uint32_t a = lane; a < c; a += 32) a5 += nested_pairs(C, a, Wp);
+    __syncwarp();
+  }
+  __syncthreads();
+  // rows with larger c: the whole CTA, one row at a time
+  const uint32_t nbig = ctr[1];
+  for (uint32_t r = 0; r < nbig; ++r) {
+    const uint32_t i = big_list[r];
+    const uint32_t *ri = R + (size_t)i * W;
+    if (wid == 0) {
+      const uint32_t c = list_bits_warp(ri, W, Sb, prefb, maxd);
+      if (lane == 0) ctr[2] = c;
+    }
+    __syncthreads();
+    const uint32_t c = ctr[2];
+    const uint32_t Wp = (c + 31) / 32;
+    if ((uint64_t)c * Wp <= big_cap) {
+      for (uint32_t a = tid; a < c; a += nt) a4 += compact_row(R + (size_t)Sb[a] * W, ri, prefb, W, Cb + (size_t)a * Wp, Wp);
+      __syncthreads();
+      for (uint32_t a = tid; a < c; a += nt) a5 += nested_pairs(Cb, a, Wp);
+    } else {
+      row_k45_groups(R, W, i, tid >> 5, nt >> 5, lane, 32, a4, a5);
+    }
+    __syncthreads();
+  }
+}
 
 // Words of shared memory one warp needs for a root of out-degree <= maxd:
 // xb[maxd] (uint64) | L[maxd] | pre[maxd+1] | R[maxd*W] | tc[maxd] (scatter)
@@ -187,7 +365,8 @@ __device__ __forceinline__ void lg_root_warp(const uint64_t *__restrict__ drow, 
 template <int G, int KMAX, bool SCATTER>
 __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, const uint32_t *__restrict__ dcol,
                                             uint32_t *t_edge, uint32_t u, uint32_t maxd, uint32_t W, uint32_t *base,
-                                            unsigned long long &a3, unsigned long long &a4, unsigned long long &a5) {
+                                            unsigned long long &a3, unsigned long long &a4, unsigned long long &a5,
+                                            uint32_t *nest = nullptr, uint32_t big_cap = 0) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
   uint64_t *xb = reinterpret_cast<uint64_t *>(base);
   uint32_t *L = base + 2 * (size_t)maxd;
@@ -228,7 +407,9 @@ __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, c
     for (uint32_t i = tid; i < d; i += nt)
       if (tc[i]) atomicAdd(&t_edge[ub + i], tc[i]);
   }
-  if (KMAX >= 4) {
+  if (KMAX >= 5 && nest != nullptr && w_used <= 32) {
+    enumerate_nested_cta(R, d, w_used, nest, maxd, big_cap, a4, a5);
+  } else if (KMAX >= 4) {
     if (w_used > 32)
       enumerate_rows_wide<KMAX>(R, d, w_used, tid / 32, nt / 32, lane, a4, a5);
     else

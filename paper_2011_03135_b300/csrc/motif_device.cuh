@@ -116,10 +116,10 @@ __device__ __forceinline__ unsigned long long c4_root_cta(const uint64_t *__rest
   const uint32_t ntouched = *s_nt;
   unsigned long long acc = 0;
   for (uint32_t i = tid; i < ntouched; i += nt) {
-    const uint32_t w = touched[i];
-    const unsigned long long c = tally[w];
+    const uint32_t w = __ldcg(touched + i);
+    // read-and-reset at L2: the tally was built by other threads' atomics
+    const unsigned long long c = atomicExch(&tally[w], 0u);
     acc += c * (c - 1) / 2;
-    tally[w] = 0;
   }
   __syncthreads();
   return acc;

@@ -64,6 +64,16 @@ QUERY_MOTIF3, QUERY_MOTIF4, QUERY_TC, QUERY_CLIQUE4, QUERY_CLIQUE5 = 3, 4, 5, 6,
 QUERY_WIDTH = {QUERY_MOTIF3: 2, QUERY_MOTIF4: 6, QUERY_TC: 1, QUERY_CLIQUE4: 1, QUERY_CLIQUE5: 1}
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("max_inflight", ctypes.c_uint32), ("reserved0", ctypes.c_uint32), ("arena_bytes", ctypes.c_uint64),
+                ("ring_items", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 4)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("graph", ctypes.c_uint32), ("kind", ctypes.c_uint32),
+                ("status", ctypes.c_int32), ("ncounts", ctypes.c_uint32), ("counts", ctypes.c_uint64 * 6)]
+
+
 class Options(ctypes.Structure):
     _fields_ = [("warp_max_degree", ctypes.c_uint32), ("cta_max_degree", ctypes.c_uint32),
                 ("blocks_per_sm", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
@@ -95,6 +105,11 @@ _SIGS = {
                        ctypes.POINTER(_u32)],
     "gpm_batch_destroy": [_vp],
     "gpm_count_batch": [_vp, _u32, _vp, _vp],
+    "gpm_server_start": [_vp, _u32, ctypes.POINTER(ServerOpts), ctypes.POINTER(_vp)],
+    "gpm_server_submit": [_vp, _u32, _u32, _u64],
+    "gpm_server_poll": [_vp, ctypes.POINTER(Completion), _u32, ctypes.POINTER(_u32)],
+    "gpm_server_stats": [_vp, ctypes.POINTER(_u32), ctypes.POINTER(_u32)],
+    "gpm_server_stop": [_vp],
     "gpm_set_options": [ctypes.POINTER(Options)],
     "gpm_get_options": [ctypes.POINTER(Options)],
 }
@@ -392,3 +407,48 @@ def plain_patterns(kind):
     if kind == QUERY_MOTIF4:
         return Pattern.motifs(4)
     return [Pattern.clique({QUERY_TC: 3, QUERY_CLIQUE4: 4, QUERY_CLIQUE5: 5}[kind])]
+
+
+class Server:
+    """Continuous-batching request loop over resident graphs (see gpm_server_start)."""
+
+    def __init__(self, graphs, max_inflight: int = 256, arena_bytes: int = 0, ring_items: int = 0):
+        self._graphs = list(graphs)
+        arr = (_vp * len(self._graphs))()
+        for i, g in enumerate(self._graphs):
+            arr[i] = g.handle
+        o = ServerOpts(max_inflight, 0, arena_bytes, ring_items)
+        h = _vp()
+        _check(_lib.gpm_server_start(arr, len(self._graphs), ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self._buf = (Completion * 4096)()
+
+    def submit(self, graph: int, kind: int, tag: int):
+        _check(_lib.gpm_server_submit(self._h, graph, kind, tag))
+
+    def poll(self) -> list:
+        """[(tag, graph, kind, status, counts)] of requests finished since the last poll."""
+        n = _u32(0)
+        _check(_lib.gpm_server_poll(self._h, self._buf, len(self._buf), ctypes.byref(n)))
+        out = []
+        for i in range(n.value):
+            c = self._buf[i]
+            out.append((int(c.tag), int(c.graph), int(c.kind), int(c.status),
+                        [int(c.counts[j]) for j in range(c.ncounts)]))
+        return out
+
+    def stats(self) -> dict:
+        a, b = _u32(), _u32()
+        _check(_lib.gpm_server_stats(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return dict(inflight=a.value, pending=b.value)
+
+    def stop(self):
+        if getattr(self, "_h", None) is not None:
+            _check(_lib.gpm_server_stop(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass

@@ -251,3 +251,44 @@ def graph_from_spec(s) -> Graph:
     if s["kind"] == "er":
         return erdos_renyi(s["n"], s["p"], seed=s["seed"], permute=True)
     raise ValueError(s)
+
+
+# ---------------- parallel generation of many graphs ----------------
+
+def _gen_worker(spec):
+    from multiprocessing import shared_memory
+    g = graph_from_spec(spec)
+    shm = shared_memory.SharedMemory(create=True, size=max(1, g.rowptr.nbytes + g.col.nbytes))
+    buf = np.ndarray((g.rowptr.nbytes + g.col.nbytes,), dtype=np.uint8, buffer=shm.buf)
+    buf[: g.rowptr.nbytes] = g.rowptr.view(np.uint8)
+    buf[g.rowptr.nbytes:] = g.col.view(np.uint8)
+    name = shm.name
+    shm.close()
+    return name, g.n, int(g.col.size), g.name
+
+
+def generate_many(specs, procs: int | None = None):
+    """Graphs for a list of specs, generated in a spawn-started process pool.
+
+    Start it before any CUDA work in the calling process (spawn is used, so
+    the workers never inherit a CUDA context). Returns Graphs in spec order.
+    """
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    procs = procs or max(1, min(len(specs), os.cpu_count() or 1))
+    out = [None] * len(specs)
+    # largest first for balance
+    order = sorted(range(len(specs)), key=lambda i: -specs[i].get("n", 0) * specs[i].get("edge_factor", 1.0))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        for i, (name, n, nnz, gname) in zip(order, pool.imap(_gen_worker, [specs[i] for i in order])):
+            shm = shared_memory.SharedMemory(name=name)
+            try:
+                raw = np.ndarray((8 * (n + 1) + 4 * nnz,), dtype=np.uint8, buffer=shm.buf)
+                rowptr = raw[: 8 * (n + 1)].view(np.uint64).copy()
+                col = raw[8 * (n + 1):].view(np.uint32).copy()
+            finally:
+                shm.close()
+                shm.unlink()
+            out[i] = Graph(n, rowptr, col, gname, dict(specs[i]))
+    return out

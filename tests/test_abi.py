@@ -27,7 +27,7 @@ def _declared():
         if h.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", h)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-            names |= set(re.findall(r"^\s*(?:int|const char \*|const char\*)\s*(gpm_\w+)\s*\(", txt, flags=re.M))
+            names |= set(re.findall(r"^\s*(?:int|uint64_t|const char \*|const char\*)\s*(gpm_\w+)\s*\(", txt, flags=re.M))
     return names
 
 
