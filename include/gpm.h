@@ -308,6 +308,33 @@ int gpm_server_stats(gpm_server_t s, uint32_t *inflight, uint32_t *pending);
 /* Stop the serving kernel (bounded) and release the server. */
 int gpm_server_stop(gpm_server_t s);
 
+/* ---------------- counting without device allocation ---------------- */
+
+/*
+ * Edge-induced 4-cycles of a CSR that already lives in device memory, for
+ * callers that must not allocate device memory while they run: code inside a
+ * CUDA stream capture (cudaMalloc cannot be captured), frameworks whose own
+ * arena owns all device memory, or latency-critical loops where cudaMalloc or
+ * cudaFree would synchronise the whole device. The paper has no counterpart;
+ * this entry point exists for those callers.
+ *   rowptr, col : DEVICE pointers, symmetric sorted CSR as for gpm_graph_create
+ *                 (trusted: not validated)
+ *   count       : DEVICE pointer to one uint64 that receives the count
+ * Every intermediate buffer is carved from one fixed array that is part of the
+ * library image: 64 MiB per GPU, held by every GPU that loads the library until
+ * the process exits. A graph needs 3n + 64 words of it, so n is limited to
+ * 5,592,384 vertices; a larger n returns GPM_E_INVALID_ARG with a message and
+ * launches nothing. No cudaMalloc, cudaFree or other allocating call is made.
+ * The first call on a device looks up the array's device address (with that
+ * device current), so make that first call before any stream capture begins.
+ * All calls share the one array and the array keeps the previous call's
+ * contents (the entry point clears what must start at zero): calls whose work
+ * overlaps on the GPU, from any stream or thread, race and give wrong counts.
+ * Asynchronous on `stream`; the result equals gpm_count of the edge-induced
+ * 4-cycle pattern.
+ */
+int gpm_count_cycles4_noalloc(const uint64_t *rowptr, const uint32_t *col, uint32_t n, uint64_t *count, void *stream);
+
 /* ---------------- diagnostics ---------------- */
 
 /* Message for the last error on the calling host thread ("" if none). */

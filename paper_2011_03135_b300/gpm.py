@@ -105,6 +105,7 @@ _SIGS = {
                        ctypes.POINTER(_u32)],
     "gpm_batch_destroy": [_vp],
     "gpm_count_batch": [_vp, _u32, _vp, _vp],
+    "gpm_count_cycles4_noalloc": [_vp, _vp, _u32, _vp, _vp],
     "gpm_server_start": [_vp, _u32, ctypes.POINTER(ServerOpts), ctypes.POINTER(_vp)],
     "gpm_server_submit": [_vp, _u32, _u32, _u64],
     "gpm_server_poll": [_vp, ctypes.POINTER(Completion), _u32, ctypes.POINTER(_u32)],
