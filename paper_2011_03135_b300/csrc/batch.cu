@@ -89,6 +89,8 @@ struct gpm_batch {
   unsigned int *d_head = nullptr;       // head, status
   uint32_t *tally_pool = nullptr;
   uint64_t tally_slot_words = 0;
+  uint32_t *lg_pool = nullptr;
+  ItemEnv env{};
   uint64_t *h_out = nullptr;  // pinned
   std::vector<uint32_t *> own_t_edge;  // per-arc buffers of repeated motif-4 graphs
   uint32_t cta_maxd = 0, cta_W = 0;
@@ -107,7 +109,7 @@ namespace {
 void free_batch(gpm_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  void *dev[] = {b->d_qs, b->d_items, b->d_acc, b->d_out, b->d_left, b->d_head, b->tally_pool};
+  void *dev[] = {b->d_qs, b->d_items, b->d_acc, b->d_out, b->d_left, b->d_head, b->tally_pool, b->lg_pool};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (b->h_out) cudaFreeHost(b->h_out);
@@ -170,11 +172,10 @@ int capture(gpm_batch *b) {
   a.items = b->d_items;
   a.nitems = b->nitems;
   a.head = b->d_head;
+  a.env = b->env;
   a.env.status = b->d_head + 1;
   a.env.tally_pool = b->tally_pool;
   a.env.tally_slot_words = b->tally_slot_words;
-  a.env.cta_maxd = b->cta_maxd;
-  a.env.cta_W = b->cta_W;
   const uint32_t nq = (uint32_t)b->queries.size();
   GPM_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
   cudaMemsetAsync(b->d_head, 0, sizeof(unsigned int), b->stream);
@@ -312,7 +313,7 @@ int gpm_batch_create(const gpm_query_t *queries, uint32_t nq, gpm_batch_t *out) 
     q.n = g->n;
     q.m = g->m;
     nmax = std::max(nmax, g->n);
-    b->cta_maxd = std::max(b->cta_maxd, g->cls_maxdeg[CLS_CTA]);
+    b->cta_maxd = std::max(b->cta_maxd, cta_root_maxd(g));
   }
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return fail(gpm_fail(GPM_E_DEVICE, "batch preparation"));
   // arenas
@@ -333,10 +334,12 @@ int gpm_batch_create(const gpm_query_t *queries, uint32_t nq, gpm_batch_t *out) 
     b->qs[i].out = b->d_out + (size_t)6 * i;
     b->qs[i].left = b->d_left + 2 * i;
   }
-  // shared memory: the largest of the item types' needs
-  b->cta_W = std::max<uint32_t>(1, (b->cta_maxd + 31) / 32);
+  // shared memory: the largest of the item types' needs (CTA roots above the
+  // shared-memory bound use global slots)
+  const uint32_t smem_maxd = std::min(b->cta_maxd, kItemCtaSmemMaxD);
+  const uint32_t smem_W = std::max<uint32_t>(1, (smem_maxd + 31) / 32);
   const size_t warp_bytes = warp_region_words() * 4 * kWarps;
-  const size_t cta_bytes = b->cta_maxd ? gpm_dev::cta_words(b->cta_maxd, b->cta_W) * 4 : 0;
+  const size_t cta_bytes = smem_maxd ? gpm_dev::cta_words(smem_maxd, smem_W) * 4 : 0;
   const size_t c4_bytes = need_c4 ? (size_t)kWarps * 2 * gpm_dev::kC4HashSlots * 4 : 0;
   b->smem = std::max(warp_bytes, std::max(cta_bytes, c4_bytes));
   if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem) != cudaSuccess)
@@ -346,6 +349,8 @@ int gpm_batch_create(const gpm_query_t *queries, uint32_t nq, gpm_batch_t *out) 
       per_sm < 1)
     per_sm = 1;
   b->grid = gpm_num_sms(b->device) * per_sm;
+  rc = setup_cta_items(b->env, b->cta_maxd, b->grid, &b->lg_pool);
+  if (rc) return fail(rc);
   if (need_c4) {
     b->tally_slot_words = 2 * (uint64_t)nmax;
     if (cudaMalloc(&b->tally_pool, sizeof(uint32_t) * b->tally_slot_words * b->grid) != cudaSuccess) {

@@ -44,11 +44,18 @@ constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kWarpMaxD = 128;
 constexpr uint64_t kWaitLimit = 1ull << 26;
 
+// CTA roots with out-degree above this build their bitmap in a per-CTA
+// global-memory slot, so the persistent kernel's shared memory stays small
+constexpr uint32_t kItemCtaSmemMaxD = 384;
+
 struct ItemEnv {
   uint32_t *tally_pool;
   uint64_t tally_slot_words;
   unsigned int *status;
-  uint32_t cta_maxd, cta_W;
+  uint32_t cta_maxd, cta_W;  // shared-memory CTA roots (out-degree <= cta_maxd)
+  uint32_t *lg_pool;         // global-memory bitmap slots, one per CTA
+  uint64_t lg_slot_words;
+  uint32_t lg_maxd, lg_W;    // larger roots
 };
 
 // shared memory carve-up: the union of the item types' needs
@@ -75,12 +82,17 @@ template <int KMAX, bool SCATTER>
 __device__ void lg_cta_item(const ItemEnv &a, const QDesc &q, const Item &it, uint32_t *smem,
                             unsigned long long &a3, unsigned long long &a4, unsigned long long &a5) {
   const uint32_t u = q.tasks[it.lo];
-  if (a.cta_W <= 8)
+  const uint32_t d = (uint32_t)(q.drow[u + 1] - q.drow[u]);
+  if (d > a.cta_maxd) {
+    uint32_t *slot = a.lg_pool + (size_t)blockIdx.x * a.lg_slot_words;
+    gpm_dev::lg_root_cta<32, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.lg_maxd, a.lg_W, slot, a3, a4, a5);
+  } else if (a.cta_W <= 8) {
     gpm_dev::lg_root_cta<8, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.cta_maxd, a.cta_W, smem, a3, a4, a5);
-  else if (a.cta_W <= 16)
+  } else if (a.cta_W <= 16) {
     gpm_dev::lg_root_cta<16, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.cta_maxd, a.cta_W, smem, a3, a4, a5);
-  else
+  } else {
     gpm_dev::lg_root_cta<32, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.cta_maxd, a.cta_W, smem, a3, a4, a5);
+  }
 }
 
 __device__ __forceinline__ void block_add(unsigned long long *dst, unsigned long long v) {
@@ -121,7 +133,11 @@ __device__ __forceinline__ void run_item(const ItemEnv &a, const QDesc &q, const
     }
     case IT_C4_BIG: {
       uint32_t *tally = a.tally_pool + (size_t)blockIdx.x * a.tally_slot_words;
-      c4 += gpm_dev::c4_root_cta(q.rowptr, q.col, q.deg, q.c4_tasks[it.lo], tally, tally + q.n, s_x, s_cnt, s_nt);
+      // the slot holds the tally in its first half and the touched list in its
+      // second half for every query size: a smaller query's touched entries
+      // must never land in a larger query's tally range
+      c4 += gpm_dev::c4_root_cta(q.rowptr, q.col, q.deg, q.c4_tasks[it.lo], tally, tally + a.tally_slot_words / 2,
+                                 s_x, s_cnt, s_nt);
       break;
     }
     case IT_EDGE: {
@@ -202,7 +218,7 @@ inline void append_query_items(const gpm_graph *g, uint32_t kind, uint32_t qi, u
     ++al;
     ++sc;
   }
-  for (uint32_t t = g->cls_begin[CLS_CTA]; t < g->cls_begin[CLS_CTA + 1]; ++t) {
+  for (uint32_t t = g->cls_begin[CLS_CTA]; t < g->cls_begin[CLS_XL + 1]; ++t) {
     heavy.push_back({IT_LG_CTA, qi, t, t + 1});
     ++al;
     ++sc;
@@ -255,13 +271,36 @@ inline int prepare_for_items(gpm_graph *g, bool need_c4, cudaStream_t st) {
     gpm_tune().warp_max_degree = old_w;
     if (rc) return rc;
   }
-  if (g->cls_begin[CLS_XL + 1] > g->cls_begin[CLS_XL])
-    return gpm_fail(GPM_E_UNSUPPORTED, "batched and served forms support root out-degrees up to 1024");
   if (need_c4 && !g->c4_ready) {
-    unsigned long long *acc = reinterpret_cast<unsigned long long *>(g->work + WK_ACC);
-    if (cudaMemsetAsync(acc, 0, ACC_WORDS * 8, st) != cudaSuccess) return gpm_fail(GPM_E_DEVICE, "acc reset");
-    rc = gpm_launch_cycles4(g, 0, g->n, acc, st);  // builds the 4-cycle root lists
+    rc = gpm_build_c4_tasks(g, st);
     if (rc) return rc;
+  }
+  return GPM_OK;
+}
+
+// Largest CTA-root out-degree of a prepared graph (CTA and global classes).
+inline uint32_t cta_root_maxd(const gpm_graph *g) {
+  return std::max(g->cls_maxdeg[CLS_CTA], g->cls_maxdeg[CLS_XL]);
+}
+
+// Shared-memory and global-slot shapes of CTA items for roots up to maxd_all;
+// allocates the global slots (one per CTA of the grid) when needed.
+inline int setup_cta_items(ItemEnv &env, uint32_t maxd_all, int grid, uint32_t **pool_out) {
+  env.cta_maxd = std::min(maxd_all, kItemCtaSmemMaxD);
+  env.cta_W = std::max<uint32_t>(1, (env.cta_maxd + 31) / 32);
+  env.lg_pool = nullptr;
+  env.lg_slot_words = 0;
+  env.lg_maxd = 0;
+  env.lg_W = 1;
+  if (maxd_all > kItemCtaSmemMaxD) {
+    env.lg_maxd = maxd_all;
+    env.lg_W = (maxd_all + 31) / 32;
+    env.lg_slot_words = (gpm_dev::cta_words(maxd_all, env.lg_W) + 63) & ~63ull;
+    if (cudaMalloc(pool_out, sizeof(uint32_t) * env.lg_slot_words * (size_t)grid) != cudaSuccess) {
+      cudaGetLastError();
+      return gpm_fail(GPM_E_OOM, "bitmap slot allocation failed");
+    }
+    env.lg_pool = *pool_out;
   }
   return GPM_OK;
 }

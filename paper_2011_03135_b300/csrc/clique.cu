@@ -153,14 +153,15 @@ int max_smem_optin(int device) {
 }
 
 template <int G, int KMAX, bool SCATTER, bool GLOBAL>
-int launch_cta(const LGArgs &a, uint32_t maxd, int blocks_cap, int device, cudaStream_t st) {
+int launch_cta(const LGArgs &a, uint32_t maxd, int blocks_cap, int device, cudaStream_t st,
+               size_t smem_limit = 0, const char *name = nullptr) {
   constexpr int kThreads = 512;
   size_t smem = GLOBAL ? 0 : (size_t)cta_words(maxd, a.W) * 4;
   uint32_t big_cap = 0;
   if (!GLOBAL && KMAX >= 5) {
     // room left after the bitmap and the per-warp nested buffers goes to the CTA-wide nested buffer
     const size_t fixed = smem + (size_t)gpm_dev::nest_words(maxd, kThreads / 32, 0) * 4 + 2048;
-    const size_t limit = (size_t)max_smem_optin(device);
+    const size_t limit = smem_limit ? smem_limit : (size_t)max_smem_optin(device);
     if (fixed + 4 * 1024 <= limit) {
       big_cap = (uint32_t)std::min<size_t>((limit - fixed) / 4, 32768);
       smem += (size_t)gpm_dev::nest_words(maxd, kThreads / 32, big_cap) * 4;
@@ -174,7 +175,8 @@ int launch_cta(const LGArgs &a, uint32_t maxd, int blocks_cap, int device, cudaS
   int blocks = gpm_num_sms(device) * per_sm;
   blocks = std::max(1, std::min<int>(blocks, (int)a.ntasks));
   if (blocks_cap > 0) blocks = std::min(blocks, blocks_cap);
-  GPM_LAUNCH(GLOBAL ? "lg_cta_global" : "lg_cta", st, kern<<<blocks, kThreads, smem, st>>>(a, maxd, big_cap));
+  GPM_LAUNCH(name ? name : (GLOBAL ? "lg_cta_global" : "lg_cta"), st,
+             kern<<<blocks, kThreads, smem, st>>>(a, maxd, big_cap));
   GPM_CUDA(cudaGetLastError());
   return GPM_OK;
 }
@@ -203,18 +205,23 @@ int launch_all(gpm_graph *g, LGArgs base, unsigned int *queues, cudaStream_t st)
       else GPM_TRY((launch_warp<256, 8, KMAX, SCATTER>(a, dev, st)));
     }
   }
-  // class CTA: shared-memory bitmap
-  {
+  // class CTA: shared-memory bitmap; roots above the split degree with the
+  // largest footprint, the rest sized for two CTAs per SM
+  for (int part = 0; part < 2; ++part) {
     LGArgs a = base;
-    a.tasks = g->tasks + g->cls_begin[CLS_CTA];
-    a.ntasks = g->cls_begin[CLS_CTA + 1] - g->cls_begin[CLS_CTA];
-    a.queue = queues + 2;
-    const uint32_t md = g->cls_maxdeg[CLS_CTA];
+    const uint32_t b0 = part == 0 ? g->cls_begin[CLS_CTA] : g->cta_split;
+    const uint32_t b1 = part == 0 ? g->cta_split : g->cls_begin[CLS_CTA + 1];
+    a.tasks = g->tasks + b0;
+    a.ntasks = b1 - b0;
+    a.queue = queues + (part == 0 ? 2 : 6);
+    const uint32_t md = part == 0 ? g->cls_maxdeg[CLS_CTA] : g->cta_lo_maxd;
     a.W = (md + 31) / 32;
+    const size_t limit = part == 0 ? 0 : (size_t)(max_smem_optin(dev) / 2 - 1024);
+    const char *nm = part == 0 ? "lg_cta_hi" : "lg_cta_lo";
     if (a.ntasks) {
-      if (a.W <= 8) GPM_TRY((launch_cta<8, KMAX, SCATTER, false>(a, md, 0, dev, st)));
-      else if (a.W <= 16) GPM_TRY((launch_cta<16, KMAX, SCATTER, false>(a, md, 0, dev, st)));
-      else GPM_TRY((launch_cta<32, KMAX, SCATTER, false>(a, md, 0, dev, st)));
+      if (a.W <= 8) GPM_TRY((launch_cta<8, KMAX, SCATTER, false>(a, md, 0, dev, st, limit, nm)));
+      else if (a.W <= 16) GPM_TRY((launch_cta<16, KMAX, SCATTER, false>(a, md, 0, dev, st, limit, nm)));
+      else GPM_TRY((launch_cta<32, KMAX, SCATTER, false>(a, md, 0, dev, st, limit, nm)));
     }
   }
   // class XL: global-memory bitmaps, one slot per resident CTA

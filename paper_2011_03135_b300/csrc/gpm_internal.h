@@ -46,6 +46,8 @@ enum : uint32_t {
 // out-degree d < 2 roots no triangle and is never a task.
 enum { CLS_W32 = 0, CLS_WARP = 1, CLS_CTA = 2, CLS_XL = 3, NUM_CLS = 4 };
 
+constexpr uint32_t kCtaSplitDegree = 384;
+
 struct gpm_tuning {
   uint32_t warp_max_degree = 128;  // class CLS_WARP upper bound (<= 256)
   uint32_t cta_max_degree = 1024;  // class CLS_CTA upper bound (<= 1024)
@@ -80,6 +82,10 @@ struct gpm_graph {
   uint32_t cls_begin[NUM_CLS + 1] = {0, 0, 0, 0, 0};
   uint32_t cls_maxdeg[NUM_CLS] = {0, 0, 0, 0};
   uint32_t tune_warp_max = 0, tune_cta_max = 0;  // thresholds the classes were built with
+  // the CTA class is ordered by decreasing out-degree; roots from cta_split on
+  // have out-degree <= kCtaSplitDegree (max cta_lo_maxd) and run with smaller
+  // shared-memory footprints, two CTAs per SM
+  uint32_t cta_split = 0, cta_lo_maxd = 0;
 
   // preparation scratch, kept for re-orientation
   uint32_t *prep_outdeg = nullptr;  // n
@@ -161,6 +167,9 @@ int gpm_num_sms(int device);
 // every triangle to the per-arc counts g->t_edge (zeroed by the caller).
 int gpm_launch_cliques(gpm_graph *g, int kmax, bool scatter, uint32_t root_lo, uint32_t root_hi,
                        unsigned long long *acc, cudaStream_t st);
+
+// 4-cycle root lists (wedge-bound classes), built once per graph.
+int gpm_build_c4_tasks(gpm_graph *g, cudaStream_t st);
 
 // 4-cycles whose order-last vertex lies in [root_lo, root_hi): acc[ACC_C4] += count.
 int gpm_launch_cycles4(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigned long long *acc, cudaStream_t st);

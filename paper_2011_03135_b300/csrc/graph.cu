@@ -319,6 +319,17 @@ int gpm_ensure_classes(gpm_graph *g, cudaStream_t st) {
     for (uint32_t i = 0; i < big; ++i) order[i] = (uint32_t)keys[i];
     GPM_CUDA(cudaMemcpyAsync(g->tasks + g->cls_begin[CLS_CTA], order.data(), sizeof(uint32_t) * big,
                              cudaMemcpyHostToDevice, st));
+    // split of the CTA class (keys of the class are sorted by decreasing out-degree)
+    const uint32_t ncta = g->cls_begin[CLS_CTA + 1] - g->cls_begin[CLS_CTA];
+    uint32_t k = 0;
+    while (k < ncta && (uint32_t)(keys[k] >> 32) > kCtaSplitDegree) ++k;
+    g->cta_split = g->cls_begin[CLS_CTA] + k;
+    g->cta_lo_maxd = (k < ncta) ? (uint32_t)(keys[k] >> 32) : 0;
+  } else {
+    const uint32_t ncta = g->cls_begin[CLS_CTA + 1] - g->cls_begin[CLS_CTA];
+    const bool hi = ncta > 0 && g->cls_maxdeg[CLS_CTA] > kCtaSplitDegree;
+    g->cta_split = hi ? g->cls_begin[CLS_CTA + 1] : g->cls_begin[CLS_CTA];
+    g->cta_lo_maxd = (ncta > 0 && !hi) ? g->cls_maxdeg[CLS_CTA] : 0;
   }
   GPM_CUDA(cudaStreamSynchronize(st));
   g->tune_warp_max = t.warp_max_degree;

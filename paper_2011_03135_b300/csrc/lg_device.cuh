@@ -7,6 +7,11 @@
 
 namespace gpm_dev {
 
+// Bitmap rows are stored with an odd stride (words + 1 when the word count is
+// even) so that rows read by different lanes fall in different shared-memory
+// banks.
+__host__ __device__ constexpr uint32_t row_stride(uint32_t words) { return words | 1u; }
+
 __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t *a, uint32_t n, uint32_t x) {
   uint32_t lo = 0, hi = n;
   while (lo < hi) {
@@ -34,7 +39,7 @@ template <bool SCATTER>
 __device__ __forceinline__ uint32_t build_rows(const uint32_t *__restrict__ dcol, uint32_t *t_edge, const uint32_t *L,
                                                const uint32_t *pre,
                                                const uint64_t *xb, uint32_t *R, uint32_t *tc, uint32_t d,
-                                               uint32_t W, uint32_t t, uint32_t nt) {
+                                               uint32_t rs, uint32_t t, uint32_t nt) {
   const uint32_t E = pre[d];
   uint32_t found = 0;
   const uint32_t lo_id = L[0], hi_id = L[d - 1];
@@ -46,7 +51,7 @@ __device__ __forceinline__ uint32_t build_rows(const uint32_t *__restrict__ dcol
     if (y < lo_id || y > hi_id) continue;
     const uint32_t j = lower_bound_u32(L, d, y);
     if (j < d && L[j] == y) {
-      atomicOr(&R[(size_t)i * W + (j >> 5)], 1u << (j & 31));
+      atomicOr(&R[(size_t)i * rs + (j >> 5)], 1u << (j & 31));
       ++found;
       if (SCATTER) {
         atomicAdd(&tc[i], 1u);
@@ -62,18 +67,18 @@ __device__ __forceinline__ uint32_t build_rows(const uint32_t *__restrict__ dcol
 // A group of G lanes handles one row at a time; lane gl of the group holds
 // word gl of the row (W <= G), so every AND is one word per lane.
 template <int G, int KMAX>
-__device__ __forceinline__ void enumerate_rows(const uint32_t *R, uint32_t d, uint32_t W, uint32_t row0,
+__device__ __forceinline__ void enumerate_rows(const uint32_t *R, uint32_t d, uint32_t W, uint32_t rs, uint32_t row0,
                                                uint32_t row_step, uint32_t gl, unsigned long long &a4,
                                                unsigned long long &a5) {
   for (uint32_t i = row0; i < d; i += row_step) {
-    const uint32_t *ri = R + (size_t)i * W;
+    const uint32_t *ri = R + (size_t)i * rs;
     const uint32_t riw = (gl < W) ? ri[gl] : 0u;
     for (uint32_t t = 0; t < W; ++t) {
       uint32_t bits = ri[t];
       while (bits) {
         const uint32_t j = t * 32 + __ffs(bits) - 1;
         bits &= bits - 1;
-        const uint32_t *rj = R + (size_t)j * W;
+        const uint32_t *rj = R + (size_t)j * rs;
         const uint32_t mw = (gl < W) ? (riw & rj[gl]) : 0u;
         a4 += __popc(mw);
         if (KMAX >= 5) {
@@ -82,7 +87,7 @@ __device__ __forceinline__ void enumerate_rows(const uint32_t *R, uint32_t d, ui
             while (b2) {
               const uint32_t l = t2 * 32 + __ffs(b2) - 1;
               b2 &= b2 - 1;
-              if (gl < W) a5 += __popc(mw & R[(size_t)l * W + gl]);
+              if (gl < W) a5 += __popc(mw & R[(size_t)l * rs + gl]);
             }
           }
         }
@@ -93,17 +98,18 @@ __device__ __forceinline__ void enumerate_rows(const uint32_t *R, uint32_t d, ui
 
 // Same for W > 32 (global-memory class): lane gl holds words gl, gl+G, ...
 template <int KMAX>
-__device__ inline void enumerate_rows_wide(const uint32_t *R, uint32_t d, uint32_t W, uint32_t row0, uint32_t row_step,
-                                    uint32_t gl, unsigned long long &a4, unsigned long long &a5) {
+__device__ inline void enumerate_rows_wide(const uint32_t *R, uint32_t d, uint32_t W, uint32_t rs, uint32_t row0,
+                                           uint32_t row_step, uint32_t gl, unsigned long long &a4,
+                                           unsigned long long &a5) {
   constexpr uint32_t G = 32;
   for (uint32_t i = row0; i < d; i += row_step) {
-    const uint32_t *ri = R + (size_t)i * W;
+    const uint32_t *ri = R + (size_t)i * rs;
     for (uint32_t t = 0; t < W; ++t) {
       uint32_t bits = ri[t];
       while (bits) {
         const uint32_t j = t * 32 + __ffs(bits) - 1;
         bits &= bits - 1;
-        const uint32_t *rj = R + (size_t)j * W;
+        const uint32_t *rj = R + (size_t)j * rs;
         for (uint32_t w = gl; w < W; w += G) a4 += __popc(ri[w] & rj[w]);
         if (KMAX >= 5) {
           for (uint32_t t2 = 0; t2 < W; ++t2) {
@@ -111,7 +117,7 @@ __device__ inline void enumerate_rows_wide(const uint32_t *R, uint32_t d, uint32
             while (b2) {
               const uint32_t l = t2 * 32 + __ffs(b2) - 1;
               b2 &= b2 - 1;
-              const uint32_t *rl = R + (size_t)l * W;
+              const uint32_t *rl = R + (size_t)l * rs;
               for (uint32_t w = gl; w < W; w += G) a5 += __popc(ri[w] & rj[w] & rl[w]);
             }
           }
@@ -138,7 +144,7 @@ __device__ inline void enumerate_rows_wide(const uint32_t *R, uint32_t d, uint32
 // ---------------------------------------------------------------------------
 constexpr uint32_t kNestWarpC = 128;  // rows with c <= this are nested by one warp
 constexpr uint32_t kNestWarpWp = 4;   // = kNestWarpC / 32
-constexpr uint32_t kNestWarpWords = kNestWarpC + 32 + kNestWarpC * kNestWarpWp;
+constexpr uint32_t kNestWarpWords = kNestWarpC + 32 + kNestWarpC * (kNestWarpWp | 1u);
 
 __host__ __device__ constexpr uint64_t nest_words(uint32_t maxd, uint32_t nwarps, uint32_t big_cap) {
   // per warp: S[128] pref[32] C[128*4]; CTA: big-row list[maxd], S[maxd], pref[32], C[big_cap], 4 counters
@@ -171,49 +177,81 @@ __device__ __forceinline__ uint32_t list_bits_warp(const uint32_t *ri, uint32_t 
   return total;
 }
 
-// compact row R_j (j = S[a]) onto the positions of ri into crow (Wp words, zeroed here)
+// Gather the bits of x (a subset of riw) to the low popc(riw) positions, in
+// order: the bits of one input word land in one contiguous output range.
+__device__ __forceinline__ uint32_t gather_bits(uint32_t x, uint32_t riw) {
+  uint32_t out = 0;
+  while (x) {
+    const uint32_t p = __ffs(x) - 1;
+    x &= x - 1;
+    out |= 1u << __popc(riw & ((1u << p) - 1u));
+  }
+  return out;
+}
+
+// compact row R_j (j = S[a]) onto the positions of ri into crow (Wp words,
+// zeroed here); returns |R_j & R_i|
 __device__ __forceinline__ uint32_t compact_row(const uint32_t *rj, const uint32_t *ri, const uint32_t *pref, uint32_t W,
                                                 uint32_t *crow, uint32_t Wp) {
   for (uint32_t k = 0; k < Wp; ++k) crow[k] = 0u;
   uint32_t bits = 0;
   for (uint32_t w = 0; w < W; ++w) {
     const uint32_t riw = ri[w];
-    uint32_t x = rj[w] & riw;
+    const uint32_t x = rj[w] & riw;
     if (!x) continue;
-    const uint32_t base = pref[w];
+    const uint32_t out = gather_bits(x, riw);
     bits += __popc(x);
-    while (x) {
-      const uint32_t p = __ffs(x) - 1;
-      x &= x - 1;
-      const uint32_t b = base + __popc(riw & ((1u << p) - 1u));
-      crow[b >> 5] |= 1u << (b & 31);
-    }
+    const uint32_t base = pref[w], wi = base >> 5, lo = base & 31;
+    crow[wi] |= out << lo;
+    if (lo && lo + __popc(riw) > 32) crow[wi + 1] |= out >> (32 - lo);
   }
   return bits;
 }
 
-// sum over set bits b of row a of |C_a & C_b| (rows of Wp words, stride Wp)
-__device__ __forceinline__ unsigned long long nested_pairs(const uint32_t *C, uint32_t a, uint32_t Wp) {
-  const uint32_t *ca = C + (size_t)a * Wp;
+// sum over the set bits b in word k of row a of |C_a & C_b| (rows of Wp words,
+// stride Wp); one (a, k) unit bounds a thread's loop to 32 bits
+__device__ __forceinline__ unsigned long long nested_pairs_unit(const uint32_t *C, uint32_t a, uint32_t k,
+                                                                uint32_t Wp, uint32_t cs) {
+  const uint32_t *ca = C + (size_t)a * cs;
   unsigned long long s = 0;
-  for (uint32_t k = 0; k < Wp; ++k) {
-    uint32_t bits = ca[k];
-    while (bits) {
-      const uint32_t b = k * 32 + __ffs(bits) - 1;
-      bits &= bits - 1;
-      const uint32_t *cb = C + (size_t)b * Wp;
-      for (uint32_t k2 = 0; k2 < Wp; ++k2) s += __popc(ca[k2] & cb[k2]);
-    }
+  uint32_t bits = ca[k];
+  while (bits) {
+    const uint32_t b = k * 32 + __ffs(bits) - 1;
+    bits &= bits - 1;
+    const uint32_t *cb = C + (size_t)b * cs;
+    for (uint32_t k2 = 0; k2 < Wp; ++k2) s += __popc(ca[k2] & cb[k2]);
   }
   return s;
 }
 
+// Rows with c <= 32: lane a keeps compacted row C_a in a register; the pairs
+// (a, b) are visited with one shuffle of C_b per b (no shared memory).
+__device__ __forceinline__ void nested_row_reg32(const uint32_t *R, uint32_t W, uint32_t rs, const uint32_t *ri,
+                                                 uint32_t c, const uint32_t *S, const uint32_t *pref,
+                                                 unsigned long long &a4, unsigned long long &a5) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t ca = 0;
+  if (lane < c) {
+    const uint32_t *rj = R + (size_t)S[lane] * rs;
+    for (uint32_t w = 0; w < W; ++w) {
+      const uint32_t riw = ri[w];
+      const uint32_t x = rj[w] & riw;
+      if (x) ca |= gather_bits(x, riw) << pref[w];  // c <= 32: every output bit is in word 0
+    }
+  }
+  a4 += __popc(ca);
+  for (uint32_t b = 0; b < c; ++b) {
+    const uint32_t cb = __shfl_sync(0xffffffffu, ca, b);
+    if ((ca >> b) & 1u) a5 += __popc(ca & cb);
+  }
+}
+
 // Row i by a group of lanes without nesting (fallback for rows too wide to
 // compact): the group takes every `ng`-th bit j of R_i.
-__device__ __forceinline__ void row_k45_groups(const uint32_t *R, uint32_t W, uint32_t i, uint32_t g, uint32_t ng,
-                                               uint32_t gl, uint32_t G, unsigned long long &a4,
+__device__ __forceinline__ void row_k45_groups(const uint32_t *R, uint32_t W, uint32_t rs, uint32_t i, uint32_t g,
+                                               uint32_t ng, uint32_t gl, uint32_t G, unsigned long long &a4,
                                                unsigned long long &a5) {
-  const uint32_t *ri = R + (size_t)i * W;
+  const uint32_t *ri = R + (size_t)i * rs;
   uint32_t seen = 0;
   for (uint32_t t = 0; t < W; ++t) {
     uint32_t bits = ri[t];
@@ -221,7 +259,7 @@ __device__ __forceinline__ void row_k45_groups(const uint32_t *R, uint32_t W, ui
       const uint32_t j = t * 32 + __ffs(bits) - 1;
       bits &= bits - 1;
       if ((seen++ % ng) != g) continue;
-      const uint32_t *rj = R + (size_t)j * W;
+      const uint32_t *rj = R + (size_t)j * rs;
       for (uint32_t w = gl; w < W; w += G) {
         const uint32_t mw = ri[w] & rj[w];
         a4 += __popc(mw);
@@ -231,7 +269,7 @@ __device__ __forceinline__ void row_k45_groups(const uint32_t *R, uint32_t W, ui
         while (b2) {
           const uint32_t l = t2 * 32 + __ffs(b2) - 1;
           b2 &= b2 - 1;
-          const uint32_t *rl = R + (size_t)l * W;
+          const uint32_t *rl = R + (size_t)l * rs;
           for (uint32_t w = gl; w < W; w += G) a5 += __popc(ri[w] & rj[w] & rl[w]);
         }
       }
@@ -241,8 +279,9 @@ __device__ __forceinline__ void row_k45_groups(const uint32_t *R, uint32_t W, ui
 
 // 4- and 5-cliques of one root's local graph R (d rows, W <= 32 words) by the
 // whole CTA with nesting. nest: nest_words(maxd, blockDim/32, big_cap) words.
-__device__ inline void enumerate_nested_cta(const uint32_t *R, uint32_t d, uint32_t W, uint32_t *nest, uint32_t maxd,
-                                     uint32_t big_cap, unsigned long long &a4, unsigned long long &a5) {
+__device__ inline void enumerate_nested_cta(const uint32_t *R, uint32_t d, uint32_t W, uint32_t rs, uint32_t *nest,
+                                            uint32_t maxd, uint32_t big_cap, unsigned long long &a4,
+                                            unsigned long long &a5) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   uint32_t *wbuf = nest + (size_t)wid * kNestWarpWords;
   uint32_t *S = wbuf, *pref = wbuf + kNestWarpC, *C = wbuf + kNestWarpC + 32;
@@ -260,20 +299,25 @@ __device__ inline void enumerate_nested_cta(const uint32_t *R, uint32_t d, uint3
     if (lane == 0) i = atomicAdd(&ctr[0], 1u);
     i = __shfl_sync(0xffffffffu, i, 0);
     if (i >= d) break;
-    const uint32_t *ri = R + (size_t)i * W;
+    const uint32_t *ri = R + (size_t)i * rs;
     const uint32_t c = list_bits_warp(ri, W, S, pref, kNestWarpC);
     if (c < 2) continue;
     if (c > kNestWarpC) {
       if (lane == 0) big_list[atomicAdd(&ctr[1], 1u)] = i;
       continue;
     }
-    const uint32_t Wp = (c + 31) / 32;
+    if (c <= 32) {
+      nested_row_reg32(R, W, rs, ri, c, S, pref, a4, a5);
+      __syncwarp();
+      continue;
+    }
+    const uint32_t Wp = (c + 31) / 32, cs = row_stride(Wp);
     for (uint32_t a = lane; a < c; a += 32) {
-      const uint32_t bits = compact_row(R + (size_t)S[a] * W, ri, pref, W, C + (size_t)a * Wp, Wp);
+      const uint32_t bits = compact_row(R + (size_t)S[a] * rs, ri, pref, W, C + (size_t)a * cs, Wp);
       a4 += bits;
     }
     __syncwarp();
-    for (uint32_t a = lane; a < c; a += 32) a5 += nested_pairs(C, a, Wp);
+    for (uint32_t u = lane; u < c * Wp; u += 32) a5 += nested_pairs_unit(C, u / Wp, u % Wp, Wp, cs);
     __syncwarp();
   }
   __syncthreads();
@@ -281,20 +325,34 @@ __device__ inline void enumerate_nested_cta(const uint32_t *R, uint32_t d, uint3
   const uint32_t nbig = ctr[1];
   for (uint32_t r = 0; r < nbig; ++r) {
     const uint32_t i = big_list[r];
-    const uint32_t *ri = R + (size_t)i * W;
+    const uint32_t *ri = R + (size_t)i * rs;
     if (wid == 0) {
       const uint32_t c = list_bits_warp(ri, W, Sb, prefb, maxd);
       if (lane == 0) ctr[2] = c;
     }
     __syncthreads();
     const uint32_t c = ctr[2];
-    const uint32_t Wp = (c + 31) / 32;
-    if ((uint64_t)c * Wp <= big_cap) {
-      for (uint32_t a = tid; a < c; a += nt) a4 += compact_row(R + (size_t)Sb[a] * W, ri, prefb, W, Cb + (size_t)a * Wp, Wp);
+    const uint32_t Wp = (c + 31) / 32, cs = row_stride(Wp);
+    if ((uint64_t)c * cs <= big_cap) {
+      for (uint32_t u = tid; u < c * cs; u += nt) Cb[u] = 0u;
       __syncthreads();
-      for (uint32_t a = tid; a < c; a += nt) a5 += nested_pairs(Cb, a, Wp);
+      // (row, word) units: every thread works on the wide row
+      for (uint32_t u = tid; u < c * W; u += nt) {
+        const uint32_t a = u / W, w = u % W;
+        const uint32_t riw = ri[w];
+        const uint32_t x = R[(size_t)Sb[a] * rs + w] & riw;
+        if (!x) continue;
+        a4 += __popc(x);
+        const uint32_t out = gather_bits(x, riw);
+        const uint32_t base = prefb[w], wi = base >> 5, lo = base & 31;
+        uint32_t *crow = Cb + (size_t)a * cs;
+        atomicOr(&crow[wi], out << lo);
+        if (lo && lo + __popc(riw) > 32) atomicOr(&crow[wi + 1], out >> (32 - lo));
+      }
+      __syncthreads();
+      for (uint32_t u = tid; u < c * Wp; u += nt) a5 += nested_pairs_unit(Cb, u / Wp, u % Wp, Wp, cs);
     } else {
-      row_k45_groups(R, W, i, tid >> 5, nt >> 5, lane, 32, a4, a5);
+      row_k45_groups(R, W, rs, i, tid >> 5, nt >> 5, lane, 32, a4, a5);
     }
     __syncthreads();
   }
@@ -303,12 +361,12 @@ __device__ inline void enumerate_nested_cta(const uint32_t *R, uint32_t d, uint3
 // Words of shared memory one warp needs for a root of out-degree <= maxd:
 // xb[maxd] (uint64) | L[maxd] | pre[maxd+1] | R[maxd*W] | tc[maxd] (scatter)
 __host__ __device__ constexpr uint32_t warp_words(uint32_t maxd, bool scatter) {
-  return ((2 * maxd + maxd + (maxd + 1) + maxd * ((maxd + 31) / 32) + (scatter ? maxd : 0)) + 1) & ~1u;
+  return ((2 * maxd + maxd + (maxd + 1) + maxd * row_stride((maxd + 31) / 32) + (scatter ? maxd : 0)) + 1) & ~1u;
 }
 
 // Same layout for one CTA-wide root with W words per row.
 __host__ __device__ constexpr uint64_t cta_words(uint32_t maxd, uint32_t W) {
-  return 2ull * maxd + maxd + (maxd + 1) + (uint64_t)maxd * W + maxd + 2;
+  return 2ull * maxd + maxd + (maxd + 1) + (uint64_t)maxd * row_stride(W) + maxd + 2;
 }
 
 // One root u (2 <= d+(u) <= MAXD) processed by the calling warp. `base` is
@@ -322,10 +380,10 @@ __device__ __forceinline__ void lg_root_warp(const uint64_t *__restrict__ drow, 
   uint32_t *L = base + 2 * MAXD;
   uint32_t *pre = L + MAXD;
   uint32_t *R = pre + MAXD + 1;
-  uint32_t *tc = R + MAXD * ((MAXD + 31) / 32);
+  uint32_t *tc = R + MAXD * row_stride((MAXD + 31) / 32);
   const uint64_t ub = drow[u];
   const uint32_t d = (uint32_t)(drow[u + 1] - ub);
-  const uint32_t w_used = (d + 31) / 32;
+  const uint32_t w_used = (d + 31) / 32, rs = row_stride(w_used);
   for (uint32_t i = lane; i < d; i += 32) {
     const uint32_t x = __ldg(dcol + ub + i);
     L[i] = x;
@@ -334,7 +392,7 @@ __device__ __forceinline__ void lg_root_warp(const uint64_t *__restrict__ drow, 
     pre[i + 1] = (uint32_t)(xe - xs);
     if (SCATTER) tc[i] = 0;
   }
-  for (uint32_t i = lane; i < d * w_used; i += 32) R[i] = 0;
+  for (uint32_t i = lane; i < d * rs; i += 32) R[i] = 0;
   if (lane == 0) pre[0] = 0;
   __syncwarp();
   uint32_t carry = 0;
@@ -349,13 +407,13 @@ __device__ __forceinline__ void lg_root_warp(const uint64_t *__restrict__ drow, 
     carry += __shfl_sync(0xffffffffu, v, 31);
   }
   __syncwarp();
-  a3 += build_rows<SCATTER>(dcol, t_edge, L, pre, xb, R, tc, d, w_used, lane, 32);
+  a3 += build_rows<SCATTER>(dcol, t_edge, L, pre, xb, R, tc, d, rs, lane, 32);
   __syncwarp();
   if (SCATTER) {
     for (uint32_t i = lane; i < d; i += 32)
       if (tc[i]) atomicAdd(&t_edge[ub + i], tc[i]);
   }
-  if (KMAX >= 4) enumerate_rows<G, KMAX>(R, d, w_used, lane / G, 32 / G, lane % G, a4, a5);
+  if (KMAX >= 4) enumerate_rows<G, KMAX>(R, d, w_used, rs, lane / G, 32 / G, lane % G, a4, a5);
   __syncwarp();
 }
 
@@ -372,10 +430,10 @@ __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, c
   uint32_t *L = base + 2 * (size_t)maxd;
   uint32_t *pre = L + maxd;
   uint32_t *R = pre + maxd + 1;
-  uint32_t *tc = R + (size_t)maxd * W;
+  uint32_t *tc = R + (size_t)maxd * row_stride(W);
   const uint64_t ub = drow[u];
   const uint32_t d = (uint32_t)(drow[u + 1] - ub);
-  const uint32_t w_used = (d + 31) / 32;
+  const uint32_t w_used = (d + 31) / 32, rs = row_stride(w_used);
   for (uint32_t i = tid; i < d; i += nt) {
     const uint32_t x = __ldg(dcol + ub + i);
     L[i] = x;
@@ -384,7 +442,7 @@ __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, c
     pre[i + 1] = (uint32_t)(xe - xs);
     if (SCATTER) tc[i] = 0;
   }
-  for (size_t i = tid; i < (size_t)d * w_used; i += nt) R[i] = 0;
+  for (size_t i = tid; i < (size_t)d * rs; i += nt) R[i] = 0;
   if (tid == 0) pre[0] = 0;
   __syncthreads();
   if (tid < 32) {
@@ -401,19 +459,19 @@ __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, c
     }
   }
   __syncthreads();
-  a3 += build_rows<SCATTER>(dcol, t_edge, L, pre, xb, R, tc, d, w_used, tid, nt);
+  a3 += build_rows<SCATTER>(dcol, t_edge, L, pre, xb, R, tc, d, rs, tid, nt);
   __syncthreads();
   if (SCATTER) {
     for (uint32_t i = tid; i < d; i += nt)
       if (tc[i]) atomicAdd(&t_edge[ub + i], tc[i]);
   }
   if (KMAX >= 5 && nest != nullptr && w_used <= 32) {
-    enumerate_nested_cta(R, d, w_used, nest, maxd, big_cap, a4, a5);
+    enumerate_nested_cta(R, d, w_used, rs, nest, maxd, big_cap, a4, a5);
   } else if (KMAX >= 4) {
     if (w_used > 32)
-      enumerate_rows_wide<KMAX>(R, d, w_used, tid / 32, nt / 32, lane, a4, a5);
+      enumerate_rows_wide<KMAX>(R, d, w_used, rs, tid / 32, nt / 32, lane, a4, a5);
     else
-      enumerate_rows<G, KMAX>(R, d, w_used, tid / G, nt / G, tid % G, a4, a5);
+      enumerate_rows<G, KMAX>(R, d, w_used, rs, tid / G, nt / G, tid % G, a4, a5);
   }
   __syncthreads();
 }

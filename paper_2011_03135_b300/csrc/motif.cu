@@ -129,9 +129,10 @@ __global__ void __launch_bounds__(256) c4_small_kernel(C4Args a) {
 }
 
 // one CTA per root, dense tally in this CTA's global-memory slot
-__global__ void __launch_bounds__(512) c4_big_kernel(C4Args a) {
+constexpr int kC4BigThreads = 256;
+__global__ void __launch_bounds__(kC4BigThreads) c4_big_kernel(C4Args a) {
   __shared__ uint32_t s_task, s_nt, s_cnt;
-  __shared__ uint32_t s_x[512];
+  __shared__ uint32_t s_x[kC4BigThreads];
   const uint32_t tid = threadIdx.x, lane = tid & 31;
   uint32_t *tally = a.pool + (size_t)blockIdx.x * 2 * a.n;
   uint32_t *touched = tally + a.n;
@@ -202,6 +203,8 @@ static int ensure_c4_tasks(gpm_graph *g, cudaStream_t st) {
   return GPM_OK;
 }
 
+int gpm_build_c4_tasks(gpm_graph *g, cudaStream_t st) { return ensure_c4_tasks(g, st); }
+
 int gpm_launch_cycles4(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigned long long *acc, cudaStream_t st) {
   GPM_TRY(ensure_c4_tasks(g, st));
   unsigned int *queues = reinterpret_cast<unsigned int *>(g->work + WK_QUEUE0) + 4;
@@ -236,20 +239,28 @@ int gpm_launch_cycles4(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigne
     b.tasks = g->c4_tasks + g->c4_begin[1];
     b.ntasks = nbig;
     b.queue = queues + 1;
-    const size_t slots = (size_t)std::min<uint32_t>((uint32_t)sms, nbig);
+    // hub roots are bound by the latency of their global tally atomics: keep many
+    // CTAs resident (each with its own tally slot), within a memory budget
+    int per_sm = 0;
+    GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c4_big_kernel, kC4BigThreads, 0));
+    const size_t slot_bytes = 2 * (size_t)std::max<uint32_t>(g->n, 1) * 4;
+    const size_t budget = (size_t)16 << 30;
+    size_t slots = (size_t)sms * (size_t)std::max(1, std::min(per_sm, 8));
+    slots = std::min(slots, std::max<size_t>(1, budget / slot_bytes));
+    slots = std::min(slots, (size_t)nbig);
     if (g->tally_slots < slots) {
       if (g->tally_pool) {
         cudaFree(g->tally_pool);
-        g->device_bytes -= g->tally_slots * 2 * (size_t)g->n * 4;
+        g->device_bytes -= g->tally_slots * slot_bytes;
         g->tally_pool = nullptr;
         g->tally_slots = 0;
       }
-      GPM_TRY(gpm_graph_alloc(g, (void **)&g->tally_pool, slots * 2 * (size_t)g->n * 4));
-      GPM_CUDA(cudaMemsetAsync(g->tally_pool, 0, slots * 2 * (size_t)g->n * 4, st));
+      GPM_TRY(gpm_graph_alloc(g, (void **)&g->tally_pool, slots * slot_bytes));
+      GPM_CUDA(cudaMemsetAsync(g->tally_pool, 0, slots * slot_bytes, st));
       g->tally_slots = slots;
     }
     b.pool = g->tally_pool;
-    GPM_LAUNCH("c4_big_kernel", st, c4_big_kernel<<<(unsigned)slots, 512, 0, st>>>(b));
+    GPM_LAUNCH("c4_big_kernel", st, c4_big_kernel<<<(unsigned)slots, kC4BigThreads, 0, st>>>(b));
     GPM_CUDA(cudaGetLastError());
   }
   return GPM_OK;

@@ -111,7 +111,9 @@ __device__ __forceinline__ unsigned long long c4_root_cta(const uint64_t *__rest
     }
     __syncthreads();
   }
-  __threadfence_block();
+  // the touched list is read below past L1 (ld.cg): make every thread's
+  // entries reach L2 before the barrier
+  __threadfence();
   __syncthreads();
   const uint32_t ntouched = *s_nt;
   unsigned long long acc = 0;

@@ -12,6 +12,11 @@
 // ran it forms the counts and writes a completion record to a ring in mapped
 // host memory; the host polls that ring.
 //
+// Two rings: requests with at most kExpressItems items go to an express ring
+// that the kernel drains first, so small requests are not queued behind the
+// thousands of items of a large one (each request stays in one ring, which
+// keeps its triangle items ahead of its edge-term items).
+//
 // Admission is by memory footprint: a request needs a free slot, room in the
 // item ring and, for 4-motif queries, a per-arc triangle-count block (4 bytes
 // per edge) from a fixed device arena; otherwise it waits in a host FIFO and
@@ -49,9 +54,11 @@ struct Completion {
   unsigned long long counts[6];
 };
 
+constexpr uint64_t kExpressItems = 64;
+
 struct Ctl {
-  unsigned long long head;  // next item position to claim
-  unsigned long long tail;  // items published by the host
+  unsigned long long head[2];  // next item position to claim, per ring (0 express, 1 bulk)
+  unsigned long long tail[2];  // items published by the host, per ring
   unsigned long long comp_tail;
   unsigned int stop;
   unsigned int status;
@@ -59,8 +66,8 @@ struct Ctl {
 
 struct ServeArgs {
   SlotState *slots;
-  const Item *ring;
-  unsigned long long ring_cap;
+  const Item *ring[2];
+  unsigned long long ring_cap[2];
   Ctl *ctl;
   Completion *comp;  // mapped host memory
   unsigned int comp_cap;
@@ -82,18 +89,23 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(ServeArgs a) {
       unsigned long long idle = 0;
       for (;;) {
         if (*(volatile unsigned int *)&a.ctl->stop) break;
-        const unsigned long long h = *(volatile unsigned long long *)&a.ctl->head;
-        const unsigned long long t = *(volatile unsigned long long *)&a.ctl->tail;
-        if (h < t) {
-          if (atomicCAS(&a.ctl->head, h, h + 1) == h) {
-            const volatile uint32_t *src = reinterpret_cast<const volatile uint32_t *>(a.ring + (h % a.ring_cap));
-            uint32_t *dst = reinterpret_cast<uint32_t *>(&s_item);
-            for (int w = 0; w < 4; ++w) dst[w] = src[w];
-            s_ok = 1;
-            break;
+        bool busy = false;
+        for (int r = 0; r < 2 && !s_ok; ++r) {
+          const unsigned long long h = *(volatile unsigned long long *)&a.ctl->head[r];
+          const unsigned long long t = *(volatile unsigned long long *)&a.ctl->tail[r];
+          if (h < t) {
+            busy = true;
+            if (atomicCAS(&a.ctl->head[r], h, h + 1) == h) {
+              const volatile uint32_t *src =
+                  reinterpret_cast<const volatile uint32_t *>(a.ring[r] + (h % a.ring_cap[r]));
+              uint32_t *dst = reinterpret_cast<uint32_t *>(&s_item);
+              for (int w = 0; w < 4; ++w) dst[w] = src[w];
+              s_ok = 1;
+            }
           }
-          continue;
         }
+        if (s_ok) break;
+        if (busy) continue;  // lost a race: retry at once
         __nanosleep(2000);
         if (++idle > a.idle_limit) break;
       }
@@ -135,20 +147,22 @@ struct gpm_server {
   bool launched = false;
   // device state
   SlotState *d_slots = nullptr;
-  Item *d_ring = nullptr;
+  Item *d_ring[2] = {nullptr, nullptr};
   Ctl *d_ctl = nullptr;
   uint32_t *d_arena = nullptr;
   uint32_t *tally_pool = nullptr;
   uint64_t tally_slot_words = 0;
+  uint32_t *lg_pool = nullptr;
+  ItemEnv env{};
   // host mapped / pinned
   Completion *h_comp = nullptr;
   Completion *d_comp = nullptr;
   Item *h_stage = nullptr;
   SlotState *h_slot_stage = nullptr;
-  unsigned long long *h_tail = nullptr;
+  unsigned long long *h_tail = nullptr;  // 2 words
   // sizes
   uint32_t nslots = 0, comp_cap = 0;
-  uint64_t ring_cap = 0, stage_cap = 0, arena_words = 0;
+  uint64_t ring_cap[2] = {0, 0}, stage_cap = 0, arena_words = 0;
   size_t smem = 0;
   int grid = 0;
   uint32_t cta_maxd = 0, cta_W = 0;
@@ -160,6 +174,7 @@ struct gpm_server {
   struct Live {
     bool busy = false;
     Req req;
+    int ring = 0;
     uint64_t ring_begin = 0, ring_end = 0;
     uint64_t arena_off = 0, arena_len = 0;
   };
@@ -169,7 +184,7 @@ struct gpm_server {
   std::deque<gpm_completion_t> instant;  // requests with no device work (empty task sets)
   uint32_t max_pending = 1u << 20;
   std::map<uint64_t, uint64_t> arena_free;  // offset -> length (words)
-  uint64_t tail = 0;
+  uint64_t tail[2] = {0, 0};
   uint64_t comp_read = 0;
   uint32_t roots_per_item = 64, verts_per_item = 8192;
   // per (graph, kind) item templates with q = 0
@@ -210,10 +225,10 @@ void arena_give(gpm_server *s, uint64_t off, uint64_t words) {
   }
 }
 
-uint64_t oldest_ring_begin(gpm_server *s) {
-  uint64_t m = s->tail;
+uint64_t oldest_ring_begin(gpm_server *s, int r) {
+  uint64_t m = s->tail[r];
   for (auto &l : s->live)
-    if (l.busy) m = std::min(m, l.ring_begin);
+    if (l.busy && l.ring == r) m = std::min(m, l.ring_begin);
   return m;
 }
 
@@ -245,17 +260,18 @@ int ensure_running(gpm_server *s) {
   if (running) return GPM_OK;
   ServeArgs a{};
   a.slots = s->d_slots;
-  a.ring = s->d_ring;
-  a.ring_cap = s->ring_cap;
+  for (int r = 0; r < 2; ++r) {
+    a.ring[r] = s->d_ring[r];
+    a.ring_cap[r] = s->ring_cap[r];
+  }
   a.ctl = s->d_ctl;
   a.comp = s->d_comp;
   a.comp_cap = s->comp_cap;
   a.idle_limit = 10000;  // about 20 ms of 2 us polls without work
+  a.env = s->env;
   a.env.status = &s->d_ctl->status;
   a.env.tally_pool = s->tally_pool;
   a.env.tally_slot_words = s->tally_slot_words;
-  a.env.cta_maxd = s->cta_maxd;
-  a.env.cta_W = s->cta_W;
   GPM_LAUNCH("serve_kernel", s->exec, serve_kernel<<<s->grid, kThreads, s->smem, s->exec>>>(a));
   GPM_CUDA(cudaGetLastError());
   GPM_CUDA(cudaEventRecord(s->kernel_done, s->exec));
@@ -283,7 +299,8 @@ int try_admit(gpm_server *s, const gpm_server::Req &r, int *rc) {
     s->instant.push_back(c);
     return 1;
   }
-  if (s->tail + nitems - oldest_ring_begin(s) > s->ring_cap) return 0;
+  const int ring = nitems <= kExpressItems ? 0 : 1;
+  if (s->tail[ring] + nitems - oldest_ring_begin(s, ring) > s->ring_cap[ring]) return 0;
   uint64_t off = 0, words = 0;
   if (r.kind == GPM_QUERY_MOTIF4) {
     words = (std::max<uint64_t>(g->m, 1) + 63) & ~63ull;
@@ -296,8 +313,9 @@ int try_admit(gpm_server *s, const gpm_server::Req &r, int *rc) {
   l.req = r;
   l.arena_off = off;
   l.arena_len = words;
-  l.ring_begin = s->tail;
-  l.ring_end = s->tail + nitems;
+  l.ring = ring;
+  l.ring_begin = s->tail[ring];
+  l.ring_end = s->tail[ring] + nitems;
   // slot state: descriptor, zero accumulators, item counters
   SlotState &st = s->h_slot_stage[slot];
   std::memset(&st, 0, sizeof(st));
@@ -327,21 +345,23 @@ int try_admit(gpm_server *s, const gpm_server::Req &r, int *rc) {
   // items, with this slot, into the ring (two pieces when it wraps)
   uint64_t done = 0;
   while (e == cudaSuccess && done < nitems) {
-    const uint64_t pos = s->tail + done;
-    const uint64_t ring_i = pos % s->ring_cap;
-    const uint64_t chunk = std::min<uint64_t>({nitems - done, s->ring_cap - ring_i, s->stage_cap});
+    const uint64_t pos = s->tail[ring] + done;
+    const uint64_t ring_i = pos % s->ring_cap[ring];
+    const uint64_t chunk = std::min<uint64_t>({nitems - done, s->ring_cap[ring] - ring_i, s->stage_cap});
     for (uint64_t k = 0; k < chunk; ++k) {
       s->h_stage[k] = tmpl[done + k];
       s->h_stage[k].q = slot;
     }
-    e = cudaMemcpyAsync(s->d_ring + ring_i, s->h_stage, sizeof(Item) * chunk, cudaMemcpyHostToDevice, s->copy);
+    e = cudaMemcpyAsync(s->d_ring[ring] + ring_i, s->h_stage, sizeof(Item) * chunk, cudaMemcpyHostToDevice,
+                        s->copy);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy);  // the staging buffer is reused
     done += chunk;
   }
-  s->tail += nitems;
-  *s->h_tail = s->tail;
+  s->tail[ring] += nitems;
+  s->h_tail[ring] = s->tail[ring];
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&s->d_ctl->tail, s->h_tail, sizeof(unsigned long long), cudaMemcpyHostToDevice, s->copy);
+    e = cudaMemcpyAsync(&s->d_ctl->tail[ring], &s->h_tail[ring], sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                        s->copy);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy);
   if (e != cudaSuccess) {
     *rc = gpm_cuda_fail(e, "server admission");
@@ -362,7 +382,7 @@ int admit_pending(gpm_server *s) {
 
 void free_server(gpm_server *s) {
   if (s->exec) cudaStreamSynchronize(s->exec);
-  void *dev[] = {s->d_slots, s->d_ring, s->d_ctl, s->d_arena, s->tally_pool};
+  void *dev[] = {s->d_slots, s->d_ring[0], s->d_ring[1], s->d_ctl, s->d_arena, s->tally_pool, s->lg_pool};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (s->h_comp) cudaFreeHost(s->h_comp);
@@ -407,22 +427,24 @@ int gpm_server_start(const gpm_graph_t *graphs, uint32_t ngraphs, const gpm_serv
     if (rc) return fail(rc);
     s->graphs.push_back(g);
     nmax = std::max(nmax, g->n);
-    s->cta_maxd = std::max(s->cta_maxd, g->cls_maxdeg[CLS_CTA]);
+    s->cta_maxd = std::max(s->cta_maxd, cta_root_maxd(g));
   }
   if (cudaStreamSynchronize(s->copy) != cudaSuccess) return fail(gpm_fail(GPM_E_DEVICE, "graph preparation"));
   s->nslots = nslots;
   s->comp_cap = nslots;
-  s->ring_cap = ring_items;
+  s->ring_cap[0] = 1u << 20;
+  s->ring_cap[1] = ring_items;
   s->stage_cap = 1u << 16;
   s->arena_words = arena_bytes / 4;
   if (cudaMalloc(&s->d_slots, sizeof(SlotState) * nslots) != cudaSuccess ||
-      cudaMalloc(&s->d_ring, sizeof(Item) * s->ring_cap) != cudaSuccess ||
+      cudaMalloc(&s->d_ring[0], sizeof(Item) * s->ring_cap[0]) != cudaSuccess ||
+      cudaMalloc(&s->d_ring[1], sizeof(Item) * s->ring_cap[1]) != cudaSuccess ||
       cudaMalloc(&s->d_ctl, sizeof(Ctl)) != cudaSuccess ||
       cudaMalloc(&s->d_arena, sizeof(uint32_t) * std::max<uint64_t>(s->arena_words, 1)) != cudaSuccess ||
       cudaHostAlloc(&s->h_comp, sizeof(Completion) * s->comp_cap, cudaHostAllocMapped) != cudaSuccess ||
       cudaHostAlloc(&s->h_stage, sizeof(Item) * s->stage_cap, cudaHostAllocDefault) != cudaSuccess ||
       cudaHostAlloc(&s->h_slot_stage, sizeof(SlotState) * nslots, cudaHostAllocDefault) != cudaSuccess ||
-      cudaHostAlloc(&s->h_tail, sizeof(unsigned long long), cudaHostAllocDefault) != cudaSuccess) {
+      cudaHostAlloc(&s->h_tail, 2 * sizeof(unsigned long long), cudaHostAllocDefault) != cudaSuccess) {
     cudaGetLastError();
     return fail(gpm_fail(GPM_E_OOM, "server allocation failed"));
   }
@@ -434,10 +456,12 @@ int gpm_server_start(const gpm_graph_t *graphs, uint32_t ngraphs, const gpm_serv
   s->arena_free[0] = s->arena_words;
   s->live.resize(nslots);
   for (uint32_t i = 0; i < nslots; ++i) s->free_slots.push_back(nslots - 1 - i);
-  // kernel shape: the union of the item types' shared memory needs
-  s->cta_W = std::max<uint32_t>(1, (s->cta_maxd + 31) / 32);
+  // kernel shape: the union of the item types' shared memory needs (CTA roots
+  // above the shared-memory bound use global slots)
+  const uint32_t smem_maxd = std::min(s->cta_maxd, kItemCtaSmemMaxD);
+  const uint32_t smem_W = std::max<uint32_t>(1, (smem_maxd + 31) / 32);
   const size_t warp_bytes = (size_t)gpm_dev::warp_words(kWarpMaxD, true) * 4 * kWarps;
-  const size_t cta_bytes = s->cta_maxd ? gpm_dev::cta_words(s->cta_maxd, s->cta_W) * 4 : 0;
+  const size_t cta_bytes = smem_maxd ? gpm_dev::cta_words(smem_maxd, smem_W) * 4 : 0;
   const size_t c4_bytes = (size_t)kWarps * 2 * gpm_dev::kC4HashSlots * 4;
   s->smem = std::max(warp_bytes, std::max(cta_bytes, c4_bytes));
   if (cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem) != cudaSuccess)
@@ -447,6 +471,10 @@ int gpm_server_start(const gpm_graph_t *graphs, uint32_t ngraphs, const gpm_serv
       per_sm < 1)
     per_sm = 1;
   s->grid = gpm_num_sms(s->device) * per_sm;
+  {
+    int rc = setup_cta_items(s->env, s->cta_maxd, s->grid, &s->lg_pool);
+    if (rc) return fail(rc);
+  }
   s->tally_slot_words = 2 * (uint64_t)nmax;
   if (cudaMalloc(&s->tally_pool, sizeof(uint32_t) * s->tally_slot_words * s->grid) != cudaSuccess) {
     cudaGetLastError();
@@ -468,7 +496,7 @@ int gpm_server_submit(gpm_server_t s, uint32_t graph, uint32_t kind, uint64_t ta
   // a request that can never fit is refused outright
   uint32_t sc, al;
   const uint64_t nitems = items_for(s, graph, kind, &sc, &al).size();
-  if (nitems > s->ring_cap) return gpm_fail(GPM_E_INVALID_ARG, "request needs more items than the ring holds");
+  if (nitems > s->ring_cap[1]) return gpm_fail(GPM_E_INVALID_ARG, "request needs more items than the ring holds");
   if (kind == GPM_QUERY_MOTIF4 && ((std::max<uint64_t>(s->graphs[graph]->m, 1) + 63) & ~63ull) > s->arena_words)
     return gpm_fail(GPM_E_INVALID_ARG, "request needs more arena memory than the server has");
   if (s->pending.empty()) {
