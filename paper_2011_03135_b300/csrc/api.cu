@@ -41,7 +41,7 @@ unsigned int *status_of(gpm_graph *g) { return reinterpret_cast<unsigned int *>(
 
 void free_graph(gpm_graph *g) {
   void *ptrs[] = {g->rowptr, g->col,   g->deg,        g->drow,       g->dcol,     g->tasks,
-                  g->work,   g->t_edge, g->xl_pool, g->tally_pool, g->list_scratch, g->c4_tasks,
+                  g->work,   g->t_edge, g->xl_pool, g->tally_pool, g->list_scratch, g->c4_tasks, g->c4_bucket_buf,
                   g->prep_outdeg, g->prep_tiles, g->prep_keys};
   for (void *p : ptrs)
     if (p) cudaFree(p);

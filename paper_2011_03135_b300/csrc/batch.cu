@@ -90,6 +90,8 @@ struct gpm_batch {
   uint32_t *tally_pool = nullptr;
   uint64_t tally_slot_words = 0;
   uint32_t *lg_pool = nullptr;
+  uint32_t *c4_buf = nullptr;
+  uint32_t c4_maxb = 0;
   ItemEnv env{};
   uint64_t *h_out = nullptr;  // pinned
   std::vector<uint32_t *> own_t_edge;  // per-arc buffers of repeated motif-4 graphs
@@ -109,7 +111,7 @@ namespace {
 void free_batch(gpm_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  void *dev[] = {b->d_qs, b->d_items, b->d_acc, b->d_out, b->d_left, b->d_head, b->tally_pool, b->lg_pool};
+  void *dev[] = {b->d_qs, b->d_items, b->d_acc, b->d_out, b->d_left, b->d_head, b->tally_pool, b->lg_pool, b->c4_buf};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (b->h_out) cudaFreeHost(b->h_out);
@@ -314,6 +316,7 @@ int gpm_batch_create(const gpm_query_t *queries, uint32_t nq, gpm_batch_t *out) 
     q.m = g->m;
     nmax = std::max(nmax, g->n);
     b->cta_maxd = std::max(b->cta_maxd, cta_root_maxd(g));
+    if (q.kind == GPM_QUERY_MOTIF4) b->c4_maxb = std::max(b->c4_maxb, g->c4_bucket_maxb);
   }
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return fail(gpm_fail(GPM_E_DEVICE, "batch preparation"));
   // arenas
@@ -336,12 +339,7 @@ int gpm_batch_create(const gpm_query_t *queries, uint32_t nq, gpm_batch_t *out) 
   }
   // shared memory: the largest of the item types' needs (CTA roots above the
   // shared-memory bound use global slots)
-  const uint32_t smem_maxd = std::min(b->cta_maxd, kItemCtaSmemMaxD);
-  const uint32_t smem_W = std::max<uint32_t>(1, (smem_maxd + 31) / 32);
-  const size_t warp_bytes = warp_region_words() * 4 * kWarps;
-  const size_t cta_bytes = smem_maxd ? gpm_dev::cta_words(smem_maxd, smem_W) * 4 : 0;
-  const size_t c4_bytes = need_c4 ? (size_t)kWarps * 2 * gpm_dev::kC4HashSlots * 4 : 0;
-  b->smem = std::max(warp_bytes, std::max(cta_bytes, c4_bytes));
+  b->smem = item_smem_bytes(std::min(b->cta_maxd, kItemCtaSmemMaxD), need_c4);
   if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem) != cudaSuccess)
     return fail(gpm_fail(GPM_E_DEVICE, "shared memory attribute"));
   int per_sm = 0;
@@ -351,6 +349,14 @@ int gpm_batch_create(const gpm_query_t *queries, uint32_t nq, gpm_batch_t *out) 
   b->grid = gpm_num_sms(b->device) * per_sm;
   rc = setup_cta_items(b->env, b->cta_maxd, b->grid, &b->lg_pool);
   if (rc) return fail(rc);
+  if (need_c4 && b->c4_maxb) {
+    b->env.c4_buf_words = ((uint64_t)b->c4_maxb + 63) & ~63ull;
+    if (cudaMalloc(&b->c4_buf, sizeof(uint32_t) * b->env.c4_buf_words * b->grid) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(gpm_fail(GPM_E_OOM, "4-cycle bucket buffer allocation failed"));
+    }
+    b->env.c4_buf = b->c4_buf;
+  }
   if (need_c4) {
     b->tally_slot_words = 2 * (uint64_t)nmax;
     if (cudaMalloc(&b->tally_pool, sizeof(uint32_t) * b->tally_slot_words * b->grid) != cudaSuccess) {

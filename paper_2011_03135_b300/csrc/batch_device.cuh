@@ -13,7 +13,9 @@
 
 namespace gpm_item {
 
-enum ItemType : uint32_t { IT_LG_WARP = 0, IT_LG_CTA = 1, IT_C4_SMALL = 2, IT_C4_BIG = 3, IT_EDGE = 4 };
+enum ItemType : uint32_t {
+  IT_LG_WARP = 0, IT_LG_CTA = 1, IT_C4_SMALL = 2, IT_C4_BIG = 3, IT_EDGE = 4, IT_C4_BUCKET = 5
+};
 
 struct Item {
   uint32_t type, q, lo, hi;
@@ -56,6 +58,8 @@ struct ItemEnv {
   uint32_t *lg_pool;         // global-memory bitmap slots, one per CTA
   uint64_t lg_slot_words;
   uint32_t lg_maxd, lg_W;    // larger roots
+  uint32_t *c4_buf;          // bucketed 4-cycle buffers, one slot per CTA
+  uint64_t c4_buf_words;
 };
 
 // shared memory carve-up: the union of the item types' needs
@@ -129,6 +133,11 @@ __device__ __forceinline__ void run_item(const ItemEnv &a, const QDesc &q, const
       uint32_t *cnt = keys + gpm_dev::kC4HashSlots;
       for (uint32_t t = it.lo + wid; t < it.hi; t += kWarps)
         c4 += gpm_dev::c4_root_warp(q.rowptr, q.col, q.deg, q.c4_tasks[t], keys, cnt, overflow);
+      break;
+    }
+    case IT_C4_BUCKET: {
+      c4 += gpm_dev::c4_root_bucketed(q.rowptr, q.col, q.deg, q.c4_tasks[it.lo],
+                                      a.c4_buf + (size_t)blockIdx.x * a.c4_buf_words, smem, s_x, s_cnt, overflow);
       break;
     }
     case IT_C4_BIG: {
@@ -229,6 +238,10 @@ inline void append_query_items(const gpm_graph *g, uint32_t kind, uint32_t qi, u
       ++al;
     }
     for (uint32_t t = g->c4_begin[1]; t < g->c4_begin[2]; ++t) {
+      heavy.push_back({IT_C4_BUCKET, qi, t, t + 1});
+      ++al;
+    }
+    for (uint32_t t = g->c4_begin[2]; t < g->c4_begin[3]; ++t) {
       heavy.push_back({IT_C4_BIG, qi, t, t + 1});
       ++al;
     }
@@ -276,6 +289,17 @@ inline int prepare_for_items(gpm_graph *g, bool need_c4, cudaStream_t st) {
     if (rc) return rc;
   }
   return GPM_OK;
+}
+
+// Shared memory of the item kernels: the largest of the item types' needs.
+inline size_t item_smem_bytes(uint32_t smem_cta_maxd, bool need_c4) {
+  const uint32_t W = std::max<uint32_t>(1, (smem_cta_maxd + 31) / 32);
+  const size_t warp_bytes = (size_t)gpm_dev::warp_words(kWarpMaxD, true) * 4 * kWarps;
+  const size_t cta_bytes = smem_cta_maxd ? gpm_dev::cta_words(smem_cta_maxd, W) * 4 : 0;
+  const size_t c4_bytes = need_c4 ? std::max<size_t>((size_t)kWarps * 2 * gpm_dev::kC4HashSlots * 4,
+                                                     (size_t)gpm_dev::c4_bucket_smem_words(kWarps) * 4)
+                                  : 0;
+  return std::max(warp_bytes, std::max(cta_bytes, c4_bytes));
 }
 
 // Largest CTA-root out-degree of a prepared graph (CTA and global classes).

@@ -104,8 +104,12 @@ struct gpm_graph {
   size_t list_scratch_bytes = 0;
   // 4-cycle roots grouped by wedge bound (small: shared-memory hash per
   // warp; big: dense global tally per CTA)
+  // classes: [0,1) small (warp hash), [1,2) bucketed, [2,3) dense tally
   uint32_t *c4_tasks = nullptr;
-  uint32_t c4_begin[3] = {0, 0, 0};
+  uint32_t c4_begin[4] = {0, 0, 0, 0};
+  uint32_t c4_bucket_maxb = 0;  // largest wedge bound among bucketed roots
+  uint32_t *c4_bucket_buf = nullptr;
+  size_t c4_bucket_bytes = 0;
   bool c4_ready = false;
 
   size_t device_bytes = 0;

@@ -68,7 +68,8 @@ __global__ void edge_terms_kernel(const uint64_t *__restrict__ drow, const uint3
 constexpr uint32_t kSmallBound = gpm_dev::kC4SmallBound;
 constexpr uint32_t kHashSlots = gpm_dev::kC4HashSlots;
 
-// wedge bound B(v0) = sum of d_x over neighbours x before v0; class 0 small, 1 big
+// wedge bound B(v0) = sum of d_x over neighbours x before v0; class 0 small
+// (warp hash), 1 bucketed, 2 dense tally
 __global__ void c4_bound_kernel(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
                                 const uint32_t *__restrict__ deg, uint32_t n, uint32_t *__restrict__ counts,
                                 uint32_t *__restrict__ tasks, uint32_t *__restrict__ cursors, int fill) {
@@ -85,9 +86,13 @@ __global__ void c4_bound_kernel(const uint64_t *__restrict__ rowptr, const uint3
     }
     b = warp_sum(b);
     if (lane == 0 && b >= 3) {  // a cycle needs two wedges, each scanning v0 itself plus w
-      const int c = (b <= kSmallBound) ? 0 : 1;
-      if (fill) tasks[atomicAdd(&cursors[c], 1u)] = (uint32_t)v;
-      else atomicAdd(&counts[c], 1u);
+      const int c = (b <= kSmallBound) ? 0 : (b <= gpm_dev::kC4BucketMaxBound ? 1 : 2);
+      if (fill) {
+        tasks[atomicAdd(&cursors[c], 1u)] = (uint32_t)v;
+      } else {
+        atomicAdd(&counts[c], 1u);
+        if (c == 1) atomicMax(&counts[3], (uint32_t)b);
+      }
     }
   }
 }
@@ -151,6 +156,30 @@ __global__ void __launch_bounds__(kC4BigThreads) c4_big_kernel(C4Args a) {
   if (lane == 0 && acc) atomicAdd(&a.acc[ACC_C4], acc);
 }
 
+// one CTA per large root, bucketed aggregation (buffer slot per CTA)
+constexpr int kC4BucketThreads = 512;
+__global__ void __launch_bounds__(kC4BucketThreads) c4_bucket_kernel(C4Args a, uint64_t slot_words) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ uint32_t s_task, s_cnt;
+  __shared__ uint32_t s_x[kC4BucketThreads];
+  uint32_t *buf = a.pool + (size_t)blockIdx.x * slot_words;
+  unsigned long long acc = 0;
+  bool overflow = false;
+  for (;;) {
+    if (threadIdx.x == 0) s_task = atomicAdd(a.queue, 1u);
+    __syncthreads();
+    const uint32_t task = s_task;
+    __syncthreads();
+    if (task >= a.ntasks) break;
+    const uint32_t v0 = a.tasks[task];
+    if (v0 < a.root_lo || v0 >= a.root_hi) continue;
+    acc += gpm_dev::c4_root_bucketed(a.rowptr, a.col, a.deg, v0, buf, smem, s_x, &s_cnt, overflow);
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(&a.acc[ACC_C4], acc);
+  if (__syncthreads_or(overflow) && threadIdx.x == 0) atomicOr(a.status, ST_CAPACITY);
+}
+
 // ---------------------------------------------------------------------------
 // finalize: requested counts from the accumulators (one thread)
 // ---------------------------------------------------------------------------
@@ -179,23 +208,27 @@ int gpm_launch_edge_terms(gpm_graph *g, bool use_t_edge, uint32_t root_lo, uint3
 static int ensure_c4_tasks(gpm_graph *g, cudaStream_t st) {
   if (g->c4_ready) return GPM_OK;
   if (!g->c4_tasks) GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4_tasks, sizeof(uint32_t) * std::max<uint32_t>(g->n, 1)));
-  uint32_t *tmp = reinterpret_cast<uint32_t *>(g->work + WK_MISC);
-  GPM_CUDA(cudaMemsetAsync(tmp, 0, 4 * sizeof(uint32_t), st));
+  uint32_t *tmp = reinterpret_cast<uint32_t *>(g->work + WK_MISC);  // counts[3], max bound, cursors[3]
+  GPM_CUDA(cudaMemsetAsync(tmp, 0, 8 * sizeof(uint32_t), st));
   const int blocks = gpm_num_sms(g->device) * 8;
   if (g->n) {
-    GPM_LAUNCH("c4_bound_kernel", st, c4_bound_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->n, tmp, nullptr, nullptr, 0));
+    GPM_LAUNCH("c4_bound_kernel", st,
+               c4_bound_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->n, tmp, nullptr, nullptr, 0));
     GPM_CUDA(cudaGetLastError());
   }
-  uint32_t h[2];
+  uint32_t h[4];
   GPM_CUDA(cudaMemcpyAsync(h, tmp, sizeof(h), cudaMemcpyDeviceToHost, st));
   GPM_CUDA(cudaStreamSynchronize(st));
   g->c4_begin[0] = 0;
   g->c4_begin[1] = h[0];
   g->c4_begin[2] = h[0] + h[1];
-  uint32_t cur[2] = {0, h[0]};
-  GPM_CUDA(cudaMemcpyAsync(tmp + 2, cur, sizeof(cur), cudaMemcpyHostToDevice, st));
+  g->c4_begin[3] = h[0] + h[1] + h[2];
+  g->c4_bucket_maxb = h[3];
+  uint32_t cur[3] = {0, h[0], h[0] + h[1]};
+  GPM_CUDA(cudaMemcpyAsync(tmp + 4, cur, sizeof(cur), cudaMemcpyHostToDevice, st));
   if (g->n) {
-    GPM_LAUNCH("c4_bound_kernel", st, c4_bound_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->n, nullptr, g->c4_tasks, tmp + 2, 1));
+    GPM_LAUNCH("c4_bound_kernel", st,
+               c4_bound_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->n, nullptr, g->c4_tasks, tmp + 4, 1));
     GPM_CUDA(cudaGetLastError());
   }
   GPM_CUDA(cudaStreamSynchronize(st));
@@ -208,7 +241,7 @@ int gpm_build_c4_tasks(gpm_graph *g, cudaStream_t st) { return ensure_c4_tasks(g
 int gpm_launch_cycles4(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigned long long *acc, cudaStream_t st) {
   GPM_TRY(ensure_c4_tasks(g, st));
   unsigned int *queues = reinterpret_cast<unsigned int *>(g->work + WK_QUEUE0) + 4;
-  GPM_CUDA(cudaMemsetAsync(queues, 0, 2 * sizeof(unsigned int), st));
+  GPM_CUDA(cudaMemsetAsync(queues, 0, 3 * sizeof(unsigned int), st));
   C4Args a{};
   a.rowptr = g->rowptr;
   a.col = g->col;
@@ -220,7 +253,8 @@ int gpm_launch_cycles4(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigne
   a.n = g->n;
   const int sms = gpm_num_sms(g->device);
   const uint32_t nsmall = g->c4_begin[1] - g->c4_begin[0];
-  const uint32_t nbig = g->c4_begin[2] - g->c4_begin[1];
+  const uint32_t nbucket = g->c4_begin[2] - g->c4_begin[1];
+  const uint32_t nbig = g->c4_begin[3] - g->c4_begin[2];
   if (nsmall) {
     C4Args s = a;
     s.tasks = g->c4_tasks;
@@ -234,9 +268,37 @@ int gpm_launch_cycles4(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigne
     GPM_LAUNCH("c4_small_kernel", st, c4_small_kernel<<<blocks, 256, smem, st>>>(s));
     GPM_CUDA(cudaGetLastError());
   }
-  if (nbig) {
+  if (nbucket) {
     C4Args b = a;
     b.tasks = g->c4_tasks + g->c4_begin[1];
+    b.ntasks = nbucket;
+    b.queue = queues + 2;
+    const size_t smem = (size_t)gpm_dev::c4_bucket_smem_words(kC4BucketThreads / 32) * 4;
+    GPM_CUDA(cudaFuncSetAttribute(c4_bucket_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c4_bucket_kernel, kC4BucketThreads, smem));
+    const uint64_t slot_words = ((uint64_t)std::max<uint32_t>(g->c4_bucket_maxb, 1) + 63) & ~63ull;
+    size_t slots = (size_t)sms * (size_t)std::max(per_sm, 1);
+    slots = std::min<size_t>(slots, nbucket);
+    const size_t need = slots * slot_words * 4;
+    if (g->c4_bucket_bytes < need) {
+      if (g->c4_bucket_buf) {
+        cudaFree(g->c4_bucket_buf);
+        g->device_bytes -= g->c4_bucket_bytes;
+        g->c4_bucket_buf = nullptr;
+        g->c4_bucket_bytes = 0;
+      }
+      GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4_bucket_buf, need));
+      g->c4_bucket_bytes = need;
+    }
+    b.pool = g->c4_bucket_buf;
+    GPM_LAUNCH("c4_bucket_kernel", st,
+               c4_bucket_kernel<<<(unsigned)slots, kC4BucketThreads, smem, st>>>(b, slot_words));
+    GPM_CUDA(cudaGetLastError());
+  }
+  if (nbig) {
+    C4Args b = a;
+    b.tasks = g->c4_tasks + g->c4_begin[2];
     b.ntasks = nbig;
     b.queue = queues + 1;
     // hub roots are bound by the latency of their global tally atomics: keep many

@@ -127,6 +127,164 @@ __device__ __forceinline__ unsigned long long c4_root_cta(const uint64_t *__rest
   return acc;
 }
 
+// ---------------------------------------------------------------------------
+// 4-cycles of a large root by bucketed aggregation. The wedge ends w of root
+// v0 are first scattered into P hash buckets in a per-CTA global buffer
+// (streaming writes and reads, instead of random read-modify-writes on a dense
+// tally that does not fit in L2); then every warp aggregates whole buckets in a
+// private shared-memory hash table. P is chosen so that a bucket holds about
+// kC4BucketTarget entries on average.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kC4BucketTarget = 256;
+constexpr uint32_t kC4BucketTable = 1024;   // per-warp hash slots
+constexpr uint32_t kC4MaxBuckets = 4096;
+constexpr uint32_t kC4BucketMaxBound = kC4MaxBuckets * 2 * kC4BucketTarget;  // larger roots: dense tally
+
+__device__ __forceinline__ uint32_t c4_bucket_hash(uint32_t w) { return (w * 0x9E3779B1u) >> 7; }
+__device__ __forceinline__ uint32_t c4_slot_hash(uint32_t w) { return (w * 0x85EBCA77u) >> 22; }  // 10 bits
+
+// shared memory words for c4_root_bucketed with nwarps warps
+__host__ __device__ constexpr uint32_t c4_bucket_smem_words(uint32_t nwarps) {
+  return 2 * kC4MaxBuckets + 4 + nwarps * 2 * kC4BucketTable;
+}
+
+// Walk the wedges v0 - x - w (x, w before v0 in the order) of root v0 with the
+// whole CTA; f(w) is called once per wedge. s_x holds blockDim.x words.
+template <typename F>
+__device__ __forceinline__ void c4_walk_wedges(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
+                                               const uint32_t *__restrict__ deg, uint32_t v0, uint32_t *s_x,
+                                               uint32_t *s_cnt, F f) {
+  const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const uint32_t d0 = deg[v0];
+  const uint64_t b0 = rowptr[v0], e0 = rowptr[v0 + 1];
+  for (uint64_t cb = b0; cb < e0; cb += nt) {
+    if (tid == 0) *s_cnt = 0;
+    __syncthreads();
+    const uint64_t ex = cb + tid;
+    if (ex < e0) {
+      const uint32_t x = col[ex];
+      if (precedes(deg[x], x, d0, v0)) s_x[atomicAdd(s_cnt, 1u)] = x;
+    }
+    __syncthreads();
+    const uint32_t cnt = *s_cnt;
+    for (uint32_t xi = wid; xi < cnt; xi += nw) {
+      const uint32_t x = s_x[xi];
+      for (uint64_t e = rowptr[x] + lane; e < rowptr[x + 1]; e += 32) {
+        const uint32_t w = col[e];
+        if (precedes(deg[w], w, d0, v0)) f(w);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// 4-cycles rooted at v0 with bucketed aggregation; buf holds at least the
+// root's wedge bound entries; sm = c4_bucket_smem_words(blockDim.x / 32) words
+// of shared memory. Every thread must call it; returns this thread's part.
+__device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *__restrict__ rowptr,
+                                                               const uint32_t *__restrict__ col,
+                                                               const uint32_t *__restrict__ deg, uint32_t v0,
+                                                               uint32_t *buf, uint32_t *sm, uint32_t *s_x,
+                                                               uint32_t *s_cnt, bool &overflow) {
+  const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  uint32_t *bcnt = sm;                       // [kC4MaxBuckets]: counts, then write cursors
+  uint32_t *boff = sm + kC4MaxBuckets;       // [kC4MaxBuckets + 1]
+  uint32_t *ctl = boff + kC4MaxBuckets + 1;  // [0] bound, [1] next bucket (shares the last word pair)
+  uint32_t *keys = sm + 2 * kC4MaxBuckets + 4 + (size_t)wid * 2 * kC4BucketTable;
+  uint32_t *vals = keys + kC4BucketTable;
+  // wedge bound -> bucket count P (a power of two)
+  if (tid == 0) ctl[0] = 0;
+  __syncthreads();
+  {
+    const uint32_t d0 = deg[v0];
+    unsigned long long b = 0;
+    for (uint64_t e = rowptr[v0] + tid; e < rowptr[v0 + 1]; e += nt) {
+      const uint32_t x = col[e];
+      const uint32_t dx = deg[x];
+      if (precedes(dx, x, d0, v0)) b += dx;
+    }
+    b = warp_sum(b);
+    if (lane == 0 && b) atomicAdd(&ctl[0], (uint32_t)(b > 0xffffffffull ? 0xffffffffull : b));
+  }
+  __syncthreads();
+  const uint32_t bound = ctl[0];
+  uint32_t P = 1;
+  while (P < kC4MaxBuckets && (unsigned long long)P * kC4BucketTarget < bound) P <<= 1;
+  const uint32_t pmask = P - 1;
+  for (uint32_t b = tid; b < P; b += nt) bcnt[b] = 0;
+  __syncthreads();
+  c4_walk_wedges(rowptr, col, deg, v0, s_x, s_cnt, [&](uint32_t w) { atomicAdd(&bcnt[c4_bucket_hash(w) & pmask], 1u); });
+  // exclusive scan of the bucket counts (one warp), cursors = offsets
+  if (wid == 0) {
+    uint32_t carry = 0;
+    for (uint32_t c0 = 0; c0 < P; c0 += 32) {
+      const uint32_t i = c0 + lane;
+      const uint32_t v = (i < P) ? bcnt[i] : 0u;
+      uint32_t incl = v;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+      }
+      if (i < P) {
+        boff[i] = carry + incl - v;
+        bcnt[i] = carry + incl - v;
+      }
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) {
+      boff[P] = carry;
+      ctl[1] = 0;
+    }
+  }
+  __syncthreads();
+  c4_walk_wedges(rowptr, col, deg, v0, s_x, s_cnt,
+                 [&](uint32_t w) { buf[atomicAdd(&bcnt[c4_bucket_hash(w) & pmask], 1u)] = w; });
+  // the buffer is read below by other warps of this CTA (plain loads, CTA scope)
+  __syncthreads();
+  // each warp aggregates whole buckets in its hash table
+  for (uint32_t i = lane; i < kC4BucketTable; i += 32) {
+    keys[i] = kC4Empty;
+    vals[i] = 0;
+  }
+  __syncwarp();
+  unsigned long long acc = 0;
+  for (;;) {
+    uint32_t b = 0;
+    if (lane == 0) b = atomicAdd(&ctl[1], 1u);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    if (b >= P) break;
+    const uint32_t e0 = boff[b], e1 = boff[b + 1];
+    if (e1 - e0 < 2) continue;  // a single wedge closes no cycle
+    for (uint32_t e = e0 + lane; e < e1; e += 32) {
+      const uint32_t w = buf[e];
+      uint32_t h = c4_slot_hash(w);
+      uint32_t probes = 0;
+      for (;;) {
+        const uint32_t k = atomicCAS(&keys[h], kC4Empty, w);
+        if (k == kC4Empty || k == w) {
+          atomicAdd(&vals[h], 1u);
+          break;
+        }
+        h = (h + 1) & (kC4BucketTable - 1);
+        if (++probes >= kC4BucketTable) {
+          overflow = true;
+          break;
+        }
+      }
+    }
+    __syncwarp();
+    for (uint32_t i = lane; i < kC4BucketTable; i += 32) {
+      const unsigned long long c = vals[i];
+      acc += c * (c - (c > 0)) / 2;
+      keys[i] = kC4Empty;
+      vals[i] = 0;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  return acc;
+}
+
 // Local-count terms of vertex u (degree terms by lane 0; arc terms over the
 // out-arcs of u in the orientation, lane-strided). With USE_T the per-arc
 // triangle counts are read (and, with CLEAR_T, reset to zero afterwards).

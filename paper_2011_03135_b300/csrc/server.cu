@@ -153,6 +153,8 @@ struct gpm_server {
   uint32_t *tally_pool = nullptr;
   uint64_t tally_slot_words = 0;
   uint32_t *lg_pool = nullptr;
+  uint32_t *c4_buf = nullptr;
+  uint32_t c4_maxb = 0;
   ItemEnv env{};
   // host mapped / pinned
   Completion *h_comp = nullptr;
@@ -382,7 +384,8 @@ int admit_pending(gpm_server *s) {
 
 void free_server(gpm_server *s) {
   if (s->exec) cudaStreamSynchronize(s->exec);
-  void *dev[] = {s->d_slots, s->d_ring[0], s->d_ring[1], s->d_ctl, s->d_arena, s->tally_pool, s->lg_pool};
+  void *dev[] = {s->d_slots, s->d_ring[0], s->d_ring[1], s->d_ctl, s->d_arena, s->tally_pool, s->lg_pool,
+                 s->c4_buf};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (s->h_comp) cudaFreeHost(s->h_comp);
@@ -428,6 +431,7 @@ int gpm_server_start(const gpm_graph_t *graphs, uint32_t ngraphs, const gpm_serv
     s->graphs.push_back(g);
     nmax = std::max(nmax, g->n);
     s->cta_maxd = std::max(s->cta_maxd, cta_root_maxd(g));
+    s->c4_maxb = std::max(s->c4_maxb, g->c4_bucket_maxb);
   }
   if (cudaStreamSynchronize(s->copy) != cudaSuccess) return fail(gpm_fail(GPM_E_DEVICE, "graph preparation"));
   s->nslots = nslots;
@@ -458,12 +462,7 @@ int gpm_server_start(const gpm_graph_t *graphs, uint32_t ngraphs, const gpm_serv
   for (uint32_t i = 0; i < nslots; ++i) s->free_slots.push_back(nslots - 1 - i);
   // kernel shape: the union of the item types' shared memory needs (CTA roots
   // above the shared-memory bound use global slots)
-  const uint32_t smem_maxd = std::min(s->cta_maxd, kItemCtaSmemMaxD);
-  const uint32_t smem_W = std::max<uint32_t>(1, (smem_maxd + 31) / 32);
-  const size_t warp_bytes = (size_t)gpm_dev::warp_words(kWarpMaxD, true) * 4 * kWarps;
-  const size_t cta_bytes = smem_maxd ? gpm_dev::cta_words(smem_maxd, smem_W) * 4 : 0;
-  const size_t c4_bytes = (size_t)kWarps * 2 * gpm_dev::kC4HashSlots * 4;
-  s->smem = std::max(warp_bytes, std::max(cta_bytes, c4_bytes));
+  s->smem = item_smem_bytes(std::min(s->cta_maxd, kItemCtaSmemMaxD), true);
   if (cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem) != cudaSuccess)
     return fail(gpm_fail(GPM_E_DEVICE, "shared memory attribute"));
   int per_sm = 0;
@@ -474,6 +473,14 @@ int gpm_server_start(const gpm_graph_t *graphs, uint32_t ngraphs, const gpm_serv
   {
     int rc = setup_cta_items(s->env, s->cta_maxd, s->grid, &s->lg_pool);
     if (rc) return fail(rc);
+  }
+  if (s->c4_maxb) {
+    s->env.c4_buf_words = ((uint64_t)s->c4_maxb + 63) & ~63ull;
+    if (cudaMalloc(&s->c4_buf, sizeof(uint32_t) * s->env.c4_buf_words * s->grid) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(gpm_fail(GPM_E_OOM, "4-cycle bucket buffer allocation failed"));
+    }
+    s->env.c4_buf = s->c4_buf;
   }
   s->tally_slot_words = 2 * (uint64_t)nmax;
   if (cudaMalloc(&s->tally_pool, sizeof(uint32_t) * s->tally_slot_words * s->grid) != cudaSuccess) {
