@@ -393,7 +393,9 @@ def run_sl(args):
     if top[0].startswith("c4_"):
         c4ms = sum(v["ms"] for k, v in prof.items() if k.startswith("c4_")) / args.steps
         ach = c4_pass_bytes(g) / (c4ms / 1000.0) / 1e9
-        roof = {"bound": "hbm", "kernel": "c4_small_kernel + c4_big_kernel", "achieved": ach, "peak": peak,
+        c4k = " + ".join(sorted(k for k in prof if k.startswith("c4_") and k.endswith("_kernel")
+                                and k not in ("c4_bound_kernel", "c4_edeg_kernel", "c4_hub_units_kernel")))
+        roof = {"bound": "hbm", "kernel": c4k, "achieved": ach, "peak": peak,
                 "unit": "GB/s", "frac": ach / peak, "traffic": None, "peak_source": peak_kind}
     G.close()
     return {"workload": SL_WORKLOAD, "counts": {"diamond": counts[0], "4-cycle": counts[1]},

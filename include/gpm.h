@@ -362,7 +362,10 @@ typedef struct {
   uint32_t warp_max_degree; /* roots with out-degree <= this run one per warp */
   uint32_t cta_max_degree;  /* ... <= this one per CTA in shared memory; larger: global-memory bitmaps */
   uint32_t blocks_per_sm;   /* persistent grid size multiplier */
-  uint32_t reserved[5];
+  uint32_t c4_hub_bound;    /* 4-cycle roots whose wedge bound (sum of the degrees of their neighbours
+                               before them) exceeds this are counted by the whole GPU a few at a time;
+                               range [513, 1048576], default 1048576 */
+  uint32_t reserved[4];
 } gpm_options_t;
 
 int gpm_set_options(const gpm_options_t *opt);

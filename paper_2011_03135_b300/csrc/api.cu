@@ -42,7 +42,8 @@ unsigned int *status_of(gpm_graph *g) { return reinterpret_cast<unsigned int *>(
 void free_graph(gpm_graph *g) {
   void *ptrs[] = {g->rowptr, g->col,   g->deg,        g->drow,       g->dcol,     g->tasks,
                   g->work,   g->t_edge, g->xl_pool, g->tally_pool, g->list_scratch, g->c4_tasks, g->c4_bucket_buf,
-                  g->prep_outdeg, g->prep_tiles, g->prep_keys};
+                  g->prep_outdeg, g->prep_tiles, g->prep_keys, g->edeg, g->c4_hub_units, g->c4_hub_tally,
+                  g->c4_hub_touched, g->c4_hub_ctr};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete g;
@@ -228,6 +229,11 @@ int gpm_set_options(const gpm_options_t *opt) {
     t.cta_max_degree = opt->cta_max_degree;
   }
   if (opt->blocks_per_sm) t.blocks_per_sm = opt->blocks_per_sm;
+  if (opt->c4_hub_bound) {
+    if (opt->c4_hub_bound <= 512 || opt->c4_hub_bound > 1048576)
+      return gpm_fail(GPM_E_INVALID_ARG, "c4_hub_bound must be in [513, 1048576]");
+    t.c4_hub_bound = opt->c4_hub_bound;
+  }
   return GPM_OK;
 }
 
@@ -237,6 +243,7 @@ int gpm_get_options(gpm_options_t *opt) {
   opt->warp_max_degree = gpm_tune().warp_max_degree;
   opt->cta_max_degree = gpm_tune().cta_max_degree;
   opt->blocks_per_sm = gpm_tune().blocks_per_sm;
+  opt->c4_hub_bound = gpm_tune().c4_hub_bound;
   return GPM_OK;
 }
 

@@ -102,6 +102,7 @@ struct gpm_batch {
   bool tuned = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  uint64_t graph_kernels = 1;  // kernels one replay launches
   std::vector<QDesc> qs;
   double tuned_ms = 0.0;
 };
@@ -128,7 +129,7 @@ void make_items(gpm_batch *b, std::vector<Item> &items) {
   for (uint32_t qi = 0; qi < nq; ++qi) {
     QDesc &q = b->qs[qi];
     append_query_items(b->queries[qi].graph, q.kind, qi, b->roots_per_item, b->verts_per_item, heavy, light, edge,
-                       &q.scatter_items, &q.all_items);
+                       &q.scatter_items, &q.all_items, true);
   }
   items.insert(items.end(), heavy.begin(), heavy.end());
   items.insert(items.end(), light.begin(), light.end());
@@ -181,9 +182,21 @@ int capture(gpm_batch *b) {
   const uint32_t nq = (uint32_t)b->queries.size();
   GPM_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
   cudaMemsetAsync(b->d_head, 0, sizeof(unsigned int), b->stream);
+  // hub-class 4-cycle roots first: whole-GPU launches per query, adding to the
+  // query's accumulator before the persistent kernel finalises it
+  b->graph_kernels = 1;
+  int hub_rc = GPM_OK;
+  for (uint32_t qi = 0; qi < nq && hub_rc == GPM_OK; ++qi) {
+    gpm_graph *g = b->queries[qi].graph;
+    if (b->qs[qi].kind != GPM_QUERY_MOTIF4 || g->c4_begin[3] == g->c4_begin[2]) continue;
+    uint32_t nl = 0;
+    hub_rc = gpm_c4_hub_enqueue(g, 0, g->n, b->d_acc + (size_t)qi * ACC_WORDS, b->stream, &nl);
+    b->graph_kernels += nl;
+  }
   GPM_LAUNCH("batch_kernel", b->stream, batch_kernel<<<b->grid, kThreads, b->smem, b->stream>>>(a));
   cudaMemcpyAsync(b->h_out, b->d_out, sizeof(uint64_t) * 6 * nq, cudaMemcpyDeviceToHost, b->stream);
   cudaError_t e = cudaStreamEndCapture(b->stream, &b->graph);
+  if (hub_rc != GPM_OK) return hub_rc;
   if (e != cudaSuccess) return gpm_cuda_fail(e, "batch capture");
   GPM_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
   return GPM_OK;
@@ -198,7 +211,7 @@ int replay(gpm_batch *b, float *ms) {
     GPM_CUDA(cudaEventRecord(e0, b->stream));
   }
   GPM_CUDA(cudaGraphLaunch(b->exec, b->stream));
-  gpm_note_launches(1);
+  gpm_note_launches(b->graph_kernels);
   if (ms) GPM_CUDA(cudaEventRecord(e1, b->stream));
   GPM_CUDA(cudaStreamSynchronize(b->stream));
   if (ms) {
@@ -274,7 +287,7 @@ int gpm_batch_create(const gpm_query_t *queries, uint32_t nq, gpm_batch_t *out) 
     gpm_graph *g = queries[i].graph;
     if (!g) return fail(gpm_fail(GPM_E_INVALID_ARG, "null graph in batch"));
     std::lock_guard<std::mutex> lk(g->mu);
-    int rc = prepare_for_items(g, queries[i].kind == GPM_QUERY_MOTIF4, b->stream);
+    int rc = prepare_for_items(g, queries[i].kind == GPM_QUERY_MOTIF4, b->stream, true);
     if (rc) return fail(rc);
     QDesc &q = b->qs[i];
     std::memset(&q, 0, sizeof(q));
@@ -312,6 +325,7 @@ int gpm_batch_create(const gpm_query_t *queries, uint32_t nq, gpm_batch_t *out) 
     }
     q.tasks = g->tasks;
     q.c4_tasks = g->c4_tasks;
+    q.edeg = g->edeg;
     q.n = g->n;
     q.m = g->m;
     nmax = std::max(nmax, g->n);

@@ -31,6 +31,7 @@ struct QDesc {
   uint32_t *t_edge;
   const uint32_t *tasks;     // LG root tasks of the graph (class order)
   const uint32_t *c4_tasks;  // 4-cycle roots
+  const uint32_t *edeg;      // degree of col[e] per CSR entry (4-cycle wedge walks)
   unsigned long long *acc;   // ACC_WORDS accumulators
   unsigned long long *out;   // 6 results
   unsigned int *left;        // [0] scatter items left, [1] items left
@@ -132,11 +133,11 @@ __device__ __forceinline__ void run_item(const ItemEnv &a, const QDesc &q, const
       uint32_t *keys = smem + (size_t)wid * 2 * gpm_dev::kC4HashSlots;
       uint32_t *cnt = keys + gpm_dev::kC4HashSlots;
       for (uint32_t t = it.lo + wid; t < it.hi; t += kWarps)
-        c4 += gpm_dev::c4_root_warp(q.rowptr, q.col, q.deg, q.c4_tasks[t], keys, cnt, overflow);
+        c4 += gpm_dev::c4_root_warp(q.rowptr, q.col, q.deg, q.edeg, q.c4_tasks[t], keys, cnt, overflow);
       break;
     }
     case IT_C4_BUCKET: {
-      c4 += gpm_dev::c4_root_bucketed(q.rowptr, q.col, q.deg, q.c4_tasks[it.lo],
+      c4 += gpm_dev::c4_root_bucketed(q.rowptr, q.col, q.deg, q.edeg, q.c4_tasks[it.lo],
                                       a.c4_buf + (size_t)blockIdx.x * a.c4_buf_words, smem, s_x, s_cnt, overflow);
       break;
     }
@@ -145,7 +146,7 @@ __device__ __forceinline__ void run_item(const ItemEnv &a, const QDesc &q, const
       // the slot holds the tally in its first half and the touched list in its
       // second half for every query size: a smaller query's touched entries
       // must never land in a larger query's tally range
-      c4 += gpm_dev::c4_root_cta(q.rowptr, q.col, q.deg, q.c4_tasks[it.lo], tally, tally + a.tally_slot_words / 2,
+      c4 += gpm_dev::c4_root_cta(q.rowptr, q.col, q.deg, q.edeg, q.c4_tasks[it.lo], tally, tally + a.tally_slot_words / 2,
                                  s_x, s_cnt, s_nt);
       break;
     }
@@ -217,9 +218,11 @@ __device__ __forceinline__ unsigned int finalize_query(const QDesc &q, unsigned 
 // Heavy items (one CTA root each) go to `heavy`, ranges of warp roots to
 // `light`, vertex ranges of local-count terms to `edge`. Returns the number
 // of items and of triangle-scatter items through *all and *scatter.
+// With hub_phase, the hub-class 4-cycle roots get no items: they are counted
+// by separate whole-GPU launches ahead of the persistent kernel.
 inline void append_query_items(const gpm_graph *g, uint32_t kind, uint32_t qi, uint32_t roots_per_item,
                                uint32_t verts_per_item, std::vector<Item> &heavy, std::vector<Item> &light,
-                               std::vector<Item> &edge, uint32_t *scatter, uint32_t *all) {
+                               std::vector<Item> &edge, uint32_t *scatter, uint32_t *all, bool hub_phase = false) {
   uint32_t sc = 0, al = 0;
   const uint32_t warp_end = g->cls_begin[CLS_WARP + 1];
   for (uint32_t t = 0; t < warp_end; t += roots_per_item) {
@@ -241,7 +244,7 @@ inline void append_query_items(const gpm_graph *g, uint32_t kind, uint32_t qi, u
       heavy.push_back({IT_C4_BUCKET, qi, t, t + 1});
       ++al;
     }
-    for (uint32_t t = g->c4_begin[2]; t < g->c4_begin[3]; ++t) {
+    for (uint32_t t = g->c4_begin[2]; t < (hub_phase ? g->c4_begin[2] : g->c4_begin[3]); ++t) {
       heavy.push_back({IT_C4_BIG, qi, t, t + 1});
       ++al;
     }
@@ -272,7 +275,7 @@ inline int formulas_for(uint32_t kind, uint32_t *f, uint32_t *nf) {
 
 // Prepare a graph for item processing: orientation, root classes with the
 // item bound on warp roots, and (for 4-motif queries) the 4-cycle root lists.
-inline int prepare_for_items(gpm_graph *g, bool need_c4, cudaStream_t st) {
+inline int prepare_for_items(gpm_graph *g, bool need_c4, cudaStream_t st, bool hub_phase = false) {
   int rc = gpm_prepare_graph(g, st);
   if (rc) return rc;
   const gpm_tuning &t = gpm_tune();
@@ -284,8 +287,8 @@ inline int prepare_for_items(gpm_graph *g, bool need_c4, cudaStream_t st) {
     gpm_tune().warp_max_degree = old_w;
     if (rc) return rc;
   }
-  if (need_c4 && !g->c4_ready) {
-    rc = gpm_build_c4_tasks(g, st);
+  if (need_c4) {
+    rc = hub_phase ? gpm_c4_hub_prepare(g, st) : gpm_build_c4_tasks(g, st);
     if (rc) return rc;
   }
   return GPM_OK;

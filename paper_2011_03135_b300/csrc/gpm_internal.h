@@ -6,6 +6,7 @@
 
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/gpm.h"
 
@@ -52,6 +53,7 @@ struct gpm_tuning {
   uint32_t warp_max_degree = 128;  // class CLS_WARP upper bound (<= 256)
   uint32_t cta_max_degree = 1024;  // class CLS_CTA upper bound (<= 1024)
   uint32_t blocks_per_sm = 0;      // 0 = occupancy-derived
+  uint32_t c4_hub_bound = 1048576; // 4-cycle roots above this wedge bound: hub path
 };
 gpm_tuning &gpm_tune();
 
@@ -102,15 +104,29 @@ struct gpm_graph {
   size_t tally_slots = 0;
   uint32_t *list_scratch = nullptr;
   size_t list_scratch_bytes = 0;
-  // 4-cycle roots grouped by wedge bound (small: shared-memory hash per
-  // warp; big: dense global tally per CTA)
-  // classes: [0,1) small (warp hash), [1,2) bucketed, [2,3) dense tally
+  // 4-cycle roots grouped by wedge bound; classes: [0,1) small (warp hash),
+  // [1,2) bucketed, [2,3) hub roots (whole-grid tally in the plain path, a
+  // dense per-CTA tally in the batched and served forms)
   uint32_t *c4_tasks = nullptr;
   uint32_t c4_begin[4] = {0, 0, 0, 0};
   uint32_t c4_bucket_maxb = 0;  // largest wedge bound among bucketed roots
   uint32_t *c4_bucket_buf = nullptr;
   size_t c4_bucket_bytes = 0;
+  uint32_t *edeg = nullptr;     // nnz: deg(col[e]), read beside col by the wedge walks
   bool c4_ready = false;
+  uint32_t c4_hub_bound = 0;    // threshold the classes were built with
+  // hub roots: host copies of the roots and their degrees, work units
+  // {x, chunk} (unit offsets per root in c4_hub_uoff), and two sets of
+  // c4_hub_R tallies + touched lists of n words each (tallies zero between calls)
+  bool c4_hub_ready = false;
+  std::vector<uint32_t> c4_hub_root, c4_hub_deg;
+  std::vector<uint64_t> c4_hub_uoff, c4_hub_bnd;
+  uint32_t *c4_hub_units = nullptr;
+  uint32_t *c4_hub_tally = nullptr;
+  uint32_t *c4_hub_touched = nullptr;
+  uint32_t c4_hub_R = 0;
+  unsigned int *c4_hub_ctr = nullptr;
+  size_t c4_hub_ctr_words = 0;
 
   size_t device_bytes = 0;
   std::mutex mu;
@@ -174,6 +190,13 @@ int gpm_launch_cliques(gpm_graph *g, int kmax, bool scatter, uint32_t root_lo, u
 
 // 4-cycle root lists (wedge-bound classes), built once per graph.
 int gpm_build_c4_tasks(gpm_graph *g, cudaStream_t st);
+
+// Hub-class 4-cycle roots (wedge bound above the hub threshold) on their own:
+// prepare builds the task lists, work units and tallies (host synchronisations);
+// enqueue only launches (capturable), adding their 4-cycles to acc[ACC_C4].
+int gpm_c4_hub_prepare(gpm_graph *g, cudaStream_t st);
+int gpm_c4_hub_enqueue(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigned long long *acc, cudaStream_t st,
+                       uint32_t *nlaunch);
 
 // 4-cycles whose order-last vertex lies in [root_lo, root_hi): acc[ACC_C4] += count.
 int gpm_launch_cycles4(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigned long long *acc, cudaStream_t st);

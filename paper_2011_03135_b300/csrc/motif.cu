@@ -18,10 +18,20 @@
 // 4-cycles: a cycle is rooted at its order-last vertex v0 (order = degree,
 // then id). All wedges v0 - x - w with x and w before v0 in the order are
 // tallied by their far end w; a cycle rooted at v0 with opposite vertex w is a
-// pair of such wedges, so the count is sum_w C(tally(w), 2). Roots with a
-// small wedge bound tally in a per-warp shared-memory hash table, the others
-// in a dense per-CTA tally array in global memory.
+// pair of such wedges, so the count is sum_w C(tally(w), 2). Roots are split
+// by their wedge bound B(v0) = sum of d_x over x before v0:
+//   small  (B <= 512): one warp, shared-memory hash table;
+//   bucketed (B <= 2M): one CTA, wedge ends scattered into hash buckets in a
+//           global buffer, each bucket aggregated in shared memory;
+//   hub    (larger): all CTAs of the GPU on a few roots at a time, each root
+//           with a dense tally of n words that stays in L2. A tally increment
+//           that returns c adds c to the count (the pairs it closes), so
+//           sum_w C(tally(w), 2) is formed without a second pass; the touched
+//           entries are listed and reset by the next launch.
+// The wedge walks read the neighbour's degree from a per-entry copy (edeg)
+// beside col instead of gathering deg[w].
 #include <algorithm>
+#include <vector>
 
 #include "gpm_internal.h"
 #include "motif_device.cuh"
@@ -71,8 +81,9 @@ constexpr uint32_t kHashSlots = gpm_dev::kC4HashSlots;
 // wedge bound B(v0) = sum of d_x over neighbours x before v0; class 0 small
 // (warp hash), 1 bucketed, 2 dense tally
 __global__ void c4_bound_kernel(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
-                                const uint32_t *__restrict__ deg, uint32_t n, uint32_t *__restrict__ counts,
-                                uint32_t *__restrict__ tasks, uint32_t *__restrict__ cursors, int fill) {
+                                const uint32_t *__restrict__ deg, const uint32_t *__restrict__ edeg, uint32_t n,
+                                uint32_t hub_bound, uint32_t *__restrict__ counts, uint32_t *__restrict__ tasks,
+                                uint32_t *__restrict__ cursors, int fill) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -81,12 +92,12 @@ __global__ void c4_bound_kernel(const uint64_t *__restrict__ rowptr, const uint3
     unsigned long long b = 0;
     for (uint64_t e = rowptr[v] + lane; e < rowptr[v + 1]; e += 32) {
       const uint32_t x = col[e];
-      const uint32_t dx = deg[x];
+      const uint32_t dx = edeg[e];
       if (precedes(dx, x, dv, (uint32_t)v)) b += dx;
     }
     b = warp_sum(b);
     if (lane == 0 && b >= 3) {  // a cycle needs two wedges, each scanning v0 itself plus w
-      const int c = (b <= kSmallBound) ? 0 : (b <= gpm_dev::kC4BucketMaxBound ? 1 : 2);
+      const int c = (b <= kSmallBound) ? 0 : (b <= hub_bound ? 1 : 2);
       if (fill) {
         tasks[atomicAdd(&cursors[c], 1u)] = (uint32_t)v;
       } else {
@@ -97,17 +108,25 @@ __global__ void c4_bound_kernel(const uint64_t *__restrict__ rowptr, const uint3
   }
 }
 
+// edeg[e] = deg[col[e]]
+__global__ void c4_edeg_kernel(const uint32_t *__restrict__ col, const uint32_t *__restrict__ deg, uint64_t nnz,
+                               uint32_t *__restrict__ edeg) {
+  const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < nnz; e += nth) edeg[e] = deg[col[e]];
+}
+
 struct C4Args {
   const uint64_t *__restrict__ rowptr;
   const uint32_t *__restrict__ col;
   const uint32_t *__restrict__ deg;
+  const uint32_t *__restrict__ edeg;
   const uint32_t *__restrict__ tasks;
   uint32_t ntasks;
   uint32_t root_lo, root_hi;
   unsigned int *queue;
   unsigned long long *acc;
   unsigned int *status;
-  uint32_t *pool;  // big class: per CTA, tally[n] then touched[n]
+  uint32_t *pool;  // bucketed class: per-CTA bucket buffers
   uint32_t n;
 };
 
@@ -126,34 +145,173 @@ __global__ void __launch_bounds__(256) c4_small_kernel(C4Args a) {
     if (task >= a.ntasks) break;
     const uint32_t v0 = a.tasks[task];
     if (v0 < a.root_lo || v0 >= a.root_hi) continue;
-    acc += gpm_dev::c4_root_warp(a.rowptr, a.col, a.deg, v0, keys, cnt, overflow);
+    acc += gpm_dev::c4_root_warp(a.rowptr, a.col, a.deg, a.edeg, v0, keys, cnt, overflow);
   }
   acc = warp_sum(acc);
   if (lane == 0 && acc) atomicAdd(&a.acc[ACC_C4], acc);
   if (__any_sync(0xffffffffu, overflow) && lane == 0) atomicOr(a.status, ST_CAPACITY);
 }
 
-// one CTA per root, dense tally in this CTA's global-memory slot
-constexpr int kC4BigThreads = 256;
-__global__ void __launch_bounds__(kC4BigThreads) c4_big_kernel(C4Args a) {
-  __shared__ uint32_t s_task, s_nt, s_cnt;
-  __shared__ uint32_t s_x[kC4BigThreads];
-  const uint32_t tid = threadIdx.x, lane = tid & 31;
-  uint32_t *tally = a.pool + (size_t)blockIdx.x * 2 * a.n;
-  uint32_t *touched = tally + a.n;
+// ---------------------------------------------------------------------------
+// hub roots: the whole grid on up to kHubMaxR roots per launch
+// ---------------------------------------------------------------------------
+constexpr uint32_t kHubChunk = 1024;  // adjacency entries of x per work unit
+constexpr int kHubMaxR = 4;
+constexpr int kHubThreads = 256;
+
+// count pass (units == nullptr): info[3j] = work units of hub root j (one per
+// kHubChunk entries of every x before v0), info[3j+1] = deg(v0), info[3j+2] =
+// wedge bound. Fill pass: units[uoff[j] ..] = {x, chunk}, x in adjacency
+// order. One warp per root.
+__global__ void c4_hub_units_kernel(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
+                                    const uint32_t *__restrict__ deg, const uint32_t *__restrict__ edeg,
+                                    const uint32_t *__restrict__ roots, uint32_t nroots,
+                                    unsigned long long *__restrict__ info, const unsigned long long *__restrict__ uoff,
+                                    uint32_t *__restrict__ units) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t j = warp; j < nroots; j += nwarps) {
+    const uint32_t v0 = roots[j], d0 = deg[v0];
+    const uint64_t b0 = rowptr[v0], e0 = rowptr[v0 + 1];
+    unsigned long long run = units ? uoff[j] : 0ull, bound = 0;
+    for (uint64_t cb = b0; cb < e0; cb += 32) {
+      const uint64_t e = cb + lane;
+      uint32_t x = 0, k = 0;
+      if (e < e0) {
+        x = col[e];
+        const uint32_t dx = edeg[e];
+        if (precedes(dx, x, d0, v0)) {
+          k = (dx + kHubChunk - 1) / kHubChunk;
+          bound += dx;
+        }
+      }
+      uint32_t incl = k;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+      }
+      if (units)
+        for (uint32_t c = 0; c < k; ++c) {
+          const unsigned long long u = run + incl - k + c;
+          units[2 * u] = x;
+          units[2 * u + 1] = c;
+        }
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    bound = warp_sum(bound);
+    if (!units && lane == 0) {
+      info[3 * j] = run;
+      info[3 * j + 1] = d0;
+      info[3 * j + 2] = bound;
+    }
+  }
+}
+
+// A root's tally is "dense" when n is small against its wedge bound: its
+// wedges are counted with fire-and-forget increments and the next launch sums
+// C(c,2) over the whole tally while clearing it. Otherwise ("sparse") every
+// increment returns the old value c, which is added to the count (the pairs
+// the new wedge closes), and first touches are listed for the reset.
+struct HubGroup {
+  uint32_t nr, prev_nr;
+  uint32_t dense, prev_dense;            // bit r: root r is dense
+  uint32_t v0[kHubMaxR], d0[kHubMaxR];
+  unsigned long long ub[kHubMaxR];       // first unit of root r
+  unsigned long long cum[kHubMaxR + 1];  // flattened unit index where root r starts
+  uint32_t *tally, *touched;             // nr slots of npad words each (this launch's set)
+  unsigned int *ntouched;                // nr counters, zero on entry
+  uint32_t *prev_tally, *prev_touched;   // previous launch's set: summed / reset here
+  const unsigned int *prev_ntouched;
+};
+
+__device__ __forceinline__ unsigned long long pairs_of(uint32_t c) { return (unsigned long long)c * (c - (c > 0)) / 2; }
+
+// Finishes the previous group's tallies, then tallies the wedges of this
+// group's roots. Each warp takes whole units (x, chunk).
+__global__ void __launch_bounds__(kHubThreads) c4_hub_kernel(const uint64_t *__restrict__ rowptr,
+                                                             const uint32_t *__restrict__ col,
+                                                             const uint32_t *__restrict__ edeg,
+                                                             const uint2 *__restrict__ units, uint64_t npad,
+                                                             HubGroup grp, unsigned long long *__restrict__ acc_out) {
+  __shared__ unsigned long long s_acc[kHubThreads / 32];
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint64_t gtid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
   unsigned long long acc = 0;
-  for (;;) {
-    if (tid == 0) s_task = atomicAdd(a.queue, 1u);
-    __syncthreads();
-    const uint32_t task = s_task;
-    __syncthreads();
-    if (task >= a.ntasks) break;
-    const uint32_t v0 = a.tasks[task];
-    if (v0 < a.root_lo || v0 >= a.root_hi) continue;
-    acc += gpm_dev::c4_root_cta(a.rowptr, a.col, a.deg, v0, tally, touched, s_x, &s_cnt, &s_nt);
+  for (uint32_t r = 0; r < grp.prev_nr; ++r) {
+    uint32_t *T = grp.prev_tally + (size_t)r * npad;
+    if ((grp.prev_dense >> r) & 1u) {
+      uint4 *T4 = reinterpret_cast<uint4 *>(T);
+      for (uint64_t i = gtid; i < npad / 4; i += nth) {
+        const uint4 v = __ldcg(T4 + i);
+        if (v.x | v.y | v.z | v.w) {
+          acc += pairs_of(v.x) + pairs_of(v.y) + pairs_of(v.z) + pairs_of(v.w);
+          __stcg(T4 + i, make_uint4(0u, 0u, 0u, 0u));
+        }
+      }
+    } else {
+      const uint32_t cnt = grp.prev_ntouched[r];
+      const uint32_t *L = grp.prev_touched + (size_t)r * npad;
+      for (uint64_t i = gtid; i < cnt; i += nth) T[__ldcg(L + i)] = 0u;
+    }
+  }
+  const unsigned long long total = grp.cum[grp.nr];
+  for (unsigned long long f = gtid >> 5; f < total; f += nth >> 5) {
+    uint32_t r = 0;
+    while (r + 1 < grp.nr && f >= grp.cum[r + 1]) ++r;
+    const uint2 unit = units[grp.ub[r] + (f - grp.cum[r])];
+    const uint32_t v0 = grp.v0[r], d0 = grp.d0[r];
+    uint32_t *tally = grp.tally + (size_t)r * npad;
+    const uint64_t e0 = rowptr[unit.x] + (uint64_t)unit.y * kHubChunk;
+    const uint64_t e1 = min(rowptr[unit.x + 1], e0 + kHubChunk);
+    const bool dense = (grp.dense >> r) & 1u;
+    for (uint64_t base = e0; base < e1; base += 128) {
+      uint32_t w[4];
+      bool v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint64_t e = base + 32 * k + lane;
+        v[k] = false;
+        w[k] = 0;
+        if (e < e1) {
+          w[k] = col[e];
+          v[k] = precedes(edeg[e], w[k], d0, v0);
+        }
+      }
+      if (dense) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (v[k]) atomicAdd(&tally[w[k]], 1u);
+        continue;
+      }
+      uint32_t old[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) old[k] = v[k] ? atomicAdd(&tally[w[k]], 1u) : 1u;
+      uint32_t *touched = grp.touched + (size_t)r * npad;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        acc += v[k] ? old[k] : 0u;
+        const bool first = v[k] && old[k] == 0u;
+        const uint32_t m = __ballot_sync(0xffffffffu, first);
+        if (m) {
+          const int leader = __ffs(m) - 1;
+          uint32_t b = 0;
+          if ((int)lane == leader) b = atomicAdd(&grp.ntouched[r], (uint32_t)__popc(m));
+          b = __shfl_sync(0xffffffffu, b, leader);
+          if (first) touched[b + __popc(m & ((1u << lane) - 1u))] = w[k];
+        }
+      }
+    }
   }
   acc = warp_sum(acc);
-  if (lane == 0 && acc) atomicAdd(&a.acc[ACC_C4], acc);
+  if (lane == 0) s_acc[wid] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int i = 0; i < kHubThreads / 32; ++i) t += s_acc[i];
+    if (t) atomicAdd(&acc_out[ACC_C4], t);
+  }
 }
 
 // one CTA per large root, bucketed aggregation (buffer slot per CTA)
@@ -173,7 +331,7 @@ __global__ void __launch_bounds__(kC4BucketThreads) c4_bucket_kernel(C4Args a, u
     if (task >= a.ntasks) break;
     const uint32_t v0 = a.tasks[task];
     if (v0 < a.root_lo || v0 >= a.root_hi) continue;
-    acc += gpm_dev::c4_root_bucketed(a.rowptr, a.col, a.deg, v0, buf, smem, s_x, &s_cnt, overflow);
+    acc += gpm_dev::c4_root_bucketed(a.rowptr, a.col, a.deg, a.edeg, v0, buf, smem, s_x, &s_cnt, overflow);
   }
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0 && acc) atomicAdd(&a.acc[ACC_C4], acc);
@@ -205,15 +363,27 @@ int gpm_launch_edge_terms(gpm_graph *g, bool use_t_edge, uint32_t root_lo, uint3
   return GPM_OK;
 }
 
+// a hub root's tally is summed densely when n <= 4 x its wedge bound
+static inline bool hub_dense(uint32_t n, uint64_t bound) { return (uint64_t)n <= 4ull * bound; }
+
 static int ensure_c4_tasks(gpm_graph *g, cudaStream_t st) {
-  if (g->c4_ready) return GPM_OK;
+  const uint32_t hub_bound = std::min(gpm_tune().c4_hub_bound, gpm_dev::kC4BucketMaxBound);
+  if (g->c4_ready && g->c4_hub_bound == hub_bound) return GPM_OK;
   if (!g->c4_tasks) GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4_tasks, sizeof(uint32_t) * std::max<uint32_t>(g->n, 1)));
+  const int blocks = gpm_num_sms(g->device) * 8;
+  if (!g->edeg) {
+    GPM_TRY(gpm_graph_alloc(g, (void **)&g->edeg, sizeof(uint32_t) * std::max<uint64_t>(g->nnz, 1)));
+    if (g->nnz) {
+      GPM_LAUNCH("c4_edeg_kernel", st, c4_edeg_kernel<<<blocks, 256, 0, st>>>(g->col, g->deg, g->nnz, g->edeg));
+      GPM_CUDA(cudaGetLastError());
+    }
+  }
   uint32_t *tmp = reinterpret_cast<uint32_t *>(g->work + WK_MISC);  // counts[3], max bound, cursors[3]
   GPM_CUDA(cudaMemsetAsync(tmp, 0, 8 * sizeof(uint32_t), st));
-  const int blocks = gpm_num_sms(g->device) * 8;
   if (g->n) {
     GPM_LAUNCH("c4_bound_kernel", st,
-               c4_bound_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->n, tmp, nullptr, nullptr, 0));
+               c4_bound_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->edeg, g->n, hub_bound, tmp,
+                                                        nullptr, nullptr, 0));
     GPM_CUDA(cudaGetLastError());
   }
   uint32_t h[4];
@@ -228,12 +398,158 @@ static int ensure_c4_tasks(gpm_graph *g, cudaStream_t st) {
   GPM_CUDA(cudaMemcpyAsync(tmp + 4, cur, sizeof(cur), cudaMemcpyHostToDevice, st));
   if (g->n) {
     GPM_LAUNCH("c4_bound_kernel", st,
-               c4_bound_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->n, nullptr, g->c4_tasks, tmp + 4, 1));
+               c4_bound_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->edeg, g->n, hub_bound,
+                                                        nullptr, g->c4_tasks, tmp + 4, 1));
     GPM_CUDA(cudaGetLastError());
   }
   GPM_CUDA(cudaStreamSynchronize(st));
   g->c4_ready = true;
+  g->c4_hub_bound = hub_bound;
+  g->c4_hub_ready = false;
   return GPM_OK;
+}
+
+// Work units and tallies of the hub roots (class 2), built once per task list.
+static int ensure_c4_hub(gpm_graph *g, cudaStream_t st) {
+  if (g->c4_hub_ready) return GPM_OK;
+  const uint32_t nhub = g->c4_begin[3] - g->c4_begin[2];
+  const uint32_t *roots = g->c4_tasks + g->c4_begin[2];
+  if (g->c4_hub_units) {
+    cudaFree(g->c4_hub_units);
+    g->c4_hub_units = nullptr;
+  }
+  g->c4_hub_root.assign(nhub, 0);
+  g->c4_hub_deg.assign(nhub, 0);
+  g->c4_hub_bnd.assign(nhub, 0);
+  g->c4_hub_uoff.assign((size_t)nhub + 1, 0);
+  if (nhub) {
+    const int blocks = gpm_num_sms(g->device) * 8;
+    unsigned long long *info = nullptr;
+    GPM_CUDA(cudaMalloc(&info, sizeof(unsigned long long) * (3 * (size_t)nhub + (size_t)nhub + 1)));
+    unsigned long long *d_uoff = info + 3 * (size_t)nhub;
+    std::vector<unsigned long long> h(3 * (size_t)nhub);
+    int rc = GPM_OK;
+    do {
+      GPM_LAUNCH("c4_hub_units_kernel", st,
+                 c4_hub_units_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->edeg, roots, nhub, info,
+                                                              nullptr, nullptr));
+      if (cudaGetLastError() != cudaSuccess ||
+          cudaMemcpyAsync(h.data(), info, sizeof(unsigned long long) * 3 * nhub, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaMemcpyAsync(g->c4_hub_root.data(), roots, sizeof(uint32_t) * nhub, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess) {
+        rc = gpm_fail(GPM_E_DEVICE, "4-cycle hub unit count failed");
+        break;
+      }
+      for (uint32_t j = 0; j < nhub; ++j) {
+        g->c4_hub_uoff[j + 1] = g->c4_hub_uoff[j] + h[3 * j];
+        g->c4_hub_deg[j] = (uint32_t)h[3 * j + 1];
+        g->c4_hub_bnd[j] = h[3 * j + 2];
+      }
+      const uint64_t U = g->c4_hub_uoff[nhub];
+      rc = gpm_graph_alloc(g, (void **)&g->c4_hub_units, sizeof(uint32_t) * 2 * std::max<uint64_t>(U, 1));
+      if (rc) break;
+      if (cudaMemcpyAsync(d_uoff, g->c4_hub_uoff.data(), sizeof(unsigned long long) * ((size_t)nhub + 1),
+                          cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        rc = gpm_fail(GPM_E_DEVICE, "4-cycle hub offsets upload failed");
+        break;
+      }
+      GPM_LAUNCH("c4_hub_units_kernel", st,
+                 c4_hub_units_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->edeg, roots, nhub, nullptr,
+                                                              d_uoff, g->c4_hub_units));
+      if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+        rc = gpm_fail(GPM_E_DEVICE, "4-cycle hub unit fill failed");
+    } while (0);
+    cudaFree(info);
+    if (rc) return rc;
+    // tallies: as many roots per launch as keep one set of tallies within 32 MiB
+    const uint64_t npad = ((uint64_t)std::max<uint32_t>(g->n, 1) + 3) & ~3ull;
+    const uint32_t R = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(kHubMaxR, (32ull << 20) / (4ull * npad)));
+    bool any_sparse = false;
+    for (uint32_t j = 0; j < nhub; ++j) any_sparse |= !hub_dense(g->n, g->c4_hub_bnd[j]);
+    const size_t words = 2 * (size_t)R * npad;
+    if (!g->c4_hub_tally || g->c4_hub_R != R) {
+      if (g->c4_hub_tally) cudaFree(g->c4_hub_tally);
+      if (g->c4_hub_touched) cudaFree(g->c4_hub_touched);
+      g->c4_hub_tally = g->c4_hub_touched = nullptr;
+      GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4_hub_tally, sizeof(uint32_t) * words));
+      GPM_CUDA(cudaMemsetAsync(g->c4_hub_tally, 0, sizeof(uint32_t) * words, st));
+      g->c4_hub_R = R;
+    }
+    if (any_sparse && !g->c4_hub_touched)
+      GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4_hub_touched, sizeof(uint32_t) * words));
+    const size_t ctr_words = ((size_t)nhub + 2) * R;
+    if (g->c4_hub_ctr_words < ctr_words) {
+      if (g->c4_hub_ctr) cudaFree(g->c4_hub_ctr);
+      g->c4_hub_ctr = nullptr;
+      GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4_hub_ctr, sizeof(unsigned int) * ctr_words));
+      g->c4_hub_ctr_words = ctr_words;
+    }
+  }
+  g->c4_hub_ready = true;
+  return GPM_OK;
+}
+
+// Hub roots in [root_lo, root_hi): one launch per group of c4_hub_R roots,
+// each also finishing the previous group's tallies, and a final launch that
+// finishes the last group. Only enqueues work (capturable in a CUDA graph).
+static int launch_c4_hub(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigned long long *acc, cudaStream_t st,
+                         uint32_t *nlaunch) {
+  std::vector<uint32_t> J;
+  for (uint32_t j = 0; j < (uint32_t)g->c4_hub_root.size(); ++j)
+    if (g->c4_hub_root[j] >= root_lo && g->c4_hub_root[j] < root_hi) J.push_back(j);
+  if (nlaunch) *nlaunch = 0;
+  if (J.empty()) return GPM_OK;
+  const uint32_t R = g->c4_hub_R;
+  const uint64_t npad = ((uint64_t)std::max<uint32_t>(g->n, 1) + 3) & ~3ull;
+  const size_t set_words = (size_t)R * npad;
+  const uint32_t ngroups = (uint32_t)((J.size() + R - 1) / R);
+  GPM_CUDA(cudaMemsetAsync(g->c4_hub_ctr, 0, sizeof(unsigned int) * (size_t)(ngroups + 1) * R, st));
+  int per_sm = 0;
+  GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c4_hub_kernel, kHubThreads, 0));
+  const unsigned blocks = (unsigned)(gpm_num_sms(g->device) * std::max(per_sm, 1));
+  const uint2 *units = reinterpret_cast<const uint2 *>(g->c4_hub_units);
+  HubGroup prev{};
+  for (uint32_t gi = 0; gi <= ngroups; ++gi) {
+    HubGroup grp{};
+    const size_t set = gi & 1u;
+    grp.tally = g->c4_hub_tally + set * set_words;
+    grp.touched = g->c4_hub_touched ? g->c4_hub_touched + set * set_words : nullptr;
+    grp.ntouched = g->c4_hub_ctr + (size_t)gi * R;
+    if (gi < ngroups) {
+      for (uint32_t k = gi * R; k < std::min<uint32_t>((gi + 1) * R, (uint32_t)J.size()); ++k) {
+        const uint32_t j = J[k], r = grp.nr++;
+        grp.v0[r] = g->c4_hub_root[j];
+        grp.d0[r] = g->c4_hub_deg[j];
+        grp.ub[r] = g->c4_hub_uoff[j];
+        grp.cum[r + 1] = grp.cum[r] + (g->c4_hub_uoff[j + 1] - g->c4_hub_uoff[j]);
+        if (hub_dense(g->n, g->c4_hub_bnd[j])) grp.dense |= 1u << r;
+      }
+    }
+    if (gi > 0) {
+      grp.prev_nr = prev.nr;
+      grp.prev_dense = prev.dense;
+      grp.prev_tally = prev.tally;
+      grp.prev_touched = prev.touched;
+      grp.prev_ntouched = prev.ntouched;
+    }
+    GPM_LAUNCH("c4_hub_kernel", st,
+               c4_hub_kernel<<<blocks, kHubThreads, 0, st>>>(g->rowptr, g->col, g->edeg, units, npad, grp, acc));
+    GPM_CUDA(cudaGetLastError());
+    prev = grp;
+  }
+  if (nlaunch) *nlaunch = ngroups + 1;
+  return GPM_OK;
+}
+
+int gpm_c4_hub_prepare(gpm_graph *g, cudaStream_t st) {
+  GPM_TRY(ensure_c4_tasks(g, st));
+  return ensure_c4_hub(g, st);
+}
+
+int gpm_c4_hub_enqueue(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigned long long *acc, cudaStream_t st,
+                       uint32_t *nlaunch) {
+  if (!g->c4_ready || !g->c4_hub_ready) return gpm_fail(GPM_E_INVALID_ARG, "4-cycle hub roots are not prepared");
+  return launch_c4_hub(g, root_lo, root_hi, acc, st, nlaunch);
 }
 
 int gpm_build_c4_tasks(gpm_graph *g, cudaStream_t st) { return ensure_c4_tasks(g, st); }
@@ -246,6 +562,7 @@ int gpm_launch_cycles4(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigne
   a.rowptr = g->rowptr;
   a.col = g->col;
   a.deg = g->deg;
+  a.edeg = g->edeg;
   a.root_lo = root_lo;
   a.root_hi = root_hi;
   a.acc = acc;
@@ -297,33 +614,8 @@ int gpm_launch_cycles4(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigne
     GPM_CUDA(cudaGetLastError());
   }
   if (nbig) {
-    C4Args b = a;
-    b.tasks = g->c4_tasks + g->c4_begin[2];
-    b.ntasks = nbig;
-    b.queue = queues + 1;
-    // hub roots are bound by the latency of their global tally atomics: keep many
-    // CTAs resident (each with its own tally slot), within a memory budget
-    int per_sm = 0;
-    GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c4_big_kernel, kC4BigThreads, 0));
-    const size_t slot_bytes = 2 * (size_t)std::max<uint32_t>(g->n, 1) * 4;
-    const size_t budget = (size_t)16 << 30;
-    size_t slots = (size_t)sms * (size_t)std::max(1, std::min(per_sm, 8));
-    slots = std::min(slots, std::max<size_t>(1, budget / slot_bytes));
-    slots = std::min(slots, (size_t)nbig);
-    if (g->tally_slots < slots) {
-      if (g->tally_pool) {
-        cudaFree(g->tally_pool);
-        g->device_bytes -= g->tally_slots * slot_bytes;
-        g->tally_pool = nullptr;
-        g->tally_slots = 0;
-      }
-      GPM_TRY(gpm_graph_alloc(g, (void **)&g->tally_pool, slots * slot_bytes));
-      GPM_CUDA(cudaMemsetAsync(g->tally_pool, 0, slots * slot_bytes, st));
-      g->tally_slots = slots;
-    }
-    b.pool = g->tally_pool;
-    GPM_LAUNCH("c4_big_kernel", st, c4_big_kernel<<<(unsigned)slots, kC4BigThreads, 0, st>>>(b));
-    GPM_CUDA(cudaGetLastError());
+    GPM_TRY(ensure_c4_hub(g, st));
+    GPM_TRY(launch_c4_hub(g, root_lo, root_hi, acc, st, nullptr));
   }
   return GPM_OK;
 }

@@ -15,6 +15,13 @@ __device__ __forceinline__ bool precedes(uint32_t da, uint32_t a, uint32_t db, u
   return da < db || (da == db && a < b);
 }
 
+// Degree of the neighbour col[e] = w: from the per-entry copy edeg when the
+// graph has one (a coalesced load beside col), else gathered from deg.
+__device__ __forceinline__ uint32_t nbr_deg(const uint32_t *__restrict__ edeg, const uint32_t *__restrict__ deg,
+                                            uint64_t e, uint32_t w) {
+  return edeg ? __ldg(edeg + e) : __ldg(deg + w);
+}
+
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
@@ -25,7 +32,8 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 // bound of v0 must be <= kC4SmallBound. Returns this lane's part of the count.
 __device__ __forceinline__ unsigned long long c4_root_warp(const uint64_t *__restrict__ rowptr,
                                                            const uint32_t *__restrict__ col,
-                                                           const uint32_t *__restrict__ deg, uint32_t v0,
+                                                           const uint32_t *__restrict__ deg,
+                                                           const uint32_t *__restrict__ edeg, uint32_t v0,
                                                            uint32_t *keys, uint32_t *cnt, bool &overflow) {
   const uint32_t lane = threadIdx.x & 31;
   for (uint32_t i = lane; i < kC4HashSlots; i += 32) {
@@ -41,7 +49,7 @@ __device__ __forceinline__ unsigned long long c4_root_warp(const uint64_t *__res
     bool ok = false;
     if (ex < e0) {
       x = col[ex];
-      ok = precedes(deg[x], x, d0, v0);
+      ok = precedes(nbr_deg(edeg, deg, ex, x), x, d0, v0);
     }
     uint32_t mask = __ballot_sync(0xffffffffu, ok);
     while (mask) {
@@ -50,7 +58,7 @@ __device__ __forceinline__ unsigned long long c4_root_warp(const uint64_t *__res
       const uint32_t xx = __shfl_sync(0xffffffffu, x, src);
       for (uint64_t f = rowptr[xx] + lane; f < rowptr[xx + 1]; f += 32) {
         const uint32_t w = col[f];
-        if (!precedes(deg[w], w, d0, v0)) continue;
+        if (!precedes(nbr_deg(edeg, deg, f, w), w, d0, v0)) continue;
         uint32_t h = (w * 2654435761u) >> 22;  // 10 bits
         uint32_t probes = 0;
         for (;;) {
@@ -84,7 +92,8 @@ __device__ __forceinline__ unsigned long long c4_root_warp(const uint64_t *__res
 // Returns this thread's part of the count.
 __device__ __forceinline__ unsigned long long c4_root_cta(const uint64_t *__restrict__ rowptr,
                                                           const uint32_t *__restrict__ col,
-                                                          const uint32_t *__restrict__ deg, uint32_t v0,
+                                                          const uint32_t *__restrict__ deg,
+                                                          const uint32_t *__restrict__ edeg, uint32_t v0,
                                                           uint32_t *tally, uint32_t *touched, uint32_t *s_x,
                                                           uint32_t *s_cnt, uint32_t *s_nt) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
@@ -97,7 +106,7 @@ __device__ __forceinline__ unsigned long long c4_root_cta(const uint64_t *__rest
     const uint64_t ex = cb + tid;
     if (ex < e0) {
       const uint32_t x = col[ex];
-      if (precedes(deg[x], x, d0, v0)) s_x[atomicAdd(s_cnt, 1u)] = x;
+      if (precedes(nbr_deg(edeg, deg, ex, x), x, d0, v0)) s_x[atomicAdd(s_cnt, 1u)] = x;
     }
     __syncthreads();
     const uint32_t cnt = *s_cnt;
@@ -105,7 +114,7 @@ __device__ __forceinline__ unsigned long long c4_root_cta(const uint64_t *__rest
       const uint32_t x = s_x[xi];
       for (uint64_t f = rowptr[x] + lane; f < rowptr[x + 1]; f += 32) {
         const uint32_t w = col[f];
-        if (!precedes(deg[w], w, d0, v0)) continue;
+        if (!precedes(nbr_deg(edeg, deg, f, w), w, d0, v0)) continue;
         if (atomicAdd(&tally[w], 1u) == 0u) touched[atomicAdd(s_nt, 1u)] = w;
       }
     }
@@ -135,13 +144,14 @@ __device__ __forceinline__ unsigned long long c4_root_cta(const uint64_t *__rest
 // private shared-memory hash table. P is chosen so that a bucket holds about
 // kC4BucketTarget entries on average.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kC4BucketTarget = 256;
-constexpr uint32_t kC4BucketTable = 1024;   // per-warp hash slots
+constexpr uint32_t kC4BucketTarget = 128;
+constexpr uint32_t kC4BucketTable = 512;    // per-warp hash slots (two CTAs of 16 warps fit an SM)
 constexpr uint32_t kC4MaxBuckets = 4096;
-constexpr uint32_t kC4BucketMaxBound = kC4MaxBuckets * 2 * kC4BucketTarget;  // larger roots: dense tally
+constexpr uint32_t kC4BucketMaxBound = kC4MaxBuckets * 2 * kC4BucketTarget;  // larger roots: hub class
 
 __device__ __forceinline__ uint32_t c4_bucket_hash(uint32_t w) { return (w * 0x9E3779B1u) >> 7; }
-__device__ __forceinline__ uint32_t c4_slot_hash(uint32_t w) { return (w * 0x85EBCA77u) >> 22; }  // 10 bits
+// slot of w in a table of 2^bits slots
+__device__ __forceinline__ uint32_t c4_slot_hash(uint32_t w, uint32_t bits) { return (w * 0x85EBCA77u) >> (32 - bits); }
 
 // shared memory words for c4_root_bucketed with nwarps warps
 __host__ __device__ constexpr uint32_t c4_bucket_smem_words(uint32_t nwarps) {
@@ -152,7 +162,8 @@ __host__ __device__ constexpr uint32_t c4_bucket_smem_words(uint32_t nwarps) {
 // whole CTA; f(w) is called once per wedge. s_x holds blockDim.x words.
 template <typename F>
 __device__ __forceinline__ void c4_walk_wedges(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
-                                               const uint32_t *__restrict__ deg, uint32_t v0, uint32_t *s_x,
+                                               const uint32_t *__restrict__ deg,
+                                               const uint32_t *__restrict__ edeg, uint32_t v0, uint32_t *s_x,
                                                uint32_t *s_cnt, F f) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   const uint32_t d0 = deg[v0];
@@ -163,7 +174,7 @@ __device__ __forceinline__ void c4_walk_wedges(const uint64_t *__restrict__ rowp
     const uint64_t ex = cb + tid;
     if (ex < e0) {
       const uint32_t x = col[ex];
-      if (precedes(deg[x], x, d0, v0)) s_x[atomicAdd(s_cnt, 1u)] = x;
+      if (precedes(nbr_deg(edeg, deg, ex, x), x, d0, v0)) s_x[atomicAdd(s_cnt, 1u)] = x;
     }
     __syncthreads();
     const uint32_t cnt = *s_cnt;
@@ -171,7 +182,7 @@ __device__ __forceinline__ void c4_walk_wedges(const uint64_t *__restrict__ rowp
       const uint32_t x = s_x[xi];
       for (uint64_t e = rowptr[x] + lane; e < rowptr[x + 1]; e += 32) {
         const uint32_t w = col[e];
-        if (precedes(deg[w], w, d0, v0)) f(w);
+        if (precedes(nbr_deg(edeg, deg, e, w), w, d0, v0)) f(w);
       }
     }
     __syncthreads();
@@ -183,7 +194,8 @@ __device__ __forceinline__ void c4_walk_wedges(const uint64_t *__restrict__ rowp
 // of shared memory. Every thread must call it; returns this thread's part.
 __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *__restrict__ rowptr,
                                                                const uint32_t *__restrict__ col,
-                                                               const uint32_t *__restrict__ deg, uint32_t v0,
+                                                               const uint32_t *__restrict__ deg,
+                                                               const uint32_t *__restrict__ edeg, uint32_t v0,
                                                                uint32_t *buf, uint32_t *sm, uint32_t *s_x,
                                                                uint32_t *s_cnt, bool &overflow) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
@@ -200,7 +212,7 @@ __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *_
     unsigned long long b = 0;
     for (uint64_t e = rowptr[v0] + tid; e < rowptr[v0 + 1]; e += nt) {
       const uint32_t x = col[e];
-      const uint32_t dx = deg[x];
+      const uint32_t dx = nbr_deg(edeg, deg, e, x);
       if (precedes(dx, x, d0, v0)) b += dx;
     }
     b = warp_sum(b);
@@ -213,7 +225,7 @@ __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *_
   const uint32_t pmask = P - 1;
   for (uint32_t b = tid; b < P; b += nt) bcnt[b] = 0;
   __syncthreads();
-  c4_walk_wedges(rowptr, col, deg, v0, s_x, s_cnt, [&](uint32_t w) { atomicAdd(&bcnt[c4_bucket_hash(w) & pmask], 1u); });
+  c4_walk_wedges(rowptr, col, deg, edeg, v0, s_x, s_cnt, [&](uint32_t w) { atomicAdd(&bcnt[c4_bucket_hash(w) & pmask], 1u); });
   // exclusive scan of the bucket counts (one warp), cursors = offsets
   if (wid == 0) {
     uint32_t carry = 0;
@@ -237,7 +249,7 @@ __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *_
     }
   }
   __syncthreads();
-  c4_walk_wedges(rowptr, col, deg, v0, s_x, s_cnt,
+  c4_walk_wedges(rowptr, col, deg, edeg, v0, s_x, s_cnt,
                  [&](uint32_t w) { buf[atomicAdd(&bcnt[c4_bucket_hash(w) & pmask], 1u)] = w; });
   // the buffer is read below by other warps of this CTA (plain loads, CTA scope)
   __syncthreads();
@@ -255,9 +267,14 @@ __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *_
     if (b >= P) break;
     const uint32_t e0 = boff[b], e1 = boff[b + 1];
     if (e1 - e0 < 2) continue;  // a single wedge closes no cycle
+    // table of the smallest power of two >= 2 x entries (32 .. kC4BucketTable
+    // slots): clearing and summing it costs at most twice the bucket
+    uint32_t bits = 5;
+    while (bits < 31 && (1u << bits) < 2 * (e1 - e0) && (1u << bits) < kC4BucketTable) ++bits;
+    const uint32_t tmask = (1u << bits) - 1;
     for (uint32_t e = e0 + lane; e < e1; e += 32) {
       const uint32_t w = buf[e];
-      uint32_t h = c4_slot_hash(w);
+      uint32_t h = c4_slot_hash(w, bits);
       uint32_t probes = 0;
       for (;;) {
         const uint32_t k = atomicCAS(&keys[h], kC4Empty, w);
@@ -265,15 +282,15 @@ __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *_
           atomicAdd(&vals[h], 1u);
           break;
         }
-        h = (h + 1) & (kC4BucketTable - 1);
-        if (++probes >= kC4BucketTable) {
+        h = (h + 1) & tmask;
+        if (++probes > tmask) {
           overflow = true;
           break;
         }
       }
     }
     __syncwarp();
-    for (uint32_t i = lane; i < kC4BucketTable; i += 32) {
+    for (uint32_t i = lane; i <= tmask; i += 32) {
       const unsigned long long c = vals[i];
       acc += c * (c - (c > 0)) / 2;
       keys[i] = kC4Empty;

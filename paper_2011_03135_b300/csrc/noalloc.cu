@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kNoAllocThreads) noalloc_c4_kernel(const uint6
     const uint32_t v0 = s_root;
     __syncthreads();
     if (v0 >= n) break;
-    acc += gpm_dev::c4_root_cta(rowptr, col, deg, v0, tally, touched, s_x, &s_cnt, &s_nt);
+    acc += gpm_dev::c4_root_cta(rowptr, col, deg, nullptr, v0, tally, touched, s_x, &s_cnt, &s_nt);
   }
   acc = gpm_dev::warp_sum(acc);
   if ((threadIdx.x & 31) == 0 && acc) atomicAdd(reinterpret_cast<unsigned long long *>(ctr + 2), acc);

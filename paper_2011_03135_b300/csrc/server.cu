@@ -333,6 +333,7 @@ int try_admit(gpm_server *s, const gpm_server::Req &r, int *rc) {
   q.t_edge = (r.kind == GPM_QUERY_MOTIF4) ? s->d_arena + off : nullptr;
   q.tasks = g->tasks;
   q.c4_tasks = g->c4_tasks;
+  q.edeg = g->edeg;
   q.n = g->n;
   q.m = g->m;
   SlotState *dslot = s->d_slots + slot;

@@ -76,7 +76,8 @@ class Completion(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("warp_max_degree", ctypes.c_uint32), ("cta_max_degree", ctypes.c_uint32),
-                ("blocks_per_sm", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
+                ("blocks_per_sm", ctypes.c_uint32), ("c4_hub_bound", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 4)]
 
 
 _vp, _u32, _u64, _i = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
@@ -179,15 +180,16 @@ def profile_report() -> dict:
     return json.loads(buf.value.decode())
 
 
-def set_options(warp_max_degree: int = 0, cta_max_degree: int = 0, blocks_per_sm: int = 0):
-    o = Options(warp_max_degree, cta_max_degree, blocks_per_sm)
+def set_options(warp_max_degree: int = 0, cta_max_degree: int = 0, blocks_per_sm: int = 0, c4_hub_bound: int = 0):
+    o = Options(warp_max_degree, cta_max_degree, blocks_per_sm, c4_hub_bound)
     _check(_lib.gpm_set_options(ctypes.byref(o)))
 
 
 def get_options() -> dict:
     o = Options()
     _check(_lib.gpm_get_options(ctypes.byref(o)))
-    return dict(warp_max_degree=o.warp_max_degree, cta_max_degree=o.cta_max_degree, blocks_per_sm=o.blocks_per_sm)
+    return dict(warp_max_degree=o.warp_max_degree, cta_max_degree=o.cta_max_degree, blocks_per_sm=o.blocks_per_sm,
+                c4_hub_bound=o.c4_hub_bound)
 
 
 class Graph:

@@ -109,4 +109,10 @@ def test_options_roundtrip(lib):
     assert lib.get_options()["warp_max_degree"] == 64
     with pytest.raises(lib.GpmError):
         lib.set_options(warp_max_degree=8)
+    assert old["c4_hub_bound"] == 1048576
+    lib.set_options(c4_hub_bound=4000)
+    assert lib.get_options()["c4_hub_bound"] == 4000
+    for bad in (512, 1048577):
+        with pytest.raises(lib.GpmError):
+            lib.set_options(c4_hub_bound=bad)
     lib.set_options(**{k: v for k, v in old.items() if v})

@@ -109,6 +109,28 @@ def test_root_ranges_match_oracle(gpm):
     G.close()
 
 
+@pytest.mark.parametrize("hub_bound", [513, 4000, 60000])
+def test_cycles4_hub_path(gpm, hub_bound):
+    # a low hub threshold sends many roots of medium graphs through the
+    # whole-grid tally path (groups of roots per launch, tally reset by the
+    # next launch); totals, root ranges and the motif inversion must not change
+    old = gpm.get_options()
+    try:
+        gpm.set_options(c4_hub_bound=hub_bound)
+        C = gpm.Pattern.spec(O.CYCLE4, induced=False)
+        for g in _medium():
+            G = gpm.Graph.from_host(g)
+            assert gpm.count(G, [C]) == [O.cycles4(g)], g.name
+            assert gpm.count(G, [C]) == [O.cycles4(g)], g.name  # tallies were left at zero
+            cuts = [0, g.n // 3, g.n // 3 + 1, g.n - 5, g.n]
+            for lo, hi in zip(cuts[:-1], cuts[1:]):
+                assert gpm.count_roots(G, [C], lo, hi) == [O.cycles4(g, lo, hi)], (g.name, lo, hi)
+            assert gpm.count(G, gpm.Pattern.motifs(4)) == O.motifs(g, 4), g.name
+            G.close()
+    finally:
+        gpm.set_options(**{k: v for k, v in old.items() if v})
+
+
 def _adjacent(g, u, v):
     nb = g.neighbors(int(u))
     i = np.searchsorted(nb, v)
