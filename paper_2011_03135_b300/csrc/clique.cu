@@ -40,6 +40,7 @@ namespace {
 struct LGArgs {
   const uint64_t *__restrict__ drow;
   const uint32_t *__restrict__ dcol;
+  const uint32_t *__restrict__ deg;  // undirected degrees (orientation order of local vertices)
   const uint32_t *__restrict__ tasks;
   uint32_t ntasks;
   uint32_t root_lo, root_hi;
@@ -112,7 +113,8 @@ __global__ void __launch_bounds__(512) lg_cta_kernel(LGArgs a, uint32_t maxd, ui
     if (u < a.root_lo || u >= a.root_hi) continue;
     const uint32_t d = (uint32_t)(a.drow[u + 1] - a.drow[u]);
     if (d < 2 || d > maxd) continue;
-    gpm_dev::lg_root_cta<G, KMAX, SCATTER>(a.drow, a.dcol, a.t_edge, u, maxd, a.W, base, a3, a4, a5, nest, big_cap);
+    gpm_dev::lg_root_cta<G, KMAX, SCATTER>(a.drow, a.dcol, a.t_edge, u, maxd, a.W, base, a3, a4, a5, nest, big_cap,
+                                           a.deg);
   }
   flush_acc(a, a3, a4, a5, KMAX);
 }
@@ -270,6 +272,7 @@ int gpm_launch_cliques(gpm_graph *g, int kmax, bool scatter, uint32_t root_lo, u
   LGArgs a{};
   a.drow = g->drow;
   a.dcol = g->dcol;
+  a.deg = g->deg;
   a.root_lo = root_lo;
   a.root_hi = root_hi;
   a.acc = acc;

@@ -35,11 +35,13 @@ __device__ __forceinline__ uint32_t row_of(const uint32_t *pre, uint32_t n, uint
 
 // Flat expansion of one root's local graph. Threads [t0, t0 + nt) of the
 // calling group cooperate; the caller synchronises before and after.
+// perm (optional): row and bit positions of L[i] (see rank_local); the
+// triangle-count scatter keeps id positions.
 template <bool SCATTER>
 __device__ __forceinline__ uint32_t build_rows(const uint32_t *__restrict__ dcol, uint32_t *t_edge, const uint32_t *L,
                                                const uint32_t *pre,
                                                const uint64_t *xb, uint32_t *R, uint32_t *tc, uint32_t d,
-                                               uint32_t rs, uint32_t t, uint32_t nt) {
+                                               uint32_t rs, uint32_t t, uint32_t nt, const uint32_t *perm = nullptr) {
   const uint32_t E = pre[d];
   uint32_t found = 0;
   const uint32_t lo_id = L[0], hi_id = L[d - 1];
@@ -51,7 +53,8 @@ __device__ __forceinline__ uint32_t build_rows(const uint32_t *__restrict__ dcol
     if (y < lo_id || y > hi_id) continue;
     const uint32_t j = lower_bound_u32(L, d, y);
     if (j < d && L[j] == y) {
-      atomicOr(&R[(size_t)i * rs + (j >> 5)], 1u << (j & 31));
+      const uint32_t ri = perm ? perm[i] : i, rj = perm ? perm[j] : j;
+      atomicOr(&R[(size_t)ri * rs + (rj >> 5)], 1u << (rj & 31));
       ++found;
       if (SCATTER) {
         atomicAdd(&tc[i], 1u);
@@ -147,8 +150,15 @@ constexpr uint32_t kNestWarpWp = 4;   // = kNestWarpC / 32
 constexpr uint32_t kNestWarpWords = kNestWarpC + 32 + kNestWarpC * (kNestWarpWp | 1u);
 
 __host__ __device__ constexpr uint64_t nest_words(uint32_t maxd, uint32_t nwarps, uint32_t big_cap) {
-  // per warp: S[128] pref[32] C[128*4]; CTA: big-row list[maxd], S[maxd], pref[32], C[big_cap], 4 counters
-  return (uint64_t)nwarps * kNestWarpWords + 2ull * maxd + 32 + big_cap + 4;
+  // counters[4], big-row list[maxd], wide-row list[maxd], then a pool that
+  // holds per warp S[128] pref[32] C[128*5] in the warp phase, and the
+  // groups' (or the CTA's) S[maxd] pref[32] C[...] in the big-row phases
+  return 4ull + 2ull * maxd + (uint64_t)nwarps * kNestWarpWords + maxd + 32 + big_cap;
+}
+
+// named barrier over `nthreads` threads (a multiple of 32) of the CTA
+__device__ __forceinline__ void group_bar(uint32_t id, uint32_t nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 // Number of set bits of row ri (W <= 32 words); when it is at most cap, their
@@ -191,11 +201,12 @@ __device__ __forceinline__ uint32_t gather_bits(uint32_t x, uint32_t riw) {
 
 // compact row R_j (j = S[a]) onto the positions of ri into crow (Wp words,
 // zeroed here); returns |R_j & R_i|
+// (words of rj below w0 are known to be zero)
 __device__ __forceinline__ uint32_t compact_row(const uint32_t *rj, const uint32_t *ri, const uint32_t *pref, uint32_t W,
-                                                uint32_t *crow, uint32_t Wp) {
+                                                uint32_t *crow, uint32_t Wp, uint32_t w0 = 0) {
   for (uint32_t k = 0; k < Wp; ++k) crow[k] = 0u;
   uint32_t bits = 0;
-  for (uint32_t w = 0; w < W; ++w) {
+  for (uint32_t w = w0; w < W; ++w) {
     const uint32_t riw = ri[w];
     const uint32_t x = rj[w] & riw;
     if (!x) continue;
@@ -210,16 +221,17 @@ __device__ __forceinline__ uint32_t compact_row(const uint32_t *rj, const uint32
 
 // sum over the set bits b in word k of row a of |C_a & C_b| (rows of Wp words,
 // stride Wp); one (a, k) unit bounds a thread's loop to 32 bits
+// (with tri, C is strictly upper triangular: C_b has no bit below b + 1)
 __device__ __forceinline__ unsigned long long nested_pairs_unit(const uint32_t *C, uint32_t a, uint32_t k,
-                                                                uint32_t Wp, uint32_t cs) {
+                                                                uint32_t Wp, uint32_t cs, bool tri = false) {
   const uint32_t *ca = C + (size_t)a * cs;
-  unsigned long long s = 0;
+  uint32_t s = 0;  // at most 32 x 32 x Wp
   uint32_t bits = ca[k];
   while (bits) {
     const uint32_t b = k * 32 + __ffs(bits) - 1;
     bits &= bits - 1;
     const uint32_t *cb = C + (size_t)b * cs;
-    for (uint32_t k2 = 0; k2 < Wp; ++k2) s += __popc(ca[k2] & cb[k2]);
+    for (uint32_t k2 = tri ? (b + 1) >> 5 : 0; k2 < Wp; ++k2) s += __popc(ca[k2] & cb[k2]);
   }
   return s;
 }
@@ -279,78 +291,155 @@ __device__ __forceinline__ void row_k45_groups(const uint32_t *R, uint32_t W, ui
 
 // 4- and 5-cliques of one root's local graph R (d rows, W <= 32 words) by the
 // whole CTA with nesting. nest: nest_words(maxd, blockDim/32, big_cap) words.
+// Rows with c <= kNestWarpC are nested by one warp each; larger rows by groups
+// of four warps (one row per group at a time, named barriers, so groups do not
+// wait for each other); rows too large for a group's share of the pool by the
+// whole CTA at the end.
+// With tri, R is strictly upper triangular (positions in the orientation's
+// order), and so is every nested C: the word loops start at the pivot.
 __device__ inline void enumerate_nested_cta(const uint32_t *R, uint32_t d, uint32_t W, uint32_t rs, uint32_t *nest,
                                             uint32_t maxd, uint32_t big_cap, unsigned long long &a4,
-                                            unsigned long long &a5) {
+                                            unsigned long long &a5, bool tri = false) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-  uint32_t *wbuf = nest + (size_t)wid * kNestWarpWords;
-  uint32_t *S = wbuf, *pref = wbuf + kNestWarpC, *C = wbuf + kNestWarpC + 32;
-  uint32_t *big_list = nest + (size_t)nw * kNestWarpWords;
-  uint32_t *Sb = big_list + maxd, *prefb = Sb + maxd, *Cb = prefb + 32;
-  uint32_t *ctr = Cb + big_cap;  // [0] next row, [1] big rows, [2] c of the current big row
+  uint32_t *ctr = nest;  // [0] next row, [1] big rows, [2] next big row, [3] wide rows
+  uint32_t *big_list = nest + 4;
+  uint32_t *wide_list = big_list + maxd;
+  uint32_t *pool = wide_list + maxd;
+  const uint32_t pool_words = nw * kNestWarpWords + maxd + 32 + big_cap;
   if (tid == 0) {
     ctr[0] = 0;
     ctr[1] = 0;
+    ctr[2] = 0;
+    ctr[3] = 0;
   }
   __syncthreads();
   // rows with c <= kNestWarpC: one warp each, pulled dynamically
-  for (;;) {
-    uint32_t i = 0;
-    if (lane == 0) i = atomicAdd(&ctr[0], 1u);
-    i = __shfl_sync(0xffffffffu, i, 0);
-    if (i >= d) break;
-    const uint32_t *ri = R + (size_t)i * rs;
-    const uint32_t c = list_bits_warp(ri, W, S, pref, kNestWarpC);
-    if (c < 2) continue;
-    if (c > kNestWarpC) {
-      if (lane == 0) big_list[atomicAdd(&ctr[1], 1u)] = i;
-      continue;
-    }
-    if (c <= 32) {
-      nested_row_reg32(R, W, rs, ri, c, S, pref, a4, a5);
+  {
+    uint32_t *wbuf = pool + (size_t)wid * kNestWarpWords;
+    uint32_t *S = wbuf, *pref = wbuf + kNestWarpC, *C = wbuf + kNestWarpC + 32;
+    for (;;) {
+      uint32_t i = 0;
+      if (lane == 0) i = atomicAdd(&ctr[0], 1u);
+      i = __shfl_sync(0xffffffffu, i, 0);
+      if (i >= d) break;
+      const uint32_t *ri = R + (size_t)i * rs;
+      const uint32_t c = list_bits_warp(ri, W, S, pref, kNestWarpC);
+      if (c < 2) continue;
+      if (c > kNestWarpC) {
+        if (lane == 0) big_list[atomicAdd(&ctr[1], 1u)] = i;
+        continue;
+      }
+      if (c <= 32) {
+        nested_row_reg32(R, W, rs, ri, c, S, pref, a4, a5);
+        __syncwarp();
+        continue;
+      }
+      const uint32_t Wp = (c + 31) / 32, cs = row_stride(Wp);
+      for (uint32_t a = lane; a < c; a += 32) {
+        const uint32_t bits =
+            compact_row(R + (size_t)S[a] * rs, ri, pref, W, C + (size_t)a * cs, Wp, tri ? (S[a] + 1) >> 5 : 0);
+        a4 += bits;
+      }
       __syncwarp();
-      continue;
+      // units in word-major order: a round of lanes takes neighbouring rows, word k alike
+      for (uint32_t u = lane; u < c * Wp; u += 32) a5 += nested_pairs_unit(C, u % c, u / c, Wp, cs, tri);
+      __syncwarp();
     }
-    const uint32_t Wp = (c + 31) / 32, cs = row_stride(Wp);
-    for (uint32_t a = lane; a < c; a += 32) {
-      const uint32_t bits = compact_row(R + (size_t)S[a] * rs, ri, pref, W, C + (size_t)a * cs, Wp);
-      a4 += bits;
-    }
-    __syncwarp();
-    for (uint32_t u = lane; u < c * Wp; u += 32) a5 += nested_pairs_unit(C, u / Wp, u % Wp, Wp, cs);
-    __syncwarp();
   }
   __syncthreads();
-  // rows with larger c: the whole CTA, one row at a time
   const uint32_t nbig = ctr[1];
-  for (uint32_t r = 0; r < nbig; ++r) {
-    const uint32_t i = big_list[r];
+  // rows with larger c: groups of four warps, one row per group at a time
+  if (nbig) {
+    constexpr uint32_t kGroupWarps = 4;
+    const uint32_t ng = nw >= kGroupWarps ? nw / kGroupWarps : 1u;
+    const uint32_t gthreads = (ng > 1) ? kGroupWarps * 32 : nt;
+    const uint32_t g = (ng > 1) ? wid / kGroupWarps : 0u;
+    if (g < ng) {  // warps beyond ng groups (nw not a multiple of 4) sit this phase out
+      const uint32_t gt = tid - g * gthreads, gw = gt >> 5;
+      const uint32_t share = pool_words / ng;
+      uint32_t *S = pool + (size_t)g * share, *pref = S + maxd, *hdr = pref + 32, *C = hdr + 4;
+      const uint32_t cap = share > maxd + 36 ? share - maxd - 36 : 0u;
+      for (;;) {
+        if (gt == 0) hdr[0] = atomicAdd(&ctr[2], 1u);
+        group_bar(1 + g, gthreads);
+        const uint32_t q = hdr[0];
+        if (q >= nbig) break;
+        const uint32_t i = big_list[q];
+        const uint32_t *ri = R + (size_t)i * rs;
+        if (gw == 0) {
+          const uint32_t c = list_bits_warp(ri, W, S, pref, maxd);
+          if (lane == 0) hdr[1] = c;
+        }
+        group_bar(1 + g, gthreads);
+        const uint32_t c = hdr[1];
+        const uint32_t Wp = (c + 31) / 32, cs = row_stride(Wp);
+        if ((uint64_t)c * cs > cap) {
+          if (gt == 0) wide_list[atomicAdd(&ctr[3], 1u)] = i;
+          continue;
+        }
+        // one thread per compacted row: no write sharing
+        if (gt == 0) hdr[2] = 0;
+        for (uint32_t a = gt; a < c; a += gthreads)
+          a4 += compact_row(R + (size_t)S[a] * rs, ri, pref, W, C + (size_t)a * cs, Wp, tri ? (S[a] + 1) >> 5 : 0);
+        group_bar(1 + g, gthreads);
+        // pair units in word-major order, 32 at a time per warp (with tri the
+        // work per unit falls steeply with the row and the word)
+        for (;;) {
+          uint32_t u0 = 0;
+          if (lane == 0) u0 = atomicAdd(&hdr[2], 32u);
+          u0 = __shfl_sync(0xffffffffu, u0, 0);
+          if (u0 >= c * Wp) break;
+          const uint32_t u = u0 + lane;
+          if (u < c * Wp) a5 += nested_pairs_unit(C, u % c, u / c, Wp, cs, tri);
+        }
+        group_bar(1 + g, gthreads);
+      }
+    }
+  }
+  __syncthreads();
+  // rows too large for a group: the whole CTA with the whole pool
+  const uint32_t nwide = ctr[3];
+  uint32_t *S = pool, *pref = pool + maxd, *C = pref + 32;
+  const uint32_t cap = pool_words - maxd - 32;
+  for (uint32_t r = 0; r < nwide; ++r) {
+    const uint32_t i = wide_list[r];
     const uint32_t *ri = R + (size_t)i * rs;
     if (wid == 0) {
-      const uint32_t c = list_bits_warp(ri, W, Sb, prefb, maxd);
-      if (lane == 0) ctr[2] = c;
+      const uint32_t c = list_bits_warp(ri, W, S, pref, maxd);
+      if (lane == 0) {
+        ctr[0] = c;
+        ctr[2] = 0;
+      }
     }
     __syncthreads();
-    const uint32_t c = ctr[2];
+    const uint32_t c = ctr[0];
     const uint32_t Wp = (c + 31) / 32, cs = row_stride(Wp);
-    if ((uint64_t)c * cs <= big_cap) {
-      for (uint32_t u = tid; u < c * cs; u += nt) Cb[u] = 0u;
+    if ((uint64_t)c * cs <= cap) {
+      for (uint32_t u = tid; u < c * cs; u += nt) C[u] = 0u;
       __syncthreads();
       // (row, word) units: every thread works on the wide row
       for (uint32_t u = tid; u < c * W; u += nt) {
         const uint32_t a = u / W, w = u % W;
+        if (tri && w < ((S[a] + 1) >> 5)) continue;
         const uint32_t riw = ri[w];
-        const uint32_t x = R[(size_t)Sb[a] * rs + w] & riw;
+        const uint32_t x = R[(size_t)S[a] * rs + w] & riw;
         if (!x) continue;
         a4 += __popc(x);
         const uint32_t out = gather_bits(x, riw);
-        const uint32_t base = prefb[w], wi = base >> 5, lo = base & 31;
-        uint32_t *crow = Cb + (size_t)a * cs;
+        const uint32_t base = pref[w], wi = base >> 5, lo = base & 31;
+        uint32_t *crow = C + (size_t)a * cs;
         atomicOr(&crow[wi], out << lo);
         if (lo && lo + __popc(riw) > 32) atomicOr(&crow[wi + 1], out >> (32 - lo));
       }
       __syncthreads();
-      for (uint32_t u = tid; u < c * Wp; u += nt) a5 += nested_pairs_unit(Cb, u / Wp, u % Wp, Wp, cs);
+      for (;;) {
+        uint32_t u0 = 0;
+        if (lane == 0) u0 = atomicAdd(&ctr[2], 32u);
+        u0 = __shfl_sync(0xffffffffu, u0, 0);
+        if (u0 >= c * Wp) break;
+        const uint32_t u = u0 + lane;
+        if (u < c * Wp) a5 += nested_pairs_unit(C, u % c, u / c, Wp, cs, tri);
+      }
     } else {
       row_k45_groups(R, W, rs, i, tid >> 5, nt >> 5, lane, 32, a4, a5);
     }
@@ -364,9 +453,39 @@ __host__ __device__ constexpr uint32_t warp_words(uint32_t maxd, bool scatter) {
   return ((2 * maxd + maxd + (maxd + 1) + maxd * row_stride((maxd + 31) / 32) + (scatter ? maxd : 0)) + 1) & ~1u;
 }
 
-// Same layout for one CTA-wide root with W words per row.
+// Same layout for one CTA-wide root with W words per row, plus perm[maxd]
+// (positions in the orientation's order, see rank_local).
 __host__ __device__ constexpr uint64_t cta_words(uint32_t maxd, uint32_t W) {
-  return 2ull * maxd + maxd + (maxd + 1) + (uint64_t)maxd * row_stride(W) + maxd + 2;
+  return 2ull * maxd + maxd + (maxd + 1) + (uint64_t)maxd * row_stride(W) + maxd + maxd + 2;
+}
+
+// Ranks of the local vertices in the orientation's order (degree, then id):
+// perm[i] = #{i' : (deg L[i'], L[i']) < (deg L[i], L[i])}. Since L is sorted by
+// id, the key (deg << 32 | i) orders like (deg, id). Bitonic sort of the padded
+// keys in `keys` (nextpow2(d) words x 2) by the whole CTA; every thread calls.
+__device__ __forceinline__ void rank_local(const uint32_t *__restrict__ deg, const uint32_t *L, uint32_t d,
+                                           uint64_t *keys, uint32_t *perm) {
+  const uint32_t tid = threadIdx.x, nt = blockDim.x;
+  uint32_t n2 = 2;
+  while (n2 < d) n2 <<= 1;
+  for (uint32_t i = tid; i < n2; i += nt) keys[i] = (i < d) ? (((uint64_t)__ldg(deg + L[i]) << 32) | i) : ~0ull;
+  __syncthreads();
+  for (uint32_t k = 2; k <= n2; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t t = tid; t < n2 / 2; t += nt) {
+        const uint32_t lo = 2 * j * (t / j) + (t % j), hi = lo + j;
+        const bool up = (lo & k) == 0;
+        const uint64_t x = keys[lo], y = keys[hi];
+        if ((x > y) == up) {
+          keys[lo] = y;
+          keys[hi] = x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (uint32_t p = tid; p < d; p += nt) perm[(uint32_t)keys[p]] = p;
+  __syncthreads();
 }
 
 // One root u (2 <= d+(u) <= MAXD) processed by the calling warp. `base` is
@@ -424,16 +543,25 @@ template <int G, int KMAX, bool SCATTER>
 __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, const uint32_t *__restrict__ dcol,
                                             uint32_t *t_edge, uint32_t u, uint32_t maxd, uint32_t W, uint32_t *base,
                                             unsigned long long &a3, unsigned long long &a4, unsigned long long &a5,
-                                            uint32_t *nest = nullptr, uint32_t big_cap = 0) {
+                                            uint32_t *nest = nullptr, uint32_t big_cap = 0,
+                                            const uint32_t *__restrict__ deg = nullptr) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
   uint64_t *xb = reinterpret_cast<uint64_t *>(base);
   uint32_t *L = base + 2 * (size_t)maxd;
   uint32_t *pre = L + maxd;
   uint32_t *R = pre + maxd + 1;
   uint32_t *tc = R + (size_t)maxd * row_stride(W);
+  uint32_t *perm = tc + maxd;
   const uint64_t ub = drow[u];
   const uint32_t d = (uint32_t)(drow[u + 1] - ub);
   const uint32_t w_used = (d + 31) / 32, rs = row_stride(w_used);
+  // the nested 5-clique search runs on positions in the orientation's order;
+  // the sort keys borrow R's space (8-byte aligned) before R is cleared
+  uint32_t n2 = 2;
+  while (n2 < d) n2 <<= 1;
+  uint64_t *keys = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(R) + 7) & ~(uintptr_t)7);
+  const bool tri = KMAX >= 5 && nest != nullptr && deg != nullptr && w_used <= 32 &&
+                   (uint64_t)maxd * row_stride(W) >= 2ull * n2 + 1;
   for (uint32_t i = tid; i < d; i += nt) {
     const uint32_t x = __ldg(dcol + ub + i);
     L[i] = x;
@@ -441,6 +569,10 @@ __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, c
     xb[i] = xs;
     pre[i + 1] = (uint32_t)(xe - xs);
     if (SCATTER) tc[i] = 0;
+  }
+  if (tri) {
+    __syncthreads();
+    rank_local(deg, L, d, keys, perm);
   }
   for (size_t i = tid; i < (size_t)d * rs; i += nt) R[i] = 0;
   if (tid == 0) pre[0] = 0;
@@ -459,14 +591,14 @@ __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, c
     }
   }
   __syncthreads();
-  a3 += build_rows<SCATTER>(dcol, t_edge, L, pre, xb, R, tc, d, rs, tid, nt);
+  a3 += build_rows<SCATTER>(dcol, t_edge, L, pre, xb, R, tc, d, rs, tid, nt, tri ? perm : nullptr);
   __syncthreads();
   if (SCATTER) {
     for (uint32_t i = tid; i < d; i += nt)
       if (tc[i]) atomicAdd(&t_edge[ub + i], tc[i]);
   }
   if (KMAX >= 5 && nest != nullptr && w_used <= 32) {
-    enumerate_nested_cta(R, d, w_used, rs, nest, maxd, big_cap, a4, a5);
+    enumerate_nested_cta(R, d, w_used, rs, nest, maxd, big_cap, a4, a5, tri);
   } else if (KMAX >= 4) {
     if (w_used > 32)
       enumerate_rows_wide<KMAX>(R, d, w_used, rs, tid / 32, nt / 32, lane, a4, a5);
