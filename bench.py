@@ -203,6 +203,18 @@ def run_batched(args, graphs=None):
         got = plain()
         plain_t.append(time.perf_counter() - t0)
         assert got == want
+    # per-query wall times of the plain path (each count returns its counts to the host)
+    per_q = []
+    for G, k in zip(Gs, kinds):
+        t0 = time.perf_counter()
+        gpm.count(G, pats[k])
+        per_q.append(time.perf_counter() - t0)
+    per_q = np.array(per_q)
+    order = np.argsort(-per_q)
+    plain_profile = {"top10pct_share": float(per_q[order[:max(1, len(per_q) // 10)]].sum() / per_q.sum()),
+                     "queries_under_1ms": int((per_q < 1e-3).sum()), "seconds_under_1ms": float(per_q[per_q < 1e-3].sum()),
+                     "largest_s": [round(float(x), 4) for x in per_q[order[:8]]],
+                     "largest_edges": [int(graphs[i].m) for i in order[:8]]}
     B = gpm.Batch(list(zip(Gs, kinds)))
     t0 = time.perf_counter()
     first = B.run()  # autotunes the item schedule
@@ -225,6 +237,7 @@ def run_batched(args, graphs=None):
     return {"workload": BATCH_WORKLOAD, "queries": nq, "edges_total": int(sum(g.m for g in graphs)),
             "plain_queries_per_s": pq, "batched_queries_per_s": bq, "speedup": bq / pq,
             "plain_s": plain_t, "batched_s": batch_t, "autotune_s": tune_s, "setup_s": setup_s,
+            "plain_per_query": plain_profile,
             "schedule": info, "equal_counts": True}
 
 

@@ -20,7 +20,9 @@
 // Admission is by memory footprint: a request needs a free slot, room in the
 // item ring and, for 4-motif queries, a per-arc triangle-count block (4 bytes
 // per edge) from a fixed device arena; otherwise it waits in a host FIFO and
-// is admitted when completions free resources.
+// is admitted when completions free resources. Express and bulk requests wait
+// in separate FIFOs, and bulk requests may hold at most three quarters of the
+// slots, so a blocked large request never holds back small ones.
 //
 // Every wait is bounded: the kernel's idle poll exits after about 20 ms
 // without work (the host relaunches it when work arrives), and the 4-motif
@@ -182,7 +184,8 @@ struct gpm_server {
   };
   std::vector<Live> live;
   std::vector<uint32_t> free_slots;
-  std::deque<Req> pending;
+  std::deque<Req> pending[2];  // 0 express, 1 bulk
+  uint32_t bulk_live = 0, bulk_max = 0;
   std::deque<gpm_completion_t> instant;  // requests with no device work (empty task sets)
   uint32_t max_pending = 1u << 20;
   std::map<uint64_t, uint64_t> arena_free;  // offset -> length (words)
@@ -289,6 +292,7 @@ int try_admit(gpm_server *s, const gpm_server::Req &r, int *rc) {
   const std::vector<Item> &tmpl = items_for(s, r.graph, r.kind, &sc, &al);
   const uint64_t nitems = tmpl.size();
   gpm_graph *g = s->graphs[r.graph];
+  if (nitems > kExpressItems && s->bulk_live >= s->bulk_max) return 0;
   if (nitems == 0) {
     // nothing rooted anywhere (no root has two out-neighbours): every count is 0
     gpm_completion_t c{};
@@ -310,6 +314,7 @@ int try_admit(gpm_server *s, const gpm_server::Req &r, int *rc) {
   }
   const uint32_t slot = s->free_slots.back();
   s->free_slots.pop_back();
+  if (ring == 1) ++s->bulk_live;
   gpm_server::Live &l = s->live[slot];
   l.busy = true;
   l.req = r;
@@ -374,13 +379,25 @@ int try_admit(gpm_server *s, const gpm_server::Req &r, int *rc) {
   return 1;
 }
 
+// Express FIFO first, then bulk FIFO; each stops at its first request that
+// does not fit.
 int admit_pending(gpm_server *s) {
-  while (!s->pending.empty()) {
-    int rc = GPM_OK;
-    if (!try_admit(s, s->pending.front(), &rc)) return rc;
-    s->pending.pop_front();
+  for (int q = 0; q < 2; ++q) {
+    while (!s->pending[q].empty()) {
+      int rc = GPM_OK;
+      if (!try_admit(s, s->pending[q].front(), &rc)) {
+        if (rc) return rc;
+        break;
+      }
+      s->pending[q].pop_front();
+    }
   }
   return GPM_OK;
+}
+
+int express_request(gpm_server *s, uint32_t graph, uint32_t kind) {
+  uint32_t sc, al;
+  return items_for(s, graph, kind, &sc, &al).size() <= kExpressItems ? 0 : 1;
 }
 
 void free_server(gpm_server *s) {
@@ -412,6 +429,7 @@ int gpm_server_start(const gpm_graph_t *graphs, uint32_t ngraphs, const gpm_serv
     return code;
   };
   const uint32_t nslots = (opts && opts->max_inflight) ? opts->max_inflight : 256;
+  s->bulk_max = std::max<uint32_t>(1, nslots - nslots / 4);
   const uint64_t arena_bytes = (opts && opts->arena_bytes) ? opts->arena_bytes : (4ull << 30);
   const uint64_t ring_items = (opts && opts->ring_items) ? opts->ring_items : (8ull << 20);
   if (cudaGetDevice(&s->device) != cudaSuccess) {
@@ -507,13 +525,15 @@ int gpm_server_submit(gpm_server_t s, uint32_t graph, uint32_t kind, uint64_t ta
   if (nitems > s->ring_cap[1]) return gpm_fail(GPM_E_INVALID_ARG, "request needs more items than the ring holds");
   if (kind == GPM_QUERY_MOTIF4 && ((std::max<uint64_t>(s->graphs[graph]->m, 1) + 63) & ~63ull) > s->arena_words)
     return gpm_fail(GPM_E_INVALID_ARG, "request needs more arena memory than the server has");
-  if (s->pending.empty()) {
+  const int q = express_request(s, graph, kind);
+  if (s->pending[q].empty()) {
     int rc = GPM_OK;
     if (try_admit(s, r, &rc)) return GPM_OK;
     if (rc) return rc;
   }
-  if (s->pending.size() >= s->max_pending) return gpm_fail(GPM_E_BUSY, "server queue is full");
-  s->pending.push_back(r);
+  if (s->pending[0].size() + s->pending[1].size() >= s->max_pending)
+    return gpm_fail(GPM_E_BUSY, "server queue is full");
+  s->pending[q].push_back(r);
   return GPM_OK;
 }
 
@@ -543,6 +563,7 @@ int gpm_server_poll(gpm_server_t s, gpm_completion_t *out, uint32_t max, uint32_
     if (o.status != GPM_OK && l.arena_len)
       cudaMemsetAsync(s->d_arena + l.arena_off, 0, l.arena_len * 4, s->copy);  // re-zero a dirty block
     if (l.arena_len) arena_give(s, l.arena_off, l.arena_len);
+    if (l.ring == 1) --s->bulk_live;
     l.busy = false;
     s->free_slots.push_back(slot);
     s->comp_read++;
@@ -562,7 +583,7 @@ int gpm_server_stats(gpm_server_t s, uint32_t *inflight, uint32_t *pending) {
   uint32_t busy = 0;
   for (auto &l : s->live) busy += l.busy;
   if (inflight) *inflight = busy;
-  if (pending) *pending = (uint32_t)s->pending.size();
+  if (pending) *pending = (uint32_t)(s->pending[0].size() + s->pending[1].size());
   return GPM_OK;
 }
 

@@ -97,3 +97,31 @@ def test_server_idle_exit_and_relaunch(gpm):
     second = _drain(S, 1)
     assert first[1][2] == second[2][2] == [O.triangles(g)]
     S.stop()
+
+
+def test_server_small_requests_overtake_blocked_large_ones(gpm):
+    # the arena holds one large 4-motif request; two more wait for it. Small
+    # (express) requests submitted after them are admitted at once and finish
+    # before the last large one.
+    big = gg.rmat(14, 16.0, seed=107)
+    small = gg.rmat(7, 8.0, seed=108)
+    Gb, Gs = gpm.Graph.from_host(big), gpm.Graph.from_host(small)
+    want_big = _plain(gpm, Gb, gpm.QUERY_MOTIF4)
+    want_small = _plain(gpm, Gs, gpm.QUERY_TC)
+    S = gpm.Server([Gb, Gs], max_inflight=8, arena_bytes=4 * (big.m + 64))
+    for tag in range(3):
+        S.submit(0, gpm.QUERY_MOTIF4, tag)
+    for tag in range(100, 110):
+        S.submit(1, gpm.QUERY_TC, tag)
+    order, got = [], {}
+    t0 = time.time()
+    while len(got) < 13 and time.time() - t0 < 120:
+        for tag, gi, kind, status, counts in S.poll():
+            assert status == 0
+            got[tag] = counts
+            order.append(tag)
+        time.sleep(0.0005)
+    assert len(got) == 13
+    assert all(got[t] == want_big for t in range(3)) and all(got[t] == want_small for t in range(100, 110))
+    assert max(order.index(t) for t in range(100, 110)) < order.index(2)
+    S.stop()
