@@ -131,10 +131,17 @@ def clique_pass_bytes(g, opts):
     return {names[c]: float(per_root[cls == c].sum()) for c in names}, int(od.max())
 
 
-# Per-launch counters of the dominant kernels from `ncu` captures of this very
-# bench command (see profiles/), valid only for the kernel sources they were
-# taken on: the digest below is of csrc/lg_device.cuh + csrc/clique.cu.
-NCU_COUNTERS = {}
+# Per-launch counters of the dominant kernel from a one-pass `ncu` capture of
+# the same kernel on the same workload (profiles/lg_cta_hi_rmat21_counters.md):
+#   ncu --metrics smsp__inst_executed.sum,gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
+#       --clock-control none -k regex:lg_cta_kernel -c 1
+#       python -m paper_2011_03135_b300.cases --case clique-rmat21 --reps 1
+# valid only for the kernel sources they were taken on (digest of
+# csrc/lg_device.cuh + csrc/clique.cu); a stale entry is ignored.
+NCU_COUNTERS = {
+    "lg_cta_hi": {"digest": "5c74c5b32f28f83f", "inst_per_launch": 160425295540,
+                  "dram_bytes_per_launch": 28331776 + 2816, "ncu_ms": 223.346},
+}
 
 
 def kernel_digest():

@@ -95,8 +95,8 @@ __global__ void __launch_bounds__(256) lg_warp_kernel(LGArgs a) {
 // one CTA per root; bitmap in shared memory (GLOBAL = false) or in this
 // CTA's global-memory slot (GLOBAL = true)
 // ---------------------------------------------------------------------------
-template <int G, int KMAX, bool SCATTER, bool GLOBAL>
-__global__ void __launch_bounds__(512) lg_cta_kernel(LGArgs a, uint32_t maxd, uint32_t big_cap) {
+template <int G, int KMAX, bool SCATTER, bool GLOBAL, int THREADS>
+__global__ void __launch_bounds__(THREADS) lg_cta_kernel(LGArgs a, uint32_t maxd, uint32_t big_cap, uint32_t wcap) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint32_t s_task;
   uint32_t *base = GLOBAL ? a.pool + (size_t)blockIdx.x * a.slot_words : smem;
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(512) lg_cta_kernel(LGArgs a, uint32_t maxd, ui
     const uint32_t d = (uint32_t)(a.drow[u + 1] - a.drow[u]);
     if (d < 2 || d > maxd) continue;
     gpm_dev::lg_root_cta<G, KMAX, SCATTER>(a.drow, a.dcol, a.t_edge, u, maxd, a.W, base, a3, a4, a5, nest, big_cap,
-                                           a.deg);
+                                           a.deg, wcap);
   }
   flush_acc(a, a3, a4, a5, KMAX);
 }
@@ -154,33 +154,44 @@ int max_smem_optin(int device) {
   return cached[device];
 }
 
-template <int G, int KMAX, bool SCATTER, bool GLOBAL>
-int launch_cta(const LGArgs &a, uint32_t maxd, int blocks_cap, int device, cudaStream_t st,
-               size_t smem_limit = 0, const char *name = nullptr) {
-  constexpr int kThreads = 512;
+// THREADS = 1024 (32 warps, one CTA per SM) for the largest shared-memory
+// roots with the nested 5-clique search: one-warp rows are capped at 64 so
+// that 32 warp buffers fit beside the bitmap.
+template <int G, int KMAX, bool SCATTER, bool GLOBAL, int THREADS>
+int launch_cta_t(const LGArgs &a, uint32_t maxd, int blocks_cap, int device, cudaStream_t st, size_t smem_limit,
+                 const char *name) {
+  const uint32_t wcap = THREADS >= 1024 ? 64u : gpm_dev::kNestWarpC;
   size_t smem = GLOBAL ? 0 : (size_t)cta_words(maxd, a.W) * 4;
   uint32_t big_cap = 0;
   if (!GLOBAL && KMAX >= 5) {
     // room left after the bitmap and the per-warp nested buffers goes to the CTA-wide nested buffer
-    const size_t fixed = smem + (size_t)gpm_dev::nest_words(maxd, kThreads / 32, 0) * 4 + 2048;
+    const size_t fixed = smem + (size_t)gpm_dev::nest_words(maxd, THREADS / 32, 0, wcap) * 4 + 2048;
     const size_t limit = smem_limit ? smem_limit : (size_t)max_smem_optin(device);
     if (fixed + 4 * 1024 <= limit) {
       big_cap = (uint32_t)std::min<size_t>((limit - fixed) / 4, 32768);
-      smem += (size_t)gpm_dev::nest_words(maxd, kThreads / 32, big_cap) * 4;
+      smem += (size_t)gpm_dev::nest_words(maxd, THREADS / 32, big_cap, wcap) * 4;
     }
   }
-  auto kern = lg_cta_kernel<G, KMAX, SCATTER, GLOBAL>;
+  auto kern = lg_cta_kernel<G, KMAX, SCATTER, GLOBAL, THREADS>;
   if (!GLOBAL) GPM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+  GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem));
   if (per_sm < 1) per_sm = 1;
   int blocks = gpm_num_sms(device) * per_sm;
   blocks = std::max(1, std::min<int>(blocks, (int)a.ntasks));
   if (blocks_cap > 0) blocks = std::min(blocks, blocks_cap);
   GPM_LAUNCH(name ? name : (GLOBAL ? "lg_cta_global" : "lg_cta"), st,
-             kern<<<blocks, kThreads, smem, st>>>(a, maxd, big_cap));
+             kern<<<blocks, THREADS, smem, st>>>(a, maxd, big_cap, wcap));
   GPM_CUDA(cudaGetLastError());
   return GPM_OK;
+}
+
+template <int G, int KMAX, bool SCATTER, bool GLOBAL>
+int launch_cta(const LGArgs &a, uint32_t maxd, int blocks_cap, int device, cudaStream_t st,
+               size_t smem_limit = 0, const char *name = nullptr, bool wide = false) {
+  if (KMAX >= 5 && !GLOBAL && wide)
+    return launch_cta_t<G, KMAX, SCATTER, GLOBAL, 1024>(a, maxd, blocks_cap, device, st, smem_limit, name);
+  return launch_cta_t<G, KMAX, SCATTER, GLOBAL, 512>(a, maxd, blocks_cap, device, st, smem_limit, name);
 }
 
 template <int KMAX, bool SCATTER>
@@ -221,9 +232,10 @@ int launch_all(gpm_graph *g, LGArgs base, unsigned int *queues, cudaStream_t st)
     const size_t limit = part == 0 ? 0 : (size_t)(max_smem_optin(dev) / 2 - 1024);
     const char *nm = part == 0 ? "lg_cta_hi" : "lg_cta_lo";
     if (a.ntasks) {
+      const bool wide = part == 0;
       if (a.W <= 8) GPM_TRY((launch_cta<8, KMAX, SCATTER, false>(a, md, 0, dev, st, limit, nm)));
-      else if (a.W <= 16) GPM_TRY((launch_cta<16, KMAX, SCATTER, false>(a, md, 0, dev, st, limit, nm)));
-      else GPM_TRY((launch_cta<32, KMAX, SCATTER, false>(a, md, 0, dev, st, limit, nm)));
+      else if (a.W <= 16) GPM_TRY((launch_cta<16, KMAX, SCATTER, false>(a, md, 0, dev, st, limit, nm, wide)));
+      else GPM_TRY((launch_cta<32, KMAX, SCATTER, false>(a, md, 0, dev, st, limit, nm, wide)));
     }
   }
   // class XL: global-memory bitmaps, one slot per resident CTA

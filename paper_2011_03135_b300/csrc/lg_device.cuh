@@ -66,6 +66,86 @@ __device__ __forceinline__ uint32_t build_rows(const uint32_t *__restrict__ dcol
   return found;
 }
 
+// Position table of L for build_rows_hashed: open addressing on the vertex id
+// with 2^hbits >= 2d slots (keys, then values). Built by the whole CTA; the
+// caller synchronises before and after.
+constexpr uint32_t kPosEmpty = 0xffffffffu;
+__device__ __forceinline__ uint32_t pos_hash(uint32_t y, uint32_t hbits) { return (y * 0x9E3779B1u) >> (32 - hbits); }
+
+__device__ __forceinline__ void build_pos_table(const uint32_t *L, uint32_t d, uint32_t *hk, uint32_t hbits,
+                                                uint32_t t, uint32_t nt) {
+  const uint32_t ns = 1u << hbits, mask = ns - 1;
+  uint32_t *hv = hk + ns;
+  for (uint32_t i = t; i < ns; i += nt) hk[i] = kPosEmpty;
+  __syncthreads();
+  for (uint32_t i = t; i < d; i += nt) {
+    const uint32_t y = L[i];
+    uint32_t h = pos_hash(y, hbits);
+    while (atomicCAS(&hk[h], kPosEmpty, y) != kPosEmpty) h = (h + 1) & mask;  // ids in L are distinct
+    hv[h] = i;
+  }
+}
+
+// build_rows with the element lookup in the position table (about two probes
+// instead of a binary search over L) and four consecutive elements per thread
+// (one search for the row of the first, then a forward step).
+template <bool SCATTER>
+__device__ __forceinline__ uint32_t build_rows_hashed(const uint32_t *__restrict__ dcol, uint32_t *t_edge,
+                                                      const uint32_t *L, const uint32_t *pre, const uint64_t *xb,
+                                                      uint32_t *R, uint32_t *tc, uint32_t d, uint32_t rs, uint32_t t,
+                                                      uint32_t nt, const uint32_t *perm, const uint32_t *hk,
+                                                      uint32_t hbits) {
+  const uint32_t E = pre[d], mask = (1u << hbits) - 1;
+  const uint32_t *hv = hk + (1u << hbits);
+  uint32_t found = 0;
+  const uint32_t lo_id = L[0], hi_id = L[d - 1];
+  for (uint32_t f0 = 4 * t; f0 < E; f0 += 4 * nt) {
+    uint32_t i = row_of(pre, d, f0);
+    uint32_t rowi[4];
+    uint64_t arc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t f = f0 + q;
+      if (f < E) {
+        while (pre[i + 1] <= f) ++i;
+        rowi[q] = i;
+        arc[q] = xb[i] + (f - pre[i]);
+      } else {
+        rowi[q] = 0xffffffffu;
+        arc[q] = 0;
+      }
+    }
+    uint32_t y[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) y[q] = (rowi[q] != 0xffffffffu) ? __ldg(dcol + arc[q]) : 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (rowi[q] == 0xffffffffu || y[q] < lo_id || y[q] > hi_id) continue;
+      uint32_t h = pos_hash(y[q], hbits), j = kPosEmpty;
+      for (;;) {
+        const uint32_t k = hk[h];
+        if (k == y[q]) {
+          j = hv[h];
+          break;
+        }
+        if (k == kPosEmpty) break;
+        h = (h + 1) & mask;
+      }
+      if (j == kPosEmpty) continue;
+      const uint32_t ii = rowi[q];
+      const uint32_t ri = perm ? perm[ii] : ii, rj = perm ? perm[j] : j;
+      atomicOr(&R[(size_t)ri * rs + (rj >> 5)], 1u << (rj & 31));
+      ++found;
+      if (SCATTER) {
+        atomicAdd(&tc[ii], 1u);
+        atomicAdd(&tc[j], 1u);
+        atomicAdd(&t_edge[arc[q]], 1u);
+      }
+    }
+  }
+  return found;
+}
+
 // Enumerate pairs (i, j in R_i) and triples for the 4- and 5-clique terms.
 // A group of G lanes handles one row at a time; lane gl of the group holds
 // word gl of the row (W <= G), so every AND is one word per lane.
@@ -145,15 +225,19 @@ __device__ inline void enumerate_rows_wide(const uint32_t *R, uint32_t d, uint32
 // W' is far narrower than W for most i, so the last level costs W' words per
 // visited 4-clique instead of W, and one thread walks one compacted row.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kNestWarpC = 128;  // rows with c <= this are nested by one warp
-constexpr uint32_t kNestWarpWp = 4;   // = kNestWarpC / 32
-constexpr uint32_t kNestWarpWords = kNestWarpC + 32 + kNestWarpC * (kNestWarpWp | 1u);
+// Rows with c <= wcap (64 or 128) are nested by one warp; a warp's buffer holds
+// S[wcap] pref[32] C[wcap rows of row_stride(wcap/32) words].
+constexpr uint32_t kNestWarpC = 128;  // largest wcap
+__host__ __device__ constexpr uint32_t nest_warp_words(uint32_t wcap) {
+  return wcap + 32 + wcap * row_stride(wcap / 32);
+}
 
-__host__ __device__ constexpr uint64_t nest_words(uint32_t maxd, uint32_t nwarps, uint32_t big_cap) {
+__host__ __device__ constexpr uint64_t nest_words(uint32_t maxd, uint32_t nwarps, uint32_t big_cap,
+                                                  uint32_t wcap = kNestWarpC) {
   // counters[4], big-row list[maxd], wide-row list[maxd], then a pool that
-  // holds per warp S[128] pref[32] C[128*5] in the warp phase, and the
-  // groups' (or the CTA's) S[maxd] pref[32] C[...] in the big-row phases
-  return 4ull + 2ull * maxd + (uint64_t)nwarps * kNestWarpWords + maxd + 32 + big_cap;
+  // holds the warps' buffers in the warp phase, and the groups' (or the
+  // CTA's) S[maxd] pref[32] C[...] in the big-row phases
+  return 4ull + 2ull * maxd + (uint64_t)nwarps * nest_warp_words(wcap) + maxd + 32 + big_cap;
 }
 
 // named barrier over `nthreads` threads (a multiple of 32) of the CTA
@@ -290,22 +374,23 @@ __device__ __forceinline__ void row_k45_groups(const uint32_t *R, uint32_t W, ui
 }
 
 // 4- and 5-cliques of one root's local graph R (d rows, W <= 32 words) by the
-// whole CTA with nesting. nest: nest_words(maxd, blockDim/32, big_cap) words.
-// Rows with c <= kNestWarpC are nested by one warp each; larger rows by groups
-// of four warps (one row per group at a time, named barriers, so groups do not
-// wait for each other); rows too large for a group's share of the pool by the
-// whole CTA at the end.
+// whole CTA with nesting. nest: nest_words(maxd, blockDim/32, big_cap, wcap)
+// words. Rows with c <= wcap are nested by one warp each; larger rows by four
+// groups of warps (one row per group at a time, named barriers, so groups do
+// not wait for each other); rows too large for a group's share of the pool by
+// the whole CTA at the end.
 // With tri, R is strictly upper triangular (positions in the orientation's
 // order), and so is every nested C: the word loops start at the pivot.
 __device__ inline void enumerate_nested_cta(const uint32_t *R, uint32_t d, uint32_t W, uint32_t rs, uint32_t *nest,
                                             uint32_t maxd, uint32_t big_cap, unsigned long long &a4,
-                                            unsigned long long &a5, bool tri = false) {
+                                            unsigned long long &a5, bool tri = false, uint32_t wcap = kNestWarpC) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   uint32_t *ctr = nest;  // [0] next row, [1] big rows, [2] next big row, [3] wide rows
   uint32_t *big_list = nest + 4;
   uint32_t *wide_list = big_list + maxd;
   uint32_t *pool = wide_list + maxd;
-  const uint32_t pool_words = nw * kNestWarpWords + maxd + 32 + big_cap;
+  const uint32_t wwords = nest_warp_words(wcap);
+  const uint32_t pool_words = nw * wwords + maxd + 32 + big_cap;
   if (tid == 0) {
     ctr[0] = 0;
     ctr[1] = 0;
@@ -315,17 +400,17 @@ __device__ inline void enumerate_nested_cta(const uint32_t *R, uint32_t d, uint3
   __syncthreads();
   // rows with c <= kNestWarpC: one warp each, pulled dynamically
   {
-    uint32_t *wbuf = pool + (size_t)wid * kNestWarpWords;
-    uint32_t *S = wbuf, *pref = wbuf + kNestWarpC, *C = wbuf + kNestWarpC + 32;
+    uint32_t *wbuf = pool + (size_t)wid * wwords;
+    uint32_t *S = wbuf, *pref = wbuf + wcap, *C = wbuf + wcap + 32;
     for (;;) {
       uint32_t i = 0;
       if (lane == 0) i = atomicAdd(&ctr[0], 1u);
       i = __shfl_sync(0xffffffffu, i, 0);
       if (i >= d) break;
       const uint32_t *ri = R + (size_t)i * rs;
-      const uint32_t c = list_bits_warp(ri, W, S, pref, kNestWarpC);
+      const uint32_t c = list_bits_warp(ri, W, S, pref, wcap);
       if (c < 2) continue;
-      if (c > kNestWarpC) {
+      if (c > wcap) {
         if (lane == 0) big_list[atomicAdd(&ctr[1], 1u)] = i;
         continue;
       }
@@ -350,10 +435,10 @@ __device__ inline void enumerate_nested_cta(const uint32_t *R, uint32_t d, uint3
   const uint32_t nbig = ctr[1];
   // rows with larger c: groups of four warps, one row per group at a time
   if (nbig) {
-    constexpr uint32_t kGroupWarps = 4;
-    const uint32_t ng = nw >= kGroupWarps ? nw / kGroupWarps : 1u;
-    const uint32_t gthreads = (ng > 1) ? kGroupWarps * 32 : nt;
-    const uint32_t g = (ng > 1) ? wid / kGroupWarps : 0u;
+    const uint32_t gwarps = nw >= 32 ? 8u : 4u;  // four groups for 16 or 32 warps
+    const uint32_t ng = nw >= gwarps ? nw / gwarps : 1u;
+    const uint32_t gthreads = (ng > 1) ? gwarps * 32 : nt;
+    const uint32_t g = (ng > 1) ? wid / gwarps : 0u;
     if (g < ng) {  // warps beyond ng groups (nw not a multiple of 4) sit this phase out
       const uint32_t gt = tid - g * gthreads, gw = gt >> 5;
       const uint32_t share = pool_words / ng;
@@ -544,7 +629,7 @@ __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, c
                                             uint32_t *t_edge, uint32_t u, uint32_t maxd, uint32_t W, uint32_t *base,
                                             unsigned long long &a3, unsigned long long &a4, unsigned long long &a5,
                                             uint32_t *nest = nullptr, uint32_t big_cap = 0,
-                                            const uint32_t *__restrict__ deg = nullptr) {
+                                            const uint32_t *__restrict__ deg = nullptr, uint32_t wcap = kNestWarpC) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
   uint64_t *xb = reinterpret_cast<uint64_t *>(base);
   uint32_t *L = base + 2 * (size_t)maxd;
@@ -576,6 +661,12 @@ __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, c
   }
   for (size_t i = tid; i < (size_t)d * rs; i += nt) R[i] = 0;
   if (tid == 0) pre[0] = 0;
+  // with the nested-search region present, its pool holds L's position table
+  // until the enumeration starts (2^hbits >= 2d slots, keys and values)
+  uint32_t hbits = 1;
+  while ((1u << hbits) < 2 * d) ++hbits;
+  uint32_t *hk = nest ? nest + 4 + 2 * (size_t)maxd : nullptr;
+  if (hk) build_pos_table(L, d, hk, hbits, tid, nt);
   __syncthreads();
   if (tid < 32) {
     uint32_t carry = 0;
@@ -591,14 +682,17 @@ __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, c
     }
   }
   __syncthreads();
-  a3 += build_rows<SCATTER>(dcol, t_edge, L, pre, xb, R, tc, d, rs, tid, nt, tri ? perm : nullptr);
+  if (hk)
+    a3 += build_rows_hashed<SCATTER>(dcol, t_edge, L, pre, xb, R, tc, d, rs, tid, nt, tri ? perm : nullptr, hk, hbits);
+  else
+    a3 += build_rows<SCATTER>(dcol, t_edge, L, pre, xb, R, tc, d, rs, tid, nt, tri ? perm : nullptr);
   __syncthreads();
   if (SCATTER) {
     for (uint32_t i = tid; i < d; i += nt)
       if (tc[i]) atomicAdd(&t_edge[ub + i], tc[i]);
   }
   if (KMAX >= 5 && nest != nullptr && w_used <= 32) {
-    enumerate_nested_cta(R, d, w_used, rs, nest, maxd, big_cap, a4, a5, tri);
+    enumerate_nested_cta(R, d, w_used, rs, nest, maxd, big_cap, a4, a5, tri, wcap);
   } else if (KMAX >= 4) {
     if (w_used > 32)
       enumerate_rows_wide<KMAX>(R, d, w_used, rs, tid / 32, nt / 32, lane, a4, a5);
