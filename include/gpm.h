@@ -232,10 +232,13 @@ typedef struct gpm_batch *gpm_batch_t;
  * problems, Section 2, for many inputs at once). Every query is cut into work
  * items of per-root tasks; all items of all queries run in ONE persistent
  * kernel captured in a CUDA graph, pulling items from a global atomic queue,
- * so small and large queries overlap on the device. The graphs must outlive
- * the batch and must not be counted concurrently by other calls while the
- * batch runs. Roots with out-degree above 1024 are not supported here
- * (GPM_E_UNSUPPORTED). Synchronises the device.
+ * so small and large queries overlap on the device. Heavy queries (plain
+ * count path at least batch_direct_us on the device, timed here) instead run
+ * that path inside the same captured graph, ahead of the persistent kernel;
+ * so do the whole-GPU launches of hub-class 4-cycle roots of item queries.
+ * The graphs must outlive the batch and must not be counted concurrently by
+ * other calls while the batch runs. Roots with out-degree above 1024 are not
+ * supported in item queries (GPM_E_UNSUPPORTED). Synchronises the device.
  */
 int gpm_batch_create(const gpm_query_t *queries, uint32_t nq, gpm_batch_t *out);
 
@@ -251,6 +254,10 @@ int gpm_batch_run(gpm_batch_t b, uint64_t *counts, void *stream);
 /* Schedule chosen by the autotuner and the persistent grid size. */
 int gpm_batch_info(gpm_batch_t b, uint32_t *nitems, uint32_t *roots_per_item, uint32_t *verts_per_item,
                    uint32_t *grid);
+
+/* Number of queries that run their plain count path inside the graph, and
+ * kernels one replay launches. */
+int gpm_batch_direct(gpm_batch_t b, uint32_t *ndirect, uint64_t *graph_kernels);
 
 int gpm_batch_destroy(gpm_batch_t b);
 
@@ -365,7 +372,11 @@ typedef struct {
   uint32_t c4_hub_bound;    /* 4-cycle roots whose wedge bound (sum of the degrees of their neighbours
                                before them) exceeds this are counted by the whole GPU a few at a time;
                                range [513, 1048576], default 1048576 */
-  uint32_t reserved[4];
+  uint32_t batch_direct_us; /* batched form: a query whose plain count path takes at least this many
+                               microseconds on the device (timed when the batch is created) runs that
+                               path inside the captured graph instead of as items; default 1000,
+                               0xffffffff = never */
+  uint32_t reserved[3];
 } gpm_options_t;
 
 int gpm_set_options(const gpm_options_t *opt);

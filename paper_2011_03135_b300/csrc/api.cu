@@ -206,6 +206,15 @@ bool is_device_pointer(const void *p) {
 
 }  // namespace
 
+int gpm_enqueue_count(gpm_graph *g, const gpm_pattern_t *pats, uint32_t npat, unsigned long long *out_dev,
+                      cudaStream_t st) {
+  return enqueue_count(g, pats, npat, 0, g->n, false, out_dev, st);
+}
+
+const unsigned int *gpm_graph_status(const gpm_graph *g) {
+  return reinterpret_cast<const unsigned int *>(g->work + WK_STATUS);
+}
+
 // ---------------------------------------------------------------------------
 // C-ABI
 // ---------------------------------------------------------------------------
@@ -234,6 +243,7 @@ int gpm_set_options(const gpm_options_t *opt) {
       return gpm_fail(GPM_E_INVALID_ARG, "c4_hub_bound must be in [513, 1048576]");
     t.c4_hub_bound = opt->c4_hub_bound;
   }
+  if (opt->batch_direct_us) t.batch_direct_us = opt->batch_direct_us;
   return GPM_OK;
 }
 
@@ -244,6 +254,7 @@ int gpm_get_options(gpm_options_t *opt) {
   opt->cta_max_degree = gpm_tune().cta_max_degree;
   opt->blocks_per_sm = gpm_tune().blocks_per_sm;
   opt->c4_hub_bound = gpm_tune().c4_hub_bound;
+  opt->batch_direct_us = gpm_tune().batch_direct_us;
   return GPM_OK;
 }
 

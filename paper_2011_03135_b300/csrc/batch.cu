@@ -104,6 +104,13 @@ struct gpm_batch {
   cudaGraphExec_t exec = nullptr;
   uint64_t graph_kernels = 1;  // kernels one replay launches
   std::vector<QDesc> qs;
+  // queries run as their plain count path inside the captured graph (heavy
+  // queries, measured at creation), with their patterns and status words
+  std::vector<uint8_t> direct;
+  std::vector<gpm_pattern_t> kind_pats[8];
+  unsigned int *d_dstatus = nullptr;
+  unsigned int *h_dstatus = nullptr;
+  uint32_t ndirect = 0;
   double tuned_ms = 0.0;
 };
 
@@ -112,10 +119,14 @@ namespace {
 void free_batch(gpm_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  void *dev[] = {b->d_qs, b->d_items, b->d_acc, b->d_out, b->d_left, b->d_head, b->tally_pool, b->lg_pool, b->c4_buf};
+  void *dev[] = {b->d_qs,       b->d_items, b->d_acc,  b->d_out,     b->d_left, b->d_head,
+                 b->tally_pool, b->lg_pool, b->c4_buf, b->d_dstatus};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (b->h_out) cudaFreeHost(b->h_out);
+  if (b->h_dstatus) cudaFreeHost(b->h_dstatus);
+  for (auto &v : b->kind_pats)
+    for (gpm_pattern_t p : v) gpm_pattern_destroy(p);
   for (uint32_t *p : b->own_t_edge) cudaFree(p);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -128,6 +139,10 @@ void make_items(gpm_batch *b, std::vector<Item> &items) {
   const uint32_t nq = (uint32_t)b->queries.size();
   for (uint32_t qi = 0; qi < nq; ++qi) {
     QDesc &q = b->qs[qi];
+    if (b->direct[qi]) {
+      q.scatter_items = q.all_items = 0;
+      continue;
+    }
     append_query_items(b->queries[qi].graph, q.kind, qi, b->roots_per_item, b->verts_per_item, heavy, light, edge,
                        &q.scatter_items, &q.all_items, true);
   }
@@ -185,16 +200,31 @@ int capture(gpm_batch *b) {
   // hub-class 4-cycle roots first: whole-GPU launches per query, adding to the
   // query's accumulator before the persistent kernel finalises it
   b->graph_kernels = 1;
+  const uint64_t captured0 = gpm_captured_launches();
   int hub_rc = GPM_OK;
+  // heavy queries: their plain count path, outputs straight to their slots
+  for (uint32_t qi = 0, k = 0; qi < nq && hub_rc == GPM_OK; ++qi) {
+    if (!b->direct[qi]) continue;
+    const std::vector<gpm_pattern_t> &pats = b->kind_pats[b->qs[qi].kind];
+    gpm_graph *g = b->queries[qi].graph;
+    hub_rc = gpm_enqueue_count(g, pats.data(), (uint32_t)pats.size(), b->d_out + (size_t)6 * qi, b->stream);
+    if (hub_rc == GPM_OK &&
+        cudaMemcpyAsync(b->d_dstatus + k++, gpm_graph_status(g), sizeof(unsigned int), cudaMemcpyDeviceToDevice,
+                        b->stream) != cudaSuccess)
+      hub_rc = gpm_fail(GPM_E_DEVICE, "batch capture (status copy)");
+  }
+  b->graph_kernels += gpm_captured_launches() - captured0;
   for (uint32_t qi = 0; qi < nq && hub_rc == GPM_OK; ++qi) {
     gpm_graph *g = b->queries[qi].graph;
-    if (b->qs[qi].kind != GPM_QUERY_MOTIF4 || g->c4_begin[3] == g->c4_begin[2]) continue;
+    if (b->direct[qi] || b->qs[qi].kind != GPM_QUERY_MOTIF4 || g->c4_begin[3] == g->c4_begin[2]) continue;
     uint32_t nl = 0;
     hub_rc = gpm_c4_hub_enqueue(g, 0, g->n, b->d_acc + (size_t)qi * ACC_WORDS, b->stream, &nl);
     b->graph_kernels += nl;
   }
   GPM_LAUNCH("batch_kernel", b->stream, batch_kernel<<<b->grid, kThreads, b->smem, b->stream>>>(a));
   cudaMemcpyAsync(b->h_out, b->d_out, sizeof(uint64_t) * 6 * nq, cudaMemcpyDeviceToHost, b->stream);
+  if (b->ndirect)
+    cudaMemcpyAsync(b->h_dstatus, b->d_dstatus, sizeof(unsigned int) * b->ndirect, cudaMemcpyDeviceToHost, b->stream);
   cudaError_t e = cudaStreamEndCapture(b->stream, &b->graph);
   if (hub_rc != GPM_OK) return hub_rc;
   if (e != cudaSuccess) return gpm_cuda_fail(e, "batch capture");
@@ -231,6 +261,77 @@ int replay(gpm_batch *b, float *ms) {
     if (status & ST_TIMEOUT) return gpm_fail(GPM_E_TIMEOUT, "batched kernel: a bounded wait gave up");
     return gpm_fail(GPM_E_OVERFLOW, "batched kernel: a motif count does not fit in 64 bits");
   }
+  for (uint32_t k = 0; k < b->ndirect; ++k)
+    if (b->h_dstatus[k]) return gpm_fail(GPM_E_OVERFLOW, "batched plain-path query: a count does not fit in 64 bits");
+  return GPM_OK;
+}
+
+// Heavy queries run their plain count path inside the captured graph: a
+// query whose plain path takes at least batch_direct_us on the device (timed
+// here; a first run also makes every lazily sized buffer) is marked direct,
+// together with every other query on the same graph. Small queries become
+// items of the persistent kernel, where they overlap instead of paying a
+// launch sequence each.
+int choose_direct(gpm_batch *b) {
+  const uint32_t direct_us = gpm_tune().batch_direct_us;
+  const float kDirectMs = direct_us == 0xffffffffu ? 3.4e38f : direct_us * 1e-3f;
+  const uint32_t nq = (uint32_t)b->queries.size();
+  b->direct.assign(nq, 0);
+  for (uint32_t i = 0; i < nq; ++i) {
+    const uint32_t kind = b->qs[i].kind;
+    std::vector<gpm_pattern_t> &v = b->kind_pats[kind];
+    if (!v.empty()) continue;
+    if (kind == GPM_QUERY_MOTIF3 || kind == GPM_QUERY_MOTIF4) {
+      gpm_pattern_t p[8];
+      uint32_t np = 0;
+      GPM_TRY(gpm_pattern_motifs(kind == GPM_QUERY_MOTIF3 ? 3 : 4, p, &np));
+      v.assign(p, p + np);
+    } else {
+      gpm_pattern_t p = nullptr;
+      GPM_TRY(gpm_pattern_clique(kind == GPM_QUERY_TC ? 3 : kind == GPM_QUERY_CLIQUE4 ? 4 : 5, &p));
+      v.push_back(p);
+    }
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  GPM_CUDA(cudaEventCreate(&e0));
+  GPM_CUDA(cudaEventCreate(&e1));
+  std::vector<gpm_graph *> heavy_graphs;
+  int rc = GPM_OK;
+  for (uint32_t i = 0; i < nq && rc == GPM_OK; ++i) {
+    gpm_graph *g = b->queries[i].graph;
+    const std::vector<gpm_pattern_t> &pats = b->kind_pats[b->qs[i].kind];
+    std::lock_guard<std::mutex> lk(g->mu);
+    float ms = 0.0f;
+    for (int rep = 0; rep < 2 && rc == GPM_OK; ++rep) {
+      if (cudaEventRecord(e0, b->stream) != cudaSuccess) rc = gpm_fail(GPM_E_DEVICE, "event record");
+      if (rc == GPM_OK) rc = gpm_enqueue_count(g, pats.data(), (uint32_t)pats.size(), b->d_out + (size_t)6 * i, b->stream);
+      if (rc == GPM_OK && (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        rc = gpm_fail(GPM_E_DEVICE, "timing a batched query's plain path");
+      if (rep == 0 && ms < 0.25f * kDirectMs) break;  // clearly small: no second run needed
+    }
+    if (rc == GPM_OK && ms >= kDirectMs) heavy_graphs.push_back(g);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  for (uint32_t i = 0; i < nq; ++i)
+    b->direct[i] = std::find(heavy_graphs.begin(), heavy_graphs.end(), b->queries[i].graph) != heavy_graphs.end();
+  b->ndirect = (uint32_t)std::count(b->direct.begin(), b->direct.end(), (uint8_t)1);
+  if (b->ndirect) {
+    if (cudaMalloc(&b->d_dstatus, sizeof(unsigned int) * b->ndirect) != cudaSuccess ||
+        cudaMallocHost(&b->h_dstatus, sizeof(unsigned int) * b->ndirect) != cudaSuccess) {
+      cudaGetLastError();
+      return gpm_fail(GPM_E_OOM, "batch status allocation failed");
+    }
+  }
+  // the timing runs left per-arc triangle counts in the graphs' buffers, which
+  // item queries expect zero at the start of a run; and counts in the output slots
+  for (uint32_t i = 0; i < nq; ++i)
+    if (!b->direct[i] && b->qs[i].t_edge)
+      GPM_CUDA(cudaMemsetAsync(b->qs[i].t_edge, 0, sizeof(uint32_t) * std::max<uint64_t>(b->qs[i].m, 1), b->stream));
+  GPM_CUDA(cudaMemsetAsync(b->d_out, 0, sizeof(unsigned long long) * 6 * nq, b->stream));
+  GPM_CUDA(cudaStreamSynchronize(b->stream));
   return GPM_OK;
 }
 
@@ -379,6 +480,8 @@ int gpm_batch_create(const gpm_query_t *queries, uint32_t nq, gpm_batch_t *out) 
     }
     cudaMemset(b->tally_pool, 0, sizeof(uint32_t) * b->tally_slot_words * b->grid);
   }
+  rc = choose_direct(b);
+  if (rc) return fail(rc);
   rc = upload_schedule(b);
   if (rc) return fail(rc);
   *out = b;
@@ -407,6 +510,13 @@ int gpm_batch_info(gpm_batch_t b, uint32_t *nitems, uint32_t *roots_per_item, ui
   if (roots_per_item) *roots_per_item = b->roots_per_item;
   if (verts_per_item) *verts_per_item = b->verts_per_item;
   if (grid) *grid = (uint32_t)b->grid;
+  return GPM_OK;
+}
+
+int gpm_batch_direct(gpm_batch_t b, uint32_t *ndirect, uint64_t *graph_kernels) {
+  if (!b) return gpm_fail(GPM_E_INVALID_ARG, "null batch");
+  if (ndirect) *ndirect = b->ndirect;
+  if (graph_kernels) *graph_kernels = b->graph_kernels;
   return GPM_OK;
 }
 

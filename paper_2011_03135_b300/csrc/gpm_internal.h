@@ -54,6 +54,7 @@ struct gpm_tuning {
   uint32_t cta_max_degree = 1024;  // class CLS_CTA upper bound (<= 1024)
   uint32_t blocks_per_sm = 0;      // 0 = occupancy-derived
   uint32_t c4_hub_bound = 1048576; // 4-cycle roots above this wedge bound: hub path
+  uint32_t batch_direct_us = 1000;  // batched queries at least this slow run their plain path
 };
 gpm_tuning &gpm_tune();
 
@@ -250,12 +251,20 @@ int gpm_launch_permute_tuples(uint32_t *buf, uint64_t count, int k, const uint32
 void gpm_prof_begin(const char *name, cudaStream_t st);
 void gpm_prof_end(cudaStream_t st);
 void gpm_note_launches(uint64_t k);  // kernels launched by a CUDA-graph replay
+uint64_t gpm_captured_launches();    // kernels this thread has launched into stream captures
 #define GPM_LAUNCH(name, st, ...)  \
   do {                             \
     gpm_prof_begin(name, st);      \
     __VA_ARGS__;                   \
     gpm_prof_end(st);              \
   } while (0)
+
+// The plain count path of a prepared graph, enqueued on `st` without host
+// synchronisation (the 4-cycle task lists must exist when the patterns need
+// them); out_dev receives npat counts, the graph's status word its error bits.
+int gpm_enqueue_count(gpm_graph *g, const gpm_pattern_t *pats, uint32_t npat, unsigned long long *out_dev,
+                      cudaStream_t st);
+const unsigned int *gpm_graph_status(const gpm_graph *g);
 
 // grow-on-demand device allocation owned by the graph
 int gpm_graph_alloc(gpm_graph *g, void **ptr, size_t bytes);

@@ -79,9 +79,13 @@ static bool capturing(cudaStream_t st) {
   return cs != cudaStreamCaptureStatusNone;
 }
 
+static thread_local uint64_t t_captured = 0;
+uint64_t gpm_captured_launches() { return t_captured; }
+
 void gpm_prof_begin(const char *name, cudaStream_t st) {
   if (capturing(st)) {
     t_open.push_back(Pending{name, nullptr, nullptr});  // launches inside a graph are counted at replay
+    ++t_captured;
     return;
   }
   g_launches.fetch_add(1, std::memory_order_relaxed);

@@ -77,7 +77,7 @@ class Completion(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("warp_max_degree", ctypes.c_uint32), ("cta_max_degree", ctypes.c_uint32),
                 ("blocks_per_sm", ctypes.c_uint32), ("c4_hub_bound", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 4)]
+                ("batch_direct_us", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
 
 
 _vp, _u32, _u64, _i = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
@@ -102,6 +102,7 @@ _SIGS = {
     "gpm_profile_report": [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
     "gpm_batch_create": [_vp, _u32, ctypes.POINTER(_vp)],
     "gpm_batch_run": [_vp, _vp, _vp],
+    "gpm_batch_direct": [_vp, ctypes.POINTER(_u32), _U64P],
     "gpm_batch_info": [_vp, ctypes.POINTER(_u32), ctypes.POINTER(_u32), ctypes.POINTER(_u32),
                        ctypes.POINTER(_u32)],
     "gpm_batch_destroy": [_vp],
@@ -180,8 +181,9 @@ def profile_report() -> dict:
     return json.loads(buf.value.decode())
 
 
-def set_options(warp_max_degree: int = 0, cta_max_degree: int = 0, blocks_per_sm: int = 0, c4_hub_bound: int = 0):
-    o = Options(warp_max_degree, cta_max_degree, blocks_per_sm, c4_hub_bound)
+def set_options(warp_max_degree: int = 0, cta_max_degree: int = 0, blocks_per_sm: int = 0, c4_hub_bound: int = 0,
+                batch_direct_us: int = 0):
+    o = Options(warp_max_degree, cta_max_degree, blocks_per_sm, c4_hub_bound, batch_direct_us)
     _check(_lib.gpm_set_options(ctypes.byref(o)))
 
 
@@ -189,7 +191,7 @@ def get_options() -> dict:
     o = Options()
     _check(_lib.gpm_get_options(ctypes.byref(o)))
     return dict(warp_max_degree=o.warp_max_degree, cta_max_degree=o.cta_max_degree, blocks_per_sm=o.blocks_per_sm,
-                c4_hub_bound=o.c4_hub_bound)
+                c4_hub_bound=o.c4_hub_bound, batch_direct_us=o.batch_direct_us)
 
 
 class Graph:
@@ -381,7 +383,10 @@ class Batch:
     def info(self) -> dict:
         a, b, c, d = _u32(), _u32(), _u32(), _u32()
         _check(_lib.gpm_batch_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
-        return dict(items=a.value, roots_per_item=b.value, verts_per_item=c.value, grid=d.value)
+        nd, gk = _u32(), ctypes.c_uint64()
+        _check(_lib.gpm_batch_direct(self._h, ctypes.byref(nd), ctypes.byref(gk)))
+        return dict(items=a.value, roots_per_item=b.value, verts_per_item=c.value, grid=d.value,
+                    direct_queries=nd.value, graph_kernels=gk.value)
 
     def close(self):
         if getattr(self, "_h", None) is not None:

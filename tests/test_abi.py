@@ -115,4 +115,7 @@ def test_options_roundtrip(lib):
     for bad in (512, 1048577):
         with pytest.raises(lib.GpmError):
             lib.set_options(c4_hub_bound=bad)
+    assert old["batch_direct_us"] == 1000
+    lib.set_options(batch_direct_us=5)
+    assert lib.get_options()["batch_direct_us"] == 5
     lib.set_options(**{k: v for k, v in old.items() if v})

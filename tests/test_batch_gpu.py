@@ -47,6 +47,29 @@ def test_batch_mixed_small(gpm):
         assert gpm.count(G, gpm.plain_patterns(k)) == _oracle(g, k, gpm)
 
 
+@pytest.mark.parametrize("direct_us", [1, 0xFFFFFFFF])
+def test_batch_direct_and_item_queries(gpm, direct_us):
+    # every query run as its plain path inside the graph (1 us), or every
+    # query as items (never); a graph used by several queries included
+    old = gpm.get_options()
+    try:
+        gpm.set_options(batch_direct_us=direct_us)
+        specs = gg.batch_query_specs(10, base_seed=700, log2n_range=(7, 11), dbar_range=(4.0, 24.0))
+        graphs = [gg.graph_from_spec(s) for s in specs]
+        Gs = [gpm.Graph.from_host(g) for g in graphs]
+        qs = [(G, gpm.QUERY_MOTIF4 if i % 2 else gpm.QUERY_MOTIF3) for i, G in enumerate(Gs)]
+        qs += [(Gs[0], gpm.QUERY_CLIQUE5), (Gs[1], gpm.QUERY_TC), (Gs[1], gpm.QUERY_MOTIF4)]
+        B = gpm.Batch(qs)
+        for rep in range(3):
+            got = B.run()
+            for i, (G, k) in enumerate(qs):
+                g = graphs[Gs.index(G)]
+                assert got[i] == _oracle(g, k, gpm), (rep, i, k)
+        B.close()
+    finally:
+        gpm.set_options(**{k: v for k, v in old.items() if v})
+
+
 def test_batch_same_graph_several_queries(gpm):
     g = gg.rmat(11, 16.0, seed=9)
     G = gpm.Graph.from_host(g)
