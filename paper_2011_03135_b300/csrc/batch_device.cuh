@@ -14,11 +14,21 @@
 namespace gpm_item {
 
 enum ItemType : uint32_t {
-  IT_LG_WARP = 0, IT_LG_CTA = 1, IT_C4_SMALL = 2, IT_C4_BIG = 3, IT_EDGE = 4, IT_C4_BUCKET = 5
+  IT_LG_WARP = 0, IT_LG_CTA = 1, IT_C4_SMALL = 2, IT_C4_BIG = 3, IT_EDGE = 4, IT_C4_BUCKET = 5,
+  IT_C4_HUBPART = 6, IT_C4_HUBSUM = 7
 };
 
+// a, b, c, d: hub items only (served form). A hub 4-cycle root is counted by
+// several PART items, each tallying the wedges of a range [lo, hi) of the
+// root's work units into a shared slot of the hub pool with fire-and-forget
+// increments, then by SUM items, each summing C(c,2) over words [lo, hi) of
+// the slot while clearing them. a = hub root index, b = slot, c = the value
+// the slot's SUM counter (PART) or PART counter (SUM) must reach first, d =
+// the number of PART (or SUM) items of this root. Every wait points at items
+// earlier in the same queue.
 struct Item {
   uint32_t type, q, lo, hi;
+  uint32_t a, b, c, d;
 };
 
 struct QDesc {
@@ -32,6 +42,8 @@ struct QDesc {
   const uint32_t *tasks;     // LG root tasks of the graph (class order)
   const uint32_t *c4_tasks;  // 4-cycle roots
   const uint32_t *edeg;      // degree of col[e] per CSR entry (4-cycle wedge walks)
+  const uint2 *hub_units;    // {x, chunk} work units of the hub-class 4-cycle roots
+  uint32_t hub_base;         // hub root j is c4_tasks[hub_base + j]
   unsigned long long *acc;   // ACC_WORDS accumulators
   unsigned long long *out;   // 6 results
   unsigned int *left;        // [0] scatter items left, [1] items left
@@ -61,7 +73,27 @@ struct ItemEnv {
   uint32_t lg_maxd, lg_W;    // larger roots
   uint32_t *c4_buf;          // bucketed 4-cycle buffers, one slot per CTA
   uint64_t c4_buf_words;
+  uint32_t *hub_pool;        // hub tallies: slots of hub_slot_words words, zero between uses
+  uint64_t hub_slot_words;
+  unsigned int *hub_done;    // per slot: [2s] PART items done, [2s+1] SUM items done
 };
+
+constexpr uint32_t kHubItemUnits = 64;          // work units per PART item
+constexpr uint32_t kHubItemWords = 1u << 18;    // tally words per SUM item
+constexpr uint32_t kHubUnitChunk = gpm_dev::kC4HubChunk;  // adjacency entries per work unit
+
+// Bounded wait of thread 0 until counter reaches target (modulo 2^32).
+__device__ __forceinline__ void wait_counter(const unsigned int *counter, uint32_t target, unsigned int *status) {
+  uint64_t n = 0;
+  while ((int)(*(volatile const unsigned int *)counter - target) < 0) {
+    __nanosleep(200);
+    if (++n > kWaitLimit) {
+      atomicOr(status, ST_TIMEOUT);
+      break;
+    }
+  }
+  __threadfence();
+}
 
 // shared memory carve-up: the union of the item types' needs
 __host__ __device__ constexpr size_t warp_region_words() { return gpm_dev::warp_words(kWarpMaxD, true); }
@@ -150,6 +182,51 @@ __device__ __forceinline__ void run_item(const ItemEnv &a, const QDesc &q, const
                                  s_x, s_cnt, s_nt);
       break;
     }
+    case IT_C4_HUBPART: {
+      if (tid == 0) wait_counter(&a.hub_done[2 * it.b + 1], it.c, a.status);
+      __syncthreads();
+      const uint32_t v0 = q.c4_tasks[q.hub_base + it.a], d0 = q.deg[v0];
+      uint32_t *tally = a.hub_pool + (size_t)it.b * a.hub_slot_words;
+      const uint32_t lane = tid & 31, wid = tid >> 5;
+      for (uint32_t u = it.lo + wid; u < it.hi; u += kWarps) {
+        const uint2 unit = q.hub_units[u];
+        const uint64_t e0 = q.rowptr[unit.x] + (uint64_t)unit.y * kHubUnitChunk;
+        const uint64_t e1 = min(q.rowptr[unit.x + 1], e0 + kHubUnitChunk);
+        for (uint64_t base = e0; base < e1; base += 128) {
+          uint32_t w[4], dw[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint64_t e = base + 32 * k + lane;
+            w[k] = (e < e1) ? q.col[e] : 0u;
+            dw[k] = (e < e1) ? q.edeg[e] : 0xffffffffu;
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (gpm_dev::precedes(dw[k], w[k], d0, v0)) atomicAdd(&tally[w[k]], 1u);
+        }
+      }
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) atomicAdd(&a.hub_done[2 * it.b], 1u);
+      break;
+    }
+    case IT_C4_HUBSUM: {
+      if (tid == 0) wait_counter(&a.hub_done[2 * it.b], it.c, a.status);
+      __syncthreads();
+      uint4 *T4 = reinterpret_cast<uint4 *>(a.hub_pool + (size_t)it.b * a.hub_slot_words);
+      for (uint32_t i = it.lo / 4 + tid; i < it.hi / 4; i += kThreads) {
+        const uint4 v = __ldcg(T4 + i);
+        if (v.x | v.y | v.z | v.w) {
+          c4 += (unsigned long long)v.x * (v.x - (v.x > 0)) / 2 + (unsigned long long)v.y * (v.y - (v.y > 0)) / 2 +
+                (unsigned long long)v.z * (v.z - (v.z > 0)) / 2 + (unsigned long long)v.w * (v.w - (v.w > 0)) / 2;
+          __stcg(T4 + i, make_uint4(0u, 0u, 0u, 0u));
+        }
+      }
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) atomicAdd(&a.hub_done[2 * it.b + 1], 1u);
+      break;
+    }
     case IT_EDGE: {
       const uint32_t wid = tid >> 5;
       if (kind == GPM_QUERY_MOTIF4) {
@@ -220,9 +297,13 @@ __device__ __forceinline__ unsigned int finalize_query(const QDesc &q, unsigned 
 // of items and of triangle-scatter items through *all and *scatter.
 // With hub_phase, the hub-class 4-cycle roots get no items: they are counted
 // by separate whole-GPU launches ahead of the persistent kernel.
+// With hub_items (served form), hub-class roots whose tally is dense (n <= 4
+// x their wedge bound) become PART and SUM items (slot and wait targets are
+// filled in at admission by assign_hub_slots); the others keep one CTA item.
 inline void append_query_items(const gpm_graph *g, uint32_t kind, uint32_t qi, uint32_t roots_per_item,
                                uint32_t verts_per_item, std::vector<Item> &heavy, std::vector<Item> &light,
-                               std::vector<Item> &edge, uint32_t *scatter, uint32_t *all, bool hub_phase = false) {
+                               std::vector<Item> &edge, uint32_t *scatter, uint32_t *all, bool hub_phase = false,
+                               bool hub_items = false, uint64_t hub_slot_words = 0) {
   uint32_t sc = 0, al = 0;
   const uint32_t warp_end = g->cls_begin[CLS_WARP + 1];
   for (uint32_t t = 0; t < warp_end; t += roots_per_item) {
@@ -245,6 +326,20 @@ inline void append_query_items(const gpm_graph *g, uint32_t kind, uint32_t qi, u
       ++al;
     }
     for (uint32_t t = g->c4_begin[2]; t < (hub_phase ? g->c4_begin[2] : g->c4_begin[3]); ++t) {
+      const uint32_t j = t - g->c4_begin[2];
+      if (hub_items && j < g->c4_hub_bnd.size() && (uint64_t)g->n <= 4ull * g->c4_hub_bnd[j]) {
+        const uint64_t u0 = g->c4_hub_uoff[j], u1 = g->c4_hub_uoff[j + 1];
+        const uint32_t P = (uint32_t)((u1 - u0 + kHubItemUnits - 1) / kHubItemUnits);
+        const uint64_t words = ((uint64_t)std::max<uint32_t>(g->n, 1) + 3) & ~3ull;
+        const uint32_t Q = (uint32_t)((words + kHubItemWords - 1) / kHubItemWords);
+        for (uint64_t u = u0; u < u1; u += kHubItemUnits)
+          heavy.push_back({IT_C4_HUBPART, qi, (uint32_t)u, (uint32_t)std::min<uint64_t>(u1, u + kHubItemUnits), j, 0, 0, P});
+        for (uint64_t w = 0; w < words; w += kHubItemWords)
+          heavy.push_back({IT_C4_HUBSUM, qi, (uint32_t)w, (uint32_t)std::min<uint64_t>(words, w + kHubItemWords), j, 0, 0, Q});
+        al += P + Q;
+        (void)hub_slot_words;
+        continue;
+      }
       heavy.push_back({IT_C4_BIG, qi, t, t + 1});
       ++al;
     }
@@ -257,6 +352,34 @@ inline void append_query_items(const gpm_graph *g, uint32_t kind, uint32_t qi, u
   }
   *scatter = (kind == GPM_QUERY_MOTIF4) ? sc : 0u;
   *all = al;
+}
+
+// Slot and wait targets of hub items, in queue order. next_slot, parts and
+// sums (per slot, counting every PART / SUM item ever issued for it) carry
+// over between calls; each root takes the next slot round robin.
+inline void assign_hub_slots(Item *items, size_t n, uint32_t nslots, uint32_t *next_slot, uint32_t *parts,
+                             uint32_t *sums) {
+  for (size_t i = 0; i < n;) {
+    if (items[i].type != IT_C4_HUBPART) {
+      ++i;
+      continue;
+    }
+    const uint32_t P = items[i].d;
+    const uint32_t Q = items[i + P].d;
+    const uint32_t s = (*next_slot)++ % nslots;
+    const uint32_t wait_sum = sums[s];
+    parts[s] += P;
+    for (uint32_t k = 0; k < P; ++k) {
+      items[i + k].b = s;
+      items[i + k].c = wait_sum;
+    }
+    for (uint32_t k = 0; k < Q; ++k) {
+      items[i + P + k].b = s;
+      items[i + P + k].c = parts[s];
+    }
+    sums[s] += Q;
+    i += P + Q;
+  }
 }
 
 inline int formulas_for(uint32_t kind, uint32_t *f, uint32_t *nf) {
@@ -275,7 +398,10 @@ inline int formulas_for(uint32_t kind, uint32_t *f, uint32_t *nf) {
 
 // Prepare a graph for item processing: orientation, root classes with the
 // item bound on warp roots, and (for 4-motif queries) the 4-cycle root lists.
-inline int prepare_for_items(gpm_graph *g, bool need_c4, cudaStream_t st, bool hub_phase = false) {
+// hub_phase: the batched form's whole-GPU hub launches (units and tallies);
+// hub_items: the served form's hub items (units only).
+inline int prepare_for_items(gpm_graph *g, bool need_c4, cudaStream_t st, bool hub_phase = false,
+                             bool hub_items = false) {
   int rc = gpm_prepare_graph(g, st);
   if (rc) return rc;
   const gpm_tuning &t = gpm_tune();
@@ -288,7 +414,7 @@ inline int prepare_for_items(gpm_graph *g, bool need_c4, cudaStream_t st, bool h
     if (rc) return rc;
   }
   if (need_c4) {
-    rc = hub_phase ? gpm_c4_hub_prepare(g, st) : gpm_build_c4_tasks(g, st);
+    rc = (hub_phase || hub_items) ? gpm_c4_hub_prepare(g, st, hub_phase) : gpm_build_c4_tasks(g, st);
     if (rc) return rc;
   }
   return GPM_OK;

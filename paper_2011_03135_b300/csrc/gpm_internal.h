@@ -195,7 +195,7 @@ int gpm_build_c4_tasks(gpm_graph *g, cudaStream_t st);
 // Hub-class 4-cycle roots (wedge bound above the hub threshold) on their own:
 // prepare builds the task lists, work units and tallies (host synchronisations);
 // enqueue only launches (capturable), adding their 4-cycles to acc[ACC_C4].
-int gpm_c4_hub_prepare(gpm_graph *g, cudaStream_t st);
+int gpm_c4_hub_prepare(gpm_graph *g, cudaStream_t st, bool tallies = true);
 int gpm_c4_hub_enqueue(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigned long long *acc, cudaStream_t st,
                        uint32_t *nlaunch);
 

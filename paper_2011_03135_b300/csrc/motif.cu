@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(256) c4_small_kernel(C4Args a) {
 // ---------------------------------------------------------------------------
 // hub roots: the whole grid on up to kHubMaxR roots per launch
 // ---------------------------------------------------------------------------
-constexpr uint32_t kHubChunk = 1024;  // adjacency entries of x per work unit
+constexpr uint32_t kHubChunk = gpm_dev::kC4HubChunk;  // adjacency entries of x per work unit
 constexpr int kHubMaxR = 4;
 constexpr int kHubThreads = 256;
 
@@ -409,20 +409,23 @@ static int ensure_c4_tasks(gpm_graph *g, cudaStream_t st) {
   return GPM_OK;
 }
 
-// Work units and tallies of the hub roots (class 2), built once per task list.
-static int ensure_c4_hub(gpm_graph *g, cudaStream_t st) {
-  if (g->c4_hub_ready) return GPM_OK;
+// Work units and (with tallies) tally sets of the hub roots (class 2), built
+// once per task list.
+static int ensure_c4_hub(gpm_graph *g, cudaStream_t st, bool tallies = true) {
   const uint32_t nhub = g->c4_begin[3] - g->c4_begin[2];
+  if (g->c4_hub_ready && (!tallies || !nhub || g->c4_hub_tally)) return GPM_OK;
   const uint32_t *roots = g->c4_tasks + g->c4_begin[2];
-  if (g->c4_hub_units) {
-    cudaFree(g->c4_hub_units);
-    g->c4_hub_units = nullptr;
+  if (!g->c4_hub_ready) {
+    if (g->c4_hub_units) {
+      cudaFree(g->c4_hub_units);
+      g->c4_hub_units = nullptr;
+    }
+    g->c4_hub_root.assign(nhub, 0);
+    g->c4_hub_deg.assign(nhub, 0);
+    g->c4_hub_bnd.assign(nhub, 0);
+    g->c4_hub_uoff.assign((size_t)nhub + 1, 0);
   }
-  g->c4_hub_root.assign(nhub, 0);
-  g->c4_hub_deg.assign(nhub, 0);
-  g->c4_hub_bnd.assign(nhub, 0);
-  g->c4_hub_uoff.assign((size_t)nhub + 1, 0);
-  if (nhub) {
+  if (nhub && !g->c4_hub_ready) {
     const int blocks = gpm_num_sms(g->device) * 8;
     unsigned long long *info = nullptr;
     GPM_CUDA(cudaMalloc(&info, sizeof(unsigned long long) * (3 * (size_t)nhub + (size_t)nhub + 1)));
@@ -461,6 +464,9 @@ static int ensure_c4_hub(gpm_graph *g, cudaStream_t st) {
     } while (0);
     cudaFree(info);
     if (rc) return rc;
+  }
+  g->c4_hub_ready = true;
+  if (nhub && tallies) {
     // tallies: as many roots per launch as keep one set of tallies within 32 MiB
     const uint64_t npad = ((uint64_t)std::max<uint32_t>(g->n, 1) + 3) & ~3ull;
     const uint32_t R = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(kHubMaxR, (32ull << 20) / (4ull * npad)));
@@ -485,7 +491,6 @@ static int ensure_c4_hub(gpm_graph *g, cudaStream_t st) {
       g->c4_hub_ctr_words = ctr_words;
     }
   }
-  g->c4_hub_ready = true;
   return GPM_OK;
 }
 
@@ -541,14 +546,15 @@ static int launch_c4_hub(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsig
   return GPM_OK;
 }
 
-int gpm_c4_hub_prepare(gpm_graph *g, cudaStream_t st) {
+int gpm_c4_hub_prepare(gpm_graph *g, cudaStream_t st, bool tallies) {
   GPM_TRY(ensure_c4_tasks(g, st));
-  return ensure_c4_hub(g, st);
+  return ensure_c4_hub(g, st, tallies);
 }
 
 int gpm_c4_hub_enqueue(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigned long long *acc, cudaStream_t st,
                        uint32_t *nlaunch) {
-  if (!g->c4_ready || !g->c4_hub_ready) return gpm_fail(GPM_E_INVALID_ARG, "4-cycle hub roots are not prepared");
+  if (!g->c4_ready || !g->c4_hub_ready || (!g->c4_hub_tally && !g->c4_hub_root.empty()))
+    return gpm_fail(GPM_E_INVALID_ARG, "4-cycle hub roots are not prepared");
   return launch_c4_hub(g, root_lo, root_hi, acc, st, nlaunch);
 }
 

@@ -8,6 +8,7 @@
 namespace gpm_dev {
 
 constexpr uint32_t kC4SmallBound = 512;  // wedge bound for the shared-memory class
+constexpr uint32_t kC4HubChunk = 1024;   // adjacency entries of x per hub work unit
 constexpr uint32_t kC4HashSlots = 1024;  // per warp, load factor <= 1/2
 constexpr uint32_t kC4Empty = 0xffffffffu;
 

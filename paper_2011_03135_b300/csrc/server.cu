@@ -57,6 +57,7 @@ struct Completion {
 };
 
 constexpr uint64_t kExpressItems = 64;
+constexpr uint32_t kHubSlots = 16;  // hub-class 4-cycle roots in flight at once
 
 struct Ctl {
   unsigned long long head[2];  // next item position to claim, per ring (0 express, 1 bulk)
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(ServeArgs a) {
               const volatile uint32_t *src =
                   reinterpret_cast<const volatile uint32_t *>(a.ring[r] + (h % a.ring_cap[r]));
               uint32_t *dst = reinterpret_cast<uint32_t *>(&s_item);
-              for (int w = 0; w < 4; ++w) dst[w] = src[w];
+              for (int w = 0; w < (int)(sizeof(Item) / 4); ++w) dst[w] = src[w];
               s_ok = 1;
             }
           }
@@ -157,6 +158,13 @@ struct gpm_server {
   uint32_t *lg_pool = nullptr;
   uint32_t *c4_buf = nullptr;
   uint32_t c4_maxb = 0;
+  // hub-class 4-cycle roots: slots of the hub pool, per-slot item counters, and
+  // the host's running totals of PART / SUM items issued per slot
+  uint32_t *hub_pool = nullptr;
+  unsigned int *hub_done = nullptr;
+  uint32_t hub_slots = 0, hub_next = 0;
+  std::vector<uint32_t> hub_parts, hub_sums;
+  std::vector<Item> admit_items;  // staging of one request's items
   ItemEnv env{};
   // host mapped / pinned
   Completion *h_comp = nullptr;
@@ -195,6 +203,7 @@ struct gpm_server {
   // per (graph, kind) item templates with q = 0
   std::map<std::pair<uint32_t, uint32_t>, std::vector<Item>> templates;
   std::map<std::pair<uint32_t, uint32_t>, std::pair<uint32_t, uint32_t>> tmpl_counts;  // (scatter, all)
+  std::map<std::pair<uint32_t, uint32_t>, bool> tmpl_hub;  // template holds hub items
   std::mutex mu;
 };
 
@@ -243,7 +252,11 @@ const std::vector<Item> &items_for(gpm_server *s, uint32_t gi, uint32_t kind, ui
   if (it == s->templates.end()) {
     std::vector<Item> heavy, light, edge, all_items;
     uint32_t sc = 0, al = 0;
-    append_query_items(s->graphs[gi], kind, 0, s->roots_per_item, s->verts_per_item, heavy, light, edge, &sc, &al);
+    append_query_items(s->graphs[gi], kind, 0, s->roots_per_item, s->verts_per_item, heavy, light, edge, &sc, &al,
+                       false, true);
+    bool hub = false;
+    for (const Item &x : heavy) hub |= x.type == IT_C4_HUBPART;
+    s->tmpl_hub[key] = hub;
     all_items.insert(all_items.end(), heavy.begin(), heavy.end());
     all_items.insert(all_items.end(), light.begin(), light.end());
     all_items.insert(all_items.end(), edge.begin(), edge.end());
@@ -305,7 +318,10 @@ int try_admit(gpm_server *s, const gpm_server::Req &r, int *rc) {
     s->instant.push_back(c);
     return 1;
   }
-  const int ring = nitems <= kExpressItems ? 0 : 1;
+  // requests with hub items use the bulk ring: their items wait on each other
+  // (and on earlier hub items), which must all be claimed in one order
+  const bool hub = s->tmpl_hub[std::make_pair(r.graph, r.kind)];
+  const int ring = (nitems <= kExpressItems && !hub) ? 0 : 1;
   if (s->tail[ring] + nitems - oldest_ring_begin(s, ring) > s->ring_cap[ring]) return 0;
   uint64_t off = 0, words = 0;
   if (r.kind == GPM_QUERY_MOTIF4) {
@@ -339,6 +355,8 @@ int try_admit(gpm_server *s, const gpm_server::Req &r, int *rc) {
   q.tasks = g->tasks;
   q.c4_tasks = g->c4_tasks;
   q.edeg = g->edeg;
+  q.hub_units = reinterpret_cast<const uint2 *>(g->c4_hub_units);
+  q.hub_base = g->c4_begin[2];
   q.n = g->n;
   q.m = g->m;
   SlotState *dslot = s->d_slots + slot;
@@ -350,16 +368,19 @@ int try_admit(gpm_server *s, const gpm_server::Req &r, int *rc) {
   st.left[0] = sc;
   st.left[1] = al;
   cudaError_t e = cudaMemcpyAsync(dslot, &st, sizeof(SlotState), cudaMemcpyHostToDevice, s->copy);
-  // items, with this slot, into the ring (two pieces when it wraps)
+  // this request's items: the slot, and the hub items' pool slots and wait targets
+  s->admit_items.assign(tmpl.begin(), tmpl.end());
+  for (Item &x : s->admit_items) x.q = slot;
+  if (hub)
+    assign_hub_slots(s->admit_items.data(), s->admit_items.size(), s->hub_slots, &s->hub_next, s->hub_parts.data(),
+                     s->hub_sums.data());
+  // items into the ring (two pieces when it wraps)
   uint64_t done = 0;
   while (e == cudaSuccess && done < nitems) {
     const uint64_t pos = s->tail[ring] + done;
     const uint64_t ring_i = pos % s->ring_cap[ring];
     const uint64_t chunk = std::min<uint64_t>({nitems - done, s->ring_cap[ring] - ring_i, s->stage_cap});
-    for (uint64_t k = 0; k < chunk; ++k) {
-      s->h_stage[k] = tmpl[done + k];
-      s->h_stage[k].q = slot;
-    }
+    for (uint64_t k = 0; k < chunk; ++k) s->h_stage[k] = s->admit_items[done + k];
     e = cudaMemcpyAsync(s->d_ring[ring] + ring_i, s->h_stage, sizeof(Item) * chunk, cudaMemcpyHostToDevice,
                         s->copy);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy);  // the staging buffer is reused
@@ -402,7 +423,7 @@ int express_request(gpm_server *s, uint32_t graph, uint32_t kind) {
 
 void free_server(gpm_server *s) {
   if (s->exec) cudaStreamSynchronize(s->exec);
-  void *dev[] = {s->d_slots, s->d_ring[0], s->d_ring[1], s->d_ctl, s->d_arena, s->tally_pool, s->lg_pool,
+  void *dev[] = {s->hub_pool, s->hub_done, s->d_slots, s->d_ring[0], s->d_ring[1], s->d_ctl, s->d_arena, s->tally_pool, s->lg_pool,
                  s->c4_buf};
   for (void *p : dev)
     if (p) cudaFree(p);
@@ -445,7 +466,7 @@ int gpm_server_start(const gpm_graph_t *graphs, uint32_t ngraphs, const gpm_serv
     gpm_graph *g = graphs[i];
     if (!g) return fail(gpm_fail(GPM_E_INVALID_ARG, "null graph"));
     std::lock_guard<std::mutex> lk(g->mu);
-    int rc = prepare_for_items(g, true, s->copy);
+    int rc = prepare_for_items(g, true, s->copy, false, true);
     if (rc) return fail(rc);
     s->graphs.push_back(g);
     nmax = std::max(nmax, g->n);
@@ -507,6 +528,20 @@ int gpm_server_start(const gpm_graph_t *graphs, uint32_t ngraphs, const gpm_serv
     return fail(gpm_fail(GPM_E_OOM, "server tally pool allocation failed"));
   }
   cudaMemset(s->tally_pool, 0, sizeof(uint32_t) * s->tally_slot_words * s->grid);
+  // hub pool: kHubSlots tallies of the largest graph's n words (rounded to 4)
+  s->hub_slots = kHubSlots;
+  s->env.hub_slot_words = ((uint64_t)nmax + 3) & ~3ull;
+  s->hub_parts.assign(s->hub_slots, 0);
+  s->hub_sums.assign(s->hub_slots, 0);
+  if (cudaMalloc(&s->hub_pool, sizeof(uint32_t) * s->env.hub_slot_words * s->hub_slots) != cudaSuccess ||
+      cudaMalloc(&s->hub_done, sizeof(unsigned int) * 2 * s->hub_slots) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(gpm_fail(GPM_E_OOM, "server hub pool allocation failed"));
+  }
+  cudaMemset(s->hub_pool, 0, sizeof(uint32_t) * s->env.hub_slot_words * s->hub_slots);
+  cudaMemset(s->hub_done, 0, sizeof(unsigned int) * 2 * s->hub_slots);
+  s->env.hub_pool = s->hub_pool;
+  s->env.hub_done = s->hub_done;
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(gpm_fail(GPM_E_DEVICE, "server set-up"));
   *out = s;
   return GPM_OK;

@@ -125,3 +125,29 @@ def test_server_small_requests_overtake_blocked_large_ones(gpm):
     assert all(got[t] == want_big for t in range(3)) and all(got[t] == want_small for t in range(100, 110))
     assert max(order.index(t) for t in range(100, 110)) < order.index(2)
     S.stop()
+
+
+def test_server_hub_items(gpm):
+    # a low hub threshold makes hundreds of 4-cycle roots hub roots: the served
+    # form splits each into PART and SUM items over a small pool of shared
+    # tally slots, reused many times within and across requests
+    old = gpm.get_options()
+    try:
+        gpm.set_options(c4_hub_bound=600)
+        graphs = [gg.rmat(11, 16.0, seed=109), gg.chung_lu(6000, 16.0, 2.1, seed=110), gg.rmat(12, 8.0, seed=111)]
+        Gs = [gpm.Graph.from_host(g) for g in graphs]
+        want = [O.motifs(g, 4) for g in graphs]
+        S = gpm.Server(Gs, max_inflight=16)
+        tags = [(t, t % len(Gs)) for t in range(24)]
+        for t, gi in tags:
+            S.submit(gi, gpm.QUERY_MOTIF4, t)
+        got = _drain(S, len(tags))
+        for t, gi in tags:
+            assert got[t] == (gi, gpm.QUERY_MOTIF4, want[gi]), t
+        # the same requests one at a time
+        for gi in range(len(Gs)):
+            S.submit(gi, gpm.QUERY_MOTIF4, 100 + gi)
+            assert list(_drain(S, 1).values())[0][2] == want[gi]
+        S.stop()
+    finally:
+        gpm.set_options(**{k: v for k, v in old.items() if v})
