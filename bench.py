@@ -472,8 +472,9 @@ def run_reference(args):
     from paper_2011_03135_b300 import graphgen as gg
     import oracle as O
     g = gg.workload_clique_rmat21()
-    # each step: the oracle on a fixed root sample sized to a few seconds
-    lo, hi = 0, 4096
+    # each step: the oracle on a fixed root sample sized so that the whole run
+    # takes about 150 s (calibrated on a short first sample)
+    lo, hi = 0, 1024
     t0 = time.perf_counter()
     O.cliques(g, 4, lo, hi)
     O.cliques(g, 5, lo, hi)
