@@ -465,7 +465,7 @@ int gpm_batch_create(const gpm_query_t *queries, uint32_t nq, gpm_batch_t *out) 
   rc = setup_cta_items(b->env, b->cta_maxd, b->grid, &b->lg_pool);
   if (rc) return fail(rc);
   if (need_c4 && b->c4_maxb) {
-    b->env.c4_buf_words = ((uint64_t)b->c4_maxb + 63) & ~63ull;
+    b->env.c4_buf_words = gpm_dev::c4_bucket_slot_words(b->c4_maxb);
     if (cudaMalloc(&b->c4_buf, sizeof(uint32_t) * b->env.c4_buf_words * b->grid) != cudaSuccess) {
       cudaGetLastError();
       return fail(gpm_fail(GPM_E_OOM, "4-cycle bucket buffer allocation failed"));

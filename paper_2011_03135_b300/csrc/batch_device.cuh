@@ -78,7 +78,7 @@ struct ItemEnv {
   unsigned int *hub_done;    // per slot: [2s] PART items done, [2s+1] SUM items done
 };
 
-constexpr uint32_t kHubItemUnits = 64;          // work units per PART item
+constexpr uint32_t kHubItemUnits = 128;         // work units per PART item
 constexpr uint32_t kHubItemWords = 1u << 18;    // tally words per SUM item
 constexpr uint32_t kHubUnitChunk = gpm_dev::kC4HubChunk;  // adjacency entries per work unit
 
@@ -169,8 +169,9 @@ __device__ __forceinline__ void run_item(const ItemEnv &a, const QDesc &q, const
       break;
     }
     case IT_C4_BUCKET: {
-      c4 += gpm_dev::c4_root_bucketed(q.rowptr, q.col, q.deg, q.edeg, q.c4_tasks[it.lo],
-                                      a.c4_buf + (size_t)blockIdx.x * a.c4_buf_words, smem, s_x, s_cnt, overflow);
+      uint32_t *lin = a.c4_buf + (size_t)blockIdx.x * a.c4_buf_words;
+      c4 += gpm_dev::c4_root_bucketed(q.rowptr, q.col, q.deg, q.edeg, q.c4_tasks[it.lo], lin, lin + a.c4_buf_words / 2,
+                                      smem, s_x, s_cnt, overflow);
       break;
     }
     case IT_C4_BIG: {

@@ -324,12 +324,12 @@ __device__ __forceinline__ unsigned long long nested_pairs_unit(const uint32_t *
 // (a, b) are visited with one shuffle of C_b per b (no shared memory).
 __device__ __forceinline__ void nested_row_reg32(const uint32_t *R, uint32_t W, uint32_t rs, const uint32_t *ri,
                                                  uint32_t c, const uint32_t *S, const uint32_t *pref,
-                                                 unsigned long long &a4, unsigned long long &a5) {
+                                                 unsigned long long &a4, unsigned long long &a5, bool tri = false) {
   const uint32_t lane = threadIdx.x & 31;
   uint32_t ca = 0;
   if (lane < c) {
     const uint32_t *rj = R + (size_t)S[lane] * rs;
-    for (uint32_t w = 0; w < W; ++w) {
+    for (uint32_t w = tri ? (S[lane] + 1) >> 5 : 0; w < W; ++w) {
       const uint32_t riw = ri[w];
       const uint32_t x = rj[w] & riw;
       if (x) ca |= gather_bits(x, riw) << pref[w];  // c <= 32: every output bit is in word 0
@@ -415,7 +415,7 @@ __device__ inline void enumerate_nested_cta(const uint32_t *R, uint32_t d, uint3
         continue;
       }
       if (c <= 32) {
-        nested_row_reg32(R, W, rs, ri, c, S, pref, a4, a5);
+        nested_row_reg32(R, W, rs, ri, c, S, pref, a4, a5, tri);
         __syncwarp();
         continue;
       }

@@ -331,7 +331,8 @@ __global__ void __launch_bounds__(kC4BucketThreads) c4_bucket_kernel(C4Args a, u
     if (task >= a.ntasks) break;
     const uint32_t v0 = a.tasks[task];
     if (v0 < a.root_lo || v0 >= a.root_hi) continue;
-    acc += gpm_dev::c4_root_bucketed(a.rowptr, a.col, a.deg, a.edeg, v0, buf, smem, s_x, &s_cnt, overflow);
+    acc += gpm_dev::c4_root_bucketed(a.rowptr, a.col, a.deg, a.edeg, v0, buf, buf + slot_words / 2, smem, s_x, &s_cnt,
+                                     overflow);
   }
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0 && acc) atomicAdd(&a.acc[ACC_C4], acc);
@@ -600,7 +601,7 @@ int gpm_launch_cycles4(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigne
     GPM_CUDA(cudaFuncSetAttribute(c4_bucket_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c4_bucket_kernel, kC4BucketThreads, smem));
-    const uint64_t slot_words = ((uint64_t)std::max<uint32_t>(g->c4_bucket_maxb, 1) + 63) & ~63ull;
+    const uint64_t slot_words = gpm_dev::c4_bucket_slot_words(std::max<uint32_t>(g->c4_bucket_maxb, 1));
     size_t slots = (size_t)sms * (size_t)std::max(per_sm, 1);
     slots = std::min<size_t>(slots, nbucket);
     const size_t need = slots * slot_words * 4;

@@ -8,7 +8,7 @@
 namespace gpm_dev {
 
 constexpr uint32_t kC4SmallBound = 512;  // wedge bound for the shared-memory class
-constexpr uint32_t kC4HubChunk = 1024;   // adjacency entries of x per hub work unit
+constexpr uint32_t kC4HubChunk = 256;    // adjacency entries of x per hub work unit
 constexpr uint32_t kC4HashSlots = 1024;  // per warp, load factor <= 1/2
 constexpr uint32_t kC4Empty = 0xffffffffu;
 
@@ -159,59 +159,40 @@ __host__ __device__ constexpr uint32_t c4_bucket_smem_words(uint32_t nwarps) {
   return 2 * kC4MaxBuckets + 4 + nwarps * 2 * kC4BucketTable;
 }
 
-// Walk the wedges v0 - x - w (x, w before v0 in the order) of root v0 with the
-// whole CTA; f(w) is called once per wedge. s_x holds blockDim.x words.
-template <typename F>
-__device__ __forceinline__ void c4_walk_wedges(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
-                                               const uint32_t *__restrict__ deg,
-                                               const uint32_t *__restrict__ edeg, uint32_t v0, uint32_t *s_x,
-                                               uint32_t *s_cnt, F f) {
-  const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-  const uint32_t d0 = deg[v0];
-  const uint64_t b0 = rowptr[v0], e0 = rowptr[v0 + 1];
-  for (uint64_t cb = b0; cb < e0; cb += nt) {
-    if (tid == 0) *s_cnt = 0;
-    __syncthreads();
-    const uint64_t ex = cb + tid;
-    if (ex < e0) {
-      const uint32_t x = col[ex];
-      if (precedes(nbr_deg(edeg, deg, ex, x), x, d0, v0)) s_x[atomicAdd(s_cnt, 1u)] = x;
-    }
-    __syncthreads();
-    const uint32_t cnt = *s_cnt;
-    for (uint32_t xi = wid; xi < cnt; xi += nw) {
-      const uint32_t x = s_x[xi];
-      for (uint64_t e = rowptr[x] + lane; e < rowptr[x + 1]; e += 32) {
-        const uint32_t w = col[e];
-        if (precedes(nbr_deg(edeg, deg, e, w), w, d0, v0)) f(w);
-      }
-    }
-    __syncthreads();
-  }
+// words of one CTA's bucket buffer (lin, then buf) for wedge bounds <= maxb
+__host__ __device__ constexpr uint64_t c4_bucket_slot_words(uint64_t maxb) {
+  return 2 * ((maxb + 63) & ~63ull);
 }
 
-// 4-cycles rooted at v0 with bucketed aggregation; buf holds at least the
-// root's wedge bound entries; sm = c4_bucket_smem_words(blockDim.x / 32) words
-// of shared memory. Every thread must call it; returns this thread's part.
+// 4-cycles rooted at v0 with bucketed aggregation. One walk over the wedges
+// v0 - x - w appends every wedge end to `lin` (warp-aggregated) and counts it
+// in its hash bucket; a streaming pass then scatters `lin` into `buf` by
+// bucket. lin and buf hold at least the root's wedge bound entries each;
+// sm = c4_bucket_smem_words(blockDim.x / 32) words of shared memory; s_x holds
+// blockDim.x words. Every thread must call it; returns this thread's part.
 __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *__restrict__ rowptr,
                                                                const uint32_t *__restrict__ col,
                                                                const uint32_t *__restrict__ deg,
                                                                const uint32_t *__restrict__ edeg, uint32_t v0,
-                                                               uint32_t *buf, uint32_t *sm, uint32_t *s_x,
-                                                               uint32_t *s_cnt, bool &overflow) {
-  const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+                                                               uint32_t *lin, uint32_t *buf, uint32_t *sm,
+                                                               uint32_t *s_x, uint32_t *s_cnt, bool &overflow) {
+  const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   uint32_t *bcnt = sm;                       // [kC4MaxBuckets]: counts, then write cursors
   uint32_t *boff = sm + kC4MaxBuckets;       // [kC4MaxBuckets + 1]
-  uint32_t *ctl = boff + kC4MaxBuckets + 1;  // [0] bound, [1] next bucket (shares the last word pair)
+  uint32_t *ctl = boff + kC4MaxBuckets + 1;  // [0] bound, [1] next bucket, [2] wedges in lin
   uint32_t *keys = sm + 2 * kC4MaxBuckets + 4 + (size_t)wid * 2 * kC4BucketTable;
   uint32_t *vals = keys + kC4BucketTable;
+  const uint32_t d0 = deg[v0];
+  const uint64_t b0 = rowptr[v0], e0 = rowptr[v0 + 1];
   // wedge bound -> bucket count P (a power of two)
-  if (tid == 0) ctl[0] = 0;
+  if (tid == 0) {
+    ctl[0] = 0;
+    ctl[2] = 0;
+  }
   __syncthreads();
   {
-    const uint32_t d0 = deg[v0];
     unsigned long long b = 0;
-    for (uint64_t e = rowptr[v0] + tid; e < rowptr[v0 + 1]; e += nt) {
+    for (uint64_t e = b0 + tid; e < e0; e += nt) {
       const uint32_t x = col[e];
       const uint32_t dx = nbr_deg(edeg, deg, e, x);
       if (precedes(dx, x, d0, v0)) b += dx;
@@ -226,7 +207,43 @@ __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *_
   const uint32_t pmask = P - 1;
   for (uint32_t b = tid; b < P; b += nt) bcnt[b] = 0;
   __syncthreads();
-  c4_walk_wedges(rowptr, col, deg, edeg, v0, s_x, s_cnt, [&](uint32_t w) { atomicAdd(&bcnt[c4_bucket_hash(w) & pmask], 1u); });
+  // the walk: x before v0 collected per chunk of v0's list, then each warp
+  // takes an x and its lanes walk N(x) in rounds of 32
+  for (uint64_t cb = b0; cb < e0; cb += nt) {
+    if (tid == 0) *s_cnt = 0;
+    __syncthreads();
+    const uint64_t ex = cb + tid;
+    if (ex < e0) {
+      const uint32_t x = col[ex];
+      if (precedes(nbr_deg(edeg, deg, ex, x), x, d0, v0)) s_x[atomicAdd(s_cnt, 1u)] = x;
+    }
+    __syncthreads();
+    const uint32_t cnt = *s_cnt;
+    for (uint32_t xi = wid; xi < cnt; xi += nw) {
+      const uint32_t x = s_x[xi];
+      const uint64_t xe = rowptr[x + 1];
+      for (uint64_t base = rowptr[x]; base < xe; base += 32) {
+        const uint64_t e = base + lane;
+        uint32_t w = 0;
+        bool v = false;
+        if (e < xe) {
+          w = col[e];
+          v = precedes(nbr_deg(edeg, deg, e, w), w, d0, v0);
+        }
+        if (v) atomicAdd(&bcnt[c4_bucket_hash(w) & pmask], 1u);
+        const uint32_t m = __ballot_sync(0xffffffffu, v);
+        if (m) {
+          const int leader = __ffs(m) - 1;
+          uint32_t pos = 0;
+          if ((int)lane == leader) pos = atomicAdd(&ctl[2], (uint32_t)__popc(m));
+          pos = __shfl_sync(0xffffffffu, pos, leader);
+          if (v) lin[pos + __popc(m & ((1u << lane) - 1u))] = w;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const uint32_t total = ctl[2];
   // exclusive scan of the bucket counts (one warp), cursors = offsets
   if (wid == 0) {
     uint32_t carry = 0;
@@ -250,8 +267,11 @@ __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *_
     }
   }
   __syncthreads();
-  c4_walk_wedges(rowptr, col, deg, edeg, v0, s_x, s_cnt,
-                 [&](uint32_t w) { buf[atomicAdd(&bcnt[c4_bucket_hash(w) & pmask], 1u)] = w; });
+  // streaming scatter by bucket (lin was written by other threads of this CTA)
+  for (uint32_t i = tid; i < total; i += nt) {
+    const uint32_t w = lin[i];
+    buf[atomicAdd(&bcnt[c4_bucket_hash(w) & pmask], 1u)] = w;
+  }
   // the buffer is read below by other warps of this CTA (plain loads, CTA scope)
   __syncthreads();
   // each warp aggregates whole buckets in its hash table

@@ -515,7 +515,7 @@ int gpm_server_start(const gpm_graph_t *graphs, uint32_t ngraphs, const gpm_serv
     if (rc) return fail(rc);
   }
   if (s->c4_maxb) {
-    s->env.c4_buf_words = ((uint64_t)s->c4_maxb + 63) & ~63ull;
+    s->env.c4_buf_words = gpm_dev::c4_bucket_slot_words(s->c4_maxb);
     if (cudaMalloc(&s->c4_buf, sizeof(uint32_t) * s->env.c4_buf_words * s->grid) != cudaSuccess) {
       cudaGetLastError();
       return fail(gpm_fail(GPM_E_OOM, "4-cycle bucket buffer allocation failed"));
