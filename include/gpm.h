@@ -292,10 +292,14 @@ typedef struct {
  * runs, so requests that arrive while others are on the GPU overlap with
  * them (continuous batching). A request is admitted when a request slot, room
  * in the item ring and, for 4-motif queries, 4 bytes per edge of the device
- * arena are free; otherwise it waits in a host FIFO. Every device-side wait is
- * bounded; the kernel exits after ~20 ms without work and is relaunched by
- * the next submit or poll. The graphs must outlive the server and must not be
- * used by other calls while it runs. Synchronises the device.
+ * arena are free; otherwise it waits in a host FIFO. Requests of at most 64
+ * items use an express ring that the kernel drains first and an express FIFO;
+ * larger ones may hold at most three quarters of the slots. Hub-class 4-cycle
+ * roots run as many short items over a pool of 16 shared tally slots (the
+ * pool holds 16 x the largest n words). Every device-side wait is bounded; the
+ * kernel exits after ~20 ms without work and is relaunched by the next submit
+ * or poll. The graphs must outlive the server and must not be used by other
+ * calls while it runs. Synchronises the device.
  */
 int gpm_server_start(const gpm_graph_t *graphs, uint32_t ngraphs, const gpm_server_opts_t *opts,
                      gpm_server_t *out);
