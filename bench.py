@@ -139,8 +139,8 @@ def clique_pass_bytes(g, opts):
 # valid only for the kernel sources they were taken on (digest of
 # csrc/lg_device.cuh + csrc/clique.cu); a stale entry is ignored.
 NCU_COUNTERS = {
-    "lg_cta_hi": {"digest": "5c74c5b32f28f83f", "inst_per_launch": 160425295540,
-                  "dram_bytes_per_launch": 28331776 + 2816, "ncu_ms": 223.346},
+    "lg_cta_hi": {"digest": "9113a9befdca8529", "inst_per_launch": 152641848237,
+                  "dram_bytes_per_launch": 28336384 + 1792, "ncu_ms": 185.770},
 }
 
 

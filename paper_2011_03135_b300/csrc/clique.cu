@@ -155,18 +155,21 @@ int max_smem_optin(int device) {
 }
 
 // THREADS = 1024 (32 warps, one CTA per SM) for the largest shared-memory
-// roots with the nested 5-clique search: one-warp rows are capped at 64 so
-// that 32 warp buffers fit beside the bitmap.
+// roots with the nested 5-clique search: 32 warp buffers for rows of up to
+// 128 candidates fit beside a bitmap of up to 1024 rows, and the big-row
+// groups reuse the same pool afterwards.
 template <int G, int KMAX, bool SCATTER, bool GLOBAL, int THREADS>
 int launch_cta_t(const LGArgs &a, uint32_t maxd, int blocks_cap, int device, cudaStream_t st, size_t smem_limit,
                  const char *name) {
-  const uint32_t wcap = THREADS >= 1024 ? 64u : gpm_dev::kNestWarpC;
   size_t smem = GLOBAL ? 0 : (size_t)cta_words(maxd, a.W) * 4;
+  const size_t limit = smem_limit ? smem_limit : (size_t)max_smem_optin(device);
+  // one-warp rows of up to 128 candidates when their buffers fit, else 64
+  uint32_t wcap = gpm_dev::kNestWarpC;
+  if (smem + (size_t)gpm_dev::nest_words(maxd, THREADS / 32, 0, wcap) * 4 + 2048 + 4 * 1024 > limit) wcap = 64;
   uint32_t big_cap = 0;
   if (!GLOBAL && KMAX >= 5) {
     // room left after the bitmap and the per-warp nested buffers goes to the CTA-wide nested buffer
     const size_t fixed = smem + (size_t)gpm_dev::nest_words(maxd, THREADS / 32, 0, wcap) * 4 + 2048;
-    const size_t limit = smem_limit ? smem_limit : (size_t)max_smem_optin(device);
     if (fixed + 4 * 1024 <= limit) {
       big_cap = (uint32_t)std::min<size_t>((limit - fixed) / 4, 32768);
       smem += (size_t)gpm_dev::nest_words(maxd, THREADS / 32, big_cap, wcap) * 4;
