@@ -66,7 +66,7 @@ __device__ __forceinline__ uint32_t build_rows(const uint32_t *__restrict__ dcol
   return found;
 }
 
-// Position table of L for build_rows_hashed: open addressing on the vertex id
+// Position table of L for build_rows_runs: open addressing on the vertex id
 // with 2^hbits >= 2d slots (keys, then values). Built by the whole CTA; the
 // caller synchronises before and after.
 constexpr uint32_t kPosEmpty = 0xffffffffu;
@@ -86,17 +86,17 @@ __device__ __forceinline__ void build_pos_table(const uint32_t *L, uint32_t d, u
   }
 }
 
-// build_rows with the element lookup in the position table (about two probes
-// instead of a binary search over L) and four consecutive elements per thread
-// (one search for the row of the first, then a forward step).
+// build_rows with four consecutive elements per thread (one search for the
+// row of the first, then a forward step) and, given a position table hk, the
+// element lookup in it (about two probes instead of a binary search over L).
 template <bool SCATTER>
-__device__ __forceinline__ uint32_t build_rows_hashed(const uint32_t *__restrict__ dcol, uint32_t *t_edge,
+__device__ __forceinline__ uint32_t build_rows_runs(const uint32_t *__restrict__ dcol, uint32_t *t_edge,
                                                       const uint32_t *L, const uint32_t *pre, const uint64_t *xb,
                                                       uint32_t *R, uint32_t *tc, uint32_t d, uint32_t rs, uint32_t t,
                                                       uint32_t nt, const uint32_t *perm, const uint32_t *hk,
                                                       uint32_t hbits) {
   const uint32_t E = pre[d], mask = (1u << hbits) - 1;
-  const uint32_t *hv = hk + (1u << hbits);
+  const uint32_t *hv = hk ? hk + (1u << hbits) : nullptr;
   uint32_t found = 0;
   const uint32_t lo_id = L[0], hi_id = L[d - 1];
   for (uint32_t f0 = 4 * t; f0 < E; f0 += 4 * nt) {
@@ -121,15 +121,21 @@ __device__ __forceinline__ uint32_t build_rows_hashed(const uint32_t *__restrict
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (rowi[q] == 0xffffffffu || y[q] < lo_id || y[q] > hi_id) continue;
-      uint32_t h = pos_hash(y[q], hbits), j = kPosEmpty;
-      for (;;) {
-        const uint32_t k = hk[h];
-        if (k == y[q]) {
-          j = hv[h];
-          break;
+      uint32_t j = kPosEmpty;
+      if (hk) {
+        uint32_t h = pos_hash(y[q], hbits);
+        for (;;) {
+          const uint32_t k = hk[h];
+          if (k == y[q]) {
+            j = hv[h];
+            break;
+          }
+          if (k == kPosEmpty) break;
+          h = (h + 1) & mask;
         }
-        if (k == kPosEmpty) break;
-        h = (h + 1) & mask;
+      } else {
+        const uint32_t jj = lower_bound_u32(L, d, y[q]);
+        if (jj < d && L[jj] == y[q]) j = jj;
       }
       if (j == kPosEmpty) continue;
       const uint32_t ii = rowi[q];
@@ -611,7 +617,7 @@ __device__ __forceinline__ void lg_root_warp(const uint64_t *__restrict__ drow, 
     carry += __shfl_sync(0xffffffffu, v, 31);
   }
   __syncwarp();
-  a3 += build_rows<SCATTER>(dcol, t_edge, L, pre, xb, R, tc, d, rs, lane, 32);
+  a3 += build_rows_runs<SCATTER>(dcol, t_edge, L, pre, xb, R, tc, d, rs, lane, 32, nullptr, nullptr, 0);
   __syncwarp();
   if (SCATTER) {
     for (uint32_t i = lane; i < d; i += 32)
@@ -683,7 +689,7 @@ __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, c
   }
   __syncthreads();
   if (hk)
-    a3 += build_rows_hashed<SCATTER>(dcol, t_edge, L, pre, xb, R, tc, d, rs, tid, nt, tri ? perm : nullptr, hk, hbits);
+    a3 += build_rows_runs<SCATTER>(dcol, t_edge, L, pre, xb, R, tc, d, rs, tid, nt, tri ? perm : nullptr, hk, hbits);
   else
     a3 += build_rows<SCATTER>(dcol, t_edge, L, pre, xb, R, tc, d, rs, tid, nt, tri ? perm : nullptr);
   __syncthreads();

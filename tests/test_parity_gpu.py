@@ -327,3 +327,23 @@ def test_fullsize_sl_chunglu4m(gpm):
         rows = np.random.default_rng(0).choice(len(tuples), size=min(2000, len(tuples)), replace=False)
         _check_tuples(g, adj, P.info(), tuples[rows])
     G.close()
+
+
+def test_complete_graph_every_class(gpm):
+    # K_1100 in degree order (ties by id): out-degrees 0..1099 cover every root
+    # class, including the 1024-thread shared-memory class at its largest
+    # (out-degree 1024, where the one-warp rows fall back to 64 candidates) and
+    # the global-memory class above it. Closed forms C(n, k).
+    import math
+    n = 1100
+    g = gg.complete(n)
+    G = gpm.Graph.from_host(g)
+    info = G.prepare().info()
+    assert info["max_out_degree"] == n - 1
+    got = gpm.count(G, [gpm.Pattern.clique(k) for k in (3, 4, 5)])
+    assert got == [math.comb(n, 3), math.comb(n, 4), math.comb(n, 5)]
+    # root ranges: the roots with out-degree in (384, 1024] alone
+    lo, hi = n - 1 - 1024, n - 1 - 384
+    got = gpm.count_roots(G, [gpm.Pattern.clique(5)], lo, hi)
+    assert got == [sum(math.comb(n - 1 - v, 4) for v in range(lo, hi))]
+    G.close()
