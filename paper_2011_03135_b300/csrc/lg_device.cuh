@@ -67,7 +67,7 @@ __device__ __forceinline__ uint32_t build_rows(const uint32_t *__restrict__ dcol
 }
 
 // Position table of L for build_rows_runs: open addressing on the vertex id
-// with 2^hbits >= 2d slots (keys, then values). Built by the whole CTA; the
+// with 2^hbits >= 4d slots (keys, then values). Built by the whole CTA; the
 // caller synchronises before and after.
 constexpr uint32_t kPosEmpty = 0xffffffffu;
 __device__ __forceinline__ uint32_t pos_hash(uint32_t y, uint32_t hbits) { return (y * 0x9E3779B1u) >> (32 - hbits); }
@@ -668,9 +668,10 @@ __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, c
   for (size_t i = tid; i < (size_t)d * rs; i += nt) R[i] = 0;
   if (tid == 0) pre[0] = 0;
   // with the nested-search region present, its pool holds L's position table
-  // until the enumeration starts (2^hbits >= 2d slots, keys and values)
+  // until the enumeration starts (2^hbits >= 4d slots, keys and values: most
+  // lookups miss, and a table a quarter full ends a miss in about 1.4 probes)
   uint32_t hbits = 1;
-  while ((1u << hbits) < 2 * d) ++hbits;
+  while ((1u << hbits) < 4 * d) ++hbits;
   uint32_t *hk = nest ? nest + 4 + 2 * (size_t)maxd : nullptr;
   if (hk) build_pos_table(L, d, hk, hbits, tid, nt);
   __syncthreads();
