@@ -6,15 +6,18 @@
 // use (lg_device.cuh, motif_device.cuh):
 //   LG_WARP  a range of roots with out-degree <= 128, one root per warp
 //   LG_CTA   one root with a larger out-degree, the whole CTA
-//   C4_SMALL a range of 4-cycle roots with a small wedge bound, one per warp
-//   C4_BIG   one 4-cycle root, the whole CTA with a dense tally slot
-//   EDGE     a range of vertices: local-count terms (4-motif queries wait
-//            until all of the query's triangle-scatter items are done)
+//   C4_SMALL  a range of 4-cycle roots with a small wedge bound, one per warp
+//   C4_BUCKET one 4-cycle root with a larger bound, bucketed by the whole CTA
+//   EDGE      a range of vertices: local-count terms (4-motif queries wait
+//             until all of the query's triangle-scatter items are done)
 // Items sit in one global queue, heavy items first and EDGE items last; every
 // CTA pulls the next item with one atomicAdd. A query's last finished item
 // computes its counts (motif inversion included) on the device. Nothing
 // synchronises the host between queries, so small queries overlap with large
 // ones instead of each paying a launch sequence and a host round trip.
+// Hub-class 4-cycle roots are counted by whole-GPU launches captured ahead of
+// the persistent kernel, and the heaviest queries (timed at creation) run
+// their plain count path there too.
 //
 // The EDGE items' wait is bounded (a spin with __nanosleep and an iteration
 // cap); on timeout the kernel sets a status bit, the host reports

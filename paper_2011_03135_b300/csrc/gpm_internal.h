@@ -106,8 +106,9 @@ struct gpm_graph {
   uint32_t *list_scratch = nullptr;
   size_t list_scratch_bytes = 0;
   // 4-cycle roots grouped by wedge bound; classes: [0,1) small (warp hash),
-  // [1,2) bucketed, [2,3) hub roots (whole-grid tally in the plain path, a
-  // dense per-CTA tally in the batched and served forms)
+  // [1,2) bucketed, [2,3) hub roots (whole-GPU tallies in the plain and
+  // batched forms, PART/SUM items in the served form; a per-CTA dense tally
+  // item where a hub root's tally would be sparse)
   uint32_t *c4_tasks = nullptr;
   uint32_t c4_begin[4] = {0, 0, 0, 0};
   uint32_t c4_bucket_maxb = 0;  // largest wedge bound among bucketed roots

@@ -79,7 +79,7 @@ constexpr uint32_t kSmallBound = gpm_dev::kC4SmallBound;
 constexpr uint32_t kHashSlots = gpm_dev::kC4HashSlots;
 
 // wedge bound B(v0) = sum of d_x over neighbours x before v0; class 0 small
-// (warp hash), 1 bucketed, 2 dense tally
+// (warp hash), 1 bucketed, 2 hub
 __global__ void c4_bound_kernel(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
                                 const uint32_t *__restrict__ deg, const uint32_t *__restrict__ edeg, uint32_t n,
                                 uint32_t hub_bound, uint32_t *__restrict__ counts, uint32_t *__restrict__ tasks,
