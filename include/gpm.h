@@ -323,11 +323,11 @@ int gpm_server_stop(gpm_server_t s);
 
 /*
  * Edge-induced 4-cycles of a CSR that already lives in device memory, for
- * callers that must not allocate device memory while they run: code inside a
- * CUDA stream capture (cudaMalloc cannot be captured), frameworks whose own
- * arena owns all device memory, or latency-critical loops where cudaMalloc or
- * cudaFree would synchronise the whole device. The paper has no counterpart;
- * this entry point exists for those callers.
+ * callers that must not allocate device memory while they run: frameworks
+ * whose own arena owns all device memory, jobs with a hard memory budget where
+ * an allocation could fail half-way through, or latency-critical loops where
+ * cudaMalloc or cudaFree would synchronise the whole device. The paper has no
+ * counterpart; this entry point exists for those callers.
  *   rowptr, col : DEVICE pointers, symmetric sorted CSR as for gpm_graph_create
  *                 (trusted: not validated)
  *   count       : DEVICE pointer to one uint64 that receives the count

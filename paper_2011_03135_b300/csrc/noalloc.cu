@@ -1,9 +1,9 @@
 // 4-cycle counting that allocates nothing.
 //
-// Some callers cannot allocate device memory while they run: code executing
-// inside a CUDA stream capture (cudaMalloc is not capturable), frameworks
-// that hand all device memory to their own arena and forbid outside
-// allocations, or latency-sensitive loops where cudaMalloc/cudaFree would
+// Some callers cannot allocate device memory while they run: frameworks that
+// hand all device memory to their own arena and forbid outside allocations,
+// jobs with a hard memory budget where an allocation could fail half-way
+// through, or latency-sensitive loops where cudaMalloc/cudaFree would
 // synchronise the whole device. For them gpm_count_cycles4_noalloc counts
 // the edge-induced 4-cycles of a CSR that the caller already holds in device
 // memory, writing the count to a device word the caller provides, with every
