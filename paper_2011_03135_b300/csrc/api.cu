@@ -281,7 +281,8 @@ int gpm_graph_create(const uint64_t *rowptr, const uint32_t *col, uint32_t n, ui
     return fail(gpm_fail(GPM_E_DEVICE, "no CUDA device"));
   }
   if ((rc = gpm_graph_alloc(g, (void **)&g->rowptr, sizeof(uint64_t) * ((size_t)n + 1)))) return fail(rc);
-  if ((rc = gpm_graph_alloc(g, (void **)&g->col, sizeof(uint32_t) * std::max<uint64_t>(nnz, 1)))) return fail(rc);
+  if ((rc = gpm_graph_alloc(g, (void **)&g->col, sizeof(uint32_t) * (std::max<uint64_t>(nnz, 1) + kCsrPadWords))))
+    return fail(rc);
   if ((rc = gpm_graph_alloc(g, (void **)&g->deg, sizeof(uint32_t) * std::max<uint32_t>(n, 1)))) return fail(rc);
   if ((rc = gpm_graph_alloc(g, (void **)&g->work, sizeof(uint64_t) * WORK_WORDS))) return fail(rc);
   const cudaMemcpyKind kind = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;

@@ -267,5 +267,9 @@ int gpm_enqueue_count(gpm_graph *g, const gpm_pattern_t *pats, uint32_t npat, un
                       cudaStream_t st);
 const unsigned int *gpm_graph_status(const gpm_graph *g);
 
+// col and edeg are allocated with this many extra words: 16-byte bulk copies
+// of an adjacency range may round its end up past the last entry
+constexpr size_t kCsrPadWords = 16;
+
 // grow-on-demand device allocation owned by the graph
 int gpm_graph_alloc(gpm_graph *g, void **ptr, size_t bytes);

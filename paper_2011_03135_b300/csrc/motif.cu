@@ -227,14 +227,77 @@ struct HubGroup {
 
 __device__ __forceinline__ unsigned long long pairs_of(uint32_t c) { return (unsigned long long)c * (c - (c > 0)) / 2; }
 
+// ---- bulk asynchronous copies (TMA engine) into shared memory, per warp ----
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// bytes and both addresses are multiples of 16
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// shared memory read by ordinary loads is about to be overwritten by a bulk copy
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// bounded wait for the completion of phase `parity`; false if the limit was hit
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 20); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+constexpr uint32_t kHubStage = kHubChunk + 8;  // words per staged array: a unit plus 16-byte rounding
+
+struct HubUnit {
+  uint32_t r, off, n;  // group root, first entry within the staged range, entries
+  uint64_t a0;         // first staged word (16-byte aligned)
+  uint32_t words;      // staged words (multiple of 4)
+};
+
+__device__ __forceinline__ HubUnit hub_unit(const uint64_t *__restrict__ rowptr, const uint2 *__restrict__ units,
+                                            const HubGroup &grp, unsigned long long f) {
+  HubUnit h;
+  h.r = 0;
+  while (h.r + 1 < grp.nr && f >= grp.cum[h.r + 1]) ++h.r;
+  const uint2 unit = units[grp.ub[h.r] + (f - grp.cum[h.r])];
+  const uint64_t e0 = rowptr[unit.x] + (uint64_t)unit.y * kHubChunk;
+  const uint64_t e1 = min(rowptr[unit.x + 1], e0 + kHubChunk);
+  h.a0 = e0 & ~3ull;
+  h.off = (uint32_t)(e0 - h.a0);
+  h.n = (uint32_t)(e1 - e0);
+  h.words = (uint32_t)(((e1 + 3) & ~3ull) - h.a0);
+  return h;
+}
+
 // Finishes the previous group's tallies, then tallies the wedges of this
-// group's roots. Each warp takes whole units (x, chunk).
+// group's roots. Each warp takes whole units (x, chunk) and stages each unit's
+// col and edeg ranges in shared memory with bulk asynchronous copies, two
+// units in flight per warp (the next one is copied while the current one is
+// tallied). Waits are bounded: on a timeout the warp records ST_TIMEOUT,
+// waits (bounded) for its copies still in flight and stops.
 __global__ void __launch_bounds__(kHubThreads) c4_hub_kernel(const uint64_t *__restrict__ rowptr,
                                                              const uint32_t *__restrict__ col,
                                                              const uint32_t *__restrict__ edeg,
                                                              const uint2 *__restrict__ units, uint64_t npad,
-                                                             HubGroup grp, unsigned long long *__restrict__ acc_out) {
-  __shared__ unsigned long long s_acc[kHubThreads / 32];
+                                                             HubGroup grp, unsigned long long *__restrict__ acc_out,
+                                                             unsigned int *__restrict__ status) {
+  constexpr uint32_t kW = kHubThreads / 32;
+  __shared__ unsigned long long s_acc[kW];
+  __shared__ __align__(16) uint32_t s_stage[kW][2][2][kHubStage];  // [warp][buffer][col, edeg][words]
+  __shared__ __align__(8) uint64_t s_bar[kW][2];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint64_t gtid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
@@ -256,60 +319,87 @@ __global__ void __launch_bounds__(kHubThreads) c4_hub_kernel(const uint64_t *__r
       for (uint64_t i = gtid; i < cnt; i += nth) T[__ldcg(L + i)] = 0u;
     }
   }
+  if (lane == 0) {
+    mbar_init(&s_bar[wid][0], 1);
+    mbar_init(&s_bar[wid][1], 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
   const unsigned long long total = grp.cum[grp.nr];
-  for (unsigned long long f = gtid >> 5; f < total; f += nth >> 5) {
-    uint32_t r = 0;
-    while (r + 1 < grp.nr && f >= grp.cum[r + 1]) ++r;
-    const uint2 unit = units[grp.ub[r] + (f - grp.cum[r])];
-    const uint32_t v0 = grp.v0[r], d0 = grp.d0[r];
-    uint32_t *tally = grp.tally + (size_t)r * npad;
-    const uint64_t e0 = rowptr[unit.x] + (uint64_t)unit.y * kHubChunk;
-    const uint64_t e1 = min(rowptr[unit.x + 1], e0 + kHubChunk);
-    const bool dense = (grp.dense >> r) & 1u;
-    for (uint64_t base = e0; base < e1; base += 128) {
-      uint32_t w[4];
-      bool v[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const uint64_t e = base + 32 * k + lane;
-        v[k] = false;
-        w[k] = 0;
-        if (e < e1) {
-          w[k] = col[e];
-          v[k] = precedes(edeg[e], w[k], d0, v0);
-        }
+  const unsigned long long stride = nth >> 5;
+  auto issue = [&](const HubUnit &h, uint32_t b) {
+    if (lane == 0) {
+      fence_proxy_async();
+      mbar_expect_tx(&s_bar[wid][b], 8u * h.words);
+      bulk_copy_g2s(s_stage[wid][b][0], col + h.a0, 4u * h.words, &s_bar[wid][b]);
+      bulk_copy_g2s(s_stage[wid][b][1], edeg + h.a0, 4u * h.words, &s_bar[wid][b]);
+    }
+  };
+  uint32_t phase = 0u, pending = 0u;  // bit b: parity to wait for / a copy in flight, buffer b
+  unsigned long long f = gtid >> 5;
+  HubUnit cur{};
+  if (f < total) {
+    cur = hub_unit(rowptr, units, grp, f);
+    issue(cur, 0);
+    pending |= 1u;
+  }
+  bool timed_out = false;
+  for (uint32_t k = 0; f < total; ++k, f += stride) {
+    const uint32_t b = k & 1u;
+    HubUnit nxt{};
+    if (f + stride < total) {
+      nxt = hub_unit(rowptr, units, grp, f + stride);
+      issue(nxt, b ^ 1u);
+      pending |= 2u >> b;
+    }
+    if (!mbar_wait(&s_bar[wid][b], (phase >> b) & 1u)) {
+      timed_out = true;
+      break;
+    }
+    phase ^= 1u << b;
+    pending &= ~(1u << b);
+    const uint32_t *sc = s_stage[wid][b][0] + cur.off;
+    const uint32_t *sd = s_stage[wid][b][1] + cur.off;
+    const uint32_t v0 = grp.v0[cur.r], d0 = grp.d0[cur.r];
+    uint32_t *tally = grp.tally + (size_t)cur.r * npad;
+    if ((grp.dense >> cur.r) & 1u) {
+      for (uint32_t i = lane; i < cur.n; i += 32) {
+        const uint32_t w = sc[i];
+        if (precedes(sd[i], w, d0, v0)) atomicAdd(&tally[w], 1u);
       }
-      if (dense) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (v[k]) atomicAdd(&tally[w[k]], 1u);
-        continue;
-      }
-      uint32_t old[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) old[k] = v[k] ? atomicAdd(&tally[w[k]], 1u) : 1u;
-      uint32_t *touched = grp.touched + (size_t)r * npad;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        acc += v[k] ? old[k] : 0u;
-        const bool first = v[k] && old[k] == 0u;
+    } else {
+      uint32_t *touched = grp.touched + (size_t)cur.r * npad;
+      for (uint32_t base = 0; base < cur.n; base += 32) {
+        const uint32_t i = base + lane;
+        const uint32_t w = (i < cur.n) ? sc[i] : 0u;
+        const bool v = (i < cur.n) && precedes(sd[i], w, d0, v0);
+        const uint32_t old = v ? atomicAdd(&tally[w], 1u) : 1u;
+        acc += v ? old : 0u;
+        const bool first = v && old == 0u;
         const uint32_t m = __ballot_sync(0xffffffffu, first);
         if (m) {
           const int leader = __ffs(m) - 1;
-          uint32_t b = 0;
-          if ((int)lane == leader) b = atomicAdd(&grp.ntouched[r], (uint32_t)__popc(m));
-          b = __shfl_sync(0xffffffffu, b, leader);
-          if (first) touched[b + __popc(m & ((1u << lane) - 1u))] = w[k];
+          uint32_t pos = 0;
+          if ((int)lane == leader) pos = atomicAdd(&grp.ntouched[cur.r], (uint32_t)__popc(m));
+          pos = __shfl_sync(0xffffffffu, pos, leader);
+          if (first) touched[pos + __popc(m & ((1u << lane) - 1u))] = w;
         }
       }
     }
+    __syncwarp();  // every lane is done with buffer b before it is refilled
+    cur = nxt;
+  }
+  if (timed_out) {
+    if (lane == 0) atomicOr(status, ST_TIMEOUT);
+    for (uint32_t b = 0; b < 2; ++b)
+      if ((pending >> b) & 1u) mbar_wait(&s_bar[wid][b], (phase >> b) & 1u);
   }
   acc = warp_sum(acc);
   if (lane == 0) s_acc[wid] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long t = 0;
-    for (int i = 0; i < kHubThreads / 32; ++i) t += s_acc[i];
+    for (uint32_t i = 0; i < kW; ++i) t += s_acc[i];
     if (t) atomicAdd(&acc_out[ACC_C4], t);
   }
 }
@@ -373,7 +463,7 @@ static int ensure_c4_tasks(gpm_graph *g, cudaStream_t st) {
   if (!g->c4_tasks) GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4_tasks, sizeof(uint32_t) * std::max<uint32_t>(g->n, 1)));
   const int blocks = gpm_num_sms(g->device) * 8;
   if (!g->edeg) {
-    GPM_TRY(gpm_graph_alloc(g, (void **)&g->edeg, sizeof(uint32_t) * std::max<uint64_t>(g->nnz, 1)));
+    GPM_TRY(gpm_graph_alloc(g, (void **)&g->edeg, sizeof(uint32_t) * (std::max<uint64_t>(g->nnz, 1) + kCsrPadWords)));
     if (g->nnz) {
       GPM_LAUNCH("c4_edeg_kernel", st, c4_edeg_kernel<<<blocks, 256, 0, st>>>(g->col, g->deg, g->nnz, g->edeg));
       GPM_CUDA(cudaGetLastError());
@@ -539,7 +629,8 @@ static int launch_c4_hub(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsig
       grp.prev_ntouched = prev.ntouched;
     }
     GPM_LAUNCH("c4_hub_kernel", st,
-               c4_hub_kernel<<<blocks, kHubThreads, 0, st>>>(g->rowptr, g->col, g->edeg, units, npad, grp, acc));
+               c4_hub_kernel<<<blocks, kHubThreads, 0, st>>>(g->rowptr, g->col, g->edeg, units, npad, grp, acc,
+                                                             reinterpret_cast<unsigned int *>(g->work + WK_STATUS)));
     GPM_CUDA(cudaGetLastError());
     prev = grp;
   }
