@@ -215,24 +215,49 @@ __device__ __forceinline__ int task_class(uint32_t d, uint32_t warp_max, uint32_
 
 __global__ void class_count_kernel(const uint64_t *__restrict__ drow, uint32_t n, uint32_t warp_max,
                                    uint32_t cta_max, uint32_t *__restrict__ counts, uint32_t *__restrict__ maxd) {
+  // per-thread tallies, one warp reduction and one atomic per class and warp
+  uint32_t cnt[NUM_CLS] = {0, 0, 0, 0}, mx[NUM_CLS] = {0, 0, 0, 0};
   for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t d = (uint32_t)(drow[v + 1] - drow[v]);
     int c = task_class(d, warp_max, cta_max);
-    if (c >= 0) {
-      atomicAdd(&counts[c], 1u);
-      atomicMax(&maxd[c], d);
+#pragma unroll
+    for (int k = 0; k < NUM_CLS; ++k)
+      if (c == k) {
+        ++cnt[k];
+        mx[k] = max(mx[k], d);
+      }
+  }
+#pragma unroll
+  for (int k = 0; k < NUM_CLS; ++k) {
+    const uint32_t tc = __reduce_add_sync(0xffffffffu, cnt[k]);
+    const uint32_t tm = __reduce_max_sync(0xffffffffu, mx[k]);
+    if ((threadIdx.x & 31) == 0 && tc) {
+      atomicAdd(&counts[k], tc);
+      atomicMax(&maxd[k], tm);
     }
   }
 }
 
-// Scatter roots into their class segment. Within a segment, roots are
-// placed by a cursor; order within a class is unspecified.
+// Scatter roots into their class segment, one cursor reservation per class
+// and warp step. Within a segment, order is unspecified.
 __global__ void class_fill_kernel(const uint64_t *__restrict__ drow, uint32_t n, uint32_t warp_max, uint32_t cta_max,
                                   uint32_t *__restrict__ cursors, uint32_t *__restrict__ tasks) {
-  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t d = (uint32_t)(drow[v + 1] - drow[v]);
-    int c = task_class(d, warp_max, cta_max);
-    if (c >= 0) tasks[atomicAdd(&cursors[c], 1u)] = (uint32_t)v;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
+    const uint64_t v = base + lane;
+    int c = -1;
+    if (v < n) c = task_class((uint32_t)(drow[v + 1] - drow[v]), warp_max, cta_max);
+#pragma unroll
+    for (int k = 0; k < NUM_CLS; ++k) {
+      const uint32_t m = __ballot_sync(0xffffffffu, c == k);
+      if (!m) continue;
+      const int leader = __ffs(m) - 1;
+      uint32_t pos = 0;
+      if ((int)lane == leader) pos = atomicAdd(&cursors[k], (uint32_t)__popc(m));
+      pos = __shfl_sync(0xffffffffu, pos, leader);
+      if (c == k) tasks[pos + __popc(m & ((1u << lane) - 1u))] = (uint32_t)v;
+    }
   }
 }
 

@@ -84,25 +84,45 @@ __global__ void c4_bound_kernel(const uint64_t *__restrict__ rowptr, const uint3
                                 const uint32_t *__restrict__ deg, const uint32_t *__restrict__ edeg, uint32_t n,
                                 uint32_t hub_bound, uint32_t *__restrict__ counts, uint32_t *__restrict__ tasks,
                                 uint32_t *__restrict__ cursors, int fill) {
+  // a warp takes 32 consecutive vertices, one at a time (lanes over the
+  // neighbours); lane k keeps vertex k's class, and the 32 outcomes are
+  // counted / placed with one atomic per class
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t v = warp; v < n; v += nwarps) {
-    const uint32_t dv = deg[v];
-    unsigned long long b = 0;
-    for (uint64_t e = rowptr[v] + lane; e < rowptr[v + 1]; e += 32) {
-      const uint32_t x = col[e];
-      const uint32_t dx = edeg[e];
-      if (precedes(dx, x, dv, (uint32_t)v)) b += dx;
+  for (uint64_t g0 = warp * 32; g0 < n; g0 += nwarps * 32) {
+    int my_c = -1;
+    uint32_t my_b = 0;
+    for (uint32_t k = 0; k < 32 && g0 + k < n; ++k) {
+      const uint64_t v = g0 + k;
+      const uint32_t dv = deg[v];
+      unsigned long long b = 0;
+      for (uint64_t e = rowptr[v] + lane; e < rowptr[v + 1]; e += 32) {
+        const uint32_t x = col[e];
+        const uint32_t dx = edeg[e];
+        if (precedes(dx, x, dv, (uint32_t)v)) b += dx;
+      }
+      b = __shfl_sync(0xffffffffu, warp_sum(b), 0);
+      if (lane == k && b >= 3) {  // a cycle needs two wedges, each scanning v0 itself plus w
+        my_c = (b <= kSmallBound) ? 0 : (b <= hub_bound ? 1 : 2);
+        my_b = (uint32_t)(b > 0xffffffffull ? 0xffffffffull : b);
+      }
     }
-    b = warp_sum(b);
-    if (lane == 0 && b >= 3) {  // a cycle needs two wedges, each scanning v0 itself plus w
-      const int c = (b <= kSmallBound) ? 0 : (b <= hub_bound ? 1 : 2);
+    for (int c = 0; c < 3; ++c) {
+      const uint32_t m = __ballot_sync(0xffffffffu, my_c == c);
+      if (!m) continue;
       if (fill) {
-        tasks[atomicAdd(&cursors[c], 1u)] = (uint32_t)v;
+        const int leader = __ffs(m) - 1;
+        uint32_t pos = 0;
+        if ((int)lane == leader) pos = atomicAdd(&cursors[c], (uint32_t)__popc(m));
+        pos = __shfl_sync(0xffffffffu, pos, leader);
+        if (my_c == c) tasks[pos + __popc(m & ((1u << lane) - 1u))] = (uint32_t)(g0 + lane);
       } else {
-        atomicAdd(&counts[c], 1u);
-        if (c == 1) atomicMax(&counts[3], (uint32_t)b);
+        const uint32_t mb = __reduce_max_sync(0xffffffffu, my_c == 1 ? my_b : 0u);
+        if (lane == 0) {
+          atomicAdd(&counts[c], (uint32_t)__popc(m));
+          if (c == 1) atomicMax(&counts[3], mb);
+        }
       }
     }
   }
