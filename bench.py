@@ -139,8 +139,8 @@ def clique_pass_bytes(g, opts):
 # valid only for the kernel sources they were taken on (digest of
 # csrc/lg_device.cuh + csrc/clique.cu); a stale entry is ignored.
 NCU_COUNTERS = {
-    "lg_cta_hi": {"digest": "60792178ba28d394", "inst_per_launch": 151171698895,
-                  "dram_bytes_per_launch": 28186624 + 2560, "ncu_ms": 183.604},
+    "lg_cta_hi": {"digest": "d75068b607f996ed", "inst_per_launch": 151171261534,
+                  "dram_bytes_per_launch": 28408832 + 2816, "ncu_ms": 183.558},
 }
 
 

@@ -37,7 +37,8 @@ __device__ __forceinline__ uint32_t row_of(const uint32_t *pre, uint32_t n, uint
 // calling group cooperate; the caller synchronises before and after.
 // perm (optional): row and bit positions of L[i] (see rank_local); the
 // triangle-count scatter keeps id positions.
-template <bool SCATTER>
+// ROWS = false (triangles only): the bitmap is not written.
+template <bool SCATTER, bool ROWS = true>
 __device__ __forceinline__ uint32_t build_rows(const uint32_t *__restrict__ dcol, uint32_t *t_edge, const uint32_t *L,
                                                const uint32_t *pre,
                                                const uint64_t *xb, uint32_t *R, uint32_t *tc, uint32_t d,
@@ -54,7 +55,7 @@ __device__ __forceinline__ uint32_t build_rows(const uint32_t *__restrict__ dcol
     const uint32_t j = lower_bound_u32(L, d, y);
     if (j < d && L[j] == y) {
       const uint32_t ri = perm ? perm[i] : i, rj = perm ? perm[j] : j;
-      atomicOr(&R[(size_t)ri * rs + (rj >> 5)], 1u << (rj & 31));
+      if (ROWS) atomicOr(&R[(size_t)ri * rs + (rj >> 5)], 1u << (rj & 31));
       ++found;
       if (SCATTER) {
         atomicAdd(&tc[i], 1u);
@@ -89,7 +90,7 @@ __device__ __forceinline__ void build_pos_table(const uint32_t *L, uint32_t d, u
 // build_rows with four consecutive elements per thread (one search for the
 // row of the first, then a forward step) and, given a position table hk, the
 // element lookup in it (about two probes instead of a binary search over L).
-template <bool SCATTER>
+template <bool SCATTER, bool ROWS = true>
 __device__ __forceinline__ uint32_t build_rows_runs(const uint32_t *__restrict__ dcol, uint32_t *t_edge,
                                                       const uint32_t *L, const uint32_t *pre, const uint64_t *xb,
                                                       uint32_t *R, uint32_t *tc, uint32_t d, uint32_t rs, uint32_t t,
@@ -140,7 +141,7 @@ __device__ __forceinline__ uint32_t build_rows_runs(const uint32_t *__restrict__
       if (j == kPosEmpty) continue;
       const uint32_t ii = rowi[q];
       const uint32_t ri = perm ? perm[ii] : ii, rj = perm ? perm[j] : j;
-      atomicOr(&R[(size_t)ri * rs + (rj >> 5)], 1u << (rj & 31));
+      if (ROWS) atomicOr(&R[(size_t)ri * rs + (rj >> 5)], 1u << (rj & 31));
       ++found;
       if (SCATTER) {
         atomicAdd(&tc[ii], 1u);
@@ -602,7 +603,8 @@ __device__ __forceinline__ void lg_root_warp(const uint64_t *__restrict__ drow, 
     pre[i + 1] = (uint32_t)(xe - xs);
     if (SCATTER) tc[i] = 0;
   }
-  for (uint32_t i = lane; i < d * rs; i += 32) R[i] = 0;
+  if (KMAX >= 4)
+    for (uint32_t i = lane; i < d * rs; i += 32) R[i] = 0;
   if (lane == 0) pre[0] = 0;
   __syncwarp();
   uint32_t carry = 0;
@@ -617,7 +619,7 @@ __device__ __forceinline__ void lg_root_warp(const uint64_t *__restrict__ drow, 
     carry += __shfl_sync(0xffffffffu, v, 31);
   }
   __syncwarp();
-  a3 += build_rows_runs<SCATTER>(dcol, t_edge, L, pre, xb, R, tc, d, rs, lane, 32, nullptr, nullptr, 0);
+  a3 += build_rows_runs<SCATTER, (KMAX >= 4)>(dcol, t_edge, L, pre, xb, R, tc, d, rs, lane, 32, nullptr, nullptr, 0);
   __syncwarp();
   if (SCATTER) {
     for (uint32_t i = lane; i < d; i += 32)
@@ -665,7 +667,8 @@ __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, c
     __syncthreads();
     rank_local(deg, L, d, keys, perm);
   }
-  for (size_t i = tid; i < (size_t)d * rs; i += nt) R[i] = 0;
+  if (KMAX >= 4)
+    for (size_t i = tid; i < (size_t)d * rs; i += nt) R[i] = 0;
   if (tid == 0) pre[0] = 0;
   // with the nested-search region present, its pool holds L's position table
   // until the enumeration starts (2^hbits >= 4d slots, keys and values: most
@@ -690,9 +693,10 @@ __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, c
   }
   __syncthreads();
   if (hk)
-    a3 += build_rows_runs<SCATTER>(dcol, t_edge, L, pre, xb, R, tc, d, rs, tid, nt, tri ? perm : nullptr, hk, hbits);
+    a3 += build_rows_runs<SCATTER, (KMAX >= 4)>(dcol, t_edge, L, pre, xb, R, tc, d, rs, tid, nt, tri ? perm : nullptr,
+                                                hk, hbits);
   else
-    a3 += build_rows<SCATTER>(dcol, t_edge, L, pre, xb, R, tc, d, rs, tid, nt, tri ? perm : nullptr);
+    a3 += build_rows<SCATTER, (KMAX >= 4)>(dcol, t_edge, L, pre, xb, R, tc, d, rs, tid, nt, tri ? perm : nullptr);
   __syncthreads();
   if (SCATTER) {
     for (uint32_t i = tid; i < d; i += nt)
