@@ -430,6 +430,8 @@ __global__ void __launch_bounds__(kC4BucketThreads) c4_bucket_kernel(C4Args a, u
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint32_t s_task, s_cnt;
   __shared__ uint32_t s_x[kC4BucketThreads];
+  __shared__ uint32_t s_pre[kC4BucketThreads + 33];
+  __shared__ uint64_t s_rp[kC4BucketThreads];
   uint32_t *buf = a.pool + (size_t)blockIdx.x * slot_words;
   unsigned long long acc = 0;
   bool overflow = false;
@@ -442,7 +444,7 @@ __global__ void __launch_bounds__(kC4BucketThreads) c4_bucket_kernel(C4Args a, u
     const uint32_t v0 = a.tasks[task];
     if (v0 < a.root_lo || v0 >= a.root_hi) continue;
     acc += gpm_dev::c4_root_bucketed(a.rowptr, a.col, a.deg, a.edeg, v0, buf, buf + slot_words / 2, smem, s_x, &s_cnt,
-                                     overflow);
+                                     overflow, s_pre, s_rp);
   }
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0 && acc) atomicAdd(&a.acc[ACC_C4], acc);

@@ -164,6 +164,86 @@ __host__ __device__ constexpr uint64_t c4_bucket_slot_words(uint64_t maxb) {
   return 2 * ((maxb + 63) & ~63ull);
 }
 
+// largest i in [0, n) with pre[i] <= f (pre ascending, pre[0] = 0 <= f)
+__device__ __forceinline__ uint32_t c4_row_of(const uint32_t *pre, uint32_t n, uint32_t f) {
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (pre[mid] <= f) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// One chunk of the bucketed walk over the concatenated lists N(x), x in
+// s_x[0..cnt): the CTA takes the entries in blocks of 128 per warp, four
+// consecutive entries per lane (one row search for the first), so short
+// lists do not leave lanes idle. s_pre holds blockDim.x + 33 words, s_rp
+// blockDim.x entries. Every thread calls it; the caller synchronises after.
+__device__ __forceinline__ void c4_walk_flat(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
+                                             const uint32_t *__restrict__ deg, const uint32_t *__restrict__ edeg,
+                                             uint32_t v0, uint32_t d0, const uint32_t *s_x, uint32_t cnt,
+                                             uint32_t *s_pre, uint64_t *s_rp, uint32_t *bcnt, uint32_t pmask,
+                                             uint32_t *ctl, uint32_t *lin) {
+  const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  uint32_t *s_wsum = s_pre + nt + 1;
+  uint32_t len = 0;
+  if (tid < cnt) {
+    const uint32_t x = s_x[tid];
+    const uint64_t rb = rowptr[x];
+    s_rp[tid] = rb;
+    len = (uint32_t)(rowptr[x + 1] - rb);
+  }
+  uint32_t incl = len;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= (uint32_t)o) incl += y;
+  }
+  if (lane == 31) s_wsum[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    const uint32_t v = (lane < nw) ? s_wsum[lane] : 0u;
+    uint32_t wi = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= (uint32_t)o) wi += y;
+    }
+    if (lane < nw) s_wsum[lane] = wi - v;
+  }
+  __syncthreads();
+  const uint32_t excl = incl - len + s_wsum[wid];
+  if (tid < cnt) s_pre[tid] = excl;
+  if (tid + 1 == cnt) s_pre[cnt] = excl + len;
+  if (cnt == 0 && tid == 0) s_pre[0] = 0;
+  __syncthreads();
+  const uint32_t total = s_pre[cnt];
+  for (uint32_t start = wid * 128; start < total; start += nw * 128) {
+    const uint32_t f0 = start + 4 * lane;
+    uint32_t i = (f0 < total) ? c4_row_of(s_pre, cnt, f0) : 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t f = f0 + q;
+      uint32_t w = 0;
+      bool v = false;
+      if (f < total) {
+        while (s_pre[i + 1] <= f) ++i;
+        const uint64_t e = s_rp[i] + (f - s_pre[i]);
+        w = col[e];
+        v = precedes(nbr_deg(edeg, deg, e, w), w, d0, v0);
+      }
+      if (v) atomicAdd(&bcnt[c4_bucket_hash(w) & pmask], 1u);
+      const uint32_t m = __ballot_sync(0xffffffffu, v);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        uint32_t pos = 0;
+        if ((int)lane == leader) pos = atomicAdd(&ctl[2], (uint32_t)__popc(m));
+        pos = __shfl_sync(0xffffffffu, pos, leader);
+        if (v) lin[pos + __popc(m & ((1u << lane) - 1u))] = w;
+      }
+    }
+  }
+}
+
 // 4-cycles rooted at v0 with bucketed aggregation. One walk over the wedges
 // v0 - x - w appends every wedge end to `lin` (warp-aggregated) and counts it
 // in its hash bucket; a streaming pass then scatters `lin` into `buf` by
@@ -175,7 +255,8 @@ __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *_
                                                                const uint32_t *__restrict__ deg,
                                                                const uint32_t *__restrict__ edeg, uint32_t v0,
                                                                uint32_t *lin, uint32_t *buf, uint32_t *sm,
-                                                               uint32_t *s_x, uint32_t *s_cnt, bool &overflow) {
+                                                               uint32_t *s_x, uint32_t *s_cnt, bool &overflow,
+                                                               uint32_t *s_pre = nullptr, uint64_t *s_rp = nullptr) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   uint32_t *bcnt = sm;                       // [kC4MaxBuckets]: counts, then write cursors
   uint32_t *boff = sm + kC4MaxBuckets;       // [kC4MaxBuckets + 1]
@@ -219,6 +300,11 @@ __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *_
     }
     __syncthreads();
     const uint32_t cnt = *s_cnt;
+    if (s_pre) {
+      c4_walk_flat(rowptr, col, deg, edeg, v0, d0, s_x, cnt, s_pre, s_rp, bcnt, pmask, ctl, lin);
+      __syncthreads();
+      continue;
+    }
     for (uint32_t xi = wid; xi < cnt; xi += nw) {
       const uint32_t x = s_x[xi];
       const uint64_t xe = rowptr[x + 1];
