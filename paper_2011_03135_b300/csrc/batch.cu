@@ -49,6 +49,8 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(BatchArgs a) {
   __shared__ Item s_item;
   __shared__ uint32_t s_idx, s_cnt, s_nt;
   __shared__ uint32_t s_x[kThreads];
+  __shared__ uint32_t s_pre[kThreads + 33];
+  __shared__ uint64_t s_rp[kThreads];
   const uint32_t tid = threadIdx.x;
   for (;;) {
     if (tid == 0) {
@@ -60,7 +62,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(BatchArgs a) {
     const Item it = s_item;
     __syncthreads();
     const QDesc &q = a.qs[it.q];
-    run_item(a.env, q, it, smem, s_x, &s_cnt, &s_nt);
+    run_item(a.env, q, it, smem, s_x, &s_cnt, &s_nt, s_pre, s_rp);
     if (tid == 0 && item_done(q, it)) {
       // last item of this query: its counts, then re-arm it for the next replay
       const unsigned int bad = finalize_query(q, q.out);

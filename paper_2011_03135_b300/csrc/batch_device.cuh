@@ -140,8 +140,11 @@ __device__ __forceinline__ void block_add(unsigned long long *dst, unsigned long
 
 // Process one item with the whole CTA and fold its partial sums into the
 // query's accumulators. q must be readable by every thread (shared memory).
+// s_pre (kThreads + 33 words) and s_rp (kThreads entries): scratch of the
+// bucketed 4-cycle walk.
 __device__ __forceinline__ void run_item(const ItemEnv &a, const QDesc &q, const Item &it, uint32_t *smem,
-                                         uint32_t *s_x, uint32_t *s_cnt, uint32_t *s_nt) {
+                                         uint32_t *s_x, uint32_t *s_cnt, uint32_t *s_nt, uint32_t *s_pre,
+                                         uint64_t *s_rp) {
   const uint32_t tid = threadIdx.x;
   unsigned long long a3 = 0, a4 = 0, a5 = 0, c4 = 0;
   gpm_dev::EdgeTerms et;
@@ -171,7 +174,7 @@ __device__ __forceinline__ void run_item(const ItemEnv &a, const QDesc &q, const
     case IT_C4_BUCKET: {
       uint32_t *lin = a.c4_buf + (size_t)blockIdx.x * a.c4_buf_words;
       c4 += gpm_dev::c4_root_bucketed(q.rowptr, q.col, q.deg, q.edeg, q.c4_tasks[it.lo], lin, lin + a.c4_buf_words / 2,
-                                      smem, s_x, s_cnt, overflow);
+                                      smem, s_x, s_cnt, overflow, s_pre, s_rp);
       break;
     }
     case IT_C4_BIG: {

@@ -85,6 +85,8 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(ServeArgs a) {
   __shared__ int s_ok;
   __shared__ uint32_t s_cnt, s_nt;
   __shared__ uint32_t s_x[kThreads];
+  __shared__ uint32_t s_pre[kThreads + 33];
+  __shared__ uint64_t s_rp[kThreads];
   const uint32_t tid = threadIdx.x;
   for (;;) {
     if (tid == 0) {
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(ServeArgs a) {
     }
     __syncthreads();
     const Item it = s_item;
-    run_item(a.env, s_q, it, smem, s_x, &s_cnt, &s_nt);
+    run_item(a.env, s_q, it, smem, s_x, &s_cnt, &s_nt, s_pre, s_rp);
     if (tid == 0 && item_done(s_q, it)) {
       unsigned long long out6[6];
       const unsigned int bad = finalize_query(s_q, out6);
