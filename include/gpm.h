@@ -169,7 +169,7 @@ int gpm_pattern_info(gpm_pattern_t p, gpm_pattern_info_t *info);
  * its number of embeddings; each distinct subgraph is counted once, i.e. the
  * count of maps divided by |Aut(P)|).
  *   counts : host uint64[npat]
- * Supported on the GPU: k-cliques (k = 1..5) and every connected pattern with
+ * Supported on the GPU: k-cliques (k = 1..6) and every connected pattern with
  * 3 or 4 vertices, induced or not; other patterns return GPM_E_UNSUPPORTED.
  * Patterns that share work are computed together (e.g. all 4-vertex motifs
  * by local counting, Section 5; 3-, 4- and 5-cliques in one pass).

@@ -96,9 +96,9 @@ int schedule(const gpm_pattern_t *pats, uint32_t npat, bool ranged, Passes *ps) 
       case PC_VERTEX: f = F_VERTEX; break;
       case PC_EDGE: f = F_EDGE; break;
       case PC_CLIQUE:
-        if (p->k > 5) return gpm_fail(GPM_E_UNSUPPORTED, "k-clique counting is implemented for k <= 5");
+        if (p->k > 6) return gpm_fail(GPM_E_UNSUPPORTED, "k-clique counting is implemented for k <= 6");
         ps->clique_kmax = std::max<int>(ps->clique_kmax, (int)p->k);
-        f = p->k == 3 ? F_TRI : (p->k == 4 ? F_K4 : F_K5);
+        f = p->k == 3 ? F_TRI : (p->k == 4 ? F_K4 : (p->k == 5 ? F_K5 : F_K6));
         break;
       case PC_WEDGE:
         ps->edge_terms = true;
@@ -139,7 +139,7 @@ int schedule(const gpm_pattern_t *pats, uint32_t npat, bool ranged, Passes *ps) 
           f = F_D_NI;
         }
         break;
-      default: return gpm_fail(GPM_E_UNSUPPORTED, "no GPU kernel for this pattern (supported: cliques k <= 5 and "
+      default: return gpm_fail(GPM_E_UNSUPPORTED, "no GPU kernel for this pattern (supported: cliques k <= 6 and "
                                                   "connected patterns with 3 or 4 vertices)");
     }
     if (ranged && !(p->cls == PC_CLIQUE || (p->cls == PC_DIAMOND && !ind) || (p->cls == PC_CYCLE4 && !ind)))
@@ -164,12 +164,12 @@ int enqueue_count(gpm_graph *g, const gpm_pattern_t *pats, uint32_t npat, uint32
     // the scatter pass covers every root (per-arc counts must be complete)
     const int k1 = std::min(ps.clique_kmax, 4);
     GPM_TRY(gpm_launch_cliques(g, std::max(k1, 3), true, 0, g->n, acc, st));
-    if (ps.clique_kmax == 5 || (ranged && ps.clique_kmax > 0)) {
-      // 5-cliques (or range-restricted cliques) from a separate pass
+    if (ps.clique_kmax >= 5 || (ranged && ps.clique_kmax > 0)) {
+      // 5- and 6-cliques (or range-restricted cliques) from a separate pass
       unsigned long long *acc2 = acc2_of(g);
       GPM_CUDA(cudaMemsetAsync(acc2, 0, ACC_WORDS * sizeof(unsigned long long), st));
       GPM_TRY(gpm_launch_cliques(g, ps.clique_kmax, false, lo, hi, acc2, st));
-      GPM_CUDA(cudaMemcpyAsync(acc + ACC_T, acc2 + ACC_T, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+      GPM_CUDA(cudaMemcpyAsync(acc + ACC_T, acc2 + ACC_T, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
                                st));
     }
   } else if (ps.clique_kmax >= 3) {

@@ -101,6 +101,7 @@ __host__ __device__ constexpr size_t warp_region_words() { return gpm_dev::warp_
 template <int KMAX, bool SCATTER>
 __device__ void lg_warp_item(const QDesc &q, const Item &it, uint32_t *smem, unsigned long long &a3,
                              unsigned long long &a4, unsigned long long &a5) {
+  unsigned long long a6_unused = 0;  // items count at most 5-cliques
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t *base = smem + (size_t)wid * warp_region_words();
   for (uint32_t t = it.lo + wid; t < it.hi; t += kWarps) {
@@ -108,9 +109,9 @@ __device__ void lg_warp_item(const QDesc &q, const Item &it, uint32_t *smem, uns
     const uint32_t d = (uint32_t)(q.drow[u + 1] - q.drow[u]);
     if (d < 2) continue;
     if (d <= 32)
-      gpm_dev::lg_root_warp<32, 1, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, base, a3, a4, a5);
+      gpm_dev::lg_root_warp<32, 1, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, base, a3, a4, a5, a6_unused);
     else
-      gpm_dev::lg_root_warp<kWarpMaxD, 4, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, base, a3, a4, a5);
+      gpm_dev::lg_root_warp<kWarpMaxD, 4, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, base, a3, a4, a5, a6_unused);
   }
   (void)lane;
 }
@@ -118,17 +119,18 @@ __device__ void lg_warp_item(const QDesc &q, const Item &it, uint32_t *smem, uns
 template <int KMAX, bool SCATTER>
 __device__ void lg_cta_item(const ItemEnv &a, const QDesc &q, const Item &it, uint32_t *smem,
                             unsigned long long &a3, unsigned long long &a4, unsigned long long &a5) {
+  unsigned long long a6_unused = 0;  // items count at most 5-cliques
   const uint32_t u = q.tasks[it.lo];
   const uint32_t d = (uint32_t)(q.drow[u + 1] - q.drow[u]);
   if (d > a.cta_maxd) {
     uint32_t *slot = a.lg_pool + (size_t)blockIdx.x * a.lg_slot_words;
-    gpm_dev::lg_root_cta<32, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.lg_maxd, a.lg_W, slot, a3, a4, a5);
+    gpm_dev::lg_root_cta<32, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.lg_maxd, a.lg_W, slot, a3, a4, a5, a6_unused);
   } else if (a.cta_W <= 8) {
-    gpm_dev::lg_root_cta<8, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.cta_maxd, a.cta_W, smem, a3, a4, a5);
+    gpm_dev::lg_root_cta<8, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.cta_maxd, a.cta_W, smem, a3, a4, a5, a6_unused);
   } else if (a.cta_W <= 16) {
-    gpm_dev::lg_root_cta<16, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.cta_maxd, a.cta_W, smem, a3, a4, a5);
+    gpm_dev::lg_root_cta<16, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.cta_maxd, a.cta_W, smem, a3, a4, a5, a6_unused);
   } else {
-    gpm_dev::lg_root_cta<32, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.cta_maxd, a.cta_W, smem, a3, a4, a5);
+    gpm_dev::lg_root_cta<32, KMAX, SCATTER>(q.drow, q.dcol, q.t_edge, u, a.cta_maxd, a.cta_W, smem, a3, a4, a5, a6_unused);
   }
 }
 

@@ -54,16 +54,18 @@ struct LGArgs {
 };
 
 __device__ __forceinline__ void flush_acc(const LGArgs &a, unsigned long long a3, unsigned long long a4,
-                                          unsigned long long a5, int kmax) {
+                                          unsigned long long a5, unsigned long long a6, int kmax) {
   for (int o = 16; o > 0; o >>= 1) {
     a3 += __shfl_down_sync(0xffffffffu, a3, o);
     a4 += __shfl_down_sync(0xffffffffu, a4, o);
     a5 += __shfl_down_sync(0xffffffffu, a5, o);
+    if (kmax >= 6) a6 += __shfl_down_sync(0xffffffffu, a6, o);
   }
   if ((threadIdx.x & 31) == 0) {
     if (a3) atomicAdd(&a.acc[3], a3);
     if (kmax >= 4 && a4) atomicAdd(&a.acc[4], a4);
     if (kmax >= 5 && a5) atomicAdd(&a.acc[5], a5);
+    if (kmax >= 6 && a6) atomicAdd(&a.acc[ACC_K6], a6);
   }
 }
 
@@ -76,7 +78,7 @@ __global__ void __launch_bounds__(256) lg_warp_kernel(LGArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t *base = smem + (size_t)wid * kStride;
-  unsigned long long a3 = 0, a4 = 0, a5 = 0;
+  unsigned long long a3 = 0, a4 = 0, a5 = 0, a6 = 0;
   for (;;) {
     uint32_t task = 0;
     if (lane == 0) task = atomicAdd(a.queue, 1u);
@@ -86,9 +88,9 @@ __global__ void __launch_bounds__(256) lg_warp_kernel(LGArgs a) {
     if (u < a.root_lo || u >= a.root_hi) continue;
     const uint32_t d = (uint32_t)(a.drow[u + 1] - a.drow[u]);
     if (d < 2 || d > MAXD) continue;
-    gpm_dev::lg_root_warp<MAXD, G, KMAX, SCATTER>(a.drow, a.dcol, a.t_edge, u, base, a3, a4, a5);
+    gpm_dev::lg_root_warp<MAXD, G, KMAX, SCATTER>(a.drow, a.dcol, a.t_edge, u, base, a3, a4, a5, a6);
   }
-  flush_acc(a, a3, a4, a5, KMAX);
+  flush_acc(a, a3, a4, a5, a6, KMAX);
 }
 
 // ---------------------------------------------------------------------------
@@ -102,7 +104,7 @@ __global__ void __launch_bounds__(THREADS) lg_cta_kernel(LGArgs a, uint32_t maxd
   uint32_t *base = GLOBAL ? a.pool + (size_t)blockIdx.x * a.slot_words : smem;
   // nested local graphs for the 5-clique level live after the bitmap (shared memory only)
   uint32_t *nest = (!GLOBAL && KMAX >= 5 && big_cap) ? smem + gpm_dev::cta_words(maxd, a.W) : nullptr;
-  unsigned long long a3 = 0, a4 = 0, a5 = 0;
+  unsigned long long a3 = 0, a4 = 0, a5 = 0, a6 = 0;
   for (;;) {
     if (threadIdx.x == 0) s_task = atomicAdd(a.queue, 1u);
     __syncthreads();
@@ -113,10 +115,10 @@ __global__ void __launch_bounds__(THREADS) lg_cta_kernel(LGArgs a, uint32_t maxd
     if (u < a.root_lo || u >= a.root_hi) continue;
     const uint32_t d = (uint32_t)(a.drow[u + 1] - a.drow[u]);
     if (d < 2 || d > maxd) continue;
-    gpm_dev::lg_root_cta<G, KMAX, SCATTER>(a.drow, a.dcol, a.t_edge, u, maxd, a.W, base, a3, a4, a5, nest, big_cap,
-                                           a.deg, wcap);
+    gpm_dev::lg_root_cta<G, KMAX, SCATTER>(a.drow, a.dcol, a.t_edge, u, maxd, a.W, base, a3, a4, a5, a6, nest,
+                                           big_cap, a.deg, wcap);
   }
-  flush_acc(a, a3, a4, a5, KMAX);
+  flush_acc(a, a3, a4, a5, a6, KMAX);
 }
 
 using gpm_dev::cta_words;
@@ -281,7 +283,7 @@ int launch_all(gpm_graph *g, LGArgs base, unsigned int *queues, cudaStream_t st)
 
 int gpm_launch_cliques(gpm_graph *g, int kmax, bool scatter, uint32_t root_lo, uint32_t root_hi,
                        unsigned long long *acc, cudaStream_t st) {
-  if (kmax < 3 || kmax > 5) return gpm_fail(GPM_E_UNSUPPORTED, "clique pass supports k = 3..5");
+  if (kmax < 3 || kmax > 6) return gpm_fail(GPM_E_UNSUPPORTED, "clique pass supports k = 3..6");
   unsigned int *queues = reinterpret_cast<unsigned int *>(g->work + WK_QUEUE0);
   GPM_CUDA(cudaMemsetAsync(queues, 0, 8 * sizeof(unsigned int), st));
   LGArgs a{};
@@ -300,5 +302,6 @@ int gpm_launch_cliques(gpm_graph *g, int kmax, bool scatter, uint32_t root_lo, u
   }
   if (kmax == 3) return launch_all<3, false>(g, a, queues, st);
   if (kmax == 4) return launch_all<4, false>(g, a, queues, st);
-  return launch_all<5, false>(g, a, queues, st);
+  if (kmax == 5) return launch_all<5, false>(g, a, queues, st);
+  return launch_all<6, false>(g, a, queues, st);
 }

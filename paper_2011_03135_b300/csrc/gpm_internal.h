@@ -184,7 +184,7 @@ int gpm_ensure_classes(gpm_graph *g, cudaStream_t st);
 // persistent grid size for a kernel
 int gpm_num_sms(int device);
 
-// Clique counts for k = 3..kmax (kmax <= 5) over roots in [root_lo, root_hi).
+// Clique counts for k = 3..kmax (kmax <= 6) over roots in [root_lo, root_hi).
 // Adds to acc[ACC_T .. kmax] (uint64, device). scatter: additionally adds
 // every triangle to the per-arc counts g->t_edge (zeroed by the caller).
 int gpm_launch_cliques(gpm_graph *g, int kmax, bool scatter, uint32_t root_lo, uint32_t root_hi,
@@ -214,6 +214,7 @@ enum {
   ACC_T = 3,     // triangles
   ACC_K4 = 4,    // 4-cliques
   ACC_K5 = 5,    // 5-cliques
+  ACC_K6 = 6,    // 6-cliques
   ACC_D = 8,     // sum over arcs C(t_e, 2)   (edge-induced diamonds)
   ACC_P = 9,     // sum over arcs (d_u-1)(d_v-1)
   ACC_S = 10,    // sum_v C(d_v, 3)
@@ -228,7 +229,7 @@ enum {
 enum Formula : uint32_t {
   F_VERTEX = 0, F_EDGE, F_TRI, F_K4, F_K5, F_WEDGE_NI, F_WEDGE_I,
   F_STAR_NI, F_PATH_NI, F_TT_NI, F_C4_NI, F_D_NI,
-  F_STAR_I, F_PATH_I, F_TT_I, F_C4_I, F_D_I, F_K4_I,
+  F_STAR_I, F_PATH_I, F_TT_I, F_C4_I, F_D_I, F_K4_I, F_K6,
 };
 struct FinalizeSpec {
   uint32_t npat;

@@ -153,13 +153,14 @@ __device__ __forceinline__ uint32_t build_rows_runs(const uint32_t *__restrict__
   return found;
 }
 
-// Enumerate pairs (i, j in R_i) and triples for the 4- and 5-clique terms.
-// A group of G lanes handles one row at a time; lane gl of the group holds
-// word gl of the row (W <= G), so every AND is one word per lane.
+// Enumerate pairs (i, j in R_i), triples and (KMAX 6) quadruples for the 4-,
+// 5- and 6-clique terms. A group of G lanes handles one row at a time; lane gl
+// of the group holds word gl of the row (W <= G), so every AND is one word
+// per lane.
 template <int G, int KMAX>
 __device__ __forceinline__ void enumerate_rows(const uint32_t *R, uint32_t d, uint32_t W, uint32_t rs, uint32_t row0,
                                                uint32_t row_step, uint32_t gl, unsigned long long &a4,
-                                               unsigned long long &a5) {
+                                               unsigned long long &a5, unsigned long long &a6) {
   for (uint32_t i = row0; i < d; i += row_step) {
     const uint32_t *ri = R + (size_t)i * rs;
     const uint32_t riw = (gl < W) ? ri[gl] : 0u;
@@ -177,7 +178,19 @@ __device__ __forceinline__ void enumerate_rows(const uint32_t *R, uint32_t d, ui
             while (b2) {
               const uint32_t l = t2 * 32 + __ffs(b2) - 1;
               b2 &= b2 - 1;
-              if (gl < W) a5 += __popc(mw & R[(size_t)l * rs + gl]);
+              const uint32_t *rl = R + (size_t)l * rs;
+              const uint32_t m5 = (gl < W) ? (mw & rl[gl]) : 0u;
+              a5 += __popc(m5);
+              if (KMAX >= 6) {
+                for (uint32_t t3 = 0; t3 < W; ++t3) {
+                  uint32_t b3 = ri[t3] & rj[t3] & rl[t3];
+                  while (b3) {
+                    const uint32_t y = t3 * 32 + __ffs(b3) - 1;
+                    b3 &= b3 - 1;
+                    if (gl < W) a6 += __popc(m5 & R[(size_t)y * rs + gl]);
+                  }
+                }
+              }
             }
           }
         }
@@ -190,7 +203,7 @@ __device__ __forceinline__ void enumerate_rows(const uint32_t *R, uint32_t d, ui
 template <int KMAX>
 __device__ inline void enumerate_rows_wide(const uint32_t *R, uint32_t d, uint32_t W, uint32_t rs, uint32_t row0,
                                            uint32_t row_step, uint32_t gl, unsigned long long &a4,
-                                           unsigned long long &a5) {
+                                           unsigned long long &a5, unsigned long long &a6) {
   constexpr uint32_t G = 32;
   for (uint32_t i = row0; i < d; i += row_step) {
     const uint32_t *ri = R + (size_t)i * rs;
@@ -209,6 +222,17 @@ __device__ inline void enumerate_rows_wide(const uint32_t *R, uint32_t d, uint32
               b2 &= b2 - 1;
               const uint32_t *rl = R + (size_t)l * rs;
               for (uint32_t w = gl; w < W; w += G) a5 += __popc(ri[w] & rj[w] & rl[w]);
+              if (KMAX >= 6) {
+                for (uint32_t t3 = 0; t3 < W; ++t3) {
+                  uint32_t b3 = ri[t3] & rj[t3] & rl[t3];
+                  while (b3) {
+                    const uint32_t y = t3 * 32 + __ffs(b3) - 1;
+                    b3 &= b3 - 1;
+                    const uint32_t *ry = R + (size_t)y * rs;
+                    for (uint32_t w = gl; w < W; w += G) a6 += __popc(ri[w] & rj[w] & rl[w] & ry[w]);
+                  }
+                }
+              }
             }
           }
         }
@@ -312,9 +336,12 @@ __device__ __forceinline__ uint32_t compact_row(const uint32_t *rj, const uint32
 
 // sum over the set bits b in word k of row a of |C_a & C_b| (rows of Wp words,
 // stride Wp); one (a, k) unit bounds a thread's loop to 32 bits
-// (with tri, C is strictly upper triangular: C_b has no bit below b + 1)
+// (with tri, C is strictly upper triangular: C_b has no bit below b + 1).
+// With K6, s6 also gets sum over x in C_a & C_b of |C_a & C_b & C_x|.
+template <bool K6 = false>
 __device__ __forceinline__ unsigned long long nested_pairs_unit(const uint32_t *C, uint32_t a, uint32_t k,
-                                                                uint32_t Wp, uint32_t cs, bool tri = false) {
+                                                                uint32_t Wp, uint32_t cs, bool tri,
+                                                                unsigned long long &s6) {
   const uint32_t *ca = C + (size_t)a * cs;
   uint32_t s = 0;  // at most 32 x 32 x Wp
   uint32_t bits = ca[k];
@@ -322,16 +349,32 @@ __device__ __forceinline__ unsigned long long nested_pairs_unit(const uint32_t *
     const uint32_t b = k * 32 + __ffs(bits) - 1;
     bits &= bits - 1;
     const uint32_t *cb = C + (size_t)b * cs;
-    for (uint32_t k2 = tri ? (b + 1) >> 5 : 0; k2 < Wp; ++k2) s += __popc(ca[k2] & cb[k2]);
+    for (uint32_t k2 = tri ? (b + 1) >> 5 : 0; k2 < Wp; ++k2) {
+      const uint32_t m = ca[k2] & cb[k2];
+      s += __popc(m);
+      if (K6) {
+        uint32_t mx = m;
+        while (mx) {
+          const uint32_t x = k2 * 32 + __ffs(mx) - 1;
+          mx &= mx - 1;
+          const uint32_t *cx = C + (size_t)x * cs;
+          for (uint32_t k3 = tri ? (x + 1) >> 5 : 0; k3 < Wp; ++k3) s6 += __popc(ca[k3] & cb[k3] & cx[k3]);
+        }
+      }
+    }
   }
   return s;
 }
 
 // Rows with c <= 32: lane a keeps compacted row C_a in a register; the pairs
 // (a, b) are visited with one shuffle of C_b per b (no shared memory).
+// With K6, Cs (32 words of the warp's buffer) holds the rows for the 6-clique
+// level: sum over b in C_a, x in C_a & C_b of |C_a & C_b & C_x|.
+template <bool K6 = false>
 __device__ __forceinline__ void nested_row_reg32(const uint32_t *R, uint32_t W, uint32_t rs, const uint32_t *ri,
                                                  uint32_t c, const uint32_t *S, const uint32_t *pref,
-                                                 unsigned long long &a4, unsigned long long &a5, bool tri = false) {
+                                                 unsigned long long &a4, unsigned long long &a5, bool tri,
+                                                 unsigned long long &a6, uint32_t *Cs) {
   const uint32_t lane = threadIdx.x & 31;
   uint32_t ca = 0;
   if (lane < c) {
@@ -343,17 +386,34 @@ __device__ __forceinline__ void nested_row_reg32(const uint32_t *R, uint32_t W, 
     }
   }
   a4 += __popc(ca);
+  if (K6) {
+    Cs[lane] = ca;
+    __syncwarp();
+  }
   for (uint32_t b = 0; b < c; ++b) {
     const uint32_t cb = __shfl_sync(0xffffffffu, ca, b);
-    if ((ca >> b) & 1u) a5 += __popc(ca & cb);
+    if ((ca >> b) & 1u) {
+      const uint32_t m = ca & cb;
+      a5 += __popc(m);
+      if (K6) {
+        uint32_t mx = m;
+        while (mx) {
+          const uint32_t x = __ffs(mx) - 1;
+          mx &= mx - 1;
+          a6 += __popc(m & Cs[x]);
+        }
+      }
+    }
   }
+  if (K6) __syncwarp();
 }
 
 // Row i by a group of lanes without nesting (fallback for rows too wide to
 // compact): the group takes every `ng`-th bit j of R_i.
+template <bool K6 = false>
 __device__ __forceinline__ void row_k45_groups(const uint32_t *R, uint32_t W, uint32_t rs, uint32_t i, uint32_t g,
                                                uint32_t ng, uint32_t gl, uint32_t G, unsigned long long &a4,
-                                               unsigned long long &a5) {
+                                               unsigned long long &a5, unsigned long long &a6) {
   const uint32_t *ri = R + (size_t)i * rs;
   uint32_t seen = 0;
   for (uint32_t t = 0; t < W; ++t) {
@@ -374,6 +434,17 @@ __device__ __forceinline__ void row_k45_groups(const uint32_t *R, uint32_t W, ui
           b2 &= b2 - 1;
           const uint32_t *rl = R + (size_t)l * rs;
           for (uint32_t w = gl; w < W; w += G) a5 += __popc(ri[w] & rj[w] & rl[w]);
+          if (K6) {
+            for (uint32_t t3 = 0; t3 < W; ++t3) {
+              uint32_t b3 = ri[t3] & rj[t3] & rl[t3];
+              while (b3) {
+                const uint32_t y = t3 * 32 + __ffs(b3) - 1;
+                b3 &= b3 - 1;
+                const uint32_t *ry = R + (size_t)y * rs;
+                for (uint32_t w = gl; w < W; w += G) a6 += __popc(ri[w] & rj[w] & rl[w] & ry[w]);
+              }
+            }
+          }
         }
       }
     }
@@ -388,9 +459,11 @@ __device__ __forceinline__ void row_k45_groups(const uint32_t *R, uint32_t W, ui
 // the whole CTA at the end.
 // With tri, R is strictly upper triangular (positions in the orientation's
 // order), and so is every nested C: the word loops start at the pivot.
+template <bool K6 = false>
 __device__ inline void enumerate_nested_cta(const uint32_t *R, uint32_t d, uint32_t W, uint32_t rs, uint32_t *nest,
                                             uint32_t maxd, uint32_t big_cap, unsigned long long &a4,
-                                            unsigned long long &a5, bool tri = false, uint32_t wcap = kNestWarpC) {
+                                            unsigned long long &a5, unsigned long long &a6, bool tri = false,
+                                            uint32_t wcap = kNestWarpC) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   uint32_t *ctr = nest;  // [0] next row, [1] big rows, [2] next big row, [3] wide rows
   uint32_t *big_list = nest + 4;
@@ -422,7 +495,7 @@ __device__ inline void enumerate_nested_cta(const uint32_t *R, uint32_t d, uint3
         continue;
       }
       if (c <= 32) {
-        nested_row_reg32(R, W, rs, ri, c, S, pref, a4, a5, tri);
+        nested_row_reg32<K6>(R, W, rs, ri, c, S, pref, a4, a5, tri, a6, C);
         __syncwarp();
         continue;
       }
@@ -434,7 +507,7 @@ __device__ inline void enumerate_nested_cta(const uint32_t *R, uint32_t d, uint3
       }
       __syncwarp();
       // units in word-major order: a round of lanes takes neighbouring rows, word k alike
-      for (uint32_t u = lane; u < c * Wp; u += 32) a5 += nested_pairs_unit(C, u % c, u / c, Wp, cs, tri);
+      for (uint32_t u = lane; u < c * Wp; u += 32) a5 += nested_pairs_unit<K6>(C, u % c, u / c, Wp, cs, tri, a6);
       __syncwarp();
     }
   }
@@ -482,7 +555,7 @@ __device__ inline void enumerate_nested_cta(const uint32_t *R, uint32_t d, uint3
           u0 = __shfl_sync(0xffffffffu, u0, 0);
           if (u0 >= c * Wp) break;
           const uint32_t u = u0 + lane;
-          if (u < c * Wp) a5 += nested_pairs_unit(C, u % c, u / c, Wp, cs, tri);
+          if (u < c * Wp) a5 += nested_pairs_unit<K6>(C, u % c, u / c, Wp, cs, tri, a6);
         }
         group_bar(1 + g, gthreads);
       }
@@ -530,10 +603,10 @@ __device__ inline void enumerate_nested_cta(const uint32_t *R, uint32_t d, uint3
         u0 = __shfl_sync(0xffffffffu, u0, 0);
         if (u0 >= c * Wp) break;
         const uint32_t u = u0 + lane;
-        if (u < c * Wp) a5 += nested_pairs_unit(C, u % c, u / c, Wp, cs, tri);
+        if (u < c * Wp) a5 += nested_pairs_unit<K6>(C, u % c, u / c, Wp, cs, tri, a6);
       }
     } else {
-      row_k45_groups(R, W, rs, i, tid >> 5, nt >> 5, lane, 32, a4, a5);
+      row_k45_groups<K6>(R, W, rs, i, tid >> 5, nt >> 5, lane, 32, a4, a5, a6);
     }
     __syncthreads();
   }
@@ -585,7 +658,7 @@ __device__ __forceinline__ void rank_local(const uint32_t *__restrict__ deg, con
 template <int MAXD, int G, int KMAX, bool SCATTER>
 __device__ __forceinline__ void lg_root_warp(const uint64_t *__restrict__ drow, const uint32_t *__restrict__ dcol,
                                              uint32_t *t_edge, uint32_t u, uint32_t *base, unsigned long long &a3,
-                                             unsigned long long &a4, unsigned long long &a5) {
+                                             unsigned long long &a4, unsigned long long &a5, unsigned long long &a6) {
   const uint32_t lane = threadIdx.x & 31;
   uint64_t *xb = reinterpret_cast<uint64_t *>(base);
   uint32_t *L = base + 2 * MAXD;
@@ -625,7 +698,7 @@ __device__ __forceinline__ void lg_root_warp(const uint64_t *__restrict__ drow, 
     for (uint32_t i = lane; i < d; i += 32)
       if (tc[i]) atomicAdd(&t_edge[ub + i], tc[i]);
   }
-  if (KMAX >= 4) enumerate_rows<G, KMAX>(R, d, w_used, rs, lane / G, 32 / G, lane % G, a4, a5);
+  if (KMAX >= 4) enumerate_rows<G, KMAX>(R, d, w_used, rs, lane / G, 32 / G, lane % G, a4, a5, a6);
   __syncwarp();
 }
 
@@ -636,7 +709,7 @@ template <int G, int KMAX, bool SCATTER>
 __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, const uint32_t *__restrict__ dcol,
                                             uint32_t *t_edge, uint32_t u, uint32_t maxd, uint32_t W, uint32_t *base,
                                             unsigned long long &a3, unsigned long long &a4, unsigned long long &a5,
-                                            uint32_t *nest = nullptr, uint32_t big_cap = 0,
+                                            unsigned long long &a6, uint32_t *nest = nullptr, uint32_t big_cap = 0,
                                             const uint32_t *__restrict__ deg = nullptr, uint32_t wcap = kNestWarpC) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
   uint64_t *xb = reinterpret_cast<uint64_t *>(base);
@@ -703,12 +776,12 @@ __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, c
       if (tc[i]) atomicAdd(&t_edge[ub + i], tc[i]);
   }
   if (KMAX >= 5 && nest != nullptr && w_used <= 32) {
-    enumerate_nested_cta(R, d, w_used, rs, nest, maxd, big_cap, a4, a5, tri, wcap);
+    enumerate_nested_cta<(KMAX >= 6)>(R, d, w_used, rs, nest, maxd, big_cap, a4, a5, a6, tri, wcap);
   } else if (KMAX >= 4) {
     if (w_used > 32)
-      enumerate_rows_wide<KMAX>(R, d, w_used, rs, tid / 32, nt / 32, lane, a4, a5);
+      enumerate_rows_wide<KMAX>(R, d, w_used, rs, tid / 32, nt / 32, lane, a4, a5, a6);
     else
-      enumerate_rows<G, KMAX>(R, d, w_used, rs, tid / G, nt / G, tid % G, a4, a5);
+      enumerate_rows<G, KMAX>(R, d, w_used, rs, tid / G, nt / G, tid % G, a4, a5, a6);
   }
   __syncthreads();
 }

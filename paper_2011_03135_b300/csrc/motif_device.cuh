@@ -475,6 +475,7 @@ __device__ __forceinline__ unsigned long long finalize_formula(uint32_t f, const
     case 15: v = iC4; bad |= (iC4 > NC4); break;
     case 16: v = iD; bad |= (iD > ND); break;
     case 17: v = iK4; break;
+    case 18: v = acc[6]; break;           // F_K6
     default: bad = true; break;
   }
   return v;

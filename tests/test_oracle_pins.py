@@ -52,8 +52,8 @@ def test_cliques_complete_graph(n, k):
     assert O.cliques(g, k) == math.comb(n, k)
 
 
-@pytest.mark.parametrize("parts", [[2, 3], [1, 1, 1, 1], [2, 2, 2], [3, 1, 4, 2], [5, 5, 1]])
-@pytest.mark.parametrize("k", [3, 4, 5])
+@pytest.mark.parametrize("parts", [[2, 3], [1, 1, 1, 1], [2, 2, 2], [3, 1, 4, 2], [5, 5, 1], [2, 1, 3, 1, 2, 2, 1]])
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
 def test_cliques_complete_multipartite(parts, k):
     g = gg.complete_multipartite(parts)
     assert O.cliques(g, k) == _esym(parts, k)
@@ -62,7 +62,7 @@ def test_cliques_complete_multipartite(parts, k):
 @pytest.mark.parametrize("g", [gg.path(9), gg.star(7), gg.empty(5), gg.cycle(7),
                                gg.from_edges(8, [(0, 1), (1, 2), (1, 3), (3, 4), (4, 5), (4, 6), (6, 7)])])
 def test_cliques_trees_and_cycles_have_none(g):
-    for k in (3, 4, 5):
+    for k in (3, 4, 5, 6):
         assert O.cliques(g, k) == 0
 
 
@@ -81,7 +81,7 @@ def test_triangles_trace_identity_small_and_rmat14():
 def test_cliques_match_subset_brute_force(mk):
     g = mk()
     adj = _py_adj(g)
-    for k in (3, 4, 5):
+    for k in (3, 4, 5, 6):
         bf = sum(1 for W in itertools.combinations(range(g.n), k)
                  if all(b in adj[a] for a, b in itertools.combinations(W, 2)))
         assert O.cliques(g, k) == bf

@@ -49,8 +49,8 @@ SMALL = [
 def test_small_graph_every_pattern(gpm, gi):
     g = SMALL[gi]
     G = gpm.Graph.from_host(g)
-    cl = [gpm.Pattern.clique(k) for k in (1, 2, 3, 4, 5)]
-    assert gpm.count(G, cl) == [g.n, g.m] + [O.cliques(g, k) for k in (3, 4, 5)]
+    cl = [gpm.Pattern.clique(k) for k in (1, 2, 3, 4, 5, 6)]
+    assert gpm.count(G, cl) == [g.n, g.m] + [O.cliques(g, k) for k in (3, 4, 5, 6)]
     m4 = gpm.Pattern.motifs(4)
     m3 = gpm.Pattern.motifs(3)
     assert gpm.count(G, m4) == O.motifs(g, 4)
@@ -84,8 +84,8 @@ def test_medium_graphs_every_root_class(gpm, opts):
             info = G.prepare().info()
             assert info["dag_arcs"] == g.m
             assert info["max_out_degree"] == int(O.out_degrees(g).max())
-            cl = [gpm.Pattern.clique(k) for k in (3, 4, 5)]
-            assert gpm.count(G, cl) == [O.cliques(g, k) for k in (3, 4, 5)], g.name
+            cl = [gpm.Pattern.clique(k) for k in (3, 4, 5, 6)]
+            assert gpm.count(G, cl) == [O.cliques(g, k) for k in (3, 4, 5, 6)], g.name
             assert gpm.count(G, gpm.Pattern.motifs(4)) == O.motifs(g, 4), g.name
             G.close()
     finally:
@@ -96,13 +96,14 @@ def test_root_ranges_match_oracle(gpm):
     g = gg.rmat(12, 16.0, seed=31)
     G = gpm.Graph.from_host(g)
     pats = [gpm.Pattern.clique(3), gpm.Pattern.clique(4), gpm.Pattern.clique(5),
-            gpm.Pattern.spec(O.DIAMOND, induced=False), gpm.Pattern.spec(O.CYCLE4, induced=False)]
+            gpm.Pattern.spec(O.DIAMOND, induced=False), gpm.Pattern.spec(O.CYCLE4, induced=False),
+            gpm.Pattern.clique(6)]
     cuts = [0, 1, 777, 2048, 2049, 3333, g.n]
-    tot = [0] * 5
+    tot = [0] * 6
     for lo, hi in zip(cuts[:-1], cuts[1:]):
         got = gpm.count_roots(G, pats, lo, hi)
         want = [O.cliques(g, 3, lo, hi), O.cliques(g, 4, lo, hi), O.cliques(g, 5, lo, hi),
-                O.diamonds(g, lo, hi), O.cycles4(g, lo, hi)]
+                O.diamonds(g, lo, hi), O.cycles4(g, lo, hi), O.cliques(g, 6, lo, hi)]
         assert got == want, (lo, hi)
         tot = [a + b for a, b in zip(tot, got)]
     assert tot == gpm.count(G, pats)
@@ -347,3 +348,32 @@ def test_complete_graph_every_class(gpm):
     got = gpm.count_roots(G, [gpm.Pattern.clique(5)], lo, hi)
     assert got == [sum(math.comb(n - 1 - v, 4) for v in range(lo, hi))]
     G.close()
+
+
+@pytest.mark.parametrize("opts", [dict(), dict(warp_max_degree=32, cta_max_degree=32),
+                                  dict(warp_max_degree=32, cta_max_degree=96)])
+def test_six_cliques_every_root_class(gpm, opts):
+    # the 6-clique level in every root class: warp rows, CTA nested rows
+    # (register, warp, group and CTA-wide paths) and global-memory bitmaps;
+    # closed forms on complete and complete multipartite graphs, the oracle elsewhere
+    import math
+    old = gpm.get_options()
+    try:
+        if opts:
+            gpm.set_options(**opts)
+        K6 = gpm.Pattern.clique(6)
+        for n in (7, 40, 160):
+            G = gpm.Graph.from_host(gg.complete(n))
+            assert gpm.count(G, [K6]) == [math.comb(n, 6)], n
+            G.close()
+        parts = [5, 9, 3, 12, 7, 4, 6]
+        G = gpm.Graph.from_host(gg.complete_multipartite(parts))
+        e6 = sum(math.prod(c) for c in __import__("itertools").combinations(parts, 6))
+        assert gpm.count(G, [K6]) == [e6]
+        G.close()
+        for g in [gg.rmat(11, 16.0, seed=21), gg.chung_lu(5000, 16.0, 2.1, seed=24), gg.rmat(12, 16.0, seed=31)]:
+            G = gpm.Graph.from_host(g)
+            assert gpm.count(G, [K6, gpm.Pattern.clique(5)]) == [O.cliques(g, 6), O.cliques(g, 5)], g.name
+            G.close()
+    finally:
+        gpm.set_options(**{k: v for k, v in old.items() if v})
