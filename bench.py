@@ -131,17 +131,29 @@ def clique_pass_bytes(g, opts):
     return {names[c]: float(per_root[cls == c].sum()) for c in names}, int(od.max())
 
 
-# Per-launch counters of the dominant kernel from a one-pass `ncu` capture of
-# the same kernel on the same workload (profiles/lg_cta_hi_rmat21_counters.md):
+# Per-launch counters of the dominant kernel, per workload, from a one-pass
+# `ncu` capture of the same kernel on the same workload
+# (profiles/lg_cta_hi_rmat21_counters.md, profiles/lg_cta_hi_k6_rmat20_counters.md):
 #   ncu --metrics smsp__inst_executed.sum,gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
 #       --clock-control none -k regex:lg_cta_kernel -c 1
-#       python -m paper_2011_03135_b300.cases --case clique-rmat21 --reps 1
+#       python -m paper_2011_03135_b300.cases --case <clique-rmat21 | clique6-rmat20> --reps 1
 # valid only for the kernel sources they were taken on (digest of
 # csrc/lg_device.cuh + csrc/clique.cu); a stale entry is ignored.
 NCU_COUNTERS = {
-    "lg_cta_hi": {"digest": "d75068b607f996ed", "inst_per_launch": 151171261534,
-                  "dram_bytes_per_launch": 28408832 + 2816, "ncu_ms": 183.558},
+    "clique-rmat21": {
+        "lg_cta_hi": {"digest": "b5eb426ffcd9af0f", "inst_per_launch": 151171618904,
+                      "dram_bytes_per_launch": 28337920 + 3072, "ncu_ms": 183.692},
+    },
+    "clique6-rmat20": {
+        "lg_cta_hi": {"digest": "b5eb426ffcd9af0f", "inst_per_launch": 1631591617792,
+                      "dram_bytes_per_launch": 13097984, "ncu_ms": 1677.904},
+    },
 }
+
+
+def counters_for(case, name):
+    cnt = NCU_COUNTERS.get(case, {}).get(name)
+    return cnt if cnt and cnt.get("digest") == kernel_digest() else None
 
 
 def kernel_digest():
@@ -425,6 +437,104 @@ def run_sl(args):
                         for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}}
 
 
+CLIQUE6_WORKLOAD = ("6-clique counting, R-MAT scale 20 (1,048,576 vertices), edge factor 16, (0.57,0.19,0.19,0.05), "
+                    "seed 2")
+
+
+def run_clique6(args):
+    """Counting 6-cliques (the large-k row): same path, a fourth bitmap level."""
+    import torch
+    from paper_2011_03135_b300 import gpm
+    from paper_2011_03135_b300 import graphgen as gg
+    g = gg.workload_clique6_rmat20()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    G = gpm.Graph(torch.from_numpy(g.rowptr.view(np.int64)).to(dev), torch.from_numpy(g.col.view(np.int32)).to(dev),
+                  g.n, validate=True, stream=stream)
+    P = [gpm.Pattern.clique(6)]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    def step():
+        G.reset()
+        return gpm.count(G, P, stream=stream)
+
+    counts = None
+    for _ in range(max(args.warmup, 3)):
+        counts = step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = gpm.kernel_launches()
+    gpm.profile_reset()
+    gpm.profile_enable(True)
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev[i][0].record(stream)
+            assert step() == counts
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    gpm.profile_enable(False)
+    launches = gpm.kernel_launches() - launches0
+    prof = gpm.profile_report()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    rp_h = torch.from_numpy(g.rowptr.view(np.int64)).pin_memory()
+    col_h = torch.from_numpy(g.col.view(np.int32)).pin_memory()
+    e2e = []
+    for i in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H = gpm.Graph(rp_h, col_h, g.n, validate=False, stream=stream)
+        c = gpm.count(H, P, stream=stream)
+        H.close()
+        if i > 0:
+            e2e.append(time.perf_counter() - t0)
+        assert c == counts
+    e2e_s = sum(e2e) / len(e2e)
+    name, st = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    per_launch_ms = st["ms"] / max(st["launches"], 1)
+    clk_now = clk.summary()
+    ipeak = issue_peak(clk_now["sm_mhz"] or 2032.0)
+    cnt = counters_for("clique6-rmat20", name)
+    roof = {"bound": "alu", "kernel": name, "unit": "G warp-instructions/s", "peak": ipeak,
+            "peak_source": "148 SMs x 4 schedulers x 1 issue/clk x median SM clock under load",
+            "achieved": None, "frac": None, "traffic": None, "kernel_digest": kernel_digest()}
+    if cnt:
+        ach = cnt["inst_per_launch"] / (per_launch_ms / 1000.0) / 1e9
+        roof.update(achieved=ach, frac=ach / ipeak, traffic=cnt.get("dram_bytes_per_launch"))
+    line = {"workload": CLIQUE6_WORKLOAD, "metric": "6-cliques counted per second", "value": counts[0] / (ms / 1000.0),
+            "unit": "cliques/s (6-cliques)", "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+            "step_ms": step_ms, "counts": {"6-clique": counts[0]}, "dtype": "u64", "data": "synthetic",
+            "config": {"l2": "flushed between steps (512 MB write)"},
+            "e2e": {"value": counts[0] / e2e_s, "unit": "cliques/s (6-cliques)",
+                    "h2d_bytes_per_step": g.rowptr.nbytes + g.col.nbytes, "d2h_bytes_per_step": 8, "seconds": e2e_s},
+            "gpu_launches": launches, "roofline": roof, "clocks": clk_now,
+            "kernels": {k: {"launches": v["launches"], "ms_per_launch": v["ms"] / max(v["launches"], 1)}
+                        for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_k6(g)
+    G.close()
+    return line
+
+
+def cpu_baseline_k6(g, seconds_target=15.0):
+    """The oracle on a bounded root sample of the 6-clique workload (ids are permuted: a random sample)."""
+    import oracle as O
+    lo, hi = 0, 256
+    t0 = time.perf_counter()
+    c6 = O.cliques(g, 6, lo, hi)
+    dt = time.perf_counter() - t0
+    if dt < seconds_target / 4:
+        hi = min(g.n, int(hi * seconds_target / max(dt, 1e-3)))
+        t0 = time.perf_counter()
+        c6 = O.cliques(g, 6, lo, hi)
+        dt = time.perf_counter() - t0
+    return {"value": c6 / dt, "unit": "cliques/s (6-cliques)", "cores": 1, "kind": "oracle",
+            "sample": f"roots with id in [{lo}, {hi}) of {g.n}; 6-CL single-threaded, {dt:.1f} s, count {c6}"}
+
+
 TC_WORKLOAD = "triangle counting, R-MAT scale 14 (16,384 vertices), edge factor 16, (0.57,0.19,0.19,0.05), seed 1"
 
 
@@ -584,7 +694,7 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     clk_now = clk.summary()
     digest = kernel_digest()
-    cnt = NCU_COUNTERS.get(name) if NCU_COUNTERS.get(name, {}).get("digest") == digest else None
+    cnt = counters_for("clique-rmat21", name)
     ipeak = issue_peak(clk_now["sm_mhz"] or 2032.0)
     roof = {"bound": "alu", "kernel": name, "unit": "G warp-instructions/s", "peak": ipeak,
             "peak_source": "148 SMs x 4 schedulers x 1 issue/clk x median SM clock under load",
@@ -627,7 +737,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["cliques", "batched", "served", "sl", "tc"], default="cliques")
+    ap.add_argument("--workload", choices=["cliques", "clique6", "batched", "served", "sl", "tc"], default="cliques")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-grace", type=float, default=10.0)
@@ -647,6 +757,9 @@ def main():
         return 0
     if args.workload == "tc":
         print(json.dumps(run_tc(args)), flush=True)
+        return 0
+    if args.workload == "clique6":
+        print(json.dumps(run_clique6(args)), flush=True)
         return 0
     return run_ours(args)
 

@@ -169,7 +169,8 @@ int gpm_pattern_info(gpm_pattern_t p, gpm_pattern_info_t *info);
  * its number of embeddings; each distinct subgraph is counted once, i.e. the
  * count of maps divided by |Aut(P)|).
  *   counts : host uint64[npat]
- * Supported on the GPU: k-cliques (k = 1..6) and every connected pattern with
+ * Supported on the GPU: k-cliques (k = 1..8; patterns hold at most 8
+ * vertices, gpm_count_cliques goes to k = 9) and every connected pattern with
  * 3 or 4 vertices, induced or not; other patterns return GPM_E_UNSUPPORTED.
  * Patterns that share work are computed together (e.g. all 4-vertex motifs
  * by local counting, Section 5; 3-, 4- and 5-cliques in one pass).
@@ -193,6 +194,23 @@ int gpm_count_async(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uin
  */
 int gpm_count_roots(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uint32_t root_lo, uint32_t root_hi,
                     uint64_t *counts, void *stream);
+
+/*
+ * k-clique count for one k = 3..9 over the roots in [root_lo, root_hi) (the
+ * root of a clique is its vertex that is first in the orientation order; the
+ * full range [0, n) gives the total). Section 2 k-CL with the local-graph
+ * search of Section 5 ("search on local graph"): for k <= 6 the fused pass of
+ * gpm_count; for k >= 7 the generic search, which keeps the shrinking
+ * candidate set as a bitmap over the root's out-neighbours and switches to
+ * per-lane register graphs once it has at most 32 members. k >= 7 needs root
+ * out-degrees <= 4096 (GPM_E_UNSUPPORTED otherwise).
+ *   *count : host uint64
+ * Errors: GPM_E_INVALID_ARG for k outside 3..9, a bad range or a null
+ * pointer. The count is accumulated in uint64 (exact below 2^64).
+ * Synchronises `stream`.
+ */
+int gpm_count_cliques(gpm_graph_t g, uint32_t k, uint32_t root_lo, uint32_t root_hi, uint64_t *count,
+                      void *stream);
 
 /* ---------------- listing ---------------- */
 

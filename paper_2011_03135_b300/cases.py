@@ -15,6 +15,7 @@ CASES = {
     # name: (generator, patterns)
     "clique-rmat20": ("rmat20", "clique45"),
     "clique-rmat21": ("rmat21", "clique45"),
+    "clique6-rmat20": ("rmat20", "clique6"),
     "tc-rmat14": ("rmat14", "tc"),
     "motif4-rmat18": ("rmat18", "motif4"),
     "sl-chunglu1m": ("chunglu1m", "sl"),
@@ -25,7 +26,7 @@ CASES = {
 def _graph(name):
     from paper_2011_03135_b300 import graphgen as gg
     if name == "rmat20":
-        return gg.rmat(20, 16.0, seed=2)
+        return gg.workload_clique6_rmat20()
     if name == "rmat21":
         return gg.workload_clique_rmat21()
     if name == "rmat14":
@@ -43,6 +44,8 @@ def _patterns(gpm, name):
     import numpy as np
     if name == "clique45":
         return [gpm.Pattern.clique(4), gpm.Pattern.clique(5)]
+    if name == "clique6":
+        return [gpm.Pattern.clique(6)]
     if name == "tc":
         return [gpm.Pattern.clique(3)]
     if name == "motif4":

@@ -77,6 +77,7 @@ int prepare_locked(gpm_graph *g, cudaStream_t st) {
 // Pass schedule for a set of patterns.
 struct Passes {
   int clique_kmax = 0;     // largest clique size needed (0 = none), from the non-scatter pass
+  uint32_t gen_k = 0;      // bit k set: a pass of the generic search for k-cliques (k = 7..9)
   bool scatter = false;    // per-arc triangle counts needed
   bool edge_terms = false; // degree terms (P, S, W)
   bool cycles4 = false;
@@ -96,7 +97,12 @@ int schedule(const gpm_pattern_t *pats, uint32_t npat, bool ranged, Passes *ps) 
       case PC_VERTEX: f = F_VERTEX; break;
       case PC_EDGE: f = F_EDGE; break;
       case PC_CLIQUE:
-        if (p->k > 6) return gpm_fail(GPM_E_UNSUPPORTED, "k-clique counting is implemented for k <= 6");
+        if (p->k > 9) return gpm_fail(GPM_E_UNSUPPORTED, "k-clique counting is implemented for k <= 9");
+        if (p->k >= 7) {
+          ps->gen_k |= 1u << p->k;
+          f = F_K7 + (p->k - 7);
+          break;
+        }
         ps->clique_kmax = std::max<int>(ps->clique_kmax, (int)p->k);
         f = p->k == 3 ? F_TRI : (p->k == 4 ? F_K4 : (p->k == 5 ? F_K5 : F_K6));
         break;
@@ -139,7 +145,7 @@ int schedule(const gpm_pattern_t *pats, uint32_t npat, bool ranged, Passes *ps) 
           f = F_D_NI;
         }
         break;
-      default: return gpm_fail(GPM_E_UNSUPPORTED, "no GPU kernel for this pattern (supported: cliques k <= 6 and "
+      default: return gpm_fail(GPM_E_UNSUPPORTED, "no GPU kernel for this pattern (supported: cliques k <= 9 and "
                                                   "connected patterns with 3 or 4 vertices)");
     }
     if (ranged && !(p->cls == PC_CLIQUE || (p->cls == PC_DIAMOND && !ind) || (p->cls == PC_CYCLE4 && !ind)))
@@ -175,6 +181,8 @@ int enqueue_count(gpm_graph *g, const gpm_pattern_t *pats, uint32_t npat, uint32
   } else if (ps.clique_kmax >= 3) {
     GPM_TRY(gpm_launch_cliques(g, ps.clique_kmax, false, lo, hi, acc, st));
   }
+  for (int k = 7; k <= 9; ++k)
+    if (ps.gen_k & (1u << k)) GPM_TRY(gpm_launch_cliques(g, k, false, lo, hi, acc, st));
   if (ps.edge_terms) GPM_TRY(gpm_launch_edge_terms(g, ps.scatter, lo, hi, acc, st));
   if (ps.cycles4) GPM_TRY(gpm_launch_cycles4(g, lo, hi, acc, st));
   GPM_TRY(gpm_launch_finalize(ps.spec, acc, g->n, g->m, out_dev, status_of(g), st));
@@ -448,6 +456,29 @@ int gpm_count_roots(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uin
   cudaStream_t st = as_stream(stream);
   GPM_TRY(prepare_locked(g, st));
   return count_to_host(g, pats, npat, root_lo, root_hi, true, counts, st);
+}
+
+int gpm_count_cliques(gpm_graph_t g, uint32_t k, uint32_t root_lo, uint32_t root_hi, uint64_t *count,
+                      void *stream) {
+  GPM_TRY(check_graph(g));
+  if (!count) return gpm_fail(GPM_E_INVALID_ARG, "null argument");
+  if (k < 3 || k > 9) return gpm_fail(GPM_E_INVALID_ARG, "gpm_count_cliques takes k = 3..9");
+  if (root_lo > root_hi || root_hi > g->n) return gpm_fail(GPM_E_INVALID_ARG, "root range outside [0, n]");
+  std::lock_guard<std::mutex> lk(g->mu);
+  cudaStream_t st = as_stream(stream);
+  GPM_TRY(prepare_locked(g, st));
+  unsigned long long *acc = acc_of(g);
+  GPM_CUDA(cudaMemsetAsync(acc, 0, ACC_WORDS * sizeof(unsigned long long), st));
+  GPM_CUDA(cudaMemsetAsync(status_of(g), 0, sizeof(uint64_t), st));
+  GPM_TRY(gpm_launch_cliques(g, (int)k, false, root_lo, root_hi, acc, st));
+  const int slot = k >= 7 ? ACC_K7 + (int)(k - 7) : (int)k;
+  uint64_t h = 0, status = 0;
+  GPM_CUDA(cudaMemcpyAsync(&h, acc + slot, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+  GPM_CUDA(cudaMemcpyAsync(&status, status_of(g), sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+  GPM_CUDA(cudaStreamSynchronize(st));
+  GPM_TRY(status_to_code((uint32_t)status));
+  *count = h;
+  return GPM_OK;
 }
 
 int gpm_list(gpm_graph_t g, gpm_pattern_t p, uint32_t *buf, uint64_t cap, uint64_t *written, uint64_t *total,

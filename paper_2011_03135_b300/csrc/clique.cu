@@ -46,7 +46,7 @@ struct LGArgs {
   uint32_t root_lo, root_hi;
   uint32_t W;  // words per bitmap row (CTA / global classes)
   unsigned int *queue;
-  unsigned long long *acc;  // acc[3] triangles, acc[4] 4-cliques, acc[5] 5-cliques
+  unsigned long long *acc;  // acc[3] triangles, acc[4..6] 4- to 6-cliques; k >= 7: acc[k - 7]
   uint32_t *t_edge;         // scatter mode
   uint32_t *pool;           // global-memory slots (XL class)
   uint64_t slot_words;
@@ -55,6 +55,12 @@ struct LGArgs {
 
 __device__ __forceinline__ void flush_acc(const LGArgs &a, unsigned long long a3, unsigned long long a4,
                                           unsigned long long a5, unsigned long long a6, int kmax) {
+  if (kmax >= 7) {
+    // the generic pass adds only its own clique size (a6 carries it)
+    for (int o = 16; o > 0; o >>= 1) a6 += __shfl_down_sync(0xffffffffu, a6, o);
+    if ((threadIdx.x & 31) == 0 && a6) atomicAdd(&a.acc[kmax - 7], a6);
+    return;
+  }
   for (int o = 16; o > 0; o >>= 1) {
     a3 += __shfl_down_sync(0xffffffffu, a3, o);
     a4 += __shfl_down_sync(0xffffffffu, a4, o);
@@ -72,9 +78,15 @@ __device__ __forceinline__ void flush_acc(const LGArgs &a, unsigned long long a3
 // ---------------------------------------------------------------------------
 // one warp per root, bitmap in shared memory
 // ---------------------------------------------------------------------------
+// per-warp shared words: the local graph, then (k >= 7) the generic search's scratch
+template <int MAXD, int KMAX, bool SCATTER>
+__host__ __device__ constexpr uint32_t warp_stride() {
+  return gpm_dev::warp_words(MAXD, SCATTER) + (KMAX >= 7 ? gpm_dev::gen_warp_words(1) : 0);
+}
+
 template <int MAXD, int G, int KMAX, bool SCATTER>
 __global__ void __launch_bounds__(256) lg_warp_kernel(LGArgs a) {
-  constexpr uint32_t kStride = gpm_dev::warp_words(MAXD, SCATTER);
+  constexpr uint32_t kStride = warp_stride<MAXD, KMAX, SCATTER>();
   extern __shared__ __align__(16) uint32_t smem[];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t *base = smem + (size_t)wid * kStride;
@@ -88,7 +100,8 @@ __global__ void __launch_bounds__(256) lg_warp_kernel(LGArgs a) {
     if (u < a.root_lo || u >= a.root_hi) continue;
     const uint32_t d = (uint32_t)(a.drow[u + 1] - a.drow[u]);
     if (d < 2 || d > MAXD) continue;
-    gpm_dev::lg_root_warp<MAXD, G, KMAX, SCATTER>(a.drow, a.dcol, a.t_edge, u, base, a3, a4, a5, a6);
+    gpm_dev::lg_root_warp<MAXD, G, KMAX, SCATTER>(a.drow, a.dcol, a.t_edge, u, base, a3, a4, a5, a6,
+                                                  base + gpm_dev::warp_words(MAXD, SCATTER));
   }
   flush_acc(a, a3, a4, a5, a6, KMAX);
 }
@@ -104,6 +117,11 @@ __global__ void __launch_bounds__(THREADS) lg_cta_kernel(LGArgs a, uint32_t maxd
   uint32_t *base = GLOBAL ? a.pool + (size_t)blockIdx.x * a.slot_words : smem;
   // nested local graphs for the 5-clique level live after the bitmap (shared memory only)
   uint32_t *nest = (!GLOBAL && KMAX >= 5 && big_cap) ? smem + gpm_dev::cta_words(maxd, a.W) : nullptr;
+  // k >= 7 with global-memory bitmaps: the generic search's counter and
+  // per-warp scratch in static shared memory (rows of up to 128 words)
+  constexpr int kNwl = (GLOBAL && KMAX >= 7) ? 4 : 1;
+  __shared__ uint32_t gen_s[(GLOBAL && KMAX >= 7) ? 4 + (THREADS / 32) * gpm_dev::gen_warp_words(4) : 1];
+  uint32_t *gen = (GLOBAL && KMAX >= 7) ? gen_s : nullptr;
   unsigned long long a3 = 0, a4 = 0, a5 = 0, a6 = 0;
   for (;;) {
     if (threadIdx.x == 0) s_task = atomicAdd(a.queue, 1u);
@@ -115,8 +133,8 @@ __global__ void __launch_bounds__(THREADS) lg_cta_kernel(LGArgs a, uint32_t maxd
     if (u < a.root_lo || u >= a.root_hi) continue;
     const uint32_t d = (uint32_t)(a.drow[u + 1] - a.drow[u]);
     if (d < 2 || d > maxd) continue;
-    gpm_dev::lg_root_cta<G, KMAX, SCATTER>(a.drow, a.dcol, a.t_edge, u, maxd, a.W, base, a3, a4, a5, a6, nest,
-                                           big_cap, a.deg, wcap);
+    gpm_dev::lg_root_cta<G, KMAX, SCATTER, kNwl>(a.drow, a.dcol, a.t_edge, u, maxd, a.W, base, a3, a4, a5, a6,
+                                                 nest, big_cap, a.deg, wcap, gen);
   }
   flush_acc(a, a3, a4, a5, a6, KMAX);
 }
@@ -127,7 +145,7 @@ using gpm_dev::warp_words;
 template <int MAXD, int G, int KMAX, bool SCATTER>
 int launch_warp(const LGArgs &a, int device, cudaStream_t st) {
   constexpr int kThreads = 256;
-  const size_t smem = (size_t)warp_words(MAXD, SCATTER) * 4 * (kThreads / 32);
+  const size_t smem = (size_t)warp_stride<MAXD, KMAX, SCATTER>() * 4 * (kThreads / 32);
   auto kern = lg_warp_kernel<MAXD, G, KMAX, SCATTER>;
   GPM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
@@ -177,6 +195,9 @@ int launch_cta_t(const LGArgs &a, uint32_t maxd, int blocks_cap, int device, cud
       smem += (size_t)gpm_dev::nest_words(maxd, THREADS / 32, big_cap, wcap) * 4;
     }
   }
+  if (KMAX >= 7 && !GLOBAL &&
+      (big_cap == 0 || gpm_dev::nest_warp_words(wcap) < gpm_dev::gen_warp_words(1) + 4))
+    return gpm_fail(GPM_E_UNSUPPORTED, "no shared memory left for the generic clique search's scratch");
   auto kern = lg_cta_kernel<G, KMAX, SCATTER, GLOBAL, THREADS>;
   if (!GLOBAL) GPM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
@@ -238,9 +259,14 @@ int launch_all(gpm_graph *g, LGArgs base, unsigned int *queues, cudaStream_t st)
     const char *nm = part == 0 ? "lg_cta_hi" : "lg_cta_lo";
     if (a.ntasks) {
       const bool wide = part == 0;
-      if (a.W <= 8) GPM_TRY((launch_cta<8, KMAX, SCATTER, false>(a, md, 0, dev, st, limit, nm)));
-      else if (a.W <= 16) GPM_TRY((launch_cta<16, KMAX, SCATTER, false>(a, md, 0, dev, st, limit, nm, wide)));
-      else GPM_TRY((launch_cta<32, KMAX, SCATTER, false>(a, md, 0, dev, st, limit, nm, wide)));
+      if constexpr (KMAX >= 7) {
+        // the generic search does not use the row-group width
+        GPM_TRY((launch_cta<32, KMAX, SCATTER, false>(a, md, 0, dev, st, limit, nm, wide && a.W > 8)));
+      } else {
+        if (a.W <= 8) GPM_TRY((launch_cta<8, KMAX, SCATTER, false>(a, md, 0, dev, st, limit, nm)));
+        else if (a.W <= 16) GPM_TRY((launch_cta<16, KMAX, SCATTER, false>(a, md, 0, dev, st, limit, nm, wide)));
+        else GPM_TRY((launch_cta<32, KMAX, SCATTER, false>(a, md, 0, dev, st, limit, nm, wide)));
+      }
     }
   }
   // class XL: global-memory bitmaps, one slot per resident CTA
@@ -252,6 +278,9 @@ int launch_all(gpm_graph *g, LGArgs base, unsigned int *queues, cudaStream_t st)
     const uint32_t md = g->cls_maxdeg[CLS_XL];
     if (a.ntasks) {
       a.W = (md + 31) / 32;
+      if (KMAX >= 7 && a.W > 128)
+        return gpm_fail(GPM_E_UNSUPPORTED, "k-clique counting for k >= 7 supports root out-degrees up to 4096 "
+                                           "(this graph has " + std::to_string(md) + ")");
       a.slot_words = (cta_words(md, a.W) + 63) & ~63ull;
       const size_t slot_bytes = a.slot_words * 4;
       const size_t budget = (size_t)4 << 30;
@@ -271,9 +300,13 @@ int launch_all(gpm_graph *g, LGArgs base, unsigned int *queues, cudaStream_t st)
         g->xl_pool_bytes = (size_t)slots * slot_bytes;
       }
       a.pool = g->xl_pool;
-      if (a.W <= 8) GPM_TRY((launch_cta<8, KMAX, SCATTER, true>(a, md, slots, dev, st)));
-      else if (a.W <= 16) GPM_TRY((launch_cta<16, KMAX, SCATTER, true>(a, md, slots, dev, st)));
-      else GPM_TRY((launch_cta<32, KMAX, SCATTER, true>(a, md, slots, dev, st)));
+      if constexpr (KMAX >= 7) {
+        GPM_TRY((launch_cta<32, KMAX, SCATTER, true>(a, md, slots, dev, st)));
+      } else {
+        if (a.W <= 8) GPM_TRY((launch_cta<8, KMAX, SCATTER, true>(a, md, slots, dev, st)));
+        else if (a.W <= 16) GPM_TRY((launch_cta<16, KMAX, SCATTER, true>(a, md, slots, dev, st)));
+        else GPM_TRY((launch_cta<32, KMAX, SCATTER, true>(a, md, slots, dev, st)));
+      }
     }
   }
   return GPM_OK;
@@ -283,7 +316,8 @@ int launch_all(gpm_graph *g, LGArgs base, unsigned int *queues, cudaStream_t st)
 
 int gpm_launch_cliques(gpm_graph *g, int kmax, bool scatter, uint32_t root_lo, uint32_t root_hi,
                        unsigned long long *acc, cudaStream_t st) {
-  if (kmax < 3 || kmax > 6) return gpm_fail(GPM_E_UNSUPPORTED, "clique pass supports k = 3..6");
+  if (kmax < 3 || kmax > 9) return gpm_fail(GPM_E_UNSUPPORTED, "clique pass supports k = 3..9");
+  if (kmax >= 7 && scatter) return gpm_fail(GPM_E_INVALID_ARG, "the per-arc scatter pass runs with k <= 4");
   unsigned int *queues = reinterpret_cast<unsigned int *>(g->work + WK_QUEUE0);
   GPM_CUDA(cudaMemsetAsync(queues, 0, 8 * sizeof(unsigned int), st));
   LGArgs a{};
@@ -303,5 +337,8 @@ int gpm_launch_cliques(gpm_graph *g, int kmax, bool scatter, uint32_t root_lo, u
   if (kmax == 3) return launch_all<3, false>(g, a, queues, st);
   if (kmax == 4) return launch_all<4, false>(g, a, queues, st);
   if (kmax == 5) return launch_all<5, false>(g, a, queues, st);
+  if (kmax == 7) return launch_all<7, false>(g, a, queues, st);
+  if (kmax == 8) return launch_all<8, false>(g, a, queues, st);
+  if (kmax == 9) return launch_all<9, false>(g, a, queues, st);
   return launch_all<6, false>(g, a, queues, st);
 }

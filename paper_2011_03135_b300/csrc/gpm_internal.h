@@ -184,7 +184,8 @@ int gpm_ensure_classes(gpm_graph *g, cudaStream_t st);
 // persistent grid size for a kernel
 int gpm_num_sms(int device);
 
-// Clique counts for k = 3..kmax (kmax <= 6) over roots in [root_lo, root_hi).
+// Clique counts for k = 3..kmax (kmax <= 6), or for k = kmax alone (7..9, into
+// acc[kmax - 7]), over roots in [root_lo, root_hi).
 // Adds to acc[ACC_T .. kmax] (uint64, device). scatter: additionally adds
 // every triangle to the per-arc counts g->t_edge (zeroed by the caller).
 int gpm_launch_cliques(gpm_graph *g, int kmax, bool scatter, uint32_t root_lo, uint32_t root_hi,
@@ -211,6 +212,7 @@ int gpm_launch_edge_terms(gpm_graph *g, bool use_t_edge, uint32_t root_lo, uint3
 
 // Accumulator slots (uint64) filled by the passes above.
 enum {
+  ACC_K7 = 0,    // 7-, 8- and 9-cliques (slots 0..2: k - 7)
   ACC_T = 3,     // triangles
   ACC_K4 = 4,    // 4-cliques
   ACC_K5 = 5,    // 5-cliques
@@ -229,7 +231,7 @@ enum {
 enum Formula : uint32_t {
   F_VERTEX = 0, F_EDGE, F_TRI, F_K4, F_K5, F_WEDGE_NI, F_WEDGE_I,
   F_STAR_NI, F_PATH_NI, F_TT_NI, F_C4_NI, F_D_NI,
-  F_STAR_I, F_PATH_I, F_TT_I, F_C4_I, F_D_I, F_K4_I, F_K6,
+  F_STAR_I, F_PATH_I, F_TT_I, F_C4_I, F_D_I, F_K4_I, F_K6, F_K7, F_K8, F_K9,
 };
 struct FinalizeSpec {
   uint32_t npat;

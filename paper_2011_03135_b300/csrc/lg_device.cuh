@@ -653,12 +653,174 @@ __device__ __forceinline__ void rank_local(const uint32_t *__restrict__ deg, con
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Cliques of any size k >= 7: the shrinking candidate set of the local-graph
+// search (k-CL on the local graph, one level per clique vertex) with the set
+// held as a bitmap over the root's local vertices, distributed over a warp
+// (lane l keeps words l, l + 32, ... of it: NWL words per lane). Once a set
+// has at most 32 members it is compacted into a register graph (lane b keeps
+// row b of the induced 32-vertex DAG) and the remaining levels run as per-lane
+// loops over single words.
+// ---------------------------------------------------------------------------
+
+// Per-warp scratch (words) of the generic search: Mw[32 NWL] | pref[32 NWL] | S[32] | Ds[32]
+__host__ __device__ constexpr uint32_t gen_warp_words(uint32_t nwl) { return 64 * nwl + 64; }
+
+// r-cliques (r >= 1) among the members m of the register graph (rows Ds in
+// shared memory; lane x also holds its own row dl = Ds[x]). The graph is a
+// DAG: row x holds x's successors, so each clique is met once, through its
+// first vertex; successors are taken from all of m, since the DAG order need
+// not follow the bit order. The whole warp walks the first r - 3 levels
+// together (m is warp-uniform); then lane x takes the third-last vertex x, a
+// loop the second-last and a popcount the last, so lanes diverge over one
+// level only. Returns this lane's share (at most C(32, r) < 2^32 in all).
+template <int r>
+__device__ __forceinline__ uint32_t reg_cliques_warp(uint32_t m, uint32_t dl, const uint32_t *Ds) {
+  const uint32_t lane = threadIdx.x & 31;
+  if constexpr (r == 1) {
+    return lane == 0 ? __popc(m) : 0u;
+  } else if constexpr (r == 2) {
+    return ((m >> lane) & 1u) ? __popc(m & dl) : 0u;
+  } else if constexpr (r == 3) {
+    uint32_t s = 0;
+    if ((m >> lane) & 1u) {
+      const uint32_t m1 = m & dl;
+      uint32_t rest = m1;
+      while (rest) {
+        const uint32_t z = __ffs(rest) - 1;
+        rest &= rest - 1;
+        s += __popc(m1 & Ds[z]);
+      }
+    }
+    return s;
+  } else {
+    uint32_t s = 0, rest = m;
+    while (rest) {
+      const uint32_t x = __ffs(rest) - 1;
+      rest &= rest - 1;
+      const uint32_t m2 = m & Ds[x];
+      if (__popc(m2) >= (uint32_t)(r - 1)) s += reg_cliques_warp<r - 1>(m2, dl, Ds);
+    }
+    return s;
+  }
+}
+
+// Q-cliques (Q >= 1) among the members of the set m (NWL words per lane) of
+// the local-graph DAG R (W words per row, stride rs). Called by a whole warp
+// with warp-uniform arguments; returns this lane's share (the warp sum is the
+// count). With tri, row j of R has no bit at or below j.
+template <int Q, int NWL>
+__device__ unsigned long long set_cliques(const uint32_t *R, uint32_t W, uint32_t rs, const uint32_t (&m)[NWL],
+                                          uint32_t *scr, bool tri) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int j = 0; j < NWL; ++j) cnt += __popc(m[j]);
+  if constexpr (Q == 1) {
+    return cnt;
+  } else {
+    const uint32_t c = __reduce_add_sync(0xffffffffu, cnt);
+    if (c < (uint32_t)Q) return 0;
+    if (c <= 32) {
+      // compact onto a register graph: S lists the members in order, pref[w]
+      // counts the members in words before w
+      uint32_t *Mw = scr, *pref = scr + 32 * NWL, *S = scr + 64 * NWL, *Ds = S + 32;
+      uint32_t run = 0;
+#pragma unroll
+      for (int j = 0; j < NWL; ++j) {
+        const uint32_t x0 = m[j], k0 = __popc(x0);
+        uint32_t incl = k0;
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= (uint32_t)o) incl += y;
+        }
+        const uint32_t w = j * 32 + lane;
+        uint32_t k = run + incl - k0, x = x0;
+        Mw[w] = x0;
+        pref[w] = k;
+        while (x) {
+          S[k++] = w * 32 + __ffs(x) - 1;
+          x &= x - 1;
+        }
+        run += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      __syncwarp();
+      uint32_t db = 0;
+      if (lane < c) {
+        const uint32_t v = S[lane];
+        const uint32_t *rv = R + (size_t)v * rs;
+        for (uint32_t w = tri ? (v + 1) >> 5 : 0; w < W; ++w) {
+          const uint32_t mw = Mw[w];
+          const uint32_t x = rv[w] & mw;
+          if (x) db |= gather_bits(x, mw) << pref[w];  // c <= 32: every output bit is in word 0
+        }
+      }
+      Ds[lane] = db;
+      __syncwarp();
+      const unsigned long long s = reg_cliques_warp<Q>(c == 32 ? ~0u : (1u << c) - 1u, db, Ds);
+      __syncwarp();
+      return s;
+    } else {
+      // first member a, then (Q-1)-cliques among the members after it in the DAG
+      unsigned long long s = 0;
+#pragma unroll 1
+      for (int j = 0; j < NWL && (uint32_t)j * 32 < W; ++j) {
+        const uint32_t tw = min(32u, W - (uint32_t)j * 32);
+#pragma unroll 1
+        for (uint32_t t = 0; t < tw; ++t) {
+          uint32_t word = __shfl_sync(0xffffffffu, m[j], t);
+          const uint32_t w = j * 32 + t;
+          while (word) {
+            const uint32_t a = w * 32 + __ffs(word) - 1;
+            word &= word - 1;
+            const uint32_t *ra = R + (size_t)a * rs;
+            uint32_t m2[NWL];
+#pragma unroll
+            for (int jj = 0; jj < NWL; ++jj) {
+              const uint32_t ww = jj * 32 + lane;
+              m2[jj] = (ww < W) ? (m[jj] & ra[ww]) : 0u;
+            }
+            s += set_cliques<Q - 1, NWL>(R, W, rs, m2, scr, tri);
+          }
+        }
+      }
+      return s;
+    }
+  }
+}
+
+// k-cliques (KMAX = k >= 7) through the root of the CTA's local graph: rows
+// pulled dynamically by warps (ctr: a shared counter), (k-2)-cliques inside
+// each row. Every thread of the CTA calls it.
+template <int KMAX, int NWL>
+__device__ __forceinline__ void rows_generic_cta(const uint32_t *R, uint32_t d, uint32_t W, uint32_t rs,
+                                                 uint32_t *ctr, uint32_t *scr, bool tri, unsigned long long &ak) {
+  const uint32_t lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) *ctr = 0;
+  __syncthreads();
+  for (;;) {
+    uint32_t i = 0;
+    if (lane == 0) i = atomicAdd(ctr, 1u);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (i >= d) break;
+    const uint32_t *ri = R + (size_t)i * rs;
+    uint32_t m[NWL];
+#pragma unroll
+    for (int j = 0; j < NWL; ++j) {
+      const uint32_t w = j * 32 + lane;
+      m[j] = (w < W) ? ri[w] : 0u;
+    }
+    ak += set_cliques<KMAX - 2, NWL>(R, W, rs, m, scr, tri);
+  }
+}
+
 // One root u (2 <= d+(u) <= MAXD) processed by the calling warp. `base` is
 // the warp's shared-memory region of warp_words(MAXD, SCATTER) words.
 template <int MAXD, int G, int KMAX, bool SCATTER>
 __device__ __forceinline__ void lg_root_warp(const uint64_t *__restrict__ drow, const uint32_t *__restrict__ dcol,
                                              uint32_t *t_edge, uint32_t u, uint32_t *base, unsigned long long &a3,
-                                             unsigned long long &a4, unsigned long long &a5, unsigned long long &a6) {
+                                             unsigned long long &a4, unsigned long long &a5, unsigned long long &a6,
+                                             uint32_t *gen = nullptr) {
   const uint32_t lane = threadIdx.x & 31;
   uint64_t *xb = reinterpret_cast<uint64_t *>(base);
   uint32_t *L = base + 2 * MAXD;
@@ -698,19 +860,27 @@ __device__ __forceinline__ void lg_root_warp(const uint64_t *__restrict__ drow, 
     for (uint32_t i = lane; i < d; i += 32)
       if (tc[i]) atomicAdd(&t_edge[ub + i], tc[i]);
   }
-  if (KMAX >= 4) enumerate_rows<G, KMAX>(R, d, w_used, rs, lane / G, 32 / G, lane % G, a4, a5, a6);
+  if constexpr (KMAX >= 7) {
+    // (k-1)-cliques among all of L; a6 carries the k-clique count
+    uint32_t m[1];
+    m[0] = (lane < w_used) ? ((lane + 1) * 32 <= d ? ~0u : (1u << (d & 31)) - 1u) : 0u;
+    a6 += set_cliques<KMAX - 1, 1>(R, w_used, rs, m, gen, false);
+  } else if (KMAX >= 4) {
+    enumerate_rows<G, KMAX>(R, d, w_used, rs, lane / G, 32 / G, lane % G, a4, a5, a6);
+  }
   __syncwarp();
 }
 
 // One root u (2 <= d+(u) <= maxd) processed by the whole CTA. `base` holds
 // cta_words(maxd, W) words (shared or global memory); W >= ceil(maxd / 32).
 // Every thread of the CTA must call it.
-template <int G, int KMAX, bool SCATTER>
+template <int G, int KMAX, bool SCATTER, int NWL = 1>
 __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, const uint32_t *__restrict__ dcol,
                                             uint32_t *t_edge, uint32_t u, uint32_t maxd, uint32_t W, uint32_t *base,
                                             unsigned long long &a3, unsigned long long &a4, unsigned long long &a5,
                                             unsigned long long &a6, uint32_t *nest = nullptr, uint32_t big_cap = 0,
-                                            const uint32_t *__restrict__ deg = nullptr, uint32_t wcap = kNestWarpC) {
+                                            const uint32_t *__restrict__ deg = nullptr, uint32_t wcap = kNestWarpC,
+                                            uint32_t *gen = nullptr) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
   uint64_t *xb = reinterpret_cast<uint64_t *>(base);
   uint32_t *L = base + 2 * (size_t)maxd;
@@ -775,7 +945,12 @@ __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, c
     for (uint32_t i = tid; i < d; i += nt)
       if (tc[i]) atomicAdd(&t_edge[ub + i], tc[i]);
   }
-  if (KMAX >= 5 && nest != nullptr && w_used <= 32) {
+  if constexpr (KMAX >= 7) {
+    // gen: a counter word, then one scratch region per warp (the nested pool
+    // is free again once the rows are built); a6 carries the k-clique count
+    uint32_t *g = gen ? gen : nest + 4 + 2 * (size_t)maxd;
+    rows_generic_cta<KMAX, NWL>(R, d, w_used, rs, g, g + 4 + (size_t)(tid >> 5) * gen_warp_words(NWL), tri, a6);
+  } else if (KMAX >= 5 && nest != nullptr && w_used <= 32) {
     enumerate_nested_cta<(KMAX >= 6)>(R, d, w_used, rs, nest, maxd, big_cap, a4, a5, a6, tri, wcap);
   } else if (KMAX >= 4) {
     if (w_used > 32)

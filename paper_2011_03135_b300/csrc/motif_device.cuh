@@ -476,6 +476,9 @@ __device__ __forceinline__ unsigned long long finalize_formula(uint32_t f, const
     case 16: v = iD; bad |= (iD > ND); break;
     case 17: v = iK4; break;
     case 18: v = acc[6]; break;           // F_K6
+    case 19: v = acc[0]; break;           // F_K7
+    case 20: v = acc[1]; break;           // F_K8
+    case 21: v = acc[2]; break;           // F_K9
     default: bad = true; break;
   }
   return v;

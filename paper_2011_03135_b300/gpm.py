@@ -95,6 +95,7 @@ _SIGS = {
     "gpm_count": [_vp, _vp, _u32, _vp, _vp],
     "gpm_count_async": [_vp, _vp, _u32, _vp, _vp],
     "gpm_count_roots": [_vp, _vp, _u32, _u32, _u32, _vp, _vp],
+    "gpm_count_cliques": [_vp, _u32, _u32, _u32, _vp, _vp],
     "gpm_list": [_vp, _vp, _vp, _u64, _U64P, _U64P, _vp],
     "gpm_graph_reset": [_vp],
     "gpm_profile_enable": [_i],
@@ -339,6 +340,14 @@ def count_roots(graph: Graph, patterns: Sequence[Pattern], root_lo: int, root_hi
     _check(_lib.gpm_count_roots(graph.handle, _handles(patterns), len(patterns), root_lo, root_hi,
                                 out.ctypes.data, _stream(stream)))
     return [int(x) for x in out]
+
+
+def count_cliques(graph: Graph, k: int, root_lo: int = 0, root_hi: int | None = None, stream=None) -> int:
+    """Number of k-cliques (k = 3..9) whose root vertex lies in [root_lo, root_hi)."""
+    out = ctypes.c_uint64(0)
+    hi = graph.n if root_hi is None else root_hi
+    _check(_lib.gpm_count_cliques(graph.handle, k, root_lo, hi, ctypes.byref(out), _stream(stream)))
+    return int(out.value)
 
 
 def list_embeddings(graph: Graph, pattern: Pattern, cap: int, out=None, stream=None):

@@ -215,6 +215,11 @@ def workload_clique_rmat21() -> Graph:
     return rmat(21, 16.0, (0.57, 0.19, 0.19, 0.05), seed=2)
 
 
+def workload_clique6_rmat20() -> Graph:
+    """Large-k clique input: R-MAT scale 20, edge factor 16, (0.57,0.19,0.19,0.05), seed 2."""
+    return rmat(20, 16.0, (0.57, 0.19, 0.19, 0.05), seed=2)
+
+
 def workload_sl_chung_lu4m() -> Graph:
     """Subgraph-listing input: Chung-Lu, 4,194,304 vertices, mean degree 24, exponent 2.1, seed 3."""
     return chung_lu(1 << 22, 24.0, 2.1, seed=3)

@@ -46,14 +46,15 @@ SMALL = [
 # ---------------- k-cliques ----------------
 
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 4, 5, 8, 11])
-@pytest.mark.parametrize("k", [3, 4, 5, 6])
+@pytest.mark.parametrize("k", [3, 4, 5, 6, 7, 8, 9])
 def test_cliques_complete_graph(n, k):
     g = gg.complete(n) if n > 0 else gg.empty(0)
     assert O.cliques(g, k) == math.comb(n, k)
 
 
-@pytest.mark.parametrize("parts", [[2, 3], [1, 1, 1, 1], [2, 2, 2], [3, 1, 4, 2], [5, 5, 1], [2, 1, 3, 1, 2, 2, 1]])
-@pytest.mark.parametrize("k", [3, 4, 5, 6])
+@pytest.mark.parametrize("parts", [[2, 3], [1, 1, 1, 1], [2, 2, 2], [3, 1, 4, 2], [5, 5, 1], [2, 1, 3, 1, 2, 2, 1],
+                                   [1, 2, 1, 3, 1, 2, 1, 1, 2, 1]])
+@pytest.mark.parametrize("k", [3, 4, 5, 6, 7, 8, 9])
 def test_cliques_complete_multipartite(parts, k):
     g = gg.complete_multipartite(parts)
     assert O.cliques(g, k) == _esym(parts, k)
@@ -85,6 +86,38 @@ def test_cliques_match_subset_brute_force(mk):
         bf = sum(1 for W in itertools.combinations(range(g.n), k)
                  if all(b in adj[a] for a, b in itertools.combinations(W, 2)))
         assert O.cliques(g, k) == bf
+
+
+@pytest.mark.parametrize("mk", [lambda: gg.random_small(16, 0.75, 21), lambda: gg.random_small(19, 0.65, 22)])
+def test_large_cliques_match_subset_brute_force(mk):
+    # k = 7..9 by a recursive extension over sorted candidate lists (written
+    # here, independent of the oracle's code)
+    g = mk()
+    adj = _py_adj(g)
+
+    def ext(cands, r):
+        if r == 0:
+            return 1
+        return sum(ext([w for w in cands[i + 1:] if w in adj[v]], r - 1) for i, v in enumerate(cands))
+
+    for k in (7, 8, 9):
+        assert O.cliques(g, k) == ext(list(range(g.n)), k), k
+
+
+def test_cliques_hub_identity():
+    # a vertex set B with its own edges, joined completely to an independent
+    # set C and to one more vertex a: every k-clique is either inside B or one
+    # vertex of {a} + C with a (k-1)-clique of B
+    rng = np.random.default_rng(5)
+    nb, nc = 60, 70
+    B = np.arange(1, 1 + nb)
+    inner = [(int(B[i]), int(B[j])) for i in range(nb) for j in range(i + 1, nb) if rng.random() < 0.3]
+    inner += [(int(B[i]), int(B[j])) for i in range(9) for j in range(i + 1, 9)]
+    e = [(0, int(b)) for b in B] + [(int(b), int(c)) for b in B for c in range(1 + nb, 1 + nb + nc)] + inner
+    g = gg.from_edges(1 + nb + nc, e)
+    gb = gg.from_edges(1 + nb, inner)
+    for k in (3, 5, 7, 8, 9):
+        assert O.cliques(g, k) == (1 + nc) * O.cliques(gb, k - 1) + O.cliques(gb, k), k
 
 
 @pytest.mark.parametrize("mk", SMALL[:4])

@@ -305,6 +305,27 @@ def test_fullsize_cliques_rmat21(gpm):
     G.close()
 
 
+def test_fullsize_clique6_rmat20(gpm):
+    # the 6-clique workload in the launch configuration bench.py times: sampled
+    # root ranges and the lightest root of the 1024-thread class against the
+    # oracle; the total against a partition of the roots and the 5-clique total
+    # against the k <= 5 pass
+    g = gg.workload_clique6_rmat20()
+    G = gpm.Graph.from_host(g)
+    K6 = gpm.Pattern.clique(6)
+    for lo, hi in _sample_ranges(g.n, 7, count=3, width=40):
+        assert gpm.count_roots(G, [K6], lo, hi) == [O.cliques(g, 6, lo, hi)], (lo, hi)
+    od = O.out_degrees(g)
+    hi_class = np.nonzero(od > 384)[0]
+    v = int(hi_class[np.argmin(od[hi_class])])
+    assert gpm.count_roots(G, [K6], v, v + 1) == [O.cliques(g, 6, v, v + 1)], v
+    tot = gpm.count(G, [gpm.Pattern.clique(5), K6])
+    cuts = [0, 1, g.n // 3, g.n // 3 + 1, g.n - 5, g.n]
+    assert sum(gpm.count_roots(G, [K6], lo, hi)[0] for lo, hi in zip(cuts[:-1], cuts[1:])) == tot[1]
+    assert gpm.count(G, [gpm.Pattern.clique(4), gpm.Pattern.clique(5)])[1] == tot[0]
+    G.close()
+
+
 def test_fullsize_sl_chunglu4m(gpm):
     g = gg.workload_sl_chung_lu4m()
     gold = _golden().get("sl_chunglu4m", {})
@@ -377,3 +398,78 @@ def test_six_cliques_every_root_class(gpm, opts):
             G.close()
     finally:
         gpm.set_options(**{k: v for k, v in old.items() if v})
+
+
+def _hub_graph(nb=420, nc=430, p=0.1, planted=(10, 9), seed=5):
+    """Vertex a and an independent set C joined completely to B (B has its own
+    sparse edges and planted cliques): a and every vertex of C are roots with
+    out-degree |B| = 420 (the 1024-thread CTA class), whose local graph is B."""
+    rng = np.random.default_rng(seed)
+    B = np.arange(1, 1 + nb)
+    C = np.arange(1 + nb, 1 + nb + nc)
+    e = [(0, int(b)) for b in B] + [(int(b), int(c)) for b in B for c in C]
+    iu = np.triu_indices(nb, 1)
+    keep = rng.random(len(iu[0])) < p
+    e += [(int(B[i]), int(B[j])) for i, j in zip(iu[0][keep], iu[1][keep])]
+    perm = rng.permutation(nb)
+    off = 0
+    for s in planted:
+        vs = B[perm[off:off + s]]
+        off += s
+        e += [(int(vs[i]), int(vs[j])) for i in range(s) for j in range(i + 1, s)]
+    return gg.from_edges(1 + nb + nc, e, name="hub")
+
+
+@pytest.mark.parametrize("opts", [dict(), dict(warp_max_degree=32, cta_max_degree=32),
+                                  dict(warp_max_degree=32, cta_max_degree=96),
+                                  dict(warp_max_degree=256, cta_max_degree=1024)])
+def test_large_k_cliques_every_root_class(gpm, opts):
+    # k = 7..9 by the generic search in every root class (warp, CTA in shared
+    # memory, CTA with global-memory bitmaps): closed forms on complete and
+    # complete multipartite graphs, the oracle elsewhere
+    import itertools
+    import math
+    old = gpm.get_options()
+    try:
+        if opts:
+            gpm.set_options(**opts)
+        for n in (9, 33, 40):
+            G = gpm.Graph.from_host(gg.complete(n))
+            assert [gpm.count_cliques(G, k) for k in (7, 8, 9)] == [math.comb(n, k) for k in (7, 8, 9)], n
+            assert gpm.count(G, [gpm.Pattern.clique(7), gpm.Pattern.clique(8)]) == [math.comb(n, 7), math.comb(n, 8)]
+            G.close()
+        parts = [3, 2, 4, 1, 3, 2, 5, 3, 1, 2]
+        G = gpm.Graph.from_host(gg.complete_multipartite(parts))
+        want = [sum(math.prod(c) for c in itertools.combinations(parts, k)) for k in (7, 8, 9)]
+        assert [gpm.count_cliques(G, k) for k in (7, 8, 9)] == want
+        G.close()
+        for g in [_hub_graph(), gg.rmat(10, 16.0, seed=21), gg.rmat(12, 8.0, seed=22),
+                  gg.chung_lu(5000, 16.0, 2.1, seed=24)]:
+            G = gpm.Graph.from_host(g)
+            assert [gpm.count_cliques(G, k) for k in (7, 8, 9)] == [O.cliques(g, k) for k in (7, 8, 9)], g.name
+            G.close()
+    finally:
+        gpm.set_options(**{k: v for k, v in old.items() if v})
+
+
+def test_count_cliques_ranges_and_small_k(gpm):
+    # gpm_count_cliques: root ranges partition the total; k = 3..6 agree with
+    # the fused pass; a mixed call (k <= 6 and k >= 7 patterns) fills both
+    g = gg.rmat(12, 8.0, seed=22)
+    G = gpm.Graph.from_host(g)
+    cuts = [0, 1, 1000, 2047, 2048, 3000, g.n]
+    for k in (7, 9):
+        parts = [gpm.count_cliques(G, k, lo, hi) for lo, hi in zip(cuts[:-1], cuts[1:])]
+        assert parts == [O.cliques(g, k, lo, hi) for lo, hi in zip(cuts[:-1], cuts[1:])], k
+        assert sum(parts) == gpm.count_cliques(G, k)
+    assert [gpm.count_cliques(G, k) for k in (3, 4, 5, 6)] == [O.cliques(g, k) for k in (3, 4, 5, 6)]
+    mixed = [gpm.Pattern.clique(4), gpm.Pattern.clique(8), gpm.Pattern.spec(O.CYCLE4, induced=False),
+             gpm.Pattern.clique(7), gpm.Pattern.clique(3)]
+    assert gpm.count(G, mixed) == [O.cliques(g, 4), O.cliques(g, 8), O.cycles4(g), O.cliques(g, 7), O.cliques(g, 3)]
+    assert gpm.count_roots(G, mixed[:2], 100, 2500) == [O.cliques(g, 4, 100, 2500), O.cliques(g, 8, 100, 2500)]
+    for bad in (0, 2, 10):
+        with pytest.raises(gpm.GpmError):
+            gpm.count_cliques(G, bad)
+    with pytest.raises(gpm.GpmError):
+        gpm.count_cliques(G, 7, 5, 3)
+    G.close()
