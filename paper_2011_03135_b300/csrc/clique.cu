@@ -238,7 +238,13 @@ int launch_all(gpm_graph *g, LGArgs base, unsigned int *queues, cudaStream_t st)
     a.ntasks = g->cls_begin[CLS_WARP + 1] - g->cls_begin[CLS_WARP];
     a.queue = queues + 1;
     const uint32_t md = g->cls_maxdeg[CLS_WARP];
-    if (a.ntasks) {
+    if (KMAX >= 7 && a.ntasks) {
+      // the generic search spreads a root over a CTA (a heavy local graph in
+      // one warp would be the last to finish)
+      a.W = (md + 31) / 32;
+      GPM_TRY((launch_cta<32, KMAX, SCATTER, false>(a, md, 0, dev, st, (size_t)(max_smem_optin(dev) / 2 - 1024),
+                                                    "lg_cta_mid")));
+    } else if (a.ntasks) {
       if (md <= 64) GPM_TRY((launch_warp<64, 2, KMAX, SCATTER>(a, dev, st)));
       else if (md <= 128) GPM_TRY((launch_warp<128, 4, KMAX, SCATTER>(a, dev, st)));
       else GPM_TRY((launch_warp<256, 8, KMAX, SCATTER>(a, dev, st)));

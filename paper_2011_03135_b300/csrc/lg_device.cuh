@@ -760,8 +760,43 @@ __device__ unsigned long long set_cliques(const uint32_t *R, uint32_t W, uint32_
       const unsigned long long s = reg_cliques_warp<Q>(c == 32 ? ~0u : (1u << c) - 1u, db, Ds);
       __syncwarp();
       return s;
+    } else if constexpr (Q <= 3) {
+      // more than 32 members, two or three levels left: lane l takes the
+      // member at bit l of each word (a uniform loop over the words), then
+      // loops over the members after it; the set stays in shared memory
+      uint32_t *Mw = scr;
+#pragma unroll
+      for (int j = 0; j < NWL; ++j) Mw[j * 32 + lane] = m[j];
+      __syncwarp();
+      unsigned long long s = 0;
+      for (uint32_t w = 0; w < W; ++w) {
+        const uint32_t mw = Mw[w];
+        if (!((mw >> lane) & 1u)) continue;
+        const uint32_t a = w * 32 + lane;
+        const uint32_t *ra = R + (size_t)a * rs;
+        const uint32_t w0 = tri ? (a + 1) >> 5 : 0u;
+        if constexpr (Q == 2) {
+          uint32_t t = 0;
+          for (uint32_t w2 = w0; w2 < W; ++w2) t += __popc(Mw[w2] & ra[w2]);
+          s += t;
+        } else {
+          for (uint32_t w1 = w0; w1 < W; ++w1) {
+            uint32_t x = Mw[w1] & ra[w1];
+            while (x) {
+              const uint32_t b = w1 * 32 + __ffs(x) - 1;
+              x &= x - 1;
+              const uint32_t *rb = R + (size_t)b * rs;
+              uint32_t t = 0;
+              for (uint32_t w2 = tri ? (b + 1) >> 5 : 0u; w2 < W; ++w2) t += __popc(Mw[w2] & ra[w2] & rb[w2]);
+              s += t;
+            }
+          }
+        }
+      }
+      __syncwarp();
+      return s;
     } else {
-      // first member a, then (Q-1)-cliques among the members after it in the DAG
+      // first member a, then (Q-1)-cliques among a's successors in the set
       unsigned long long s = 0;
 #pragma unroll 1
       for (int j = 0; j < NWL && (uint32_t)j * 32 < W; ++j) {
@@ -789,28 +824,45 @@ __device__ unsigned long long set_cliques(const uint32_t *R, uint32_t W, uint32_
   }
 }
 
-// k-cliques (KMAX = k >= 7) through the root of the CTA's local graph: rows
-// pulled dynamically by warps (ctr: a shared counter), (k-2)-cliques inside
-// each row. Every thread of the CTA calls it.
+// k-cliques (KMAX = k >= 7) through the root of the CTA's local graph. The
+// work is cut into (row i, word w) units, claimed dynamically by warps (ctr: a
+// shared counter) in word-major order, so that the rows of a heavy local
+// graph spread over the CTA: a unit takes each member a in word w of R_i and
+// counts the (k-3)-cliques among R_i & R_a. Every thread of the CTA calls it.
 template <int KMAX, int NWL>
 __device__ __forceinline__ void rows_generic_cta(const uint32_t *R, uint32_t d, uint32_t W, uint32_t rs,
                                                  uint32_t *ctr, uint32_t *scr, bool tri, unsigned long long &ak) {
   const uint32_t lane = threadIdx.x & 31;
   if (threadIdx.x == 0) *ctr = 0;
   __syncthreads();
+  const uint32_t units = d * W;
   for (;;) {
-    uint32_t i = 0;
-    if (lane == 0) i = atomicAdd(ctr, 1u);
-    i = __shfl_sync(0xffffffffu, i, 0);
-    if (i >= d) break;
+    uint32_t u = 0;
+    if (lane == 0) u = atomicAdd(ctr, 1u);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= units) break;
+    const uint32_t i = u % d, w = u / d;
     const uint32_t *ri = R + (size_t)i * rs;
-    uint32_t m[NWL];
+    uint32_t word = ri[w];
+    if (!word) continue;
+    uint32_t mi[NWL];
 #pragma unroll
     for (int j = 0; j < NWL; ++j) {
-      const uint32_t w = j * 32 + lane;
-      m[j] = (w < W) ? ri[w] : 0u;
+      const uint32_t ww = j * 32 + lane;
+      mi[j] = (ww < W) ? ri[ww] : 0u;
     }
-    ak += set_cliques<KMAX - 2, NWL>(R, W, rs, m, scr, tri);
+    while (word) {
+      const uint32_t a = w * 32 + __ffs(word) - 1;
+      word &= word - 1;
+      const uint32_t *ra = R + (size_t)a * rs;
+      uint32_t m2[NWL];
+#pragma unroll
+      for (int j = 0; j < NWL; ++j) {
+        const uint32_t ww = j * 32 + lane;
+        m2[j] = (ww < W) ? (mi[j] & ra[ww]) : 0u;
+      }
+      ak += set_cliques<KMAX - 3, NWL>(R, W, rs, m2, scr, tri);
+    }
   }
 }
 
