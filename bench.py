@@ -133,20 +133,27 @@ def clique_pass_bytes(g, opts):
 
 # Per-launch counters of the dominant kernel, per workload, from a one-pass
 # `ncu` capture of the same kernel on the same workload
-# (profiles/lg_cta_hi_rmat21_counters.md, profiles/lg_cta_hi_k6_rmat20_counters.md):
+# (profiles/lg_cta_hi_rmat21_counters.md, profiles/lg_cta_hi_k6_rmat20_counters.md,
+# profiles/lg_cta_lo_k789_chunglu1m_counters.md):
 #   ncu --metrics smsp__inst_executed.sum,gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
 #       --clock-control none -k regex:lg_cta_kernel -c 1
 #       python -m paper_2011_03135_b300.cases --case <clique-rmat21 | clique6-rmat20> --reps 1
+#   (clique789-cl1m: -c 6, every lg_cta_kernel launch of one step)
 # valid only for the kernel sources they were taken on (digest of
 # csrc/lg_device.cuh + csrc/clique.cu); a stale entry is ignored.
 NCU_COUNTERS = {
     "clique-rmat21": {
-        "lg_cta_hi": {"digest": "b5eb426ffcd9af0f", "inst_per_launch": 151171618904,
-                      "dram_bytes_per_launch": 28337920 + 3072, "ncu_ms": 183.692},
+        "lg_cta_hi": {"digest": "1b388c324607b5fe", "inst_per_launch": 151171162061,
+                      "dram_bytes_per_launch": 28381696 + 2816, "ncu_ms": 183.561},
     },
     "clique6-rmat20": {
-        "lg_cta_hi": {"digest": "b5eb426ffcd9af0f", "inst_per_launch": 1631591617792,
-                      "dram_bytes_per_launch": 13097984, "ncu_ms": 1677.904},
+        "lg_cta_hi": {"digest": "1b388c324607b5fe", "inst_per_step": 1631591263842,
+                      "dram_bytes_per_step": 13099264, "ncu_ms": 1676.886},
+    },
+    # three launches per step (k = 7, 8, 9), summed
+    "clique789-cl1m": {
+        "lg_cta_lo": {"digest": "1b388c324607b5fe", "inst_per_step": 19988345607 + 62451078763 + 192306344749,
+                      "dram_bytes_per_step": 6905344 + 6651648 + 6982656, "ncu_ms": 41.100 + 160.195 + 622.944},
     },
 }
 
@@ -439,25 +446,25 @@ def run_sl(args):
 
 CLIQUE6_WORKLOAD = ("6-clique counting, R-MAT scale 20 (1,048,576 vertices), edge factor 16, (0.57,0.19,0.19,0.05), "
                     "seed 2")
+CLIQUE789_WORKLOAD = ("k-clique counting k = 7, 8, 9 (one count per k), Chung-Lu 1,048,576 vertices, mean degree 24, "
+                      "exponent 2.1, seed 3")
 
 
-def run_clique6(args):
-    """Counting 6-cliques (the large-k row): same path, a fourth bitmap level."""
+def run_large_k(args, workload, g, ks, case):
+    """Counting k-cliques for large k through gpm_count_cliques: k = 6 is the
+    fused pass with a fourth bitmap level, k >= 7 the generic search."""
     import torch
     from paper_2011_03135_b300 import gpm
-    from paper_2011_03135_b300 import graphgen as gg
-    g = gg.workload_clique6_rmat20()
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(device=dev)
     G = gpm.Graph(torch.from_numpy(g.rowptr.view(np.int64)).to(dev), torch.from_numpy(g.col.view(np.int32)).to(dev),
                   g.n, validate=True, stream=stream)
-    P = [gpm.Pattern.clique(6)]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
 
     def step():
         G.reset()
-        return gpm.count(G, P, stream=stream)
+        return [gpm.count_cliques(G, k, stream=stream) for k in ks]
 
     counts = None
     for _ in range(max(args.warmup, 3)):
@@ -480,6 +487,7 @@ def run_clique6(args):
     prof = gpm.profile_report()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
+    total = sum(counts)
     rp_h = torch.from_numpy(g.rowptr.view(np.int64)).pin_memory()
     col_h = torch.from_numpy(g.col.view(np.int32)).pin_memory()
     e2e = []
@@ -487,7 +495,7 @@ def run_clique6(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         H = gpm.Graph(rp_h, col_h, g.n, validate=False, stream=stream)
-        c = gpm.count(H, P, stream=stream)
+        c = [gpm.count_cliques(H, k, stream=stream) for k in ks]
         H.close()
         if i > 0:
             e2e.append(time.perf_counter() - t0)
@@ -497,42 +505,46 @@ def run_clique6(args):
     per_launch_ms = st["ms"] / max(st["launches"], 1)
     clk_now = clk.summary()
     ipeak = issue_peak(clk_now["sm_mhz"] or 2032.0)
-    cnt = counters_for("clique6-rmat20", name)
+    cnt = counters_for(case, name)
     roof = {"bound": "alu", "kernel": name, "unit": "G warp-instructions/s", "peak": ipeak,
             "peak_source": "148 SMs x 4 schedulers x 1 issue/clk x median SM clock under load",
             "achieved": None, "frac": None, "traffic": None, "kernel_digest": kernel_digest()}
     if cnt:
-        ach = cnt["inst_per_launch"] / (per_launch_ms / 1000.0) / 1e9
-        roof.update(achieved=ach, frac=ach / ipeak, traffic=cnt.get("dram_bytes_per_launch"))
-    line = {"workload": CLIQUE6_WORKLOAD, "metric": "6-cliques counted per second", "value": counts[0] / (ms / 1000.0),
-            "unit": "cliques/s (6-cliques)", "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
-            "step_ms": step_ms, "counts": {"6-clique": counts[0]}, "dtype": "u64", "data": "synthetic",
-            "config": {"l2": "flushed between steps (512 MB write)"},
-            "e2e": {"value": counts[0] / e2e_s, "unit": "cliques/s (6-cliques)",
-                    "h2d_bytes_per_step": g.rowptr.nbytes + g.col.nbytes, "d2h_bytes_per_step": 8, "seconds": e2e_s},
+        # counters summed over the kernel's launches in one step (one per k)
+        kms = prof[name]["ms"] / args.steps
+        ach = cnt["inst_per_step"] / (kms / 1000.0) / 1e9
+        roof.update(achieved=ach, frac=ach / ipeak, traffic=cnt.get("dram_bytes_per_step"),
+                    traffic_note="DRAM bytes per step of this kernel (all its launches)")
+    unit = "cliques/s (" + ", ".join(f"{k}-cliques" for k in ks) + ")"
+    line = {"workload": workload, "metric": unit.split(" (")[0] + " counted per second", "value": total / (ms / 1000.0),
+            "unit": unit, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+            "step_ms": step_ms, "counts": {f"{k}-clique": c for k, c in zip(ks, counts)}, "dtype": "u64",
+            "data": "synthetic", "config": {"l2": "flushed between steps (512 MB write)"},
+            "e2e": {"value": total / e2e_s, "unit": unit, "h2d_bytes_per_step": g.rowptr.nbytes + g.col.nbytes,
+                    "d2h_bytes_per_step": 8 * len(ks), "seconds": e2e_s},
             "gpu_launches": launches, "roofline": roof, "clocks": clk_now,
             "kernels": {k: {"launches": v["launches"], "ms_per_launch": v["ms"] / max(v["launches"], 1)}
                         for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_k6(g)
+        line["cpu_baseline"] = cpu_baseline_large_k(g, ks, unit)
     G.close()
     return line
 
 
-def cpu_baseline_k6(g, seconds_target=15.0):
-    """The oracle on a bounded root sample of the 6-clique workload (ids are permuted: a random sample)."""
+def cpu_baseline_large_k(g, ks, unit, seconds_target=15.0):
+    """The oracle on a bounded root sample of the same workload (ids are permuted: a random sample)."""
     import oracle as O
     lo, hi = 0, 256
     t0 = time.perf_counter()
-    c6 = O.cliques(g, 6, lo, hi)
+    cs = [O.cliques(g, k, lo, hi) for k in ks]
     dt = time.perf_counter() - t0
     if dt < seconds_target / 4:
         hi = min(g.n, int(hi * seconds_target / max(dt, 1e-3)))
         t0 = time.perf_counter()
-        c6 = O.cliques(g, 6, lo, hi)
+        cs = [O.cliques(g, k, lo, hi) for k in ks]
         dt = time.perf_counter() - t0
-    return {"value": c6 / dt, "unit": "cliques/s (6-cliques)", "cores": 1, "kind": "oracle",
-            "sample": f"roots with id in [{lo}, {hi}) of {g.n}; 6-CL single-threaded, {dt:.1f} s, count {c6}"}
+    return {"value": sum(cs) / dt, "unit": unit, "cores": 1, "kind": "oracle",
+            "sample": f"roots with id in [{lo}, {hi}) of {g.n}; single-threaded, {dt:.1f} s, counts {cs}"}
 
 
 TC_WORKLOAD = "triangle counting, R-MAT scale 14 (16,384 vertices), edge factor 16, (0.57,0.19,0.19,0.05), seed 1"
@@ -737,7 +749,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["cliques", "clique6", "batched", "served", "sl", "tc"], default="cliques")
+    ap.add_argument("--workload", choices=["cliques", "clique6", "clique789", "batched", "served", "sl", "tc"],
+                    default="cliques")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-grace", type=float, default=10.0)
@@ -759,7 +772,14 @@ def main():
         print(json.dumps(run_tc(args)), flush=True)
         return 0
     if args.workload == "clique6":
-        print(json.dumps(run_clique6(args)), flush=True)
+        from paper_2011_03135_b300 import graphgen as gg
+        print(json.dumps(run_large_k(args, CLIQUE6_WORKLOAD, gg.workload_clique6_rmat20(), (6,), "clique6-rmat20")),
+              flush=True)
+        return 0
+    if args.workload == "clique789":
+        from paper_2011_03135_b300 import graphgen as gg
+        print(json.dumps(run_large_k(args, CLIQUE789_WORKLOAD, gg.workload_clique789_chung_lu1m(), (7, 8, 9),
+                                     "clique789-cl1m")), flush=True)
         return 0
     return run_ours(args)
 

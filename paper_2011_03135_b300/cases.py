@@ -16,6 +16,8 @@ CASES = {
     "clique-rmat20": ("rmat20", "clique45"),
     "clique-rmat21": ("rmat21", "clique45"),
     "clique6-rmat20": ("rmat20", "clique6"),
+    "clique789-cl1m": ("chunglu1m", "clique789"),
+    "clique7-rmat16": ("rmat16", "clique7"),
     "tc-rmat14": ("rmat14", "tc"),
     "motif4-rmat18": ("rmat18", "motif4"),
     "sl-chunglu1m": ("chunglu1m", "sl"),
@@ -31,10 +33,12 @@ def _graph(name):
         return gg.workload_clique_rmat21()
     if name == "rmat14":
         return gg.workload_tc_rmat14()
+    if name == "rmat16":
+        return gg.rmat(16, 16.0, seed=2)
     if name == "rmat18":
         return gg.rmat(18, 16.0, seed=2)
     if name == "chunglu1m":
-        return gg.chung_lu(1 << 20, 24.0, 2.1, seed=3)
+        return gg.workload_clique789_chung_lu1m()
     if name == "chunglu4m":
         return gg.workload_sl_chung_lu4m()
     raise ValueError(name)
@@ -46,6 +50,10 @@ def _patterns(gpm, name):
         return [gpm.Pattern.clique(4), gpm.Pattern.clique(5)]
     if name == "clique6":
         return [gpm.Pattern.clique(6)]
+    if name == "clique789":
+        return [7, 8, 9]
+    if name == "clique7":
+        return [7]
     if name == "tc":
         return [gpm.Pattern.clique(3)]
     if name == "motif4":
@@ -77,7 +85,7 @@ def main():
         G.reset()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        out = gpm.count(G, pats)
+        out = [gpm.count_cliques(G, k) for k in pats] if isinstance(pats[0], int) else gpm.count(G, pats)
         dt = time.perf_counter() - t0
     print(json.dumps({"case": a.case, "n": g.n, "m": g.m, "counts": out, "last_seconds": dt}))
     G.close()

@@ -220,6 +220,11 @@ def workload_clique6_rmat20() -> Graph:
     return rmat(20, 16.0, (0.57, 0.19, 0.19, 0.05), seed=2)
 
 
+def workload_clique789_chung_lu1m() -> Graph:
+    """Large-k clique input (k = 7, 8, 9): Chung-Lu, 1,048,576 vertices, mean degree 24, exponent 2.1, seed 3."""
+    return chung_lu(1 << 20, 24.0, 2.1, seed=3)
+
+
 def workload_sl_chung_lu4m() -> Graph:
     """Subgraph-listing input: Chung-Lu, 4,194,304 vertices, mean degree 24, exponent 2.1, seed 3."""
     return chung_lu(1 << 22, 24.0, 2.1, seed=3)

@@ -326,6 +326,25 @@ def test_fullsize_clique6_rmat20(gpm):
     G.close()
 
 
+def test_fullsize_clique789_chunglu1m(gpm):
+    # the k = 7..9 workload as bench.py counts it (gpm_count_cliques): a root
+    # range, the ragged tail, the lightest root of the 129..384 out-degree class
+    # and the heaviest root against the oracle; the total against a partition
+    g = gg.workload_clique789_chung_lu1m()
+    G = gpm.Graph.from_host(g)
+    od = O.out_degrees(g)
+    lo_class = np.nonzero(od > 128)[0]
+    v_lo = int(lo_class[np.argmin(od[lo_class])])
+    v_max = int(np.argmax(od))
+    for lo, hi in [(0, 600), (g.n - 7, g.n), (v_lo, v_lo + 1), (v_max, v_max + 1)]:
+        assert [gpm.count_cliques(G, k, lo, hi) for k in (7, 8, 9)] == [O.cliques(g, k, lo, hi) for k in (7, 8, 9)], \
+            (lo, hi)
+    cuts = [0, g.n // 2, g.n // 2 + 1, g.n]
+    for k in (7, 9):
+        assert sum(gpm.count_cliques(G, k, a, b) for a, b in zip(cuts[:-1], cuts[1:])) == gpm.count_cliques(G, k)
+    G.close()
+
+
 def test_fullsize_sl_chunglu4m(gpm):
     g = gg.workload_sl_chung_lu4m()
     gold = _golden().get("sl_chunglu4m", {})
