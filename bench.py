@@ -143,17 +143,17 @@ def clique_pass_bytes(g, opts):
 # csrc/lg_device.cuh + csrc/clique.cu); a stale entry is ignored.
 NCU_COUNTERS = {
     "clique-rmat21": {
-        "lg_cta_hi": {"digest": "1b388c324607b5fe", "inst_per_launch": 151171162061,
-                      "dram_bytes_per_launch": 28381696 + 2816, "ncu_ms": 183.561},
+        "lg_cta_hi": {"digest": "f565272433abcc2f", "inst_per_launch": 151169580694,
+                      "dram_bytes_per_launch": 28267008 + 4608, "ncu_ms": 184.415},
     },
     "clique6-rmat20": {
-        "lg_cta_hi": {"digest": "1b388c324607b5fe", "inst_per_step": 1631591263842,
-                      "dram_bytes_per_step": 13099264, "ncu_ms": 1676.886},
+        "lg_cta_hi": {"digest": "f565272433abcc2f", "inst_per_step": 1638151535205,
+                      "dram_bytes_per_step": 13153024, "ncu_ms": 1689.476},
     },
     # three launches per step (k = 7, 8, 9), summed
     "clique789-cl1m": {
-        "lg_cta_lo": {"digest": "1b388c324607b5fe", "inst_per_step": 19988345607 + 62451078763 + 192306344749,
-                      "dram_bytes_per_step": 6905344 + 6651648 + 6982656, "ncu_ms": 41.100 + 160.195 + 622.944},
+        "lg_cta_lo": {"digest": "f565272433abcc2f", "inst_per_step": 21389875939 + 63809099464 + 189284979075,
+                      "dram_bytes_per_step": 6645504 + 6878464 + 6976256, "ncu_ms": 34.498 + 120.533 + 403.512},
     },
 }
 

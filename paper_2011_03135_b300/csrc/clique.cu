@@ -50,6 +50,7 @@ struct LGArgs {
   uint32_t *t_edge;         // scatter mode
   uint32_t *pool;           // global-memory slots (XL class)
   uint64_t slot_words;
+  uint32_t slices;          // CTAs per root (k >= 7: a root's units are split over them)
   unsigned int *status;
 };
 
@@ -128,13 +129,13 @@ __global__ void __launch_bounds__(THREADS) lg_cta_kernel(LGArgs a, uint32_t maxd
     __syncthreads();
     const uint32_t task = s_task;
     __syncthreads();
-    if (task >= a.ntasks) break;
-    const uint32_t u = a.tasks[task];
+    if (task >= a.ntasks * a.slices) break;
+    const uint32_t u = a.tasks[task / a.slices];
     if (u < a.root_lo || u >= a.root_hi) continue;
     const uint32_t d = (uint32_t)(a.drow[u + 1] - a.drow[u]);
     if (d < 2 || d > maxd) continue;
     gpm_dev::lg_root_cta<G, KMAX, SCATTER, kNwl>(a.drow, a.dcol, a.t_edge, u, maxd, a.W, base, a3, a4, a5, a6,
-                                                 nest, big_cap, a.deg, wcap, gen);
+                                                 nest, big_cap, a.deg, wcap, gen, task % a.slices, a.slices);
   }
   flush_acc(a, a3, a4, a5, a6, KMAX);
 }
@@ -204,7 +205,7 @@ int launch_cta_t(const LGArgs &a, uint32_t maxd, int blocks_cap, int device, cud
   GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem));
   if (per_sm < 1) per_sm = 1;
   int blocks = gpm_num_sms(device) * per_sm;
-  blocks = std::max(1, std::min<int>(blocks, (int)a.ntasks));
+  blocks = std::max(1, std::min<int>(blocks, (int)(a.ntasks * a.slices)));
   if (blocks_cap > 0) blocks = std::min(blocks, blocks_cap);
   GPM_LAUNCH(name ? name : (GLOBAL ? "lg_cta_global" : "lg_cta"), st,
              kern<<<blocks, THREADS, smem, st>>>(a, maxd, big_cap, wcap));
@@ -327,6 +328,7 @@ int gpm_launch_cliques(gpm_graph *g, int kmax, bool scatter, uint32_t root_lo, u
   unsigned int *queues = reinterpret_cast<unsigned int *>(g->work + WK_QUEUE0);
   GPM_CUDA(cudaMemsetAsync(queues, 0, 8 * sizeof(unsigned int), st));
   LGArgs a{};
+  a.slices = kmax >= 7 ? 4u : 1u;
   a.drow = g->drow;
   a.dcol = g->dcol;
   a.deg = g->deg;
