@@ -52,6 +52,17 @@ def test_version_and_errors_without_gpu(lib):
     assert e.value.name == "K_TOO_LARGE"
 
 
+def test_count_cliques_validates_before_any_device_work(lib):
+    # a null graph handle and a null output are rejected on the host
+    so = ctypes.CDLL(lib.LIB_PATH)
+    so.gpm_count_cliques.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                     ctypes.c_void_p, ctypes.c_void_p]
+    out = ctypes.c_uint64(0)
+    invalid = so.gpm_count_cliques(None, 7, 0, 0, ctypes.byref(out), None)
+    assert invalid != 0
+    assert so.gpm_count_cliques(None, 7, 0, 0, None, None) == invalid
+
+
 @pytest.mark.parametrize("idx", range(6))
 def test_planner_motif4(lib, idx):
     pats = lib.Pattern.motifs(4)
