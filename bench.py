@@ -594,17 +594,20 @@ def run_reference(args):
     from paper_2011_03135_b300 import graphgen as gg
     import oracle as O
     g = gg.workload_clique_rmat21()
-    # each step: the oracle on a fixed root sample sized so that the whole run
-    # takes about 150 s (calibrated on a short first sample)
-    lo, hi = 0, 1024
-    t0 = time.perf_counter()
-    O.cliques(g, 4, lo, hi)
-    O.cliques(g, 5, lo, hi)
-    dt = time.perf_counter() - t0
-    budget = 150.0 / max(1, args.steps + args.warmup)
-    hi = max(256, min(g.n, int(hi * budget / max(dt, 1e-3))))
-    for _ in range(args.warmup):
-        O.cliques(g, 4, lo, min(hi, 256))
+    # each step: the oracle on a fixed root sample [0, hi) sized so that the
+    # whole run takes about 150 s. Vertex ids are a random permutation, so a
+    # prefix of ids is a random sample; hi grows by half until one sample takes at
+    # least half a step's share (these trials are the warm-up)
+    lo, hi = 0, 256
+    step_budget = 150.0 / max(1, args.steps + args.warmup)
+    while True:
+        t0 = time.perf_counter()
+        O.cliques(g, 4, lo, hi)
+        O.cliques(g, 5, lo, hi)
+        dt = time.perf_counter() - t0
+        if dt >= step_budget / 2 or hi >= g.n:
+            break
+        hi = min(g.n, hi + hi // 2)
     times, total = [], 0
     for _ in range(args.steps):
         t0 = time.perf_counter()
