@@ -223,7 +223,7 @@ int gpm_count_cliques(gpm_graph_t g, uint32_t k, uint32_t root_lo, uint32_t root
  * subgraph. Which min(total, cap) embeddings are written is unspecified.
  *   *written : number of tuples written = min(total, cap)
  *   *total   : exact number of embeddings (= gpm_count of p)
- * Supported: edge-induced diamond and 4-cycle, k-cliques k = 3..5.
+ * Supported: edge-induced diamond and 4-cycle, k-cliques k = 3..8.
  * Synchronises `stream`.
  */
 int gpm_list(gpm_graph_t g, gpm_pattern_t p, uint32_t *buf, uint64_t cap, uint64_t *written, uint64_t *total,

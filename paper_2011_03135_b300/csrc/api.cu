@@ -485,11 +485,11 @@ int gpm_list(gpm_graph_t g, gpm_pattern_t p, uint32_t *buf, uint64_t cap, uint64
              void *stream) {
   GPM_TRY(check_graph(g));
   if (!p || !written || !total || (cap && !buf)) return gpm_fail(GPM_E_INVALID_ARG, "null argument");
-  const bool clique = p->cls == PC_CLIQUE && p->k >= 3 && p->k <= 5;
+  const bool clique = p->cls == PC_CLIQUE && p->k >= 3 && p->k <= 8;
   const bool sl = !p->induced && (p->cls == PC_DIAMOND || p->cls == PC_CYCLE4);
   if (!clique && !sl)
     return gpm_fail(GPM_E_UNSUPPORTED, "listing is implemented for the edge-induced diamond and 4-cycle and for "
-                                       "k-cliques with k = 3..5");
+                                       "k-cliques with k = 3..8");
   std::lock_guard<std::mutex> lk(g->mu);
   cudaStream_t st = as_stream(stream);
   GPM_TRY(prepare_locked(g, st));

@@ -15,7 +15,8 @@
 //            Guided Search (Matching Order)", the order the paper selects)
 //   4-cycle  (v0, w, x, y): cycle v0-x-w-y-v0, v0 the smallest id, w opposite
 //            to v0, x < y
-//   k-clique ascending ids
+//   k-clique ascending ids (k = 3..5 with unrolled levels, 6..8 with a
+//            per-warp stack of candidate levels)
 #include <algorithm>
 
 #include "gpm_internal.h"
@@ -218,6 +219,68 @@ __global__ void list_cliques_kernel(const uint64_t *__restrict__ drow, const uin
   }
 }
 
+// k-cliques, k = 6..8: the same per-root search with the candidate sets of
+// all k - 2 levels on a per-warp stack in scratch, walked depth first by the
+// whole warp (the position in every level is warp-uniform). Level l holds the
+// candidates for the next vertex after u, x and the picks of levels 1..l-1;
+// the last level is written out.
+__global__ void list_cliques_deep_kernel(const uint64_t *__restrict__ drow, const uint32_t *__restrict__ dcol,
+                                         uint32_t n, int k, uint32_t *__restrict__ buf, uint64_t cap,
+                                         unsigned long long *counter, uint32_t *__restrict__ scratch,
+                                         uint64_t level_words) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  uint32_t *stack = scratch + warp * (uint64_t)(k - 2) * level_words;
+  const int last = k - 2;
+  for (uint64_t u = warp; u < n; u += nwarps) {
+    const uint64_t ub = drow[u], ue = drow[u + 1];
+    if (ue - ub < (uint64_t)(k - 1)) continue;
+    for (uint64_t e = ub; e < ue; ++e) {
+      if (stop_now(counter, cap)) return;
+      const uint32_t x = dcol[e];
+      uint32_t cnt[8], pos[8], pick[8];
+      cnt[1] = warp_intersect(dcol + ub, ue - ub, dcol + drow[x], drow[x + 1] - drow[x], stack);
+      pos[1] = 0;
+      int l = 1;
+      while (l >= 1) {
+        const uint32_t *Cl = stack + (uint64_t)(l - 1) * level_words;
+        if (l == last) {
+          const uint32_t c = cnt[l];
+          if (c) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(counter, (unsigned long long)c);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            for (uint32_t i = lane; i < c; i += 32)
+              if (base + i < cap) {
+                uint32_t t[8];
+                t[0] = (uint32_t)u;
+                t[1] = x;
+                for (int q = 1; q < l; ++q) t[1 + q] = pick[q];
+                t[k - 1] = Cl[i];
+                sort_small(t, k);
+                for (int q = 0; q < k; ++q) buf[(base + i) * k + q] = t[q];
+              }
+          }
+          --l;
+          continue;
+        }
+        if (pos[l] >= cnt[l]) {
+          --l;
+          continue;
+        }
+        if (stop_now(counter, cap)) return;
+        const uint32_t y = Cl[pos[l]++];
+        pick[l] = y;
+        cnt[l + 1] = warp_intersect(Cl, cnt[l], dcol + drow[y], drow[y + 1] - drow[y],
+                                    stack + (uint64_t)l * level_words);
+        pos[l + 1] = 0;
+        ++l;
+      }
+    }
+  }
+}
+
 struct Perm8 {
   uint32_t p[8];
 };
@@ -273,11 +336,20 @@ int gpm_launch_list_cycle4(gpm_graph *g, uint32_t *buf, uint64_t cap, unsigned l
 
 int gpm_launch_list_cliques(gpm_graph *g, int k, uint32_t *buf, uint64_t cap, unsigned long long *counter,
                             cudaStream_t st) {
-  if (k < 3 || k > 5) return gpm_fail(GPM_E_UNSUPPORTED, "clique listing supports k = 3..5");
+  if (k < 3 || k > 8) return gpm_fail(GPM_E_UNSUPPORTED, "clique listing supports k = 3..8");
   int blocks;
   listing_grid(g, &blocks);
   const uint64_t warps = (uint64_t)blocks * 8;
   const uint64_t words = std::max<uint64_t>(g->max_outdeg, 1);
+  if (k >= 6) {
+    GPM_TRY(ensure_list_scratch(g, warps * (uint64_t)(k - 2) * words * 4));
+    if (g->n)
+      GPM_LAUNCH("list_cliques_deep_kernel", st,
+                 list_cliques_deep_kernel<<<blocks, 256, 0, st>>>(g->drow, g->dcol, g->n, k, buf, cap, counter,
+                                                                  g->list_scratch, words));
+    GPM_CUDA(cudaGetLastError());
+    return GPM_OK;
+  }
   GPM_TRY(ensure_list_scratch(g, warps * 3 * words * 4));
   if (g->n) GPM_LAUNCH("list_cliques_kernel", st, list_cliques_kernel<<<blocks, 256, 0, st>>>(g->drow, g->dcol, g->n, k, buf, cap, counter, g->list_scratch,
                                                         words));

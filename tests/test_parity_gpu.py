@@ -170,6 +170,7 @@ LIST_PATTERNS = [
     (O.pattern(4, [(2, 3), (2, 0), (2, 1), (3, 0), (3, 1)]), False),   # diamond, other numbering
     (O.pattern(4, [(0, 1), (1, 2), (2, 3), (3, 0)]), False),           # 4-cycle, other numbering
     (O.clique_pattern(3), True), (O.clique_pattern(4), True), (O.clique_pattern(5), True),
+    (O.clique_pattern(6), True), (O.clique_pattern(7), True), (O.clique_pattern(8), True),
 ]
 
 
@@ -492,3 +493,22 @@ def test_count_cliques_ranges_and_small_k(gpm):
     with pytest.raises(gpm.GpmError):
         gpm.count_cliques(G, 7, 5, 3)
     G.close()
+
+
+def test_listing_deep_cliques_dense(gpm):
+    # k = 6..8 listing on graphs dense enough to hold many of them: complete
+    # graphs (C(n, k) tuples), a complete multipartite graph and a dense G(n, p)
+    for g in [gg.complete(12), gg.complete_multipartite([2, 3, 1, 2, 2, 1, 3, 2, 1]), gg.random_small(20, 0.7, 23)]:
+        G = gpm.Graph.from_host(g)
+        for k in (6, 7, 8):
+            adj = O.clique_pattern(k)
+            P = gpm.Pattern.spec(adj, induced=True)
+            want = O.cliques(g, k)  # distinct valid cliques, as many as the oracle counts: all of them
+            tuples, total = gpm.list_embeddings(G, P, cap=want + 3)
+            assert total == want == len(tuples), (g.name, k)
+            assert len(_check_tuples(g, adj, P.info(), tuples)) == want
+            if total > 1:
+                part, total2 = gpm.list_embeddings(G, P, cap=total // 2)
+                assert total2 == total and len(part) == total // 2
+                _check_tuples(g, adj, P.info(), part)
+        G.close()
