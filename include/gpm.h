@@ -229,6 +229,18 @@ int gpm_count_cliques(gpm_graph_t g, uint32_t k, uint32_t root_lo, uint32_t root
 int gpm_list(gpm_graph_t g, gpm_pattern_t p, uint32_t *buf, uint64_t cap, uint64_t *written, uint64_t *total,
              void *stream);
 
+/*
+ * Existence query (Section 3.1: the optional early-termination condition of
+ * the API, used for pattern existence): *found = 1 if g holds at least one
+ * embedding of p, else 0. Runs the listing search with room for one match and
+ * no counting pass, so every warp stops at its next check once a match is
+ * written. witness (host uint32[k], may be NULL): on *found = 1, one
+ * embedding in PATTERN vertex order, as gpm_list writes it.
+ * Supported: as gpm_list (edge-induced diamond and 4-cycle, k-cliques k = 3..8).
+ * Synchronises `stream`.
+ */
+int gpm_exists(gpm_graph_t g, gpm_pattern_t p, int *found, uint32_t *witness, void *stream);
+
 /* ---------------- batched form ---------------- */
 
 #define GPM_QUERY_MOTIF3 3u  /* 2 induced counts: wedge, triangle */

@@ -481,6 +481,37 @@ int gpm_count_cliques(gpm_graph_t g, uint32_t k, uint32_t root_lo, uint32_t root
   return GPM_OK;
 }
 
+int gpm_exists(gpm_graph_t g, gpm_pattern_t p, int *found, uint32_t *witness, void *stream) {
+  GPM_TRY(check_graph(g));
+  if (!p || !found) return gpm_fail(GPM_E_INVALID_ARG, "null argument");
+  const bool clique = p->cls == PC_CLIQUE && p->k >= 3 && p->k <= 8;
+  const bool sl = !p->induced && (p->cls == PC_DIAMOND || p->cls == PC_CYCLE4);
+  if (!clique && !sl)
+    return gpm_fail(GPM_E_UNSUPPORTED, "existence queries are implemented for the edge-induced diamond and 4-cycle "
+                                       "and for k-cliques with k = 3..8");
+  std::lock_guard<std::mutex> lk(g->mu);
+  cudaStream_t st = as_stream(stream);
+  GPM_TRY(prepare_locked(g, st));
+  // the listing kernels with room for one match: every warp stops at its next
+  // check once the slot counter is non-zero (no counting pass)
+  uint32_t *dbuf = reinterpret_cast<uint32_t *>(out_of(g));  // 128 bytes, 16-byte aligned
+  unsigned long long *counter = reinterpret_cast<unsigned long long *>(g->work + WK_MISC);
+  GPM_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+  const uint32_t k = p->k;
+  if (p->cls == PC_DIAMOND) GPM_TRY(gpm_launch_list_diamond(g, dbuf, 1, counter, st));
+  else if (p->cls == PC_CYCLE4) GPM_TRY(gpm_launch_list_cycle4(g, dbuf, 1, counter, st));
+  else GPM_TRY(gpm_launch_list_cliques(g, (int)k, dbuf, 1, counter, st));
+  unsigned long long c = 0;
+  uint32_t t[8] = {0};
+  GPM_CUDA(cudaMemcpyAsync(&c, counter, sizeof(c), cudaMemcpyDeviceToHost, st));
+  GPM_CUDA(cudaMemcpyAsync(t, dbuf, k * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  GPM_CUDA(cudaStreamSynchronize(st));
+  *found = c > 0 ? 1 : 0;
+  if (witness && c > 0)
+    for (uint32_t j = 0; j < k; ++j) witness[p->tmpl_to_pat[j]] = t[j];  // template order -> pattern numbering
+  return GPM_OK;
+}
+
 int gpm_list(gpm_graph_t g, gpm_pattern_t p, uint32_t *buf, uint64_t cap, uint64_t *written, uint64_t *total,
              void *stream) {
   GPM_TRY(check_graph(g));

@@ -96,6 +96,7 @@ _SIGS = {
     "gpm_count_async": [_vp, _vp, _u32, _vp, _vp],
     "gpm_count_roots": [_vp, _vp, _u32, _u32, _u32, _vp, _vp],
     "gpm_count_cliques": [_vp, _u32, _u32, _u32, _vp, _vp],
+    "gpm_exists": [_vp, _vp, _vp, _vp, _vp],
     "gpm_list": [_vp, _vp, _vp, _u64, _U64P, _U64P, _vp],
     "gpm_graph_reset": [_vp],
     "gpm_profile_enable": [_i],
@@ -348,6 +349,16 @@ def count_cliques(graph: Graph, k: int, root_lo: int = 0, root_hi: int | None = 
     hi = graph.n if root_hi is None else root_hi
     _check(_lib.gpm_count_cliques(graph.handle, k, root_lo, hi, ctypes.byref(out), _stream(stream)))
     return int(out.value)
+
+
+def exists(graph: Graph, pattern: Pattern, stream=None):
+    """(found, witness): whether the graph holds an embedding of the pattern,
+    and one such embedding (pattern vertex order) or None; stops at the first match."""
+    k = pattern.info()["k"]
+    found = ctypes.c_int(0)
+    w = np.zeros(k, dtype=np.uint32)
+    _check(_lib.gpm_exists(graph.handle, pattern.handle, ctypes.byref(found), w.ctypes.data, _stream(stream)))
+    return bool(found.value), (w if found.value else None)
 
 
 def list_embeddings(graph: Graph, pattern: Pattern, cap: int, out=None, stream=None):

@@ -512,3 +512,27 @@ def test_listing_deep_cliques_dense(gpm):
                 assert total2 == total and len(part) == total // 2
                 _check_tuples(g, adj, P.info(), part)
         G.close()
+
+
+def test_exists_matches_oracle_counts(gpm):
+    # the existence query (early exit at the first match): found exactly when
+    # the oracle's count is non-zero; the witness is an embedding of the pattern
+    graphs = SMALL[:8] + SMALL[12:20] + [gg.path(9), gg.star(7), gg.cycle(7), gg.complete_multipartite([3, 3, 3]),
+                                         gg.rmat(10, 16.0, seed=21), gg.chung_lu(5000, 16.0, 2.1, seed=24)]
+    pats = [(O.clique_pattern(k), True) for k in range(3, 9)] + LIST_PATTERNS[:4]
+    for g in graphs:
+        G = gpm.Graph.from_host(g)
+        for adj, induced in pats:
+            P = gpm.Pattern.spec(adj, induced=induced)
+            k = adj.shape[0]
+            nedges = int(np.triu(adj).sum())
+            want = O.cliques(g, k) if induced else (O.diamonds(g) if nedges == 5 else O.cycles4(g))
+            found, w = gpm.exists(G, P)
+            assert found == (want > 0), (g.name, k)
+            if found:
+                assert len(set(w.tolist())) == k
+                for i in range(k):
+                    for j in range(i + 1, k):
+                        if adj[i, j]:
+                            assert _adjacent(g, w[i], w[j]), (g.name, w, i, j)
+        G.close()
