@@ -63,6 +63,8 @@ def _load():
                 "orc_out_degrees": ([u32, vp, vp, vp], ctypes.c_int),
                 "orc_cliques": ([u32, vp, vp, u32, u32, u32, U64P], ctypes.c_int),
                 "orc_triangles": ([u32, vp, vp, U64P], ctypes.c_int),
+                "orc_core_numbers": ([u32, vp, vp, vp], ctypes.c_int),
+                "orc_cliques_keyed": ([u32, vp, vp, vp, u32, u32, u32, U64P], ctypes.c_int),
                 "orc_diamonds": ([u32, vp, vp, u32, u32, U64P], ctypes.c_int),
                 "orc_cycles4": ([u32, vp, vp, u32, u32, U64P], ctypes.c_int),
                 "orc_noninduced_terms": ([u32, vp, vp, u32, vp], ctypes.c_int),
@@ -175,6 +177,25 @@ def cliques(g, k: int, root_lo: int = 0, root_hi: int | None = None) -> int:
     out = ctypes.c_uint64(0)
     _check(_load().orc_cliques(g.n, rp.ctypes.data, col.ctypes.data, k, root_lo, hi, ctypes.byref(out)),
            "cliques")
+    return int(out.value)
+
+
+def core_numbers(g) -> np.ndarray:
+    """Core number of every vertex (the key of the core value based orientation)."""
+    rp, col = _csr(g)
+    out = np.zeros(max(g.n, 1), dtype=np.uint32)
+    _check(_load().orc_core_numbers(g.n, rp.ctypes.data, col.ctypes.data, out.ctypes.data), "core_numbers")
+    return out[: g.n]
+
+
+def cliques_keyed(g, key, k: int, root_lo: int = 0, root_hi: int | None = None) -> int:
+    """k-cliques whose first vertex in the order (key, id) lies in [root_lo, root_hi)."""
+    rp, col = _csr(g)
+    key = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    hi = g.n if root_hi is None else root_hi
+    out = ctypes.c_uint64(0)
+    _check(_load().orc_cliques_keyed(g.n, rp.ctypes.data, col.ctypes.data, key.ctypes.data, k, root_lo, hi,
+                                     ctypes.byref(out)), "cliques_keyed")
     return int(out.value)
 
 

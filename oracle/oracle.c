@@ -383,6 +383,113 @@ int orc_cliques(uint32_t n, const uint64_t *rp, const uint32_t *col, uint32_t k,
   return ORC_OK;
 }
 
+/* Core numbers (appendix "Orientation (Total Order)", the core value based
+ * order): core[v] is the largest c such that v belongs to a subgraph whose
+ * every vertex has degree >= c in it. Textbook peeling with a bucket queue
+ * (Batagelj and Zaversnik 2003): take a vertex of minimum remaining degree,
+ * fix its core number, lower the remaining degree of its neighbours that
+ * are still present (never below the current core number). */
+int orc_core_numbers(uint32_t n, const uint64_t *rp, const uint32_t *col, uint32_t *core) {
+  uint32_t md = 0;
+  for (uint32_t v = 0; v < n; ++v)
+    if (deg_of(rp, v) > md) md = (uint32_t)deg_of(rp, v);
+  uint32_t *d = (uint32_t *)malloc(((size_t)n + 1) * sizeof(uint32_t));
+  uint32_t *bin = (uint32_t *)calloc((size_t)md + 2, sizeof(uint32_t));
+  uint32_t *pos = (uint32_t *)malloc(((size_t)n + 1) * sizeof(uint32_t));
+  uint32_t *vert = (uint32_t *)malloc(((size_t)n + 1) * sizeof(uint32_t));
+  if (!d || !bin || !pos || !vert) {
+    free(d), free(bin), free(pos), free(vert);
+    return ORC_E_OOM;
+  }
+  for (uint32_t v = 0; v < n; ++v) {
+    d[v] = (uint32_t)deg_of(rp, v);
+    bin[d[v]]++;
+  }
+  uint32_t start = 0; /* bin[x] = first slot of degree x in vert */
+  for (uint32_t x = 0; x <= md; ++x) {
+    uint32_t c = bin[x];
+    bin[x] = start;
+    start += c;
+  }
+  for (uint32_t v = 0; v < n; ++v) {
+    pos[v] = bin[d[v]];
+    vert[pos[v]] = v;
+    bin[d[v]]++;
+  }
+  for (uint32_t x = md; x > 0; --x) bin[x] = bin[x - 1];
+  bin[0] = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    uint32_t v = vert[i];
+    for (uint64_t e = rp[v]; e < rp[v + 1]; ++e) {
+      uint32_t u = col[e];
+      if (d[u] > d[v]) {
+        /* move u to the front of its bucket, then one bucket down */
+        uint32_t du = d[u], pu = pos[u], pw = bin[du], w = vert[pw];
+        if (u != w) {
+          pos[u] = pw;
+          vert[pu] = w;
+          pos[w] = pu;
+          vert[pw] = u;
+        }
+        bin[du]++;
+        d[u]--;
+      }
+    }
+  }
+  for (uint32_t v = 0; v < n; ++v) core[v] = d[v];
+  free(d), free(bin), free(pos), free(vert);
+  return ORC_OK;
+}
+
+/* k-cliques whose first vertex in the order (key, id) lies in [root_lo,
+ * root_hi): the same search over the orientation v -> w iff (key v, v) <
+ * (key w, w). With key = the core numbers this is the core value based
+ * orientation of the appendix; the total over all roots does not depend on
+ * the order. */
+int orc_cliques_keyed(uint32_t n, const uint64_t *rp, const uint32_t *col, const uint32_t *key, uint32_t k,
+                      uint32_t root_lo, uint32_t root_hi, uint64_t *out) {
+  if (k < 2 || k > 16 || root_lo > root_hi || root_hi > n) return ORC_E_ARG;
+  out_csr o;
+  o.rp = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
+  if (!o.rp) return ORC_E_OOM;
+  for (uint32_t v = 0; v < n; ++v) {
+    uint64_t c = 0;
+    for (uint64_t e = rp[v]; e < rp[v + 1]; ++e) {
+      uint32_t w = col[e];
+      c += key[v] < key[w] || (key[v] == key[w] && v < w);
+    }
+    o.rp[v + 1] = o.rp[v] + c;
+  }
+  o.col = (uint32_t *)malloc((o.rp[n] ? o.rp[n] : 1) * sizeof(uint32_t));
+  if (!o.col) {
+    free(o.rp);
+    return ORC_E_OOM;
+  }
+  uint64_t maxd = 0;
+  for (uint32_t v = 0; v < n; ++v) {
+    uint64_t w = o.rp[v];
+    for (uint64_t e = rp[v]; e < rp[v + 1]; ++e) {
+      uint32_t x = col[e];
+      if (key[v] < key[x] || (key[v] == key[x] && v < x)) o.col[w++] = x;
+    }
+    if (o.rp[v + 1] - o.rp[v] > maxd) maxd = o.rp[v + 1] - o.rp[v];
+  }
+  uint64_t stride = maxd + 1;
+  uint32_t *scratch = (uint32_t *)malloc(stride * (k + 1) * sizeof(uint32_t));
+  if (!scratch) {
+    free_out(&o);
+    return ORC_E_OOM;
+  }
+  u128 total = 0;
+  for (uint32_t u = root_lo; u < root_hi; ++u)
+    total += extend_clique(&o, o.col + o.rp[u], o.rp[u + 1] - o.rp[u], k - 1, scratch, stride);
+  free(scratch);
+  free_out(&o);
+  if (total >= U64_LIMIT) return ORC_E_OVERFLOW;
+  *out = (uint64_t)total;
+  return ORC_OK;
+}
+
 /* Triangles (Section 2, TC): 3-cliques. */
 int orc_triangles(uint32_t n, const uint64_t *rp, const uint32_t *col, uint64_t *out) {
   return orc_cliques(n, rp, col, 3, 0, n, out);

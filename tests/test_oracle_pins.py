@@ -361,3 +361,40 @@ def test_orders_satisfying_counts_permutations():
     assert O.orders_satisfying(4, []) == 24
     assert O.orders_satisfying(4, [(0, 1), (1, 2), (2, 3)]) == 1
     assert O.orders_satisfying(3, [(0, 1)]) == 3
+
+
+# ---------------- core numbers and the core value based orientation ----------------
+
+@pytest.mark.parametrize("mk", SMALL + [lambda: gg.rmat(10, 8.0, seed=5), lambda: gg.chung_lu(3000, 12.0, 2.1, seed=6),
+                                        lambda: gg.complete(7), lambda: gg.empty(4)])
+def test_core_numbers_match_networkx(mk):
+    import networkx as nx
+    g = mk()
+    G = nx.Graph()
+    G.add_nodes_from(range(g.n))
+    G.add_edges_from(g.edges().tolist())
+    want = nx.core_number(G)
+    assert O.core_numbers(g).tolist() == [want[v] for v in range(g.n)]
+
+
+@pytest.mark.parametrize("mk", SMALL[:6] + [lambda: gg.rmat(10, 16.0, seed=21)])
+def test_cliques_under_core_order(mk):
+    # the total does not depend on the order; root ranges follow the order
+    # (key, id) by the definition (brute force on the small graphs)
+    g = mk()
+    core = O.core_numbers(g)
+    for k in (3, 4, 5):
+        assert O.cliques_keyed(g, core, k) == O.cliques(g, k)
+    if g.n <= 30:
+        adj = _py_adj(g)
+        for k in (3, 4):
+            roots = [0] * g.n
+            for W in itertools.combinations(range(g.n), k):
+                if all(b in adj[a] for a, b in itertools.combinations(W, 2)):
+                    roots[min(W, key=lambda v: (int(core[v]), v))] += 1
+            cuts = [0, g.n // 3, g.n // 2, g.n]
+            assert [O.cliques_keyed(g, core, k, cuts[i], cuts[i + 1]) for i in range(3)] == \
+                [sum(roots[cuts[i]:cuts[i + 1]]) for i in range(3)]
+    # with the degrees as the key it is the degree order
+    deg = np.diff(g.rowptr).astype(np.uint32)
+    assert O.cliques_keyed(g, deg, 4, 0, g.n // 2) == O.cliques(g, 4, 0, g.n // 2)
