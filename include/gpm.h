@@ -84,9 +84,9 @@ int gpm_graph_create(const uint64_t *rowptr, const uint32_t *col, uint32_t n, ui
 int gpm_graph_destroy(gpm_graph_t g);
 
 /*
- * Build the degree-ordered orientation (appendix "Orientation (Total Order)":
- * every edge points to the endpoint of higher degree, ties to the larger id)
- * and the task lists used by the kernels. Idempotent; called implicitly by
+ * Build the orientation (appendix "Orientation (Total Order)": by default
+ * every edge points to the endpoint of higher degree, ties to the larger id;
+ * see gpm_graph_set_orientation) and the task lists used by the kernels. Idempotent; called implicitly by
  * the first count. Synchronises `stream`.
  */
 int gpm_graph_prepare(gpm_graph_t g, void *stream);
@@ -97,6 +97,29 @@ int gpm_graph_prepare(gpm_graph_t g, void *stream);
  * Used to time the whole path, orientation included, on a resident graph.
  */
 int gpm_graph_reset(gpm_graph_t g);
+
+#define GPM_ORIENT_DEGREE 0u /* edges point to the endpoint of higher degree (default) */
+#define GPM_ORIENT_CORE 1u   /* edges point to the endpoint of higher core number */
+
+/*
+ * Choose the total order of the orientation (appendix "Orientation (Total
+ * Order)": degree based, or core value based, where the core numbers take
+ * the place of the degrees; ties go to the larger id in both). Takes effect
+ * at the next prepare (the current orientation is dropped when the mode
+ * changes). Totals do not depend on the order; the root of a clique or of a
+ * diamond in gpm_count_roots / gpm_count_cliques follows it. The core order
+ * costs a k-core peel on the device at prepare time.
+ * Errors: GPM_E_INVALID_ARG for an unknown mode.
+ */
+int gpm_graph_set_orientation(gpm_graph_t g, uint32_t mode);
+
+/*
+ * Core number of every vertex (the largest c such that the vertex lies in a
+ * subgraph of minimum degree >= c), by level-synchronous k-core peeling on
+ * the device. core: uint32[n], host or device memory. Prepares the graph if
+ * needed. Synchronises `stream`.
+ */
+int gpm_graph_core_numbers(gpm_graph_t g, uint32_t *core, void *stream);
 
 typedef struct {
   uint32_t n;

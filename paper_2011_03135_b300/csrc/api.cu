@@ -43,7 +43,7 @@ void free_graph(gpm_graph *g) {
   void *ptrs[] = {g->rowptr, g->col,   g->deg,        g->drow,       g->dcol,     g->tasks,
                   g->work,   g->t_edge, g->xl_pool, g->tally_pool, g->list_scratch, g->c4_tasks, g->c4_bucket_buf,
                   g->prep_outdeg, g->prep_tiles, g->prep_keys, g->edeg, g->c4_hub_units, g->c4_hub_tally,
-                  g->c4_hub_touched, g->c4_hub_ctr};
+                  g->c4_hub_touched, g->c4_hub_ctr, g->core, g->core_work};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete g;
@@ -333,6 +333,31 @@ int gpm_graph_reset(gpm_graph_t g) {
   g->prepared = false;
   g->c4_ready = false;
   g->tune_warp_max = g->tune_cta_max = 0;
+  return GPM_OK;
+}
+
+int gpm_graph_set_orientation(gpm_graph_t g, uint32_t mode) {
+  GPM_TRY(check_graph(g));
+  if (mode != GPM_ORIENT_DEGREE && mode != GPM_ORIENT_CORE)
+    return gpm_fail(GPM_E_INVALID_ARG, "orientation must be GPM_ORIENT_DEGREE or GPM_ORIENT_CORE");
+  std::lock_guard<std::mutex> lk(g->mu);
+  if (g->orient_mode != mode) {
+    g->orient_mode = mode;
+    g->prepared = false;
+    g->tune_warp_max = g->tune_cta_max = 0;
+  }
+  return GPM_OK;
+}
+
+int gpm_graph_core_numbers(gpm_graph_t g, uint32_t *core, void *stream) {
+  GPM_TRY(check_graph(g));
+  if (!core && g->n) return gpm_fail(GPM_E_INVALID_ARG, "null argument");
+  std::lock_guard<std::mutex> lk(g->mu);
+  cudaStream_t st = as_stream(stream);
+  GPM_TRY(prepare_locked(g, st));
+  if (g->orient_mode != GPM_ORIENT_CORE) GPM_TRY(gpm_core_numbers(g, st));
+  if (g->n) GPM_CUDA(cudaMemcpyAsync(core, g->core, sizeof(uint32_t) * g->n, cudaMemcpyDefault, st));
+  GPM_CUDA(cudaStreamSynchronize(st));
   return GPM_OK;
 }
 

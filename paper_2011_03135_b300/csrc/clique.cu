@@ -331,7 +331,7 @@ int gpm_launch_cliques(gpm_graph *g, int kmax, bool scatter, uint32_t root_lo, u
   a.slices = kmax >= 7 ? 4u : 1u;
   a.drow = g->drow;
   a.dcol = g->dcol;
-  a.deg = g->deg;
+  a.deg = g->okey ? g->okey : g->deg;  // the key of the orientation order
   a.root_lo = root_lo;
   a.root_hi = root_hi;
   a.acc = acc;

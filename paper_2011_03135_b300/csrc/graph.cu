@@ -362,6 +362,124 @@ int gpm_ensure_classes(gpm_graph *g, cudaStream_t st) {
   return GPM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Core numbers by level-synchronous peeling (the core value based order of
+// the appendix "Orientation (Total Order)"). At level k every vertex still
+// present whose remaining degree is <= k gets core number k and is peeled;
+// peeling lowers the remaining degree of the neighbours still present, and a
+// neighbour whose degree drops to k joins the next frontier of the same
+// level. When a level's frontier empties, the next level is the smallest
+// remaining degree (at least k + 1).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr uint32_t kCoreUnset = 0xffffffffu;
+
+__global__ void core_init_kernel(const uint32_t *__restrict__ deg, uint32_t n, uint32_t *__restrict__ cdeg,
+                                 uint32_t *__restrict__ core) {
+  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+    cdeg[v] = deg[v];
+    core[v] = kCoreUnset;
+  }
+}
+
+// frontier of level k among the vertices still present; cnt[0] its size,
+// cnt[1] the smallest remaining degree of the vertices left out
+__global__ void core_scan_kernel(uint32_t n, uint32_t k, const uint32_t *__restrict__ cdeg, uint32_t *__restrict__ core,
+                                 uint32_t *__restrict__ frontier, uint32_t *__restrict__ cnt) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t mn = kCoreUnset;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < n; base += stride) {
+    const uint64_t v = base + threadIdx.x;
+    bool join = false;
+    if (v < n && core[v] == kCoreUnset) {
+      const uint32_t c = cdeg[v];
+      if (c <= k) {
+        core[v] = k;
+        join = true;
+      } else {
+        mn = min(mn, c);
+      }
+    }
+    const uint32_t m = __ballot_sync(0xffffffffu, join);
+    uint32_t at = 0;
+    if (m && lane == 0) at = atomicAdd(&cnt[0], (uint32_t)__popc(m));
+    at = __shfl_sync(0xffffffffu, at, 0);
+    if (join) frontier[at + __popc(m & ((1u << lane) - 1u))] = (uint32_t)v;
+  }
+  mn = __reduce_min_sync(0xffffffffu, mn);
+  if (lane == 0 && mn != kCoreUnset) atomicMin(&cnt[1], mn);
+}
+
+// one warp per peeled vertex: lower the remaining degree of its neighbours
+// still present; those that drop to k join the next frontier (claimed once)
+__global__ void core_peel_kernel(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
+                                 const uint32_t *__restrict__ fin, uint32_t nin, uint32_t k, uint32_t *__restrict__ cdeg,
+                                 uint32_t *__restrict__ core, uint32_t *__restrict__ fout, uint32_t *__restrict__ nout) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t i = warp; i < nin; i += nwarps) {
+    const uint32_t v = fin[i];
+    const uint64_t b = rowptr[v], e = rowptr[v + 1];
+    for (uint64_t j = b + lane; j < e; j += 32) {
+      const uint32_t w = col[j];
+      if (*(volatile uint32_t *)&core[w] != kCoreUnset) continue;
+      const uint32_t old = atomicSub(&cdeg[w], 1u);
+      if (old == k + 1 && atomicCAS(&core[w], kCoreUnset, k) == kCoreUnset) fout[atomicAdd(nout, 1u)] = w;
+    }
+  }
+}
+
+}  // namespace
+
+int gpm_core_numbers(gpm_graph *g, cudaStream_t st) {
+  const uint32_t n = g->n;
+  if (!g->core) GPM_TRY(gpm_graph_alloc(g, (void **)&g->core, sizeof(uint32_t) * (size_t)std::max<uint32_t>(n, 1)));
+  if (!g->core_work)
+    GPM_TRY(gpm_graph_alloc(g, (void **)&g->core_work, sizeof(uint32_t) * 3 * (size_t)std::max<uint32_t>(n, 1)));
+  if (n == 0) return GPM_OK;
+  uint32_t *cdeg = g->core_work, *fa = cdeg + n, *fb = fa + n;
+  // [0] frontier size, [1] smallest degree left out; past the two words that
+  // prepare keeps its maximum degrees in
+  uint32_t *cnt = reinterpret_cast<uint32_t *>(g->work + WK_MISC + 2);
+  const int sms = gpm_num_sms(g->device);
+  GPM_LAUNCH("core_init_kernel", st, core_init_kernel<<<sms * 4, 256, 0, st>>>(g->deg, n, cdeg, g->core));
+  GPM_CUDA(cudaGetLastError());
+  uint64_t left = n;
+  uint32_t k = 0;
+  while (left > 0) {
+    const uint32_t init[2] = {0u, kCoreUnset};
+    GPM_CUDA(cudaMemcpyAsync(cnt, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    GPM_LAUNCH("core_scan_kernel", st, core_scan_kernel<<<sms * 4, 256, 0, st>>>(n, k, cdeg, g->core, fa, cnt));
+    GPM_CUDA(cudaGetLastError());
+    uint32_t h[2];
+    GPM_CUDA(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st));
+    GPM_CUDA(cudaStreamSynchronize(st));
+    if (h[0] == 0) {
+      if (h[1] == kCoreUnset || h[1] <= k) return gpm_fail(GPM_E_DEVICE, "core peel made no progress");
+      k = h[1];  // no vertex left at this level: jump to the smallest remaining degree
+      continue;
+    }
+    uint32_t nin = h[0];
+    uint32_t *fin = fa, *fout = fb;
+    while (nin > 0) {
+      left -= nin;
+      GPM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t), st));
+      const unsigned blocks = (unsigned)std::min<uint64_t>(((uint64_t)nin + 7) / 8, (uint64_t)sms * 16);
+      GPM_LAUNCH("core_peel_kernel", st,
+                 core_peel_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, fin, nin, k, cdeg, g->core, fout, cnt));
+      GPM_CUDA(cudaGetLastError());
+      GPM_CUDA(cudaMemcpyAsync(&nin, cnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+      GPM_CUDA(cudaStreamSynchronize(st));
+      std::swap(fin, fout);
+    }
+    ++k;
+  }
+  return GPM_OK;
+}
+
 int gpm_prepare_graph(gpm_graph *g, cudaStream_t st) {
   if (g->prepared) return gpm_ensure_classes(g, st);
   const uint32_t n = g->n;
@@ -380,11 +498,16 @@ int gpm_prepare_graph(gpm_graph *g, cudaStream_t st) {
   const int sms = gpm_num_sms(g->device);
   if (e == cudaSuccess && n > 0) {
     GPM_LAUNCH("degree_kernel", st, degree_kernel<<<sms * 4, 256, 0, st>>>(g->rowptr, n, g->deg, dmax));
-    GPM_LAUNCH("outdeg_kernel", st, outdeg_kernel<<<sms * 8, 256, 0, st>>>(g->rowptr, g->col, g->deg, n, outdeg, dmax + 1));
+    g->okey = g->deg;
+    if (g->orient_mode == GPM_ORIENT_CORE) {
+      GPM_TRY(gpm_core_numbers(g, st));
+      g->okey = g->core;
+    }
+    GPM_LAUNCH("outdeg_kernel", st, outdeg_kernel<<<sms * 8, 256, 0, st>>>(g->rowptr, g->col, g->okey, n, outdeg, dmax + 1));
     GPM_LAUNCH("scan_tiles_kernel", st, scan_tiles_kernel<<<(unsigned)ntiles, kScanThreads, 0, st>>>(outdeg, n, g->drow, tile_sums));
     GPM_LAUNCH("scan_sums_kernel", st, scan_sums_kernel<<<1, kScanThreads, 0, st>>>(tile_sums, ntiles));
     GPM_LAUNCH("scan_add_kernel", st, scan_add_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g->drow, n, tile_sums, outdeg));
-    GPM_LAUNCH("fill_dag_kernel", st, fill_dag_kernel<<<sms * 8, 256, 0, st>>>(g->rowptr, g->col, g->deg, n, g->drow, g->dcol));
+    GPM_LAUNCH("fill_dag_kernel", st, fill_dag_kernel<<<sms * 8, 256, 0, st>>>(g->rowptr, g->col, g->okey, n, g->drow, g->dcol));
     e = cudaGetLastError();
   } else if (e == cudaSuccess) {
     e = cudaMemsetAsync(g->drow, 0, sizeof(uint64_t), st);

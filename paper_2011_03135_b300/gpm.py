@@ -99,6 +99,8 @@ _SIGS = {
     "gpm_exists": [_vp, _vp, _vp, _vp, _vp],
     "gpm_list": [_vp, _vp, _vp, _u64, _U64P, _U64P, _vp],
     "gpm_graph_reset": [_vp],
+    "gpm_graph_set_orientation": [_vp, _u32],
+    "gpm_graph_core_numbers": [_vp, _vp, _vp],
     "gpm_profile_enable": [_i],
     "gpm_profile_reset": [],
     "gpm_profile_report": [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
@@ -238,6 +240,20 @@ class Graph:
         """Drop the orientation so the next count rebuilds it (buffers are kept)."""
         _check(_lib.gpm_graph_reset(self.handle))
         return self
+
+    def set_orientation(self, mode: str):
+        """Order of the orientation: "degree" (default) or "core" (core numbers)."""
+        modes = {"degree": 0, "core": 1}
+        if mode not in modes:
+            raise ValueError("orientation is 'degree' or 'core'")
+        _check(_lib.gpm_graph_set_orientation(self.handle, modes[mode]))
+        return self
+
+    def core_numbers(self, stream=None) -> np.ndarray:
+        """Core number of every vertex (k-core peeling on the device), as a host array."""
+        out = np.zeros(max(self.n, 1), dtype=np.uint32)
+        _check(_lib.gpm_graph_core_numbers(self.handle, out.ctypes.data, _stream(stream)))
+        return out[: self.n]
 
     def info(self) -> dict:
         i = GraphInfo()

@@ -536,3 +536,63 @@ def test_exists_matches_oracle_counts(gpm):
                         if adj[i, j]:
                             assert _adjacent(g, w[i], w[j]), (g.name, w, i, j)
         G.close()
+
+
+def _core_out_degrees(g, core):
+    d = np.diff(g.rowptr).astype(np.int64)
+    src = np.repeat(np.arange(g.n, dtype=np.int64), d)
+    dst = g.col.astype(np.int64)
+    c = core.astype(np.int64)
+    keep = (c[src] < c[dst]) | ((c[src] == c[dst]) & (src < dst))
+    return np.bincount(src[keep], minlength=g.n)
+
+
+@pytest.mark.parametrize("opts", [dict(), dict(warp_max_degree=32, cta_max_degree=96)])
+def test_core_numbers_and_core_orientation(gpm, opts):
+    # the k-core peel against the oracle's bucket-queue core numbers; under the
+    # core order the totals are those of the degree order, the root ranges
+    # follow (core, id), and switching back restores the degree order
+    old = gpm.get_options()
+    try:
+        if opts:
+            gpm.set_options(**opts)
+        K = [gpm.Pattern.clique(k) for k in (3, 4, 5, 6)]
+        for g in SMALL[:8] + _medium() + [gg.complete(40), gg.empty(5), gg.star(9)]:
+            G = gpm.Graph.from_host(g)
+            core = O.core_numbers(g)
+            assert G.core_numbers().tolist() == core.tolist(), g.name
+            G.set_orientation("core")
+            info = G.prepare().info()
+            assert info["dag_arcs"] == g.m
+            assert info["max_out_degree"] == (int(_core_out_degrees(g, core).max()) if g.n else 0), g.name
+            assert G.core_numbers().tolist() == core.tolist()
+            assert gpm.count(G, K) == [O.cliques(g, k) for k in (3, 4, 5, 6)], g.name
+            assert gpm.count_cliques(G, 7) == O.cliques(g, 7), g.name
+            assert gpm.count(G, gpm.Pattern.motifs(4)) == O.motifs(g, 4), g.name
+            cuts = [0, g.n // 3, g.n // 3 + 1, g.n]
+            for lo, hi in zip(cuts[:-1], cuts[1:]):
+                assert gpm.count_roots(G, K[1:3], lo, hi) == [O.cliques_keyed(g, core, k, lo, hi) for k in (4, 5)], \
+                    (g.name, lo, hi)
+                assert gpm.count_cliques(G, 7, lo, hi) == O.cliques_keyed(g, core, 7, lo, hi), (g.name, lo, hi)
+            G.set_orientation("degree")
+            assert gpm.count_roots(G, K[1:2], 0, g.n // 3) == [O.cliques(g, 4, 0, g.n // 3)]
+            G.close()
+    finally:
+        gpm.set_options(**{k: v for k, v in old.items() if v})
+
+
+def test_core_orientation_fullsize_rmat21(gpm):
+    # the headline graph under the core order: core numbers against the
+    # oracle, 4- and 5-clique totals against the stored oracle totals
+    g = gg.workload_clique_rmat21()
+    gold = _golden().get("clique_rmat21", {})
+    G = gpm.Graph.from_host(g)
+    assert G.core_numbers().tolist() == O.core_numbers(g).tolist()
+    G.set_orientation("core")
+    got = gpm.count(G, [gpm.Pattern.clique(4), gpm.Pattern.clique(5)])
+    if gold:
+        assert gold["digest"] == g.digest()
+        assert got == [gold["clique4"], gold["clique5"]]
+    G.set_orientation("degree")
+    assert gpm.count(G, [gpm.Pattern.clique(4), gpm.Pattern.clique(5)]) == got
+    G.close()
