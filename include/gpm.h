@@ -99,12 +99,14 @@ int gpm_graph_prepare(gpm_graph_t g, void *stream);
 int gpm_graph_reset(gpm_graph_t g);
 
 #define GPM_ORIENT_DEGREE 0u /* edges point to the endpoint of higher degree (default) */
-#define GPM_ORIENT_CORE 1u   /* edges point to the endpoint of higher core number */
+#define GPM_ORIENT_CORE 1u   /* core value based: the degeneracy (peeling) order */
 
 /*
  * Choose the total order of the orientation (appendix "Orientation (Total
- * Order)": degree based, or core value based, where the core numbers take
- * the place of the degrees; ties go to the larger id in both). Takes effect
+ * Order)": degree based, ties to the larger id; or core value based, read as
+ * the degeneracy order of k-core peeling: vertices in the order the
+ * level-synchronous peel removes them (by round, ties to the larger id), so
+ * that no vertex has more successors than its core number). Takes effect
  * at the next prepare (the current orientation is dropped when the mode
  * changes). Totals do not depend on the order; the root of a clique or of a
  * diamond in gpm_count_roots / gpm_count_cliques follows it. The core order

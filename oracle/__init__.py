@@ -64,6 +64,7 @@ def _load():
                 "orc_cliques": ([u32, vp, vp, u32, u32, u32, U64P], ctypes.c_int),
                 "orc_triangles": ([u32, vp, vp, U64P], ctypes.c_int),
                 "orc_core_numbers": ([u32, vp, vp, vp], ctypes.c_int),
+                "orc_core_order": ([u32, vp, vp, vp], ctypes.c_int),
                 "orc_cliques_keyed": ([u32, vp, vp, vp, u32, u32, u32, U64P], ctypes.c_int),
                 "orc_diamonds": ([u32, vp, vp, u32, u32, U64P], ctypes.c_int),
                 "orc_cycles4": ([u32, vp, vp, u32, u32, U64P], ctypes.c_int),
@@ -185,6 +186,14 @@ def core_numbers(g) -> np.ndarray:
     rp, col = _csr(g)
     out = np.zeros(max(g.n, 1), dtype=np.uint32)
     _check(_load().orc_core_numbers(g.n, rp.ctypes.data, col.ctypes.data, out.ctypes.data), "core_numbers")
+    return out[: g.n]
+
+
+def core_order(g) -> np.ndarray:
+    """Round of the level-synchronous peel that takes each vertex (the degeneracy order)."""
+    rp, col = _csr(g)
+    out = np.zeros(max(g.n, 1), dtype=np.uint32)
+    _check(_load().orc_core_order(g.n, rp.ctypes.data, col.ctypes.data, out.ctypes.data), "core_order")
     return out[: g.n]
 
 

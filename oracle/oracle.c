@@ -441,6 +441,69 @@ int orc_core_numbers(uint32_t n, const uint64_t *rp, const uint32_t *col, uint32
   return ORC_OK;
 }
 
+/* The degeneracy order of level-synchronous peeling (the reading taken of the
+ * core value based order): at level k, every vertex still present with
+ * remaining degree <= k is taken in round r; taking a round's vertices lowers
+ * the remaining degree of their neighbours still present, and those that
+ * drop to k are taken in round r + 1 (same level); an empty level moves to
+ * the smallest remaining degree. order[v] = the round that took v. Written
+ * as plain sequential loops over whole rounds, so the rounds are the sets the
+ * definition gives whatever the processing order within a round. */
+int orc_core_order(uint32_t n, const uint64_t *rp, const uint32_t *col, uint32_t *order) {
+  uint32_t *d = (uint32_t *)malloc(((size_t)n + 1) * sizeof(uint32_t));
+  unsigned char *taken = (unsigned char *)calloc((size_t)n + 1, 1);
+  uint32_t *cur = (uint32_t *)malloc(((size_t)n + 1) * sizeof(uint32_t));
+  uint32_t *nxt = (uint32_t *)malloc(((size_t)n + 1) * sizeof(uint32_t));
+  if (!d || !taken || !cur || !nxt) {
+    free(d), free(taken), free(cur), free(nxt);
+    return ORC_E_OOM;
+  }
+  for (uint32_t v = 0; v < n; ++v) d[v] = (uint32_t)deg_of(rp, v);
+  uint64_t left = n;
+  uint32_t k = 0, round = 0;
+  while (left > 0) {
+    uint32_t nc = 0, mn = UINT32_MAX;
+    for (uint32_t v = 0; v < n; ++v) {
+      if (taken[v]) continue;
+      if (d[v] <= k) {
+        taken[v] = 1;
+        order[v] = round;
+        cur[nc++] = v;
+      } else if (d[v] < mn) {
+        mn = d[v];
+      }
+    }
+    if (nc == 0) {
+      k = mn;
+      continue;
+    }
+    while (nc > 0) {
+      left -= nc;
+      uint32_t nn = 0;
+      for (uint32_t i = 0; i < nc; ++i) {
+        uint32_t v = cur[i];
+        for (uint64_t e = rp[v]; e < rp[v + 1]; ++e) {
+          uint32_t w = col[e];
+          if (taken[w]) continue;
+          if (--d[w] == k) {
+            taken[w] = 1;
+            order[w] = round + 1;
+            nxt[nn++] = w;
+          }
+        }
+      }
+      uint32_t *t = cur;
+      cur = nxt;
+      nxt = t;
+      nc = nn;
+      ++round;
+    }
+    ++k;
+  }
+  free(d), free(taken), free(cur), free(nxt);
+  return ORC_OK;
+}
+
 /* k-cliques whose first vertex in the order (key, id) lies in [root_lo,
  * root_hi): the same search over the orientation v -> w iff (key v, v) <
  * (key w, w). With key = the core numbers this is the core value based

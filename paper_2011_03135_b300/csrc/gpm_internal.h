@@ -76,7 +76,8 @@ struct gpm_graph {
   // in both; okey points at the key array of the order in use
   uint32_t orient_mode = 0;      // GPM_ORIENT_DEGREE or GPM_ORIENT_CORE
   uint32_t *core = nullptr;      // n core numbers (core order only)
-  uint32_t *core_work = nullptr; // 3n: remaining degrees and two frontiers of the peel
+  uint32_t *core_work = nullptr; // 4n: remaining degrees, two frontiers, peel rounds
+  uint32_t *core_order = nullptr; // n (inside core_work): round of the peel that took each vertex
   uint32_t *okey = nullptr;
   bool prepared = false;
   uint64_t m = 0;                // arcs = nnz/2
@@ -185,8 +186,8 @@ int gpm_plan_pattern(gpm_pattern *p);  // fills cls, info, tmpl_to_pat
 int gpm_launch_validate(gpm_graph *g, cudaStream_t st, uint32_t *d_status);
 int gpm_prepare_graph(gpm_graph *g, cudaStream_t st);
 int gpm_ensure_classes(gpm_graph *g, cudaStream_t st);
-// core numbers of every vertex into g->core (k-core peeling on the device);
-// needs g->deg
+// core numbers of every vertex into g->core and the peel round of every
+// vertex into g->core_order (k-core peeling on the device); needs g->deg
 int gpm_core_numbers(gpm_graph *g, cudaStream_t st);
 
 // persistent grid size for a kernel

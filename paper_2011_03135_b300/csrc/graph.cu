@@ -369,7 +369,11 @@ int gpm_ensure_classes(gpm_graph *g, cudaStream_t st) {
 // peeling lowers the remaining degree of the neighbours still present, and a
 // neighbour whose degree drops to k joins the next frontier of the same
 // level. When a level's frontier empties, the next level is the smallest
-// remaining degree (at least k + 1).
+// remaining degree (at least k + 1). Each vertex also records the round in
+// which it is peeled (rounds count across levels): ordered by (round, id),
+// every vertex has at most core-number many successors, since its successors
+// were all still present, and its remaining degree was at most k, when it
+// was taken.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -385,7 +389,8 @@ __global__ void core_init_kernel(const uint32_t *__restrict__ deg, uint32_t n, u
 
 // frontier of level k among the vertices still present; cnt[0] its size,
 // cnt[1] the smallest remaining degree of the vertices left out
-__global__ void core_scan_kernel(uint32_t n, uint32_t k, const uint32_t *__restrict__ cdeg, uint32_t *__restrict__ core,
+__global__ void core_scan_kernel(uint32_t n, uint32_t k, uint32_t round, const uint32_t *__restrict__ cdeg,
+                                 uint32_t *__restrict__ core, uint32_t *__restrict__ order,
                                  uint32_t *__restrict__ frontier, uint32_t *__restrict__ cnt) {
   const uint32_t lane = threadIdx.x & 31;
   uint32_t mn = kCoreUnset;
@@ -397,6 +402,7 @@ __global__ void core_scan_kernel(uint32_t n, uint32_t k, const uint32_t *__restr
       const uint32_t c = cdeg[v];
       if (c <= k) {
         core[v] = k;
+        order[v] = round;
         join = true;
       } else {
         mn = min(mn, c);
@@ -415,8 +421,9 @@ __global__ void core_scan_kernel(uint32_t n, uint32_t k, const uint32_t *__restr
 // one warp per peeled vertex: lower the remaining degree of its neighbours
 // still present; those that drop to k join the next frontier (claimed once)
 __global__ void core_peel_kernel(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
-                                 const uint32_t *__restrict__ fin, uint32_t nin, uint32_t k, uint32_t *__restrict__ cdeg,
-                                 uint32_t *__restrict__ core, uint32_t *__restrict__ fout, uint32_t *__restrict__ nout) {
+                                 const uint32_t *__restrict__ fin, uint32_t nin, uint32_t k, uint32_t next_round,
+                                 uint32_t *__restrict__ cdeg, uint32_t *__restrict__ core, uint32_t *__restrict__ order,
+                                 uint32_t *__restrict__ fout, uint32_t *__restrict__ nout) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -427,7 +434,10 @@ __global__ void core_peel_kernel(const uint64_t *__restrict__ rowptr, const uint
       const uint32_t w = col[j];
       if (*(volatile uint32_t *)&core[w] != kCoreUnset) continue;
       const uint32_t old = atomicSub(&cdeg[w], 1u);
-      if (old == k + 1 && atomicCAS(&core[w], kCoreUnset, k) == kCoreUnset) fout[atomicAdd(nout, 1u)] = w;
+      if (old == k + 1 && atomicCAS(&core[w], kCoreUnset, k) == kCoreUnset) {
+        order[w] = next_round;
+        fout[atomicAdd(nout, 1u)] = w;
+      }
     }
   }
 }
@@ -438,7 +448,8 @@ int gpm_core_numbers(gpm_graph *g, cudaStream_t st) {
   const uint32_t n = g->n;
   if (!g->core) GPM_TRY(gpm_graph_alloc(g, (void **)&g->core, sizeof(uint32_t) * (size_t)std::max<uint32_t>(n, 1)));
   if (!g->core_work)
-    GPM_TRY(gpm_graph_alloc(g, (void **)&g->core_work, sizeof(uint32_t) * 3 * (size_t)std::max<uint32_t>(n, 1)));
+    GPM_TRY(gpm_graph_alloc(g, (void **)&g->core_work, sizeof(uint32_t) * 4 * (size_t)std::max<uint32_t>(n, 1)));
+  g->core_order = g->core_work + 3 * (size_t)std::max<uint32_t>(n, 1);
   if (n == 0) return GPM_OK;
   uint32_t *cdeg = g->core_work, *fa = cdeg + n, *fb = fa + n;
   // [0] frontier size, [1] smallest degree left out; past the two words that
@@ -448,11 +459,11 @@ int gpm_core_numbers(gpm_graph *g, cudaStream_t st) {
   GPM_LAUNCH("core_init_kernel", st, core_init_kernel<<<sms * 4, 256, 0, st>>>(g->deg, n, cdeg, g->core));
   GPM_CUDA(cudaGetLastError());
   uint64_t left = n;
-  uint32_t k = 0;
+  uint32_t k = 0, round = 0;
   while (left > 0) {
     const uint32_t init[2] = {0u, kCoreUnset};
     GPM_CUDA(cudaMemcpyAsync(cnt, init, sizeof(init), cudaMemcpyHostToDevice, st));
-    GPM_LAUNCH("core_scan_kernel", st, core_scan_kernel<<<sms * 4, 256, 0, st>>>(n, k, cdeg, g->core, fa, cnt));
+    GPM_LAUNCH("core_scan_kernel", st, core_scan_kernel<<<sms * 4, 256, 0, st>>>(n, k, round, cdeg, g->core, g->core_order, fa, cnt));
     GPM_CUDA(cudaGetLastError());
     uint32_t h[2];
     GPM_CUDA(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -469,11 +480,13 @@ int gpm_core_numbers(gpm_graph *g, cudaStream_t st) {
       GPM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t), st));
       const unsigned blocks = (unsigned)std::min<uint64_t>(((uint64_t)nin + 7) / 8, (uint64_t)sms * 16);
       GPM_LAUNCH("core_peel_kernel", st,
-                 core_peel_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, fin, nin, k, cdeg, g->core, fout, cnt));
+                 core_peel_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, fin, nin, k, round + 1, cdeg, g->core,
+                                                          g->core_order, fout, cnt));
       GPM_CUDA(cudaGetLastError());
       GPM_CUDA(cudaMemcpyAsync(&nin, cnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
       GPM_CUDA(cudaStreamSynchronize(st));
       std::swap(fin, fout);
+      ++round;
     }
     ++k;
   }
@@ -501,7 +514,7 @@ int gpm_prepare_graph(gpm_graph *g, cudaStream_t st) {
     g->okey = g->deg;
     if (g->orient_mode == GPM_ORIENT_CORE) {
       GPM_TRY(gpm_core_numbers(g, st));
-      g->okey = g->core;
+      g->okey = g->core_order;
     }
     GPM_LAUNCH("outdeg_kernel", st, outdeg_kernel<<<sms * 8, 256, 0, st>>>(g->rowptr, g->col, g->okey, n, outdeg, dmax + 1));
     GPM_LAUNCH("scan_tiles_kernel", st, scan_tiles_kernel<<<(unsigned)ntiles, kScanThreads, 0, st>>>(outdeg, n, g->drow, tile_sums));

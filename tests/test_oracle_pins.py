@@ -398,3 +398,24 @@ def test_cliques_under_core_order(mk):
     # with the degrees as the key it is the degree order
     deg = np.diff(g.rowptr).astype(np.uint32)
     assert O.cliques_keyed(g, deg, 4, 0, g.n // 2) == O.cliques(g, 4, 0, g.n // 2)
+
+
+@pytest.mark.parametrize("mk", SMALL + [lambda: gg.rmat(12, 16.0, seed=31), lambda: gg.chung_lu(5000, 16.0, 2.1, seed=24),
+                                        lambda: gg.complete(9), lambda: gg.star(8), lambda: gg.empty(3)])
+def test_core_order_is_a_degeneracy_order(mk):
+    # ordered by (round, id): no vertex has more successors than its core
+    # number, core numbers never decrease along the order, and the totals of
+    # the clique counts do not change
+    g = mk()
+    core = O.core_numbers(g).astype(np.int64)
+    order = O.core_order(g).astype(np.int64)
+    d = np.diff(g.rowptr).astype(np.int64)
+    src = np.repeat(np.arange(g.n, dtype=np.int64), d)
+    dst = g.col.astype(np.int64)
+    keep = (order[src] < order[dst]) | ((order[src] == order[dst]) & (src < dst))
+    outdeg = np.bincount(src[keep], minlength=g.n)
+    assert np.all(outdeg <= core)
+    by = np.lexsort((np.arange(g.n), order))
+    assert np.all(np.diff(core[by]) >= 0)
+    for k in (3, 4):
+        assert O.cliques_keyed(g, order, k) == O.cliques(g, k)

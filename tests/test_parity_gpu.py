@@ -538,11 +538,11 @@ def test_exists_matches_oracle_counts(gpm):
         G.close()
 
 
-def _core_out_degrees(g, core):
+def _keyed_out_degrees(g, key):
     d = np.diff(g.rowptr).astype(np.int64)
     src = np.repeat(np.arange(g.n, dtype=np.int64), d)
     dst = g.col.astype(np.int64)
-    c = core.astype(np.int64)
+    c = key.astype(np.int64)
     keep = (c[src] < c[dst]) | ((c[src] == c[dst]) & (src < dst))
     return np.bincount(src[keep], minlength=g.n)
 
@@ -550,8 +550,9 @@ def _core_out_degrees(g, core):
 @pytest.mark.parametrize("opts", [dict(), dict(warp_max_degree=32, cta_max_degree=96)])
 def test_core_numbers_and_core_orientation(gpm, opts):
     # the k-core peel against the oracle's bucket-queue core numbers; under the
-    # core order the totals are those of the degree order, the root ranges
-    # follow (core, id), and switching back restores the degree order
+    # core value based (degeneracy) order the totals are those of the degree
+    # order, the root ranges follow (peel round, id) and no vertex has more
+    # successors than its core number; switching back restores the degree order
     old = gpm.get_options()
     try:
         if opts:
@@ -560,20 +561,22 @@ def test_core_numbers_and_core_orientation(gpm, opts):
         for g in SMALL[:8] + _medium() + [gg.complete(40), gg.empty(5), gg.star(9)]:
             G = gpm.Graph.from_host(g)
             core = O.core_numbers(g)
+            order = O.core_order(g)
             assert G.core_numbers().tolist() == core.tolist(), g.name
             G.set_orientation("core")
             info = G.prepare().info()
             assert info["dag_arcs"] == g.m
-            assert info["max_out_degree"] == (int(_core_out_degrees(g, core).max()) if g.n else 0), g.name
+            assert info["max_out_degree"] == (int(_keyed_out_degrees(g, order).max()) if g.n else 0), g.name
+            assert info["max_out_degree"] <= (int(core.max()) if g.n else 0)
             assert G.core_numbers().tolist() == core.tolist()
             assert gpm.count(G, K) == [O.cliques(g, k) for k in (3, 4, 5, 6)], g.name
             assert gpm.count_cliques(G, 7) == O.cliques(g, 7), g.name
             assert gpm.count(G, gpm.Pattern.motifs(4)) == O.motifs(g, 4), g.name
             cuts = [0, g.n // 3, g.n // 3 + 1, g.n]
             for lo, hi in zip(cuts[:-1], cuts[1:]):
-                assert gpm.count_roots(G, K[1:3], lo, hi) == [O.cliques_keyed(g, core, k, lo, hi) for k in (4, 5)], \
+                assert gpm.count_roots(G, K[1:3], lo, hi) == [O.cliques_keyed(g, order, k, lo, hi) for k in (4, 5)], \
                     (g.name, lo, hi)
-                assert gpm.count_cliques(G, 7, lo, hi) == O.cliques_keyed(g, core, 7, lo, hi), (g.name, lo, hi)
+                assert gpm.count_cliques(G, 7, lo, hi) == O.cliques_keyed(g, order, 7, lo, hi), (g.name, lo, hi)
             G.set_orientation("degree")
             assert gpm.count_roots(G, K[1:2], 0, g.n // 3) == [O.cliques(g, 4, 0, g.n // 3)]
             G.close()
@@ -587,9 +590,11 @@ def test_core_orientation_fullsize_rmat21(gpm):
     g = gg.workload_clique_rmat21()
     gold = _golden().get("clique_rmat21", {})
     G = gpm.Graph.from_host(g)
-    assert G.core_numbers().tolist() == O.core_numbers(g).tolist()
+    core = O.core_numbers(g)
+    assert G.core_numbers().tolist() == core.tolist()
     G.set_orientation("core")
     got = gpm.count(G, [gpm.Pattern.clique(4), gpm.Pattern.clique(5)])
+    assert G.info()["max_out_degree"] == int(_keyed_out_degrees(g, O.core_order(g)).max()) <= int(core.max())
     if gold:
         assert gold["digest"] == g.digest()
         assert got == [gold["clique4"], gold["clique5"]]
