@@ -63,6 +63,19 @@ def test_count_cliques_validates_before_any_device_work(lib):
     assert so.gpm_count_cliques(None, 7, 0, 0, None, None) == invalid
 
 
+def test_orientation_and_existence_validate_on_the_host(lib):
+    # null handles and outputs are rejected before any device work
+    so = ctypes.CDLL(lib.LIB_PATH)
+    so.gpm_graph_set_orientation.argtypes = [ctypes.c_void_p, ctypes.c_uint32]
+    so.gpm_graph_core_numbers.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    so.gpm_exists.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert so.gpm_graph_set_orientation(None, 1) != 0
+    assert so.gpm_graph_core_numbers(None, None, None) != 0
+    found = ctypes.c_int(7)
+    assert so.gpm_exists(None, None, ctypes.byref(found), None, None) != 0
+    assert found.value == 7  # untouched on error
+
+
 @pytest.mark.parametrize("idx", range(6))
 def test_planner_motif4(lib, idx):
     pats = lib.Pattern.motifs(4)
