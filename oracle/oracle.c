@@ -732,6 +732,162 @@ int orc_motifs(uint32_t n, const uint64_t *rp, const uint32_t *col, uint32_t k, 
 }
 
 /* ------------------------------------------------------------------ */
+/* 5-vertex motifs (Section 2 k-MC for k = 5): every connected induced   */
+/* 5-vertex subgraph, enumerated once by ESU (Wernicke 2006: extend a   */
+/* connected set only by vertices after its first vertex and outside   */
+/* the neighbourhood of the set so far), classified by isomorphism     */
+/* class through a canonical adjacency mask (minimum over the 120      */
+/* vertex permutations).                                                */
+/* ------------------------------------------------------------------ */
+
+/* pair (i, j), i < j, of 5 vertices -> bit index 0..9 in lexicographic order */
+static int pair_bit5(int i, int j) {
+  static const int base[4] = {0, 4, 7, 9};
+  if (i > j) {
+    int t = i;
+    i = j;
+    j = t;
+  }
+  return base[i] + (j - i - 1);
+}
+
+static uint32_t canon5(uint32_t mask) {
+  uint32_t best = 0xffffffffu;
+  int p[5];
+  /* the 120 permutations p of {0..4}: vertex i of the mask becomes p[i] */
+  for (p[0] = 0; p[0] < 5; ++p[0])
+    for (p[1] = 0; p[1] < 5; ++p[1])
+      for (p[2] = 0; p[2] < 5; ++p[2])
+        for (p[3] = 0; p[3] < 5; ++p[3])
+          for (p[4] = 0; p[4] < 5; ++p[4]) {
+            int used = (1 << p[0]) | (1 << p[1]) | (1 << p[2]) | (1 << p[3]) | (1 << p[4]);
+            if (used != 31) continue;
+            uint32_t m = 0;
+            for (int i = 0; i < 5; ++i)
+              for (int j = i + 1; j < 5; ++j)
+                if (mask >> pair_bit5(i, j) & 1u) m |= 1u << pair_bit5(p[i], p[j]);
+            if (m < best) best = m;
+          }
+  return best;
+}
+
+static int connected5(uint32_t mask) {
+  uint32_t seen = 1u, grow = 1u;
+  while (grow) {
+    uint32_t next = 0;
+    for (int i = 0; i < 5; ++i)
+      if (grow >> i & 1u)
+        for (int j = 0; j < 5; ++j)
+          if (j != i && (mask >> pair_bit5(i, j) & 1u) && !(seen >> j & 1u)) next |= 1u << j;
+    seen |= next;
+    grow = next;
+  }
+  return seen == 31u;
+}
+
+/* class index of every 10-bit mask (255 = not connected); classes ordered
+ * by edge count, then by canonical mask */
+static int motif5_table(uint8_t *cls, uint32_t *class_mask) {
+  uint32_t canon[1024];
+  int nc = 0;
+  for (uint32_t m = 0; m < 1024; ++m) canon[m] = connected5(m) ? canon5(m) : 0xffffffffu;
+  for (uint32_t m = 0; m < 1024; ++m) {
+    if (canon[m] != m) continue; /* m is canonical and connected */
+    class_mask[nc++] = m;
+  }
+  for (int i = 1; i < nc; ++i) /* insertion sort by (edges, mask) */
+    for (int j = i; j > 0; --j) {
+      uint32_t a = class_mask[j - 1], b = class_mask[j];
+      int ea = __builtin_popcount(a), eb = __builtin_popcount(b);
+      if (ea < eb || (ea == eb && a < b)) break;
+      class_mask[j - 1] = b;
+      class_mask[j] = a;
+    }
+  for (uint32_t m = 0; m < 1024; ++m) {
+    cls[m] = 255;
+    if (canon[m] == 0xffffffffu) continue;
+    for (int i = 0; i < nc; ++i)
+      if (class_mask[i] == canon[m]) cls[m] = (uint8_t)i;
+  }
+  return nc;
+}
+
+typedef struct {
+  const uint64_t *rp;
+  const uint32_t *col;
+  const uint8_t *cls;
+  uint64_t *cnt;
+  uint32_t *ext_pool; /* 5 levels */
+  uint64_t level_cap;
+  uint32_t v;
+} esu_ctx;
+
+static void esu_extend(esu_ctx *x, uint32_t *sub, int ns, const uint32_t *ext, uint64_t next, int level) {
+  if (ns == 5) {
+    uint32_t mask = 0;
+    for (int i = 0; i < 5; ++i)
+      for (int j = i + 1; j < 5; ++j)
+        if (adjacent(x->rp, x->col, sub[i], sub[j])) mask |= 1u << pair_bit5(i, j);
+    x->cnt[x->cls[mask]]++;
+    return;
+  }
+  uint32_t *ext2 = x->ext_pool + (uint64_t)level * x->level_cap;
+  while (next > 0) {
+    uint32_t w = ext[--next];
+    uint64_t n2 = 0;
+    for (uint64_t i = 0; i < next; ++i) ext2[n2++] = ext[i];
+    for (uint64_t e = x->rp[w]; e < x->rp[w + 1]; ++e) {
+      uint32_t u = x->col[e];
+      if (u <= x->v) continue;
+      int excl = 1;
+      for (int i = 0; i < ns && excl; ++i)
+        if (u == sub[i] || adjacent(x->rp, x->col, sub[i], u)) excl = 0;
+      if (excl) ext2[n2++] = u;
+    }
+    sub[ns] = w;
+    esu_extend(x, sub, ns + 1, ext2, n2, level + 1);
+  }
+}
+
+/* Induced counts of the 21 connected 5-vertex patterns; class_mask[i] is the
+ * canonical adjacency mask of class i (edge {a, b} of vertices 0..4 at the
+ * bit pair_bit5(a, b) gives: pairs in lexicographic order (0,1) = bit 0 ...
+ * (3,4) = bit 9); classes ordered by edge count, then by mask. */
+int orc_motifs5(uint32_t n, const uint64_t *rp, const uint32_t *col, uint64_t *out, uint32_t *class_mask) {
+  uint8_t cls[1024];
+  uint32_t cm[32];
+  int nc = motif5_table(cls, cm);
+  if (nc != 21) return ORC_E_ARG;
+  uint64_t maxd = 0;
+  for (uint32_t v = 0; v < n; ++v)
+    if (deg_of(rp, v) > maxd) maxd = deg_of(rp, v);
+  esu_ctx x;
+  x.rp = rp;
+  x.col = col;
+  x.cls = cls;
+  x.cnt = out;
+  x.level_cap = 5 * maxd + 1;
+  x.ext_pool = (uint32_t *)malloc(6 * x.level_cap * sizeof(uint32_t));
+  if (!x.ext_pool) return ORC_E_OOM;
+  for (int i = 0; i < 21; ++i) {
+    out[i] = 0;
+    if (class_mask) class_mask[i] = cm[i];
+  }
+  uint32_t sub[5];
+  for (uint32_t v = 0; v < n; ++v) {
+    x.v = v;
+    uint32_t *ext = x.ext_pool;
+    uint64_t ne = 0;
+    for (uint64_t e = rp[v]; e < rp[v + 1]; ++e)
+      if (col[e] > v) ext[ne++] = col[e];
+    sub[0] = v;
+    esu_extend(&x, sub, 1, ext, ne, 1);
+  }
+  free(x.ext_pool);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* worked examples of the paper                                        */
 /* ------------------------------------------------------------------ */
 

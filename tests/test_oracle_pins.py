@@ -419,3 +419,74 @@ def test_core_order_is_a_degeneracy_order(mk):
     assert np.all(np.diff(core[by]) >= 0)
     for k in (3, 4):
         assert O.cliques_keyed(g, order, k) == O.cliques(g, k)
+
+
+# ---------------- 5-vertex motifs ----------------
+
+def _mask_graph5(mask):
+    import networkx as nx
+    pairs = [(a, b) for a in range(5) for b in range(a + 1, 5)]
+    G = nx.Graph()
+    G.add_nodes_from(range(5))
+    G.add_edges_from(p for i, p in enumerate(pairs) if mask >> i & 1)
+    return G
+
+
+def test_motif5_classes_are_the_21_connected_graphs():
+    # the class masks are pairwise non-isomorphic connected 5-vertex graphs,
+    # one per connected 5-vertex graph of the networkx graph atlas
+    import networkx as nx
+    _, masks = O.motifs5(gg.complete(5))
+    assert len(masks) == 21
+    gs = [_mask_graph5(m) for m in masks]
+    assert all(nx.is_connected(G) for G in gs)
+    atlas = [G for G in nx.graph_atlas_g() if G.number_of_nodes() == 5 and nx.is_connected(G)]
+    assert len(atlas) == 21
+    for A in atlas:
+        assert sum(nx.is_isomorphic(A, G) for G in gs) == 1
+    edges = [G.number_of_edges() for G in gs]
+    assert edges == sorted(edges)
+
+
+# want = {edge count of the only class present: its count}
+@pytest.mark.parametrize("mk, want", [
+    (lambda: gg.complete(8), {10: 56}),          # K5: C(8, 5)
+    (lambda: gg.path(9), {4: 5}),                # 5-paths: n - 4
+    (lambda: gg.cycle(5), {5: 1}),               # one 5-cycle
+    (lambda: gg.star(6), {4: 15}),               # 4-stars: C(6, 4)
+])
+def test_motifs5_closed_forms(mk, want):
+    import networkx as nx
+    g = mk()
+    counts, masks = O.motifs5(g)
+    assert sum(counts) == sum(want.values())
+    # the class holding the count has the expected shape
+    (edges, c), = want.items()
+    got = [i for i, x in enumerate(counts) if x]
+    assert len(got) == 1 and counts[got[0]] == c
+    G = _mask_graph5(masks[got[0]])
+    assert G.number_of_edges() == edges
+    if g.n >= 5 and edges == 4:
+        deg = sorted(d for _, d in G.degree())
+        assert deg == ([1, 1, 1, 1, 4] if g.name.startswith("S") else [1, 1, 2, 2, 2])
+
+
+@pytest.mark.parametrize("mk", [lambda: gg.random_small(11, 0.4, 31), lambda: gg.random_small(13, 0.3, 32),
+                                lambda: gg.petersen(), lambda: gg.complete_multipartite([2, 3, 2]),
+                                lambda: gg.random_small(10, 0.7, 33)])
+def test_motifs5_match_subset_brute_force(mk):
+    # every 5-subset, its induced subgraph classified by networkx isomorphism
+    import networkx as nx
+    g = mk()
+    adj = _py_adj(g)
+    counts, masks = O.motifs5(g)
+    gs = [_mask_graph5(m) for m in masks]
+    want = [0] * 21
+    for W in itertools.combinations(range(g.n), 5):
+        H = nx.Graph()
+        H.add_nodes_from(W)
+        H.add_edges_from((a, b) for a, b in itertools.combinations(W, 2) if b in adj[a])
+        if not nx.is_connected(H):
+            continue
+        want[[i for i, G in enumerate(gs) if nx.is_isomorphic(G, H)][0]] += 1
+    assert counts == want
