@@ -17,13 +17,18 @@ from __future__ import annotations
 import numpy as np
 
 
-def root_costs(rowptr: np.ndarray, col: np.ndarray) -> np.ndarray:
-    """Estimated cost per root: (out-degree in the degree orientation)^2 + 1."""
+def root_costs(rowptr: np.ndarray, col: np.ndarray, key: np.ndarray | None = None) -> np.ndarray:
+    """Estimated cost per root: (out-degree in the orientation)^2 + 1.
+
+    key: the order's key per vertex (ties to the larger id), by default the
+    degree; for the core value based orientation pass the peel round of each
+    vertex (its roots then follow that order)."""
     d = np.diff(rowptr).astype(np.int64)
     n = len(d)
+    kv = d if key is None else np.asarray(key, dtype=np.int64)
     src = np.repeat(np.arange(n, dtype=np.int64), d)
     dst = col.astype(np.int64)
-    out = (d[src] < d[dst]) | ((d[src] == d[dst]) & (src < dst))
+    out = (kv[src] < kv[dst]) | ((kv[src] == kv[dst]) & (src < dst))
     od = np.bincount(src[out], minlength=n)
     return od.astype(np.float64) ** 2 + 1.0
 

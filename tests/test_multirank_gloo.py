@@ -33,9 +33,15 @@ def _worker(rank, world, port, out_dir):
         lambda lo, hi: [O.cliques(g, 3, lo, hi), O.cliques(g, 4, lo, hi), O.diamonds(g, lo, hi),
                         O.cycles4(g, lo, hi)],
         g.n, costs, rank, world)
+    # the core value based order: roots and costs follow the peel rounds, and
+    # large k goes through the same ranges
+    order = O.core_order(g)
+    got_core = shard.sharded_count(
+        lambda lo, hi: [O.cliques_keyed(g, order, 4, lo, hi), O.cliques_keyed(g, order, 7, lo, hi)],
+        g.n, shard.root_costs(g.rowptr, g.col, key=order), rank, world)
     # a value above 2^32 survives the exact split reduction
     big = shard.allreduce_counts([(1 << 40) + rank, 2 ** 63 + 5 * rank])
-    np.save(os.path.join(out_dir, f"r{rank}.npy"), np.array(got + big, dtype=object), allow_pickle=True)
+    np.save(os.path.join(out_dir, f"r{rank}.npy"), np.array(got + got_core + big, dtype=object), allow_pickle=True)
     dist.barrier()
     dist.destroy_process_group()
 
@@ -66,4 +72,17 @@ def test_two_gloo_ranks_sum_to_single_rank(tmp_path):
     assert r0 == r1
     g = gg.rmat(11, 16.0, seed=77)
     assert r0[:4] == [O.cliques(g, 3), O.cliques(g, 4), O.diamonds(g), O.cycles4(g)]
-    assert r0[4:] == [2 * (1 << 40) + 1, 2 * 2 ** 63 + 5]
+    assert r0[4:6] == [O.cliques(g, 4), O.cliques(g, 7)]
+    assert r0[6:] == [2 * (1 << 40) + 1, 2 * 2 ** 63 + 5]
+
+
+def test_root_costs_follow_the_key():
+    g = gg.rmat(9, 8.0, seed=3)
+    import oracle as O
+    order = O.core_order(g)
+    c_deg = shard.root_costs(g.rowptr, g.col)
+    c_key = shard.root_costs(g.rowptr, g.col, key=order)
+    core = O.core_numbers(g)
+    # under the degeneracy order no out-degree exceeds the core number
+    assert np.all(np.sqrt(c_key - 1.0) <= core + 1e-9)
+    assert c_deg.sum() == shard.root_costs(g.rowptr, g.col, key=np.diff(g.rowptr)).sum()
