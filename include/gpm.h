@@ -86,8 +86,8 @@ int gpm_graph_destroy(gpm_graph_t g);
 /*
  * Build the orientation (appendix "Orientation (Total Order)": by default
  * every edge points to the endpoint of higher degree, ties to the larger id;
- * see gpm_graph_set_orientation) and the task lists used by the kernels. Idempotent; called implicitly by
- * the first count. Synchronises `stream`.
+ * see gpm_graph_set_orientation) and the task lists used by the kernels.
+ * Idempotent; called implicitly by the first count. Synchronises `stream`.
  */
 int gpm_graph_prepare(gpm_graph_t g, void *stream);
 
