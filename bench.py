@@ -11,6 +11,12 @@ Under torchrun (N > 1) every rank counts its own replica of the workload
 (weak scaling, no collective on the data path); the slowest rank's time sets
 the step time. `--impl reference` times the CPU oracle (single-threaded C) on
 a bounded root sample of the same workload.
+
+Other legs (one GPU, one JSON line each): `--workload tc` (triangles, R-MAT
+14), `sl` (diamonds and 4-cycles, Chung-Lu 4M), `clique6` (6-cliques, R-MAT
+20), `clique789` (7-, 8-, 9-cliques, Chung-Lu 1M), `batched` and `served`
+(many small queries); `--orientation core` runs the headline leg under the
+core value based (degeneracy) order, k-core peel included in each step.
 """
 from __future__ import annotations
 
