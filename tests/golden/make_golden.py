@@ -32,6 +32,7 @@ def _graph(name):
         "tc_rmat14": gg.workload_tc_rmat14,
         "clique_rmat21": gg.workload_clique_rmat21,
         "sl_chunglu4m": gg.workload_sl_chung_lu4m,
+        "clique789_chunglu1m": gg.workload_clique789_chung_lu1m,
     }[name]()
 
 
@@ -72,6 +73,7 @@ PLAN = {
     "tc_rmat14": ["clique3", "clique4", "clique5"],
     "clique_rmat21": ["clique3", "clique4", "clique5"],
     "sl_chunglu4m": ["diamond", "cycle4", "clique3"],
+    "clique789_chunglu1m": ["clique7", "clique8", "clique9"],
 }
 
 

@@ -343,6 +343,13 @@ def test_fullsize_clique789_chunglu1m(gpm):
     cuts = [0, g.n // 2, g.n // 2 + 1, g.n]
     for k in (7, 9):
         assert sum(gpm.count_cliques(G, k, a, b) for a, b in zip(cuts[:-1], cuts[1:])) == gpm.count_cliques(G, k)
+    # the totals against the oracle's (tests/golden/make_golden.py)
+    gold = _golden().get("clique789_chunglu1m", {})
+    if gold:
+        assert gold["digest"] == g.digest()
+        for k in (7, 8, 9):
+            if f"clique{k}" in gold:
+                assert gpm.count_cliques(G, k) == gold[f"clique{k}"], k
     G.close()
 
 
