@@ -143,7 +143,7 @@ def clique_pass_bytes(g, opts):
 # profiles/lg_cta_lo_k789_chunglu1m_counters.md):
 #   ncu --metrics smsp__inst_executed.sum,gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
 #       --clock-control none -k regex:lg_cta_kernel -c 1
-#       python -m paper_2011_03135_b300.cases --case <clique-rmat21 | clique6-rmat20> --reps 1
+#       python bench.py --case <clique-rmat21 | clique6-rmat20> --reps 1
 #   (clique789-cl1m: -c 6, every lg_cta_kernel launch of one step)
 # valid only for the kernel sources they were taken on (digest of
 # csrc/lg_device.cuh + csrc/clique.cu); a stale entry is ignored.
@@ -155,6 +155,12 @@ NCU_COUNTERS = {
     "clique6-rmat20": {
         "lg_cta_hi": {"digest": "2b577df7558f17b7", "inst_per_step": 1638151502659,
                       "dram_bytes_per_step": 13073920, "ncu_ms": 1688.935},
+    },
+    # every 4-cycle kernel launch of one step (c4_bound x 2, c4_range,
+    # c4_bucket, c4_small; the per-graph c4_edeg and c4_roff tables excluded),
+    # summed; profiles/c4_sl_chunglu4m_dram.md; digest of motif.cu + motif_device.cuh
+    "sl-chunglu4m": {
+        "c4": {"digest": "91324121aec85ca0", "dram_bytes_per_step": 134.73e9},
     },
     # three launches per step (k = 7, 8, 9), summed
     "clique789-cl1m": {
@@ -173,6 +179,14 @@ def kernel_digest():
     import hashlib
     h = hashlib.sha256()
     for f in ("lg_device.cuh", "clique.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2011_03135_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def c4_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("motif.cu", "motif_device.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2011_03135_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -198,9 +212,65 @@ def cpu_baseline(g, seconds_target=15.0):
         c4 = O.cliques(g, 4, lo, hi)
         c5 = O.cliques(g, 5, lo, hi)
         dt = time.perf_counter() - t0
-    return {"value": (c4 + c5) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": (c4 + c5) / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": _cpu_model(),
+            "roots": hi - lo, "seconds": dt,
             "sample": f"roots with id in [{lo}, {hi}) of {g.n} (random sample: ids are permuted); "
                       f"4-CL + 5-CL single-threaded, {dt:.1f} s, counts {c4} + {c5}"}
+
+
+_CPU_G = None
+
+
+def _cpu_init(n, rp_path, col_path):
+    """Worker set-up of the all-core oracle leg: the CSR, memory-mapped."""
+    global _CPU_G
+    from paper_2011_03135_b300 import graphgen as gg
+    _CPU_G = gg.Graph(n, np.load(rp_path, mmap_mode="r"), np.load(col_path, mmap_mode="r"))
+
+
+def _cpu_work(task):
+    ks, lo, hi = task
+    import oracle as O
+    return sum(O.cliques(_CPU_G, k, lo, hi) for k in ks)
+
+
+def _cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_baseline_all_cores(g, ks, unit, single, seconds_target=4.0):
+    """The same oracle code, unchanged, over root ranges on every host core
+    (a spawn-started process pool: no fork after the GPU is in use). The
+    sample is the prefix [0, hi) of the randomly permuted ids, sized from the
+    single-threaded rate for about `seconds_target` of wall time, cut into
+    interleaved chunks so that the heavy roots spread over the workers."""
+    import multiprocessing as mp
+    import tempfile
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    per_root_s = single["seconds"] / max(single["roots"], 1)
+    hi = int(min(g.n, max(single["roots"], cores * seconds_target / max(per_root_s, 1e-9))))
+    nchunks = max(1, min(hi, cores * 64))
+    bounds = [hi * i // nchunks for i in range(nchunks + 1)]
+    tasks = [(tuple(ks), bounds[i], bounds[i + 1]) for i in range(nchunks) if bounds[i + 1] > bounds[i]]
+    with tempfile.TemporaryDirectory(prefix="gpm_cpu_") as d:
+        rp_path, col_path = os.path.join(d, "rowptr.npy"), os.path.join(d, "col.npy")
+        np.save(rp_path, g.rowptr)
+        np.save(col_path, g.col)
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores, initializer=_cpu_init, initargs=(g.n, rp_path, col_path)) as pool:
+            pool.map(_cpu_work, [tasks[0]])  # workers started before the clock
+            t0 = time.perf_counter()
+            total = sum(pool.map(_cpu_work, tasks, chunksize=1))
+            dt = time.perf_counter() - t0
+    return {"value": total / dt, "unit": unit, "cores": cores, "kind": "oracle", "cpu": _cpu_model(),
+            "sample": f"roots with id in [0, {hi}) of {g.n} (random sample: ids are permuted) in {len(tasks)} chunks "
+                      f"over {cores} processes; {'+'.join(str(k) for k in ks)}-cliques, {dt:.1f} s wall, total {total}"}
 
 
 BATCH_WORKLOAD = ("batched 3-/4-motif counting: 512 queries, each on its own seeded graph, Erdos-Renyi (mean degree "
@@ -397,6 +467,10 @@ def run_sl(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(device=dev)
+    c4opts = {k: v for k, v in dict(c4_range_bound=args.c4_range_bound, c4_range_width=args.c4_range_width,
+                                    c4_hub_bound=args.c4_hub_bound).items() if v}
+    if c4opts:
+        gpm.set_options(**c4opts)
     G = gpm.Graph(torch.from_numpy(g.rowptr.view(np.int64)).to(dev), torch.from_numpy(g.col.view(np.int32)).to(dev),
                   g.n, validate=True, stream=stream)
     D = gpm.Pattern.spec(O.DIAMOND, induced=False)
@@ -440,14 +514,43 @@ def run_sl(args):
         ach = c4_pass_bytes(g) / (c4ms / 1000.0) / 1e9
         c4k = " + ".join(sorted(k for k in prof if k.startswith("c4_") and k.endswith("_kernel")
                                 and k not in ("c4_bound_kernel", "c4_edeg_kernel", "c4_hub_units_kernel")))
+        alg = c4_pass_bytes(g)
         roof = {"bound": "hbm", "kernel": c4k, "achieved": ach, "peak": peak,
-                "unit": "GB/s", "frac": ach / peak, "traffic": None, "peak_source": peak_kind}
+                "unit": "GB/s", "frac": ach / peak, "traffic": None, "peak_source": peak_kind,
+                "algorithmic_bytes_per_step": alg, "ms_per_step_4cycle_kernels": c4ms,
+                "kernel_digest": c4_digest()}
+        cnt = NCU_COUNTERS.get("sl-chunglu4m", {}).get("c4")
+        if cnt and cnt.get("digest") == c4_digest():
+            roof.update(traffic=cnt["dram_bytes_per_step"], traffic_over_algorithmic=cnt["dram_bytes_per_step"] / alg,
+                        traffic_note="DRAM bytes per step of the 4-cycle kernels (ncu, every launch of one step)")
     G.close()
-    return {"workload": SL_WORKLOAD, "counts": {"diamond": counts[0], "4-cycle": counts[1]},
+    return {"workload": SL_WORKLOAD, "c4_options": gpm.get_options(), "counts": {"diamond": counts[0], "4-cycle": counts[1]},
             "ms_per_step": ms, "matches_per_s": (counts[0] + counts[1]) / (ms / 1000.0),
             "listing_s_for_2x10^6": list_s, "gpu_launches": launches, "roofline": roof, "clocks": clk.summary(),
             "kernels": {k: {"launches": v["launches"], "ms_per_launch": v["ms"] / max(v["launches"], 1)}
                         for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}}
+
+
+def _golden(name):
+    p = os.path.join(ROOT, "tests", "golden", "fullsize_counts.json")
+    try:
+        return json.load(open(p)).get(name)
+    except (OSError, ValueError):
+        return None
+
+
+def compact_sl(d):
+    """The SL leg for the headline line: counts (and whether they equal the
+    oracle's stored totals), time per step, the 4-cycle pass roofline."""
+    gold = _golden("sl_chunglu4m")
+    keep = ("workload", "counts", "ms_per_step", "matches_per_s", "listing_s_for_2x10^6", "gpu_launches",
+            "roofline", "clocks")
+    out = {k: d[k] for k in keep if k in d}
+    out["kernels"] = dict(list(d["kernels"].items())[:6])
+    if gold:
+        out["equal_to_oracle_totals"] = (d["counts"]["diamond"] == gold.get("diamond")
+                                         and d["counts"]["4-cycle"] == gold.get("cycle4"))
+    return out
 
 
 CLIQUE6_WORKLOAD = ("6-clique counting, R-MAT scale 20 (1,048,576 vertices), edge factor 16, (0.57,0.19,0.19,0.05), "
@@ -588,7 +691,9 @@ def run_tc(args):
     ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
     ms2 = sum(a.elapsed_time(b) for a, b in ev2) / len(ev2)
     G.close()
-    return {"workload": TC_WORKLOAD, "triangles": want[0], "ms_per_step_with_orientation": ms,
+    gold = _golden("tc_rmat14")
+    return {"workload": TC_WORKLOAD, "triangles": want[0], "equal_to_oracle_total": bool(gold) and gold.get("clique3") == want[0],
+            "ms_per_step_with_orientation": ms,
             "ms_count_only": ms2, "triangles_per_s": want[0] / (ms2 / 1000.0),
             "note": "the graph (1.7 MB CSR) is L2-resident; the path is launch/latency-bound"}
 
@@ -749,11 +854,95 @@ def run_ours(args):
             "step_ms": step_ms}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g)
+        line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(g, (4, 5), UNIT, line["cpu_baseline"])
+    G.close()
+    del rp_d, col_d, flush
+    if rank == 0 and world == 1 and not args.no_legs:
+        # the other configurations on the same GPU, compact (full lines: --workload sl / tc)
+        line["legs"] = {"sl": compact_sl(run_sl(args)), "tc": run_tc(args)}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    G.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+# Named workloads for profilers (`--case NAME --reps N`): build the seeded
+# input, upload it once, repeat the counting path (orientation included) `reps`
+# times and print the counts. No timing is reported: a profiler measures.
+CASES = {
+    "clique-rmat20": ("rmat20", "clique45"),
+    "clique-rmat21": ("rmat21", "clique45"),
+    "clique6-rmat20": ("rmat20", "clique6"),
+    "clique789-cl1m": ("chunglu1m", "clique789"),
+    "clique7-rmat16": ("rmat16", "clique7"),
+    "tc-rmat14": ("rmat14", "tc"),
+    "motif4-rmat18": ("rmat18", "motif4"),
+    "sl-chunglu1m": ("chunglu1m", "sl"),
+    "sl-chunglu2m": ("chunglu2m", "sl"),
+    "sl-chunglu4m": ("chunglu4m", "sl"),
+}
+
+
+def _case_graph(name):
+    from paper_2011_03135_b300 import graphgen as gg
+    if name == "rmat20":
+        return gg.workload_clique6_rmat20()
+    if name == "rmat21":
+        return gg.workload_clique_rmat21()
+    if name == "rmat14":
+        return gg.workload_tc_rmat14()
+    if name == "rmat16":
+        return gg.rmat(16, 16.0, seed=2)
+    if name == "rmat18":
+        return gg.rmat(18, 16.0, seed=2)
+    if name == "chunglu1m":
+        return gg.workload_clique789_chung_lu1m()
+    if name == "chunglu2m":
+        return gg.chung_lu(1 << 21, 24.0, 2.1, seed=3)
+    if name == "chunglu4m":
+        return gg.workload_sl_chung_lu4m()
+    raise ValueError(name)
+
+
+def _case_patterns(gpm, name):
+    if name == "clique45":
+        return [gpm.Pattern.clique(4), gpm.Pattern.clique(5)]
+    if name == "clique6":
+        return [gpm.Pattern.clique(6)]
+    if name == "clique789":
+        return [7, 8, 9]
+    if name == "clique7":
+        return [7]
+    if name == "tc":
+        return [gpm.Pattern.clique(3)]
+    if name == "motif4":
+        return gpm.Pattern.motifs(4)
+    if name == "sl":
+        d = np.zeros((4, 4), np.uint8)
+        for a, b in [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3)]:
+            d[a, b] = d[b, a] = 1
+        c = np.zeros((4, 4), np.uint8)
+        for a, b in [(0, 2), (2, 1), (1, 3), (3, 0)]:
+            c[a, b] = c[b, a] = 1
+        return [gpm.Pattern.spec(d, induced=False), gpm.Pattern.spec(c, induced=False)]
+    raise ValueError(name)
+
+
+def run_case(args):
+    import torch
+    from paper_2011_03135_b300 import gpm
+    gname, pname = CASES[args.case]
+    g = _case_graph(gname)
+    G = gpm.Graph.from_host(g)
+    pats = _case_patterns(gpm, pname)
+    out = None
+    for _ in range(args.reps):
+        G.reset()
+        out = [gpm.count_cliques(G, k) for k in pats] if isinstance(pats[0], int) else gpm.count(G, pats)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "n": g.n, "m": g.m, "counts": out}))
+    G.close()
     return 0
 
 
@@ -766,6 +955,7 @@ def main():
     ap.add_argument("--orientation", choices=["degree", "core"], default="degree",
                     help="order of the orientation for the k-clique leg (core: k-core peel at prepare time)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-legs", action="store_true", help="headline leg only (no sl / tc legs in its line)")
     ap.add_argument("--workload", choices=["cliques", "clique6", "clique789", "batched", "served", "sl", "tc"],
                     default="cliques")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
@@ -773,7 +963,14 @@ def main():
     ap.add_argument("--serve-grace", type=float, default=10.0)
     ap.add_argument("--batch-queries", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--c4-range-bound", type=int, default=0, help="4-cycle tuning for the sl leg (0: library default)")
+    ap.add_argument("--c4-range-width", type=int, default=0)
+    ap.add_argument("--c4-hub-bound", type=int, default=0)
+    ap.add_argument("--case", choices=sorted(CASES), help="run a named workload for a profiler and exit")
+    ap.add_argument("--reps", type=int, default=1)
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":

@@ -43,7 +43,8 @@ void free_graph(gpm_graph *g) {
   void *ptrs[] = {g->rowptr, g->col,   g->deg,        g->drow,       g->dcol,     g->tasks,
                   g->work,   g->t_edge, g->xl_pool, g->tally_pool, g->list_scratch, g->c4_tasks, g->c4_bucket_buf,
                   g->prep_outdeg, g->prep_tiles, g->prep_keys, g->edeg, g->c4_hub_units, g->c4_hub_tally,
-                  g->c4_hub_touched, g->c4_hub_ctr, g->core, g->core_work};
+                  g->c4_hub_touched, g->c4_hub_ctr, g->core, g->core_work, g->c4p_tasks, g->c4p_bval,
+                  g->c4p_items, g->c4_roff};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete g;
@@ -252,6 +253,15 @@ int gpm_set_options(const gpm_options_t *opt) {
     t.c4_hub_bound = opt->c4_hub_bound;
   }
   if (opt->batch_direct_us) t.batch_direct_us = opt->batch_direct_us;
+  if (opt->c4_range_bound) {
+    if (opt->c4_range_bound < 512) return gpm_fail(GPM_E_INVALID_ARG, "c4_range_bound must be >= 512");
+    t.c4_range_bound = opt->c4_range_bound;
+  }
+  if (opt->c4_range_width) {
+    if (opt->c4_range_width < 64 || opt->c4_range_width > 98304 || (opt->c4_range_width & 1u))
+      return gpm_fail(GPM_E_INVALID_ARG, "c4_range_width must be even and in [64, 98304]");
+    t.c4_range_width = opt->c4_range_width;
+  }
   return GPM_OK;
 }
 
@@ -263,6 +273,8 @@ int gpm_get_options(gpm_options_t *opt) {
   opt->blocks_per_sm = gpm_tune().blocks_per_sm;
   opt->c4_hub_bound = gpm_tune().c4_hub_bound;
   opt->batch_direct_us = gpm_tune().batch_direct_us;
+  opt->c4_range_bound = gpm_tune().c4_range_bound;
+  opt->c4_range_width = gpm_tune().c4_range_width;
   return GPM_OK;
 }
 
@@ -332,6 +344,7 @@ int gpm_graph_reset(gpm_graph_t g) {
   std::lock_guard<std::mutex> lk(g->mu);
   g->prepared = false;
   g->c4_ready = false;
+  g->c4p_ready = false;
   g->tune_warp_max = g->tune_cta_max = 0;
   return GPM_OK;
 }
@@ -462,7 +475,7 @@ int gpm_count_async(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uin
   std::lock_guard<std::mutex> lk(g->mu);
   if (!g->prepared) return gpm_fail(GPM_E_INVALID_ARG, "graph is not prepared (call gpm_graph_prepare first)");
   for (uint32_t i = 0; i < npat; ++i)
-    if (pats[i] && pats[i]->cls == PC_CYCLE4 && !g->c4_ready) {
+    if (pats[i] && pats[i]->cls == PC_CYCLE4 && !gpm_c4_plain_ready(g)) {
       // the 4-cycle task lists are built (with a host synchronisation) on first use
       uint64_t tmp[16];
       GPM_TRY(count_to_host(g, pats, npat, 0, g->n, false, tmp, as_stream(stream)));

@@ -55,6 +55,11 @@ struct gpm_tuning {
   uint32_t blocks_per_sm = 0;      // 0 = occupancy-derived
   uint32_t c4_hub_bound = 1048576; // 4-cycle roots above this wedge bound: hub path
   uint32_t batch_direct_us = 1000;  // batched queries at least this slow run their plain path
+  // plain count path: 4-cycle roots whose wedge bound exceeds this are counted
+  // by range-partitioned shared-memory tallies (0xffffffff: never; then the
+  // bucketed and hub classes above take them)
+  uint32_t c4_range_bound = 1048576;
+  uint32_t c4_range_width = 98304;  // vertex ids per tally range (even, <= 98304)
 };
 gpm_tuning &gpm_tune();
 
@@ -135,6 +140,23 @@ struct gpm_graph {
   uint32_t c4_hub_R = 0;
   unsigned int *c4_hub_ctr = nullptr;
   size_t c4_hub_ctr_words = 0;
+  // plain count path with range tallies: its own root classes [0,1) small,
+  // [1,2) bucketed, [2,3) range roots; range roots become items
+  // {v0, first range, end range} ordered by decreasing wedge bound.
+  // c4_roff: per vertex, c4_nr1 = ranges + 1 positions in col (32-bit) where
+  // the ids of each range of c4_roff_width ids begin in its list (built once
+  // per graph and width, like edeg)
+  uint32_t *c4p_tasks = nullptr;
+  uint32_t *c4p_bval = nullptr;
+  uint32_t c4p_begin[4] = {0, 0, 0, 0};
+  uint32_t c4p_bucket_maxb = 0;
+  uint32_t c4p_bound = 0, c4p_width = 0;
+  bool c4p_ready = false;
+  uint32_t *c4p_items = nullptr;  // uint4 per item
+  size_t c4p_items_cap = 0;
+  uint32_t c4p_nitems = 0;
+  uint32_t *c4_roff = nullptr;
+  uint32_t c4_roff_width = 0, c4_nr1 = 0;
 
   size_t device_bytes = 0;
   std::mutex mu;
@@ -211,6 +233,9 @@ int gpm_c4_hub_enqueue(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigne
                        uint32_t *nlaunch);
 
 // 4-cycles whose order-last vertex lies in [root_lo, root_hi): acc[ACC_C4] += count.
+// The first call per graph builds the root classes with host synchronisations;
+// gpm_c4_plain_ready tells whether they exist (later calls only enqueue).
+bool gpm_c4_plain_ready(const gpm_graph *g);
 int gpm_launch_cycles4(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigned long long *acc, cudaStream_t st);
 
 // Per-arc and per-vertex local-count terms (ACC_D .. ACC_T3). With

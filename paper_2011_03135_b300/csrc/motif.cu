@@ -83,7 +83,8 @@ constexpr uint32_t kHashSlots = gpm_dev::kC4HashSlots;
 __global__ void c4_bound_kernel(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
                                 const uint32_t *__restrict__ deg, const uint32_t *__restrict__ edeg, uint32_t n,
                                 uint32_t hub_bound, uint32_t *__restrict__ counts, uint32_t *__restrict__ tasks,
-                                uint32_t *__restrict__ cursors, int fill) {
+                                uint32_t *__restrict__ cursors, int fill, uint32_t *__restrict__ bvals = nullptr,
+                                uint32_t begin2 = 0) {
   // a warp takes 32 consecutive vertices, one at a time (lanes over the
   // neighbours); lane k keeps vertex k's class, and the 32 outcomes are
   // counted / placed with one atomic per class
@@ -116,7 +117,11 @@ __global__ void c4_bound_kernel(const uint64_t *__restrict__ rowptr, const uint3
         uint32_t pos = 0;
         if ((int)lane == leader) pos = atomicAdd(&cursors[c], (uint32_t)__popc(m));
         pos = __shfl_sync(0xffffffffu, pos, leader);
-        if (my_c == c) tasks[pos + __popc(m & ((1u << lane) - 1u))] = (uint32_t)(g0 + lane);
+        if (my_c == c) {
+          const uint32_t at = pos + __popc(m & ((1u << lane) - 1u));
+          tasks[at] = (uint32_t)(g0 + lane);
+          if (c == 2 && bvals) bvals[at - begin2] = my_b;
+        }
       } else {
         const uint32_t mb = __reduce_max_sync(0xffffffffu, my_c == 1 ? my_b : 0u);
         if (lane == 0) {
@@ -452,6 +457,183 @@ __global__ void __launch_bounds__(kC4BucketThreads) c4_bucket_kernel(C4Args a, u
 }
 
 // ---------------------------------------------------------------------------
+// large roots, plain count path: range-partitioned tallies in shared memory.
+// The wedge ends w of a root lie in [0, n); the id space is cut into ranges of
+// `width` ids, and a CTA takes the ranges of a root one after the other,
+// keeping a dense tally of the current range in shared memory (16-bit
+// counters, two per word: a count is at most the root's degree, < 65536).
+// For range r the wedges with an end in it are the segments of the lists
+// N(x), x before v0, between the precomputed offsets roff[x][r] and
+// roff[x][r+1] (lists are sorted by id), so every wedge is read once and
+// counted once in shared memory; C(c,2) is summed over the range's tally while
+// it is cleared for the next range.
+// ---------------------------------------------------------------------------
+constexpr int kRangeThreads = 1024;
+constexpr uint32_t kRangeMaxWidth = 98304;
+constexpr uint32_t kRangeTallyWords = kRangeMaxWidth / 2;  // 192 KB, a multiple of 4 words
+constexpr int kRangeRun = 4;  // wedge ends per lane in flight in the walk
+// dynamic shared memory: tally, segment prefix (threads + 1), warp sums (32),
+// segment starts (threads)
+constexpr size_t kRangeSmemBytes = 4ull * (kRangeTallyWords + kRangeThreads + 1 + 32 + kRangeThreads);
+
+// roff[x * nr1 + r] = rowptr[x] + (number of entries of N(x) with id < r *
+// width), for r = 0 .. nr1 - 1 (absolute positions in col; the last one is
+// rowptr[x + 1]). One warp per vertex; entry p writes the offsets of the
+// ranges that begin after its predecessor and at or before it, so every
+// offset is written once.
+__global__ void c4_roff_kernel(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col, uint32_t n,
+                               uint32_t width, uint32_t nr1, uint32_t *__restrict__ roff) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t x = warp; x < n; x += nwarps) {
+    const uint64_t b = rowptr[x];
+    const uint32_t d = (uint32_t)(rowptr[x + 1] - b);
+    uint32_t *row = roff + x * nr1;
+    for (uint32_t p = lane; p <= d; p += 32) {
+      const uint32_t lo = (p == 0) ? 0u : col[b + p - 1] / width + 1u;
+      const uint32_t hi = (p == d) ? nr1 - 1u : col[b + p] / width;
+      for (uint32_t r = lo; r <= hi; ++r) row[r] = (uint32_t)(b + p);
+    }
+  }
+}
+
+struct C4RangeArgs {
+  const uint64_t *__restrict__ rowptr;
+  const uint32_t *__restrict__ col;
+  const uint32_t *__restrict__ deg;
+  const uint32_t *__restrict__ edeg;
+  const uint32_t *__restrict__ roff;  // absolute positions in col
+  uint32_t nr1, width;
+  const uint4 *__restrict__ items;  // {v0, first range, end range, 0}
+  uint32_t nitems;
+  uint32_t root_lo, root_hi;
+  unsigned int *queue;
+  unsigned long long *acc;
+};
+
+// C(a,2) + C(b,2) for the two 16-bit counters of a tally word
+__device__ __forceinline__ unsigned long long pairs16(uint32_t v) {
+  const unsigned long long a = v & 0xffffu, b = v >> 16;
+  return (a * (a - (a > 0)) + b * (b - (b > 0))) >> 1;
+}
+
+__global__ void __launch_bounds__(kRangeThreads, 1) c4_range_kernel(C4RangeArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t *T = smem;
+  uint32_t *s_pre = T + kRangeTallyWords;        // kRangeThreads + 1
+  uint32_t *s_wsum = s_pre + kRangeThreads + 1;  // 32
+  uint32_t *s_base = s_wsum + 32;                // kRangeThreads
+  __shared__ uint4 s_item;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  uint4 *T4 = reinterpret_cast<uint4 *>(T);
+  for (uint32_t i = tid; i < kRangeTallyWords / 4; i += kRangeThreads) T4[i] = make_uint4(0u, 0u, 0u, 0u);
+  const uint32_t tw4 = (a.width / 2 + 3) / 4;  // uint4 words of one range's tally
+  unsigned long long acc = 0;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) {
+      const uint32_t it = atomicAdd(a.queue, 1u);
+      s_item = it < a.nitems ? a.items[it] : make_uint4(0xffffffffu, 0u, 0u, 0u);
+    }
+    __syncthreads();
+    const uint4 item = s_item;
+    if (item.x == 0xffffffffu) break;
+    const uint32_t v0 = item.x;
+    if (v0 < a.root_lo || v0 >= a.root_hi) continue;
+    const uint32_t d0 = a.deg[v0];
+    const uint64_t b0 = a.rowptr[v0], e0 = a.rowptr[v0 + 1];
+    for (uint32_t r = item.y; r < item.z; ++r) {
+      const uint32_t wbase = r * a.width;
+      for (uint64_t cb = b0; cb < e0; cb += kRangeThreads) {
+        // segment of N(x) in range r for this thread's x (length 0 unless x precedes v0)
+        const uint64_t e = cb + tid;
+        uint32_t len = 0, start = 0;
+        if (e < e0) {
+          const uint32_t x = a.col[e];
+          if (precedes(a.edeg[e], x, d0, v0)) {
+            const uint32_t *ro = a.roff + (uint64_t)x * a.nr1 + r;
+            const uint32_t o0 = ro[0];
+            len = ro[1] - o0;
+            start = o0;
+          }
+        }
+        const uint32_t cnt = (e0 - cb < (uint64_t)kRangeThreads) ? (uint32_t)(e0 - cb) : (uint32_t)kRangeThreads;
+        uint32_t incl = len;
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= (uint32_t)o) incl += y;
+        }
+        if (lane == 31) s_wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+          const uint32_t v = s_wsum[lane];
+          uint32_t wi = v;
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= (uint32_t)o) wi += y;
+          }
+          s_wsum[lane] = wi - v;
+        }
+        __syncthreads();
+        const uint32_t excl = incl - len + s_wsum[wid];
+        s_pre[tid] = excl;
+        if (tid == kRangeThreads - 1) s_pre[kRangeThreads] = excl + len;
+        s_base[tid] = start;
+        __syncthreads();
+        const uint32_t total = s_pre[cnt];
+        // blocks of kRangeRun * 32 wedge ends per warp, 32 consecutive ends per
+        // load (coalesced); the segment of an end is searched among the rows
+        // that the block's first and last ends fall in
+        for (uint32_t blk = wid * (32u * kRangeRun); blk < total; blk += kRangeThreads * kRangeRun) {
+          const uint32_t flast = min(blk + 32u * kRangeRun - 1u, total - 1u);
+          uint32_t ib = 0;
+          if (lane < 2) ib = gpm_dev::c4_row_of(s_pre, cnt, lane ? flast : blk);
+          const uint32_t ilo = __shfl_sync(0xffffffffu, ib, 0), ihi = __shfl_sync(0xffffffffu, ib, 1);
+          uint32_t wv[kRangeRun];
+          bool ok[kRangeRun];
+#pragma unroll
+          for (int q = 0; q < kRangeRun; ++q) {
+            const uint32_t f = blk + 32u * q + lane;
+            ok[q] = false;
+            wv[q] = 0;
+            if (f < total) {
+              uint32_t lo = ilo, hi = ihi + 1;  // largest i in [lo, hi) with s_pre[i] <= f
+              while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (s_pre[mid] <= f) lo = mid;
+                else hi = mid;
+              }
+              const uint32_t ee = s_base[lo] + (f - s_pre[lo]);
+              wv[q] = __ldg(a.col + ee);
+              ok[q] = precedes(__ldg(a.edeg + ee), wv[q], d0, v0);
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < kRangeRun; ++q)
+            if (ok[q]) {
+              const uint32_t t = wv[q] - wbase;
+              atomicAdd(&T[t >> 1], 1u << ((t & 1u) << 4));
+            }
+        }
+        __syncthreads();
+      }
+      // C(c,2) over the range's tally, clearing it for the next range
+      for (uint32_t i = tid; i < tw4; i += kRangeThreads) {
+        const uint4 v = T4[i];
+        if (v.x | v.y | v.z | v.w) {
+          acc += pairs16(v.x) + pairs16(v.y) + pairs16(v.z) + pairs16(v.w);
+          T4[i] = make_uint4(0u, 0u, 0u, 0u);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  acc = warp_sum(acc);
+  if (lane == 0 && acc) atomicAdd(&a.acc[ACC_C4], acc);
+}
+
+// ---------------------------------------------------------------------------
 // finalize: requested counts from the accumulators (one thread)
 // ---------------------------------------------------------------------------
 __global__ void finalize_kernel(FinalizeSpec spec, const unsigned long long *__restrict__ acc, uint64_t n, uint64_t m,
@@ -479,18 +661,24 @@ int gpm_launch_edge_terms(gpm_graph *g, bool use_t_edge, uint32_t root_lo, uint3
 // a hub root's tally is summed densely when n <= 4 x its wedge bound
 static inline bool hub_dense(uint32_t n, uint64_t bound) { return (uint64_t)n <= 4ull * bound; }
 
+// edeg[e] = deg(col[e]), built once per graph
+static int ensure_edeg(gpm_graph *g, cudaStream_t st) {
+  if (g->edeg) return GPM_OK;
+  const int blocks = gpm_num_sms(g->device) * 8;
+  GPM_TRY(gpm_graph_alloc(g, (void **)&g->edeg, sizeof(uint32_t) * (std::max<uint64_t>(g->nnz, 1) + kCsrPadWords)));
+  if (g->nnz) {
+    GPM_LAUNCH("c4_edeg_kernel", st, c4_edeg_kernel<<<blocks, 256, 0, st>>>(g->col, g->deg, g->nnz, g->edeg));
+    GPM_CUDA(cudaGetLastError());
+  }
+  return GPM_OK;
+}
+
 static int ensure_c4_tasks(gpm_graph *g, cudaStream_t st) {
   const uint32_t hub_bound = std::min(gpm_tune().c4_hub_bound, gpm_dev::kC4BucketMaxBound);
   if (g->c4_ready && g->c4_hub_bound == hub_bound) return GPM_OK;
   if (!g->c4_tasks) GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4_tasks, sizeof(uint32_t) * std::max<uint32_t>(g->n, 1)));
   const int blocks = gpm_num_sms(g->device) * 8;
-  if (!g->edeg) {
-    GPM_TRY(gpm_graph_alloc(g, (void **)&g->edeg, sizeof(uint32_t) * (std::max<uint64_t>(g->nnz, 1) + kCsrPadWords)));
-    if (g->nnz) {
-      GPM_LAUNCH("c4_edeg_kernel", st, c4_edeg_kernel<<<blocks, 256, 0, st>>>(g->col, g->deg, g->nnz, g->edeg));
-      GPM_CUDA(cudaGetLastError());
-    }
-  }
+  GPM_TRY(ensure_edeg(g, st));
   uint32_t *tmp = reinterpret_cast<uint32_t *>(g->work + WK_MISC);  // counts[3], max bound, cursors[3]
   GPM_CUDA(cudaMemsetAsync(tmp, 0, 8 * sizeof(uint32_t), st));
   if (g->n) {
@@ -674,7 +862,219 @@ int gpm_c4_hub_enqueue(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigne
 
 int gpm_build_c4_tasks(gpm_graph *g, cudaStream_t st) { return ensure_c4_tasks(g, st); }
 
+
+// ---------------------------------------------------------------------------
+// plain count path with range tallies for the large roots
+// ---------------------------------------------------------------------------
+// the range tallies use 16-bit counters (a count is at most the root's
+// degree) and 32-bit positions in col
+static bool c4_use_range(const gpm_graph *g) {
+  return gpm_tune().c4_range_bound != 0xffffffffu && g->max_degree <= 0xffffu && g->nnz < (1ull << 32);
+}
+
+// range offsets of every list for ranges of `width` ids, built once per graph and width
+static int ensure_c4_roff(gpm_graph *g, uint32_t width, cudaStream_t st) {
+  if (g->c4_roff && g->c4_roff_width == width) return GPM_OK;
+  if (g->c4_roff) {
+    cudaFree(g->c4_roff);
+    g->device_bytes -= sizeof(uint32_t) * (size_t)g->c4_nr1 * std::max<uint32_t>(g->n, 1);
+    g->c4_roff = nullptr;
+  }
+  const uint32_t nr = std::max<uint32_t>(1, (uint32_t)(((uint64_t)g->n + width - 1) / width));
+  const uint32_t nr1 = nr + 1;
+  GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4_roff, sizeof(uint32_t) * (size_t)nr1 * std::max<uint32_t>(g->n, 1)));
+  g->c4_roff_width = width;
+  g->c4_nr1 = nr1;
+  if (g->n) {
+    const int blocks = gpm_num_sms(g->device) * 8;
+    GPM_LAUNCH("c4_roff_kernel", st,
+               c4_roff_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, g->n, width, nr1, g->c4_roff));
+    GPM_CUDA(cudaGetLastError());
+  }
+  return GPM_OK;
+}
+
+// Root classes of the plain path (small, bucketed, range) and the range items:
+// one item per (root, range), roots in order of decreasing wedge bound and the
+// ranges of a root consecutive, so that the items running at the same time
+// belong to a few roots whose neighbour lists stay in L2 while every range of
+// those roots is tallied.
+static int ensure_c4_plain(gpm_graph *g, cudaStream_t st) {
+  const uint32_t bound = std::max<uint32_t>(gpm_tune().c4_range_bound, kSmallBound);
+  const uint32_t width = gpm_tune().c4_range_width;
+  if (g->c4p_ready && g->c4p_bound == bound && g->c4p_width == width) return GPM_OK;
+  GPM_TRY(ensure_edeg(g, st));
+  GPM_TRY(ensure_c4_roff(g, width, st));
+  const size_t nw = std::max<uint32_t>(g->n, 1);
+  if (!g->c4p_tasks) GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4p_tasks, sizeof(uint32_t) * nw));
+  if (!g->c4p_bval) GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4p_bval, sizeof(uint32_t) * nw));
+  const int blocks = gpm_num_sms(g->device) * 8;
+  uint32_t *tmp = reinterpret_cast<uint32_t *>(g->work + WK_MISC);  // counts[3], max bound, cursors[3]
+  GPM_CUDA(cudaMemsetAsync(tmp, 0, 8 * sizeof(uint32_t), st));
+  if (g->n) {
+    GPM_LAUNCH("c4_bound_kernel", st,
+               c4_bound_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->edeg, g->n, bound, tmp, nullptr,
+                                                        nullptr, 0));
+    GPM_CUDA(cudaGetLastError());
+  }
+  uint32_t h[4];
+  GPM_CUDA(cudaMemcpyAsync(h, tmp, sizeof(h), cudaMemcpyDeviceToHost, st));
+  GPM_CUDA(cudaStreamSynchronize(st));
+  g->c4p_begin[0] = 0;
+  g->c4p_begin[1] = h[0];
+  g->c4p_begin[2] = h[0] + h[1];
+  g->c4p_begin[3] = h[0] + h[1] + h[2];
+  g->c4p_bucket_maxb = h[3];
+  const uint32_t cur[3] = {0, h[0], h[0] + h[1]};
+  GPM_CUDA(cudaMemcpyAsync(tmp + 4, cur, sizeof(cur), cudaMemcpyHostToDevice, st));
+  if (g->n) {
+    GPM_LAUNCH("c4_bound_kernel", st,
+               c4_bound_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->edeg, g->n, bound, nullptr,
+                                                        g->c4p_tasks, tmp + 4, 1, g->c4p_bval, g->c4p_begin[2]));
+    GPM_CUDA(cudaGetLastError());
+  }
+  const uint32_t nbig = h[2];
+  std::vector<uint32_t> roots(nbig), bv(nbig);
+  if (nbig) {
+    GPM_CUDA(cudaMemcpyAsync(roots.data(), g->c4p_tasks + g->c4p_begin[2], sizeof(uint32_t) * nbig,
+                             cudaMemcpyDeviceToHost, st));
+    GPM_CUDA(cudaMemcpyAsync(bv.data(), g->c4p_bval, sizeof(uint32_t) * nbig, cudaMemcpyDeviceToHost, st));
+  }
+  GPM_CUDA(cudaStreamSynchronize(st));
+  std::vector<uint32_t> ord(nbig);
+  for (uint32_t i = 0; i < nbig; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) {
+    return bv[x] != bv[y] ? bv[x] > bv[y] : roots[x] < roots[y];
+  });
+  const uint32_t nr = g->c4_nr1 - 1;
+  std::vector<uint32_t> items;
+  items.reserve(4 * (size_t)nbig * nr);
+  for (uint32_t i : ord) {
+    for (uint32_t r = 0; r < nr; ++r) {
+      items.push_back(roots[i]);
+      items.push_back(r);
+      items.push_back(r + 1);
+      items.push_back(0u);
+    }
+  }
+  g->c4p_nitems = (uint32_t)(items.size() / 4);
+  const size_t bytes = sizeof(uint32_t) * std::max<size_t>(items.size(), 4);
+  if (g->c4p_items_cap < bytes) {
+    if (g->c4p_items) {
+      cudaFree(g->c4p_items);
+      g->device_bytes -= g->c4p_items_cap;
+      g->c4p_items = nullptr;
+      g->c4p_items_cap = 0;
+    }
+    GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4p_items, bytes));
+    g->c4p_items_cap = bytes;
+  }
+  if (!items.empty())
+    GPM_CUDA(cudaMemcpyAsync(g->c4p_items, items.data(), sizeof(uint32_t) * items.size(), cudaMemcpyHostToDevice, st));
+  GPM_CUDA(cudaStreamSynchronize(st));
+  g->c4p_ready = true;
+  g->c4p_bound = bound;
+  g->c4p_width = width;
+  return GPM_OK;
+}
+
+bool gpm_c4_plain_ready(const gpm_graph *g) { return c4_use_range(g) ? g->c4p_ready : g->c4_ready; }
+
+static int launch_c4_bucketed(gpm_graph *g, const C4Args &a, const uint32_t *tasks, uint32_t ntasks, uint32_t maxb,
+                              unsigned int *queue, cudaStream_t st) {
+  const int sms = gpm_num_sms(g->device);
+  C4Args b = a;
+  b.tasks = tasks;
+  b.ntasks = ntasks;
+  b.queue = queue;
+  const size_t smem = (size_t)gpm_dev::c4_bucket_smem_words(kC4BucketThreads / 32) * 4;
+  GPM_CUDA(cudaFuncSetAttribute(c4_bucket_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c4_bucket_kernel, kC4BucketThreads, smem));
+  const uint64_t slot_words = gpm_dev::c4_bucket_slot_words(std::max<uint32_t>(maxb, 1));
+  size_t slots = (size_t)sms * (size_t)std::max(per_sm, 1);
+  slots = std::min<size_t>(slots, ntasks);
+  const size_t need = slots * slot_words * 4;
+  if (g->c4_bucket_bytes < need) {
+    if (g->c4_bucket_buf) {
+      cudaFree(g->c4_bucket_buf);
+      g->device_bytes -= g->c4_bucket_bytes;
+      g->c4_bucket_buf = nullptr;
+      g->c4_bucket_bytes = 0;
+    }
+    GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4_bucket_buf, need));
+    g->c4_bucket_bytes = need;
+  }
+  b.pool = g->c4_bucket_buf;
+  GPM_LAUNCH("c4_bucket_kernel", st, c4_bucket_kernel<<<(unsigned)slots, kC4BucketThreads, smem, st>>>(b, slot_words));
+  GPM_CUDA(cudaGetLastError());
+  return GPM_OK;
+}
+
+static int launch_c4_small(gpm_graph *g, const C4Args &a, const uint32_t *tasks, uint32_t ntasks, unsigned int *queue,
+                           cudaStream_t st) {
+  const int sms = gpm_num_sms(g->device);
+  C4Args s = a;
+  s.tasks = tasks;
+  s.ntasks = ntasks;
+  s.queue = queue;
+  const size_t smem = (size_t)8 * 2 * kHashSlots * 4;
+  GPM_CUDA(cudaFuncSetAttribute(c4_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c4_small_kernel, 256, smem));
+  int blocks = std::max(1, std::min<int>(sms * std::max(per_sm, 1), (int)((ntasks + 7) / 8)));
+  GPM_LAUNCH("c4_small_kernel", st, c4_small_kernel<<<blocks, 256, smem, st>>>(s));
+  GPM_CUDA(cudaGetLastError());
+  return GPM_OK;
+}
+
+static int launch_cycles4_range(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigned long long *acc,
+                                cudaStream_t st) {
+  GPM_TRY(ensure_c4_plain(g, st));
+  unsigned int *queues = reinterpret_cast<unsigned int *>(g->work + WK_QUEUE0) + 4;
+  GPM_CUDA(cudaMemsetAsync(queues, 0, 3 * sizeof(unsigned int), st));
+  C4Args a{};
+  a.rowptr = g->rowptr;
+  a.col = g->col;
+  a.deg = g->deg;
+  a.edeg = g->edeg;
+  a.root_lo = root_lo;
+  a.root_hi = root_hi;
+  a.acc = acc;
+  a.status = reinterpret_cast<unsigned int *>(g->work + WK_STATUS);
+  a.n = g->n;
+  if (g->c4p_nitems) {
+    C4RangeArgs r{};
+    r.rowptr = g->rowptr;
+    r.col = g->col;
+    r.deg = g->deg;
+    r.edeg = g->edeg;
+    r.roff = g->c4_roff;
+    r.nr1 = g->c4_nr1;
+    r.width = g->c4_roff_width;
+    r.items = reinterpret_cast<const uint4 *>(g->c4p_items);
+    r.nitems = g->c4p_nitems;
+    r.root_lo = root_lo;
+    r.root_hi = root_hi;
+    r.queue = queues + 1;
+    r.acc = acc;
+    GPM_CUDA(cudaFuncSetAttribute(c4_range_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRangeSmemBytes));
+    int per_sm = 0;
+    GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c4_range_kernel, kRangeThreads, kRangeSmemBytes));
+    const unsigned blocks = (unsigned)std::min<uint64_t>((uint64_t)gpm_num_sms(g->device) * std::max(per_sm, 1),
+                                                         g->c4p_nitems);
+    GPM_LAUNCH("c4_range_kernel", st, c4_range_kernel<<<blocks, kRangeThreads, kRangeSmemBytes, st>>>(r));
+    GPM_CUDA(cudaGetLastError());
+  }
+  const uint32_t nsmall = g->c4p_begin[1], nbucket = g->c4p_begin[2] - g->c4p_begin[1];
+  if (nbucket)
+    GPM_TRY(launch_c4_bucketed(g, a, g->c4p_tasks + g->c4p_begin[1], nbucket, g->c4p_bucket_maxb, queues + 2, st));
+  if (nsmall) GPM_TRY(launch_c4_small(g, a, g->c4p_tasks, nsmall, queues, st));
+  return GPM_OK;
+}
+
 int gpm_launch_cycles4(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigned long long *acc, cudaStream_t st) {
+  if (c4_use_range(g)) return launch_cycles4_range(g, root_lo, root_hi, acc, st);
   GPM_TRY(ensure_c4_tasks(g, st));
   unsigned int *queues = reinterpret_cast<unsigned int *>(g->work + WK_QUEUE0) + 4;
   GPM_CUDA(cudaMemsetAsync(queues, 0, 3 * sizeof(unsigned int), st));
@@ -688,51 +1088,12 @@ int gpm_launch_cycles4(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigne
   a.acc = acc;
   a.status = reinterpret_cast<unsigned int *>(g->work + WK_STATUS);
   a.n = g->n;
-  const int sms = gpm_num_sms(g->device);
   const uint32_t nsmall = g->c4_begin[1] - g->c4_begin[0];
   const uint32_t nbucket = g->c4_begin[2] - g->c4_begin[1];
   const uint32_t nbig = g->c4_begin[3] - g->c4_begin[2];
-  if (nsmall) {
-    C4Args s = a;
-    s.tasks = g->c4_tasks;
-    s.ntasks = nsmall;
-    s.queue = queues;
-    const size_t smem = (size_t)8 * 2 * kHashSlots * 4;
-    GPM_CUDA(cudaFuncSetAttribute(c4_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c4_small_kernel, 256, smem));
-    int blocks = std::max(1, std::min<int>(sms * std::max(per_sm, 1), (int)((nsmall + 7) / 8)));
-    GPM_LAUNCH("c4_small_kernel", st, c4_small_kernel<<<blocks, 256, smem, st>>>(s));
-    GPM_CUDA(cudaGetLastError());
-  }
-  if (nbucket) {
-    C4Args b = a;
-    b.tasks = g->c4_tasks + g->c4_begin[1];
-    b.ntasks = nbucket;
-    b.queue = queues + 2;
-    const size_t smem = (size_t)gpm_dev::c4_bucket_smem_words(kC4BucketThreads / 32) * 4;
-    GPM_CUDA(cudaFuncSetAttribute(c4_bucket_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c4_bucket_kernel, kC4BucketThreads, smem));
-    const uint64_t slot_words = gpm_dev::c4_bucket_slot_words(std::max<uint32_t>(g->c4_bucket_maxb, 1));
-    size_t slots = (size_t)sms * (size_t)std::max(per_sm, 1);
-    slots = std::min<size_t>(slots, nbucket);
-    const size_t need = slots * slot_words * 4;
-    if (g->c4_bucket_bytes < need) {
-      if (g->c4_bucket_buf) {
-        cudaFree(g->c4_bucket_buf);
-        g->device_bytes -= g->c4_bucket_bytes;
-        g->c4_bucket_buf = nullptr;
-        g->c4_bucket_bytes = 0;
-      }
-      GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4_bucket_buf, need));
-      g->c4_bucket_bytes = need;
-    }
-    b.pool = g->c4_bucket_buf;
-    GPM_LAUNCH("c4_bucket_kernel", st,
-               c4_bucket_kernel<<<(unsigned)slots, kC4BucketThreads, smem, st>>>(b, slot_words));
-    GPM_CUDA(cudaGetLastError());
-  }
+  if (nsmall) GPM_TRY(launch_c4_small(g, a, g->c4_tasks, nsmall, queues, st));
+  if (nbucket)
+    GPM_TRY(launch_c4_bucketed(g, a, g->c4_tasks + g->c4_begin[1], nbucket, g->c4_bucket_maxb, queues + 2, st));
   if (nbig) {
     GPM_TRY(ensure_c4_hub(g, st));
     GPM_TRY(launch_c4_hub(g, root_lo, root_hi, acc, st, nullptr));

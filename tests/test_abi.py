@@ -142,4 +142,12 @@ def test_options_roundtrip(lib):
     assert old["batch_direct_us"] == 1000
     lib.set_options(batch_direct_us=5)
     assert lib.get_options()["batch_direct_us"] == 5
+    assert old["c4_range_bound"] == 1048576 and old["c4_range_width"] == 98304
+    lib.set_options(c4_range_bound=0xffffffff, c4_range_width=512)
+    assert lib.get_options()["c4_range_bound"] == 0xffffffff
+    assert lib.get_options()["c4_range_width"] == 512
+    for bad in (dict(c4_range_bound=100), dict(c4_range_width=63), dict(c4_range_width=98306),
+                dict(c4_range_width=1001)):
+        with pytest.raises(lib.GpmError):
+            lib.set_options(**bad)
     lib.set_options(**{k: v for k, v in old.items() if v})

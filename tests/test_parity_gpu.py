@@ -110,14 +110,55 @@ def test_root_ranges_match_oracle(gpm):
     G.close()
 
 
+def _multi_hub_graph(hubs=(1500, 2200, 3100), nl=3200, nm=120, per=3, seed=6):
+    """Hubs joined to random subsets of a set L, each vertex of L joined to
+    `per` random vertices of a set M: the hubs are 4-cycle roots whose lists
+    are longer than one 1024-entry chunk, with wedges hub - x - w through L."""
+    rng = np.random.default_rng(seed)
+    nh = len(hubs)
+    L0, M0 = nh, nh + nl
+    e = []
+    for h, d in enumerate(hubs):
+        e += [(h, L0 + int(x)) for x in rng.choice(nl, size=d, replace=False)]
+    for x in range(nl):
+        e += [(L0 + x, M0 + int(w)) for w in rng.choice(nm, size=per, replace=False)]
+    return gg.from_edges(nh + nl + nm, e, name="multihub")
+
+
+@pytest.mark.parametrize("width,bound", [(98304, 1048576), (98304, 512), (512, 512), (64, 2000), (1000, 4000)])
+def test_cycles4_range_path(gpm, width, bound):
+    # large roots counted range by range over vertex ids with a dense
+    # shared-memory tally: narrow ranges make many ranges per root, a low bound
+    # sends most roots there, and the multi-hub graph has roots whose lists
+    # span several 1024-entry chunks; totals, root ranges and the motif
+    # inversion against the oracle
+    old = gpm.get_options()
+    try:
+        gpm.set_options(c4_range_width=width, c4_range_bound=bound)
+        C = gpm.Pattern.spec(O.CYCLE4, induced=False)
+        for g in _medium() + [gg.rmat(12, 16.0, seed=31), _multi_hub_graph()]:
+            G = gpm.Graph.from_host(g)
+            want = O.cycles4(g)
+            assert gpm.count(G, [C]) == [want], g.name
+            assert gpm.count(G, [C]) == [want], g.name  # the tally was left at zero
+            cuts = [0, g.n // 3, g.n // 3 + 1, g.n - 5, g.n]
+            for lo, hi in zip(cuts[:-1], cuts[1:]):
+                assert gpm.count_roots(G, [C], lo, hi) == [O.cycles4(g, lo, hi)], (g.name, lo, hi)
+            assert gpm.count(G, gpm.Pattern.motifs(4)) == O.motifs(g, 4), g.name
+            G.close()
+    finally:
+        gpm.set_options(**{k: v for k, v in old.items() if v})
+
+
 @pytest.mark.parametrize("hub_bound", [513, 4000, 60000])
 def test_cycles4_hub_path(gpm, hub_bound):
     # a low hub threshold sends many roots of medium graphs through the
     # whole-grid tally path (groups of roots per launch, tally reset by the
-    # next launch); totals, root ranges and the motif inversion must not change
+    # next launch); totals, root ranges and the motif inversion must not change.
+    # The plain path takes the hub class only with the range tallies switched off.
     old = gpm.get_options()
     try:
-        gpm.set_options(c4_hub_bound=hub_bound)
+        gpm.set_options(c4_hub_bound=hub_bound, c4_range_bound=0xffffffff)
         C = gpm.Pattern.spec(O.CYCLE4, induced=False)
         for g in _medium():
             G = gpm.Graph.from_host(g)
