@@ -157,10 +157,15 @@ int gpm_pattern_clique(uint32_t k, gpm_pattern_t *out);
 
 /*
  * All connected k-vertex patterns, vertex-induced (Section 2, k-MC; the
- * helper "generate all k-vertex patterns" of Section 3.1), k = 3 or 4.
- * Writes *npat handles to out[] (room for 6 must be provided), in the fixed
+ * helper "generate all k-vertex patterns" of Section 3.1), k = 3, 4 or 5.
+ * Writes *npat handles to out[] (room for 21 must be provided), in the fixed
  * order  k=3: wedge, triangle;
- *        k=4: 3-star, 4-path, tailed triangle, 4-cycle, diamond, 4-clique.
+ *        k=4: 3-star, 4-path, tailed triangle, 4-cycle, diamond, 4-clique;
+ *        k=5: the 21 connected 5-vertex graphs by number of edges, then by
+ *             their smallest pair mask over the 120 vertex orders, where the
+ *             pair mask of a 5-vertex graph has bit b set for the b-th pair
+ *             of (0,1), (0,2), (0,3), (0,4), (1,2), (1,3), (1,4), (2,3), (2,4),
+ *             (3,4) that is an edge (so 0: 4-path, ..., 20: 5-clique).
  */
 int gpm_pattern_motifs(uint32_t k, gpm_pattern_t *out, uint32_t *npat);
 
@@ -170,6 +175,7 @@ int gpm_pattern_destroy(gpm_pattern_t p);
 #define GPM_STRATEGY_CLIQUE_DAG 1    /* orientation + local-graph bitmap search */
 #define GPM_STRATEGY_LOCAL_COUNT 2   /* local counting (Section 5) for 3/4-vertex patterns */
 #define GPM_STRATEGY_EDGE 3          /* single edge / vertex: closed form */
+#define GPM_STRATEGY_ENUMERATE 4     /* pattern-oblivious enumeration with connectivity codes (5 vertices) */
 
 typedef struct {
   uint32_t k;
@@ -177,7 +183,7 @@ typedef struct {
   uint32_t induced;
   uint32_t is_clique;
   uint32_t strategy;           /* GPM_STRATEGY_* */
-  uint32_t motif_index;        /* position in the k=3/k=4 motif order, or UINT32_MAX */
+  uint32_t motif_index;        /* position in the k = 3, 4, 5 motif order, or UINT32_MAX */
   uint64_t automorphisms;      /* |Aut(P)| */
   uint32_t n_sb_pairs;         /* symmetry-breaking constraints id(f(a)) < id(f(b)) */
   uint32_t sb_pairs[2 * 28];   /* (a_0, b_0, a_1, b_1, ...) in pattern vertex numbering */
@@ -196,12 +202,31 @@ int gpm_pattern_info(gpm_pattern_t p, gpm_pattern_info_t *info);
  *   counts : host uint64[npat]
  * Supported on the GPU: k-cliques (k = 1..8; patterns hold at most 8
  * vertices, gpm_count_cliques goes to k = 9) and every connected pattern with
- * 3 or 4 vertices, induced or not; other patterns return GPM_E_UNSUPPORTED.
+ * 3, 4 or 5 vertices, induced or not; other patterns return GPM_E_UNSUPPORTED.
  * Patterns that share work are computed together (e.g. all 4-vertex motifs
- * by local counting, Section 5; 3-, 4- and 5-cliques in one pass).
- * Synchronises `stream`.
+ * by local counting, Section 5; 3-, 4- and 5-cliques in one pass; every
+ * non-clique 5-vertex pattern of a call from one enumeration, as
+ * gpm_count_enumerate). Synchronises `stream`.
  */
 int gpm_count(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uint64_t *counts, void *stream);
+
+/*
+ * Counts by pattern-oblivious enumeration (Section 4.2, "Memoization of
+ * Embedding Connectivity"; appendix "Example for Connectivity Code"): every
+ * connected induced k-vertex subgraph of g is generated once by vertex
+ * extension from its smallest vertex, each added vertex carries its
+ * connectivity code to the vertices before it, and the concatenated code of
+ * a complete embedding selects its pattern class. An induced pattern gets
+ * its class count; an edge-induced pattern gets the sum over classes of the
+ * class count times the number of spanning subgraphs of the class graph that
+ * are copies of the pattern. All patterns must have the same k = 3, 4 or 5
+ * (GPM_E_UNSUPPORTED otherwise); the results equal gpm_count's, which for
+ * k = 3, 4 takes local counting instead, so this call is an independent
+ * check of it. The work grows with the number of connected k-vertex subsets,
+ * which is large around high-degree vertices. counts: host uint64[npat];
+ * a sum beyond 2^64 returns GPM_E_OVERFLOW. Synchronises `stream`.
+ */
+int gpm_count_enumerate(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uint64_t *counts, void *stream);
 
 /* As gpm_count, but writes the counts to DEVICE memory `counts_dev`
  * (uint64[npat]) and does not synchronise. The graph must be prepared. */

@@ -83,15 +83,36 @@ struct Passes {
   bool edge_terms = false; // degree terms (P, S, W)
   bool cycles4 = false;
   bool tri = false;        // triangles needed (from any clique pass)
+  uint32_t enum_k = 0;     // pattern-oblivious enumeration of k-vertex subgraphs (0 = none)
   FinalizeSpec spec{};
+  EnumFinalize espec{};
 };
 
-int schedule(const gpm_pattern_t *pats, uint32_t npat, bool ranged, Passes *ps) {
+// Pattern i counted from the class counts of the enumeration.
+int schedule_enum(const gpm_pattern *p, uint32_t i, Passes *ps) {
+  if (ps->enum_k && ps->enum_k != p->k)
+    return gpm_fail(GPM_E_UNSUPPORTED, "enumerated patterns of one call must have the same number of vertices");
+  ps->enum_k = p->k;
+  const uint32_t j = ps->espec.npat++;
+  ps->espec.slot[j] = i;
+  uint32_t nc = 0;
+  GPM_TRY(gpm_enum_coefficients(*p, ps->espec.coef[j], &nc));
+  ps->espec.nclass = nc;
+  ps->spec.formula[i] = F_VERTEX;  // placeholder, overwritten by the enumeration's finalize
+  return GPM_OK;
+}
+
+int schedule(const gpm_pattern_t *pats, uint32_t npat, bool ranged, Passes *ps, bool enumerate_all = false) {
   if (npat > 16) return gpm_fail(GPM_E_INVALID_ARG, "at most 16 patterns per call");
   ps->spec.npat = npat;
   for (uint32_t i = 0; i < npat; ++i) {
     const gpm_pattern *p = pats[i];
     if (!p) return gpm_fail(GPM_E_INVALID_ARG, "null pattern handle");
+    if (enumerate_all || (p->cls == PC_OTHER && p->k == 5)) {
+      if (ranged) return gpm_fail(GPM_E_UNSUPPORTED, "root-range counts are defined for cliques, diamonds and 4-cycles");
+      GPM_TRY(schedule_enum(p, i, ps));
+      continue;
+    }
     uint32_t f = 0;
     const bool ind = p->induced != 0;
     switch (p->cls) {
@@ -147,7 +168,7 @@ int schedule(const gpm_pattern_t *pats, uint32_t npat, bool ranged, Passes *ps) 
         }
         break;
       default: return gpm_fail(GPM_E_UNSUPPORTED, "no GPU kernel for this pattern (supported: cliques k <= 9 and "
-                                                  "connected patterns with 3 or 4 vertices)");
+                                                  "connected patterns with 3, 4 or 5 vertices)");
     }
     if (ranged && !(p->cls == PC_CLIQUE || (p->cls == PC_DIAMOND && !ind) || (p->cls == PC_CYCLE4 && !ind)))
       return gpm_fail(GPM_E_UNSUPPORTED, "root-range counts are defined for cliques, diamonds and 4-cycles");
@@ -159,9 +180,9 @@ int schedule(const gpm_pattern_t *pats, uint32_t npat, bool ranged, Passes *ps) 
 
 // Enqueue every pass and the finalize kernel; results in out_dev[0..npat).
 int enqueue_count(gpm_graph *g, const gpm_pattern_t *pats, uint32_t npat, uint32_t lo, uint32_t hi, bool ranged,
-                  unsigned long long *out_dev, cudaStream_t st) {
+                  unsigned long long *out_dev, cudaStream_t st, bool enumerate_all = false) {
   Passes ps;
-  GPM_TRY(schedule(pats, npat, ranged, &ps));
+  GPM_TRY(schedule(pats, npat, ranged, &ps, enumerate_all));
   unsigned long long *acc = acc_of(g);
   GPM_CUDA(cudaMemsetAsync(acc, 0, ACC_WORDS * sizeof(unsigned long long), st));
   GPM_CUDA(cudaMemsetAsync(status_of(g), 0, sizeof(uint64_t), st));
@@ -186,14 +207,19 @@ int enqueue_count(gpm_graph *g, const gpm_pattern_t *pats, uint32_t npat, uint32
     if (ps.gen_k & (1u << k)) GPM_TRY(gpm_launch_cliques(g, k, false, lo, hi, acc, st));
   if (ps.edge_terms) GPM_TRY(gpm_launch_edge_terms(g, ps.scatter, lo, hi, acc, st));
   if (ps.cycles4) GPM_TRY(gpm_launch_cycles4(g, lo, hi, acc, st));
+  if (ps.enum_k) {
+    if (!g->enum_counts) GPM_TRY(gpm_graph_alloc(g, (void **)&g->enum_counts, 32 * sizeof(unsigned long long)));
+    GPM_TRY(gpm_launch_enumerate(g, ps.enum_k, g->enum_counts, st));
+  }
   GPM_TRY(gpm_launch_finalize(ps.spec, acc, g->n, g->m, out_dev, status_of(g), st));
+  if (ps.enum_k) GPM_TRY(gpm_launch_enum_finalize(ps.espec, g->enum_counts, out_dev, status_of(g), st));
   return GPM_OK;
 }
 
 int count_to_host(gpm_graph *g, const gpm_pattern_t *pats, uint32_t npat, uint32_t lo, uint32_t hi, bool ranged,
-                  uint64_t *counts, cudaStream_t st) {
+                  uint64_t *counts, cudaStream_t st, bool enumerate_all = false) {
   unsigned long long *out = out_of(g);
-  GPM_TRY(enqueue_count(g, pats, npat, lo, hi, ranged, out, st));
+  GPM_TRY(enqueue_count(g, pats, npat, lo, hi, ranged, out, st, enumerate_all));
   uint64_t h[16];
   uint64_t status = 0;
   GPM_CUDA(cudaMemcpyAsync(h, out, npat * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
@@ -428,8 +454,19 @@ int gpm_pattern_motifs(uint32_t k, gpm_pattern_t *out, uint32_t *npat) {
         {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}},  // diamond
         {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}},
     };
+  } else if (k == 5) {
+    // the 21 connected 5-vertex graphs, by edge count, then smallest pair mask
+    uint32_t cm[32];
+    const int nc = gpm_enum_classes(5, cm, 32);
+    for (int c = 0; c < nc; ++c) {
+      std::vector<std::pair<int, int>> es;
+      for (uint32_t i = 0; i < 5; ++i)
+        for (uint32_t j = i + 1; j < 5; ++j)
+          if (cm[c] >> gpm_enum_pair_index(5, i, j) & 1u) es.emplace_back((int)i, (int)j);
+      pats.push_back(es);
+    }
   } else {
-    return gpm_fail(GPM_E_UNSUPPORTED, "motif sets are provided for k = 3 and k = 4");
+    return gpm_fail(GPM_E_UNSUPPORTED, "motif sets are provided for k = 3, 4 and 5");
   }
   std::vector<gpm_pattern_t> made;
   for (auto &es : pats) {
@@ -483,6 +520,20 @@ int gpm_count_async(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uin
     }
   return enqueue_count(g, pats, npat, 0, g->n, false, reinterpret_cast<unsigned long long *>(counts_dev),
                        as_stream(stream));
+}
+
+int gpm_count_enumerate(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uint64_t *counts, void *stream) {
+  GPM_TRY(check_graph(g));
+  if (!pats || !counts || npat == 0) return gpm_fail(GPM_E_INVALID_ARG, "null argument or no patterns");
+  for (uint32_t i = 0; i < npat; ++i) {
+    if (!pats[i]) return gpm_fail(GPM_E_INVALID_ARG, "null pattern handle");
+    if (pats[i]->k < 3 || pats[i]->k > 5)
+      return gpm_fail(GPM_E_UNSUPPORTED, "pattern-oblivious enumeration covers patterns with 3, 4 or 5 vertices");
+  }
+  std::lock_guard<std::mutex> lk(g->mu);
+  cudaStream_t st = as_stream(stream);
+  GPM_TRY(prepare_locked(g, st));
+  return count_to_host(g, pats, npat, 0, g->n, false, counts, st, true);
 }
 
 int gpm_count_roots(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uint32_t root_lo, uint32_t root_hi,

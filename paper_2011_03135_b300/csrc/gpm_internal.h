@@ -157,6 +157,12 @@ struct gpm_graph {
   uint32_t c4p_nitems = 0;
   uint32_t *c4_roff = nullptr;
   uint32_t c4_roff_width = 0, c4_nr1 = 0;
+  // pattern-oblivious enumeration: class of every connectivity code (k = 3..5),
+  // per-warp candidate lists, class counts (32 words)
+  uint8_t *enum_cls[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  uint32_t *enum_scratch = nullptr;
+  size_t enum_scratch_bytes = 0;
+  unsigned long long *enum_counts = nullptr;
 
   size_t device_bytes = 0;
   std::mutex mu;
@@ -275,6 +281,26 @@ struct FinalizeSpec {
 // inconsistent (a term overflowed 64 bits).
 int gpm_launch_finalize(const FinalizeSpec &spec, const unsigned long long *acc, uint64_t n, uint64_t m,
                         unsigned long long *out, unsigned int *status, cudaStream_t st);
+
+// Pattern-oblivious enumeration of connected k-vertex induced subgraphs
+// (k = 3, 4, 5) classified by connectivity code: counts[c] (32 words, zeroed
+// here) = induced count of class c; classes of connected k-vertex graphs are
+// numbered by edge count, then by the smallest pair mask over vertex orders
+// (pairs (0,1), (0,2), ..., (k-2,k-1) as bits 0, 1, ...).
+int gpm_launch_enumerate(gpm_graph *g, uint32_t k, unsigned long long *counts, cudaStream_t st);
+int gpm_enum_classes(uint32_t k, uint32_t *class_mask, uint32_t cap);  // number of classes
+uint32_t gpm_enum_pair_index(uint32_t k, uint32_t i, uint32_t j);
+int gpm_enum_class_of(const gpm_pattern &p);  // class of an induced pattern, -1 outside k = 3..5
+// coef[c] = copies of pattern p (induced: 1 for its own class; edge-induced:
+// spanning subgraphs of class c isomorphic to p) for every class c
+int gpm_enum_coefficients(const gpm_pattern &p, uint16_t *coef, uint32_t *nclass);
+struct EnumFinalize {
+  uint32_t npat, nclass;
+  uint32_t slot[16];       // output position of each enumerated pattern
+  uint16_t coef[16][32];   // out[slot[i]] = sum_c coef[i][c] * counts[c]
+};
+int gpm_launch_enum_finalize(const EnumFinalize &spec, const unsigned long long *cnt, unsigned long long *out,
+                             unsigned int *status, cudaStream_t st);
 
 // Listing.
 int gpm_launch_list_diamond(gpm_graph *g, uint32_t *buf, uint64_t cap, unsigned long long *counter,

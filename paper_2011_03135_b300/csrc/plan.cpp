@@ -19,7 +19,8 @@
 //   - degree filter thresholds (each pattern vertex's degree, Section 4.3 DF);
 //   - the execution strategy: the orientation for cliques (the paper enables
 //     it exactly when |E| = |V|(|V|-1)/2), local counting for the other 3- and
-//     4-vertex patterns (Section 5).
+//     4-vertex patterns (Section 5), pattern-oblivious enumeration with
+//     connectivity codes for the other 5-vertex patterns (Section 4.2).
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -205,10 +206,11 @@ int gpm_plan_pattern(gpm_pattern *p) {
     case PC_VERTEX:
     case PC_EDGE: info.strategy = GPM_STRATEGY_EDGE; break;
     case PC_CLIQUE: info.strategy = GPM_STRATEGY_CLIQUE_DAG; break;
-    case PC_OTHER: info.strategy = 0; break;
+    case PC_OTHER: info.strategy = (k == 5) ? GPM_STRATEGY_ENUMERATE : 0; break;
     default: info.strategy = GPM_STRATEGY_LOCAL_COUNT; break;
   }
   if (k == 3) info.motif_index = (p->cls == PC_WEDGE) ? 0u : 1u;
+  if (k == 5) info.motif_index = (uint32_t)gpm_enum_class_of(*p);
   if (k == 4) {
     switch (p->cls) {
       case PC_STAR3: info.motif_index = 0; break;

@@ -96,6 +96,7 @@ _SIGS = {
     "gpm_count": [_vp, _vp, _u32, _vp, _vp],
     "gpm_count_async": [_vp, _vp, _u32, _vp, _vp],
     "gpm_count_roots": [_vp, _vp, _u32, _u32, _u32, _vp, _vp],
+    "gpm_count_enumerate": [_vp, _vp, _u32, _vp, _vp],
     "gpm_count_cliques": [_vp, _u32, _u32, _u32, _vp, _vp],
     "gpm_exists": [_vp, _vp, _vp, _vp, _vp],
     "gpm_list": [_vp, _vp, _vp, _u64, _U64P, _U64P, _vp],
@@ -303,7 +304,7 @@ class Pattern:
 
     @classmethod
     def motifs(cls, k: int):
-        arr = (_vp * 8)()
+        arr = (_vp * 32)()
         npat = _u32(0)
         _check(_lib.gpm_pattern_motifs(k, arr, ctypes.byref(npat)))
         return [cls(_vp(arr[i])) for i in range(npat.value)]
@@ -352,6 +353,14 @@ def count_async(graph: Graph, patterns: Sequence[Pattern], out, stream=None):
     if not dev:
         raise ValueError("count_async needs a device output tensor")
     _check(_lib.gpm_count_async(graph.handle, _handles(patterns), len(patterns), p, _stream(stream)))
+
+
+def count_enumerate(graph: Graph, patterns: Sequence[Pattern], stream=None) -> list:
+    """Counts by pattern-oblivious enumeration with connectivity codes (all patterns with the same k = 3, 4, 5)."""
+    out = np.zeros(len(patterns), dtype=np.uint64)
+    _check(_lib.gpm_count_enumerate(graph.handle, _handles(patterns), len(patterns), out.ctypes.data,
+                                    _stream(stream)))
+    return [int(x) for x in out]
 
 
 def count_roots(graph: Graph, patterns: Sequence[Pattern], root_lo: int, root_hi: int, stream=None) -> list:

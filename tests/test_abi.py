@@ -124,7 +124,7 @@ def test_planner_five_vertex_pattern(lib):
     info = lib.Pattern.spec(house).info()
     assert info["automorphisms"] == O.automorphisms(house)
     assert O.orders_satisfying(5, info["sb_pairs"]) * info["automorphisms"] == 120
-    assert info["strategy"] == 0
+    assert info["strategy"] == 4 and info["motif_index"] < 21  # pattern-oblivious enumeration
 
 
 def test_options_roundtrip(lib):
