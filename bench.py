@@ -162,6 +162,11 @@ NCU_COUNTERS = {
     "sl-chunglu4m": {
         "c4": {"digest": "91324121aec85ca0", "dram_bytes_per_step": 134.73e9},
     },
+    # profiles/enum_k5_er1m_counters.md; digest of enumerate.cu
+    "motif5-er1m": {
+        "enum_kernel_k5": {"digest": "bb0dcc50081af389", "inst_per_launch": 226039588066,
+                           "dram_bytes_per_launch": 45073920 + 975872, "ncu_ms": 267.053},
+    },
     # three launches per step (k = 7, 8, 9), summed
     "clique789-cl1m": {
         "lg_cta_lo": {"digest": "2b577df7558f17b7", "inst_per_step": 21389936851 + 63809191151 + 189284984651,
@@ -656,6 +661,90 @@ def cpu_baseline_large_k(g, ks, unit, seconds_target=15.0):
             "sample": f"roots with id in [{lo}, {hi}) of {g.n}; single-threaded, {dt:.1f} s, counts {cs}"}
 
 
+MOTIF5_WORKLOAD = ("5-vertex motif counting (all 21 connected induced 5-vertex patterns) by pattern-oblivious "
+                   "enumeration with connectivity codes: Erdos-Renyi 1,048,576 vertices, mean degree 8, seed 7")
+
+
+def enum_digest():
+    import hashlib
+    return hashlib.sha256(open(os.path.join(ROOT, "paper_2011_03135_b300", "csrc", "enumerate.cu"), "rb").read()
+                          ).hexdigest()[:16]
+
+
+def run_motif5(args):
+    """All 21 induced 5-vertex motif counts in one call (one enumeration per step)."""
+    import torch
+    from paper_2011_03135_b300 import gpm
+    from paper_2011_03135_b300 import graphgen as gg
+    g = gg.workload_motif5_er1m()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    G = gpm.Graph(torch.from_numpy(g.rowptr.view(np.int64)).to(dev), torch.from_numpy(g.col.view(np.int32)).to(dev),
+                  g.n, validate=True, stream=stream)
+    M = gpm.Pattern.motifs(5)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    def step():
+        G.reset()
+        return gpm.count(G, M, stream=stream)
+
+    counts = None
+    for _ in range(max(args.warmup, 3)):
+        counts = step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = gpm.kernel_launches()
+    gpm.profile_reset()
+    gpm.profile_enable(True)
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev[i][0].record(stream)
+            assert step() == counts
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    gpm.profile_enable(False)
+    launches = gpm.kernel_launches() - launches0
+    prof = gpm.profile_report()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+    total = sum(counts)
+    clk_now = clk.summary()
+    ipeak = issue_peak(clk_now["sm_mhz"] or 2032.0)
+    kname = "enum_kernel_k5"
+    kms = prof.get(kname, {"ms": 0.0})["ms"] / args.steps
+    roof = {"bound": "alu", "kernel": kname, "unit": "G warp-instructions/s", "peak": ipeak,
+            "peak_source": "148 SMs x 4 schedulers x 1 issue/clk x median SM clock under load",
+            "achieved": None, "frac": None, "traffic": None, "kernel_digest": enum_digest()}
+    cnt = NCU_COUNTERS.get("motif5-er1m", {}).get(kname)
+    if cnt and cnt.get("digest") == enum_digest() and kms > 0:
+        ach = cnt["inst_per_launch"] / (kms / 1000.0) / 1e9
+        roof.update(achieved=ach, frac=ach / ipeak, traffic=cnt.get("dram_bytes_per_launch"))
+    line = {"workload": MOTIF5_WORKLOAD, "metric": "connected induced 5-vertex subgraphs counted per second",
+            "value": total / (ms / 1000.0), "unit": "5-vertex subgraphs/s", "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "counts": counts, "subgraphs": total, "dtype": "u64",
+            "data": "synthetic", "config": {"l2": "flushed between steps (512 MB write)"}, "gpu_launches": launches,
+            "roofline": roof, "clocks": clk_now,
+            "kernels": {k: {"launches": v["launches"], "ms_per_launch": v["ms"] / max(v["launches"], 1)}
+                        for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}}
+    if not args.no_cpu_baseline:
+        import oracle as O
+        hi = 256
+        t0 = time.perf_counter()
+        c, _ = O.motifs5(g, 0, hi)
+        dt = time.perf_counter() - t0
+        hi = min(g.n, int(hi * 10.0 / max(dt, 1e-3)))
+        t0 = time.perf_counter()
+        c, _ = O.motifs5(g, 0, hi)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": sum(c) / dt, "unit": "5-vertex subgraphs/s", "cores": 1, "kind": "oracle",
+                                "sample": f"roots (smallest vertex) with id in [0, {hi}) of {g.n}; single-threaded, "
+                                          f"{dt:.1f} s, {sum(c)} subgraphs"}
+    G.close()
+    return line
+
+
 TC_WORKLOAD = "triangle counting, R-MAT scale 14 (16,384 vertices), edge factor 16, (0.57,0.19,0.19,0.05), seed 1"
 
 
@@ -881,6 +970,7 @@ CASES = {
     "sl-chunglu1m": ("chunglu1m", "sl"),
     "sl-chunglu2m": ("chunglu2m", "sl"),
     "sl-chunglu4m": ("chunglu4m", "sl"),
+    "motif5-er1m": ("er1m", "motif5"),
 }
 
 
@@ -902,6 +992,8 @@ def _case_graph(name):
         return gg.chung_lu(1 << 21, 24.0, 2.1, seed=3)
     if name == "chunglu4m":
         return gg.workload_sl_chung_lu4m()
+    if name == "er1m":
+        return gg.workload_motif5_er1m()
     raise ValueError(name)
 
 
@@ -918,6 +1010,8 @@ def _case_patterns(gpm, name):
         return [gpm.Pattern.clique(3)]
     if name == "motif4":
         return gpm.Pattern.motifs(4)
+    if name == "motif5":
+        return gpm.Pattern.motifs(5)
     if name == "sl":
         d = np.zeros((4, 4), np.uint8)
         for a, b in [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3)]:
@@ -956,7 +1050,7 @@ def main():
                     help="order of the orientation for the k-clique leg (core: k-core peel at prepare time)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-legs", action="store_true", help="headline leg only (no sl / tc legs in its line)")
-    ap.add_argument("--workload", choices=["cliques", "clique6", "clique789", "batched", "served", "sl", "tc"],
+    ap.add_argument("--workload", choices=["cliques", "clique6", "clique789", "batched", "served", "sl", "tc", "motif5"],
                     default="cliques")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -984,6 +1078,9 @@ def main():
         return 0
     if args.workload == "tc":
         print(json.dumps(run_tc(args)), flush=True)
+        return 0
+    if args.workload == "motif5":
+        print(json.dumps(run_motif5(args)), flush=True)
         return 0
     if args.workload == "clique6":
         from paper_2011_03135_b300 import graphgen as gg

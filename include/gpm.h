@@ -239,7 +239,8 @@ int gpm_count_async(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uin
  * orientation order (degree, id):
  *   k-clique : the clique vertex that is first in the order;
  *   diamond (edge-induced): the order-first endpoint of the shared edge;
- *   4-cycle (edge-induced): the cycle vertex that is last in the order.
+ *   4-cycle (edge-induced): the cycle vertex that is last in the order;
+ *   other 5-vertex patterns (counted by enumeration): the smallest vertex id.
  * Other patterns return GPM_E_UNSUPPORTED. counts: host uint64[npat].
  */
 int gpm_count_roots(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uint32_t root_lo, uint32_t root_hi,

@@ -66,6 +66,7 @@ def _load():
                 "orc_core_numbers": ([u32, vp, vp, vp], ctypes.c_int),
                 "orc_core_order": ([u32, vp, vp, vp], ctypes.c_int),
                 "orc_motifs5": ([u32, vp, vp, vp, vp], ctypes.c_int),
+                "orc_motifs5_roots": ([u32, vp, vp, u32, u32, vp, vp], ctypes.c_int),
                 "orc_cliques_keyed": ([u32, vp, vp, vp, u32, u32, u32, U64P], ctypes.c_int),
                 "orc_diamonds": ([u32, vp, vp, u32, u32, U64P], ctypes.c_int),
                 "orc_cycles4": ([u32, vp, vp, u32, u32, U64P], ctypes.c_int),
@@ -250,14 +251,17 @@ def motifs(g, k: int) -> list:
     return [int(x) for x in out[: (2 if k == 3 else 6)]]
 
 
-def motifs5(g):
+def motifs5(g, root_lo: int = 0, root_hi: int | None = None):
     """(counts, class_masks): induced counts of the 21 connected 5-vertex
     patterns and each class's canonical adjacency mask (bit of pair (a, b),
-    a < b, in lexicographic pair order), ordered by edge count, then mask."""
+    a < b, in lexicographic pair order), ordered by edge count, then mask.
+    With a root range, only the subgraphs whose smallest vertex lies in it."""
     rp, col = _csr(g)
     out = np.zeros(21, dtype=np.uint64)
     masks = np.zeros(21, dtype=np.uint32)
-    _check(_load().orc_motifs5(g.n, rp.ctypes.data, col.ctypes.data, out.ctypes.data, masks.ctypes.data), "motifs5")
+    hi = g.n if root_hi is None else root_hi
+    _check(_load().orc_motifs5_roots(g.n, rp.ctypes.data, col.ctypes.data, root_lo, hi, out.ctypes.data,
+                                     masks.ctypes.data), "motifs5")
     return [int(x) for x in out], [int(m) for m in masks]
 
 

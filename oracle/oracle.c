@@ -853,7 +853,16 @@ static void esu_extend(esu_ctx *x, uint32_t *sub, int ns, const uint32_t *ext, u
  * canonical adjacency mask of class i (edge {a, b} of vertices 0..4 at the
  * bit pair_bit5(a, b) gives: pairs in lexicographic order (0,1) = bit 0 ...
  * (3,4) = bit 9); classes ordered by edge count, then by mask. */
+int orc_motifs5_roots(uint32_t n, const uint64_t *rp, const uint32_t *col, uint32_t root_lo, uint32_t root_hi,
+                      uint64_t *out, uint32_t *class_mask);
 int orc_motifs5(uint32_t n, const uint64_t *rp, const uint32_t *col, uint64_t *out, uint32_t *class_mask) {
+  return orc_motifs5_roots(n, rp, col, 0, n, out, class_mask);
+}
+
+/* As orc_motifs5, restricted to the subgraphs whose smallest vertex (the
+ * root ESU extends from) lies in [root_lo, root_hi). */
+int orc_motifs5_roots(uint32_t n, const uint64_t *rp, const uint32_t *col, uint32_t root_lo, uint32_t root_hi,
+                      uint64_t *out, uint32_t *class_mask) {
   uint8_t cls[1024];
   uint32_t cm[32];
   int nc = motif5_table(cls, cm);
@@ -874,7 +883,8 @@ int orc_motifs5(uint32_t n, const uint64_t *rp, const uint32_t *col, uint64_t *o
     if (class_mask) class_mask[i] = cm[i];
   }
   uint32_t sub[5];
-  for (uint32_t v = 0; v < n; ++v) {
+  if (root_hi > n) root_hi = n;
+  for (uint32_t v = root_lo; v < root_hi; ++v) {
     x.v = v;
     uint32_t *ext = x.ext_pool;
     uint64_t ne = 0;

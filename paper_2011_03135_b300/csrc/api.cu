@@ -103,14 +103,13 @@ int schedule_enum(const gpm_pattern *p, uint32_t i, Passes *ps) {
 }
 
 int schedule(const gpm_pattern_t *pats, uint32_t npat, bool ranged, Passes *ps, bool enumerate_all = false) {
-  if (npat > 16) return gpm_fail(GPM_E_INVALID_ARG, "at most 16 patterns per call");
+  if (npat > kMaxPatterns) return gpm_fail(GPM_E_INVALID_ARG, "at most 32 patterns per call");
   ps->spec.npat = npat;
   for (uint32_t i = 0; i < npat; ++i) {
     const gpm_pattern *p = pats[i];
     if (!p) return gpm_fail(GPM_E_INVALID_ARG, "null pattern handle");
     if (enumerate_all || (p->cls == PC_OTHER && p->k == 5)) {
-      if (ranged) return gpm_fail(GPM_E_UNSUPPORTED, "root-range counts are defined for cliques, diamonds and 4-cycles");
-      GPM_TRY(schedule_enum(p, i, ps));
+      GPM_TRY(schedule_enum(p, i, ps));  // root: the smallest vertex of the subgraph
       continue;
     }
     uint32_t f = 0;
@@ -171,7 +170,8 @@ int schedule(const gpm_pattern_t *pats, uint32_t npat, bool ranged, Passes *ps, 
                                                   "connected patterns with 3, 4 or 5 vertices)");
     }
     if (ranged && !(p->cls == PC_CLIQUE || (p->cls == PC_DIAMOND && !ind) || (p->cls == PC_CYCLE4 && !ind)))
-      return gpm_fail(GPM_E_UNSUPPORTED, "root-range counts are defined for cliques, diamonds and 4-cycles");
+      return gpm_fail(GPM_E_UNSUPPORTED, "root-range counts are defined for cliques, diamonds, 4-cycles and 5-vertex "
+                                         "patterns");
     ps->spec.formula[i] = f;
   }
   if (ps->tri) ps->clique_kmax = std::max(ps->clique_kmax, 3);
@@ -209,7 +209,7 @@ int enqueue_count(gpm_graph *g, const gpm_pattern_t *pats, uint32_t npat, uint32
   if (ps.cycles4) GPM_TRY(gpm_launch_cycles4(g, lo, hi, acc, st));
   if (ps.enum_k) {
     if (!g->enum_counts) GPM_TRY(gpm_graph_alloc(g, (void **)&g->enum_counts, 32 * sizeof(unsigned long long)));
-    GPM_TRY(gpm_launch_enumerate(g, ps.enum_k, g->enum_counts, st));
+    GPM_TRY(gpm_launch_enumerate(g, ps.enum_k, lo, hi, g->enum_counts, st));
   }
   GPM_TRY(gpm_launch_finalize(ps.spec, acc, g->n, g->m, out_dev, status_of(g), st));
   if (ps.enum_k) GPM_TRY(gpm_launch_enum_finalize(ps.espec, g->enum_counts, out_dev, status_of(g), st));
@@ -220,7 +220,7 @@ int count_to_host(gpm_graph *g, const gpm_pattern_t *pats, uint32_t npat, uint32
                   uint64_t *counts, cudaStream_t st, bool enumerate_all = false) {
   unsigned long long *out = out_of(g);
   GPM_TRY(enqueue_count(g, pats, npat, lo, hi, ranged, out, st, enumerate_all));
-  uint64_t h[16];
+  uint64_t h[kMaxPatterns];
   uint64_t status = 0;
   GPM_CUDA(cudaMemcpyAsync(h, out, npat * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
   GPM_CUDA(cudaMemcpyAsync(&status, status_of(g), sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
@@ -514,7 +514,7 @@ int gpm_count_async(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uin
   for (uint32_t i = 0; i < npat; ++i)
     if (pats[i] && pats[i]->cls == PC_CYCLE4 && !gpm_c4_plain_ready(g)) {
       // the 4-cycle task lists are built (with a host synchronisation) on first use
-      uint64_t tmp[16];
+      uint64_t tmp[kMaxPatterns];
       GPM_TRY(count_to_host(g, pats, npat, 0, g->n, false, tmp, as_stream(stream)));
       break;
     }

@@ -66,8 +66,8 @@ struct EnumArgs {
   const uint64_t *__restrict__ rowptr;
   const uint32_t *__restrict__ col;
   uint32_t n;
-  uint64_t nnz;
-  unsigned long long *queue;       // next adjacency position to claim
+  uint32_t root_lo, root_hi;       // roots (smallest vertices) counted
+  unsigned long long *queue;       // adjacency positions claimed so far
   uint32_t *scratch;               // per warp: candidate lists E2, E3 (vertices), codes after them
   uint64_t warp_words;             // words of scratch per warp
   uint64_t cap2, cap3;             // capacities of E2 and E3
@@ -143,12 +143,14 @@ __global__ void __launch_bounds__(kEnumThreads) enum_kernel(EnumArgs a) {
   uint32_t *E3 = E2 + a.cap2;
   uint8_t *C2 = reinterpret_cast<uint8_t *>(E3 + a.cap3);
   uint8_t *C3 = C2 + a.cap2;
+  // items: the adjacency positions of the roots in [root_lo, root_hi)
+  const uint64_t qbase = a.rowptr[a.root_lo], qend = a.rowptr[a.root_hi];
   for (;;) {
     unsigned long long p0 = 0;
-    if (lane == 0) p0 = atomicAdd(a.queue, (unsigned long long)kEnumChunk);
+    if (lane == 0) p0 = qbase + atomicAdd(a.queue, (unsigned long long)kEnumChunk);
     p0 = __shfl_sync(0xffffffffu, p0, 0);
-    if (p0 >= a.nnz) break;
-    const uint64_t p1 = min((uint64_t)p0 + kEnumChunk, a.nnz);
+    if (p0 >= qend) break;
+    const uint64_t p1 = min((uint64_t)p0 + kEnumChunk, qend);
     // row of position p0
     uint32_t v;
     {
@@ -384,7 +386,8 @@ int gpm_enum_coefficients(const gpm_pattern &p, uint16_t *coef, uint32_t *nclass
   return GPM_OK;
 }
 
-int gpm_launch_enumerate(gpm_graph *g, uint32_t k, unsigned long long *counts, cudaStream_t st) {
+int gpm_launch_enumerate(gpm_graph *g, uint32_t k, uint32_t root_lo, uint32_t root_hi, unsigned long long *counts,
+                         cudaStream_t st) {
   if (k < 3 || k > 5) return gpm_fail(GPM_E_UNSUPPORTED, "pattern-oblivious enumeration covers k = 3, 4, 5");
   const ClassTable &t = class_table(k);
   const uint32_t L = k * (k - 1) / 2;
@@ -393,7 +396,7 @@ int gpm_launch_enumerate(gpm_graph *g, uint32_t k, unsigned long long *counts, c
     GPM_CUDA(cudaMemcpyAsync(g->enum_cls[k], t.by_code.data(), 1u << L, cudaMemcpyHostToDevice, st));
   }
   GPM_CUDA(cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * 32, st));
-  if (g->nnz == 0) return GPM_OK;
+  if (g->nnz == 0 || root_lo >= root_hi) return GPM_OK;
   int per_sm = 0;
   cudaError_t e;
   if (k == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, enum_kernel<3>, kEnumThreads, 0);
@@ -422,7 +425,8 @@ int gpm_launch_enumerate(gpm_graph *g, uint32_t k, unsigned long long *counts, c
   a.rowptr = g->rowptr;
   a.col = g->col;
   a.n = g->n;
-  a.nnz = g->nnz;
+  a.root_lo = root_lo;
+  a.root_hi = root_hi;
   a.queue = queue;
   a.scratch = g->enum_scratch;
   a.warp_words = warp_words;

@@ -168,15 +168,18 @@ struct gpm_graph {
   std::mutex mu;
 };
 
+// patterns per count call
+constexpr uint32_t kMaxPatterns = 32;
+
 // layout of gpm_graph::work (uint64 words)
 enum {
   WK_QUEUE0 = 0,   // 16 uint32 queue heads
   WK_ACC = 8,      // 16 accumulators
   WK_ACC2 = 24,    // 16 accumulators of a second pass
-  WK_OUT = 40,     // 16 results
   WK_STATUS = 56,  // status bits
   WK_MISC = 57,    // 7 misc words
-  WORK_WORDS = 64,
+  WK_OUT = 64,     // kMaxPatterns results
+  WORK_WORDS = 96,
 };
 
 // ---------------------------------------------------------------------------
@@ -275,7 +278,7 @@ enum Formula : uint32_t {
 };
 struct FinalizeSpec {
   uint32_t npat;
-  uint32_t formula[16];
+  uint32_t formula[32];
 };
 // out[i] = formula[i](acc); status |= ST_CAPACITY when an induced count is
 // inconsistent (a term overflowed 64 bits).
@@ -287,7 +290,9 @@ int gpm_launch_finalize(const FinalizeSpec &spec, const unsigned long long *acc,
 // here) = induced count of class c; classes of connected k-vertex graphs are
 // numbered by edge count, then by the smallest pair mask over vertex orders
 // (pairs (0,1), (0,2), ..., (k-2,k-1) as bits 0, 1, ...).
-int gpm_launch_enumerate(gpm_graph *g, uint32_t k, unsigned long long *counts, cudaStream_t st);
+// Only subgraphs whose smallest vertex lies in [root_lo, root_hi) are counted.
+int gpm_launch_enumerate(gpm_graph *g, uint32_t k, uint32_t root_lo, uint32_t root_hi, unsigned long long *counts,
+                         cudaStream_t st);
 int gpm_enum_classes(uint32_t k, uint32_t *class_mask, uint32_t cap);  // number of classes
 uint32_t gpm_enum_pair_index(uint32_t k, uint32_t i, uint32_t j);
 int gpm_enum_class_of(const gpm_pattern &p);  // class of an induced pattern, -1 outside k = 3..5
@@ -296,8 +301,8 @@ int gpm_enum_class_of(const gpm_pattern &p);  // class of an induced pattern, -1
 int gpm_enum_coefficients(const gpm_pattern &p, uint16_t *coef, uint32_t *nclass);
 struct EnumFinalize {
   uint32_t npat, nclass;
-  uint32_t slot[16];       // output position of each enumerated pattern
-  uint16_t coef[16][32];   // out[slot[i]] = sum_c coef[i][c] * counts[c]
+  uint32_t slot[32];       // output position of each enumerated pattern
+  uint16_t coef[32][32];   // out[slot[i]] = sum_c coef[i][c] * counts[c]
 };
 int gpm_launch_enum_finalize(const EnumFinalize &spec, const unsigned long long *cnt, unsigned long long *out,
                              unsigned int *status, cudaStream_t st);

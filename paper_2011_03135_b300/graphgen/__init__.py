@@ -230,6 +230,13 @@ def workload_sl_chung_lu4m() -> Graph:
     return chung_lu(1 << 22, 24.0, 2.1, seed=3)
 
 
+def workload_motif5_er1m() -> Graph:
+    """5-vertex motif input: Erdos-Renyi G(n, p), n = 1,048,576, mean degree 8 (p = 8 / (n - 1)), seed 7,
+    ids permuted."""
+    n = 1 << 20
+    return erdos_renyi(n, 8.0 / (n - 1), seed=7, permute=True)
+
+
 def batch_query_specs(nq: int = 512, base_seed: int = 1000, log2n_range=(10, 20), dbar_range=(8.0, 64.0)):
     """Seeded descriptions of the mixed 3-/4-motif batch.
 

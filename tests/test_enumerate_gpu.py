@@ -93,6 +93,16 @@ def test_motifs5_medium(gpm, gi):
     M = gpm.Pattern.motifs(5)
     got = gpm.count(G, M[:11]) + gpm.count(G, M[11:])
     assert got == want, g.name
+    # root ranges partition the total. Root: the smallest vertex for the
+    # enumerated classes; the 5-clique (class 20) is counted by the clique
+    # path, whose root is its first vertex in the orientation order
+    cuts = [0, 1, g.n // 3, g.n // 3 + 1, g.n - 7, g.n]
+    acc = [0] * 21
+    for lo, hi in zip(cuts[:-1], cuts[1:]):
+        part = gpm.count_roots(G, M[:11], lo, hi) + gpm.count_roots(G, M[11:], lo, hi)
+        assert part == O.motifs5(g, lo, hi)[0][:20] + [O.cliques(g, 5, lo, hi)], (g.name, lo, hi)
+        acc = [x + y for x, y in zip(acc, part)]
+    assert acc == want
     G.close()
 
 
@@ -134,8 +144,25 @@ def test_enumeration_rejects(gpm):
         gpm.count_enumerate(G, [gpm.Pattern.motifs(3)[0], gpm.Pattern.motifs(4)[0]])
     with pytest.raises(gpm.GpmError):
         gpm.count_enumerate(G, [gpm.Pattern.clique(6)])
-    with pytest.raises(gpm.GpmError):
-        gpm.count_roots(G, [gpm.Pattern.motifs(5)[3]], 0, 3)
     # the 5-clique through the enumeration equals C(6, 5)
     assert gpm.count_enumerate(G, [gpm.Pattern.clique(5)]) == [6]
+    G.close()
+
+
+def test_motif5_fullsize_sampled(gpm):
+    # the 5-motif workload (Erdos-Renyi 2^20 vertices, mean degree 8): root
+    # ranges the oracle counts in seconds, and a partition of the roots whose
+    # parts add up to the total
+    g = gg.workload_motif5_er1m()
+    G = gpm.Graph.from_host(g)
+    M = gpm.Pattern.motifs(5)
+    for lo, hi in [(0, 120), (g.n // 2, g.n // 2 + 400), (g.n - 600, g.n)]:
+        # 5-cliques (class 20) are rooted by the clique path's convention
+        want = O.motifs5(g, lo, hi)[0][:20] + [O.cliques(g, 5, lo, hi)]
+        assert gpm.count_roots(G, M, lo, hi) == want, (lo, hi)
+    total = gpm.count(G, M)
+    cuts = [0, 12345, g.n // 2, g.n - 1, g.n]
+    parts = [gpm.count_roots(G, M, lo, hi) for lo, hi in zip(cuts[:-1], cuts[1:])]
+    assert [sum(c) for c in zip(*parts)] == total
+    assert sum(total) > 4 * 10 ** 9
     G.close()

@@ -490,3 +490,29 @@ def test_motifs5_match_subset_brute_force(mk):
             continue
         want[[i for i, G in enumerate(gs) if nx.is_isomorphic(G, H)][0]] += 1
     assert counts == want
+
+
+def test_motifs5_root_ranges_brute_force():
+    # restricted to the subsets whose smallest vertex lies in [lo, hi): every
+    # 5-subset classified by networkx isomorphism; the ranges partition the total
+    import networkx as nx
+    g = gg.random_small(12, 0.45, 34)
+    adj = _py_adj(g)
+    total, masks = O.motifs5(g)
+    gs = [_mask_graph5(m) for m in masks]
+    cuts = [0, 1, 4, 5, 9, g.n]
+    acc = [0] * 21
+    for lo, hi in zip(cuts[:-1], cuts[1:]):
+        want = [0] * 21
+        for W in itertools.combinations(range(g.n), 5):
+            if not lo <= W[0] < hi:
+                continue
+            H = nx.Graph()
+            H.add_nodes_from(W)
+            H.add_edges_from((a, b) for a, b in itertools.combinations(W, 2) if b in adj[a])
+            if nx.is_connected(H):
+                want[[i for i, G in enumerate(gs) if nx.is_isomorphic(G, H)][0]] += 1
+        got, _ = O.motifs5(g, lo, hi)
+        assert got == want, (lo, hi)
+        acc = [a + b for a, b in zip(acc, got)]
+    assert acc == total
