@@ -200,9 +200,12 @@ int gpm_pattern_info(gpm_pattern_t p, gpm_pattern_info_t *info);
  * its number of embeddings; each distinct subgraph is counted once, i.e. the
  * count of maps divided by |Aut(P)|).
  *   counts : host uint64[npat]
- * Supported on the GPU: k-cliques (k = 1..8; patterns hold at most 8
- * vertices, gpm_count_cliques goes to k = 9) and every connected pattern with
- * 3, 4 or 5 vertices, induced or not; other patterns return GPM_E_UNSUPPORTED.
+ * Supported on the GPU: every connected pattern with up to 8 vertices,
+ * induced or not (k-cliques to k = 9 through gpm_count_cliques); at most 32
+ * patterns per call. Cliques run the orientation and local-graph search,
+ * other 3- and 4-vertex patterns local counting, other 5-vertex patterns the
+ * pattern-oblivious enumeration, other 6- to 8-vertex patterns the
+ * pattern-guided search.
  * Patterns that share work are computed together (e.g. all 4-vertex motifs
  * by local counting, Section 5; 3-, 4- and 5-cliques in one pass; every
  * non-clique 5-vertex pattern of a call from one enumeration, as
@@ -227,6 +230,22 @@ int gpm_count(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uint64_t 
  * a sum beyond 2^64 returns GPM_E_OVERFLOW. Synchronises `stream`.
  */
 int gpm_count_enumerate(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uint64_t *counts, void *stream);
+
+/*
+ * Counts by the pattern-guided search (appendix "Pattern-Guided Search
+ * (Matching Order)", "Symmetry Breaking (Partial Order)"; Section 4.3 degree
+ * filtering), for any connected pattern with 3..8 vertices, induced or not:
+ * the pattern's vertices are matched in the planner's matching order
+ * (gpm_pattern_info), each candidate list is the neighbour list of one
+ * matched pattern neighbour intersected with the lists of the others (and
+ * differenced with the non-neighbours' lists for induced patterns), bounded
+ * by the symmetry-breaking id constraints and the degree filter, so each
+ * distinct subgraph is matched once. gpm_count takes this path for patterns
+ * with 6..8 vertices that are not cliques; this call forces it for any
+ * pattern (a second, independent path for the others). One search per
+ * pattern. counts: host uint64[npat]. Synchronises `stream`.
+ */
+int gpm_count_guided(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uint64_t *counts, void *stream);
 
 /* As gpm_count, but writes the counts to DEVICE memory `counts_dev`
  * (uint64[npat]) and does not synchronise. The graph must be prepared. */
@@ -274,8 +293,10 @@ int gpm_count_cliques(gpm_graph_t g, uint32_t k, uint32_t root_lo, uint32_t root
  * subgraph. Which min(total, cap) embeddings are written is unspecified.
  *   *written : number of tuples written = min(total, cap)
  *   *total   : exact number of embeddings (= gpm_count of p)
- * Supported: edge-induced diamond and 4-cycle, k-cliques k = 3..8.
- * Synchronises `stream`.
+ * Supported: every connected pattern with 3..8 vertices, induced or not.
+ * The edge-induced diamond and 4-cycle and the k-cliques have their own
+ * kernels; every other pattern runs the pattern-guided search (see
+ * gpm_count_guided). Synchronises `stream`.
  */
 int gpm_list(gpm_graph_t g, gpm_pattern_t p, uint32_t *buf, uint64_t cap, uint64_t *written, uint64_t *total,
              void *stream);
@@ -287,7 +308,7 @@ int gpm_list(gpm_graph_t g, gpm_pattern_t p, uint32_t *buf, uint64_t cap, uint64
  * no counting pass, so every warp stops at its next check once a match is
  * written. witness (host uint32[k], may be NULL): on *found = 1, one
  * embedding in PATTERN vertex order, as gpm_list writes it.
- * Supported: as gpm_list (edge-induced diamond and 4-cycle, k-cliques k = 3..8).
+ * Supported: as gpm_list (every connected pattern with 3..8 vertices).
  * Synchronises `stream`.
  */
 int gpm_exists(gpm_graph_t g, gpm_pattern_t p, int *found, uint32_t *witness, void *stream);

@@ -86,6 +86,7 @@ struct Passes {
   uint32_t enum_k = 0;     // pattern-oblivious enumeration of k-vertex subgraphs (0 = none)
   FinalizeSpec spec{};
   EnumFinalize espec{};
+  std::vector<std::pair<uint32_t, GuidedPlan>> guided;  // patterns counted by the pattern-guided search
 };
 
 // Pattern i counted from the class counts of the enumeration.
@@ -102,12 +103,23 @@ int schedule_enum(const gpm_pattern *p, uint32_t i, Passes *ps) {
   return GPM_OK;
 }
 
-int schedule(const gpm_pattern_t *pats, uint32_t npat, bool ranged, Passes *ps, bool enumerate_all = false) {
+enum Force { FORCE_NONE = 0, FORCE_ENUMERATE, FORCE_GUIDED };
+
+int schedule(const gpm_pattern_t *pats, uint32_t npat, bool ranged, Passes *ps, Force force = FORCE_NONE) {
   if (npat > kMaxPatterns) return gpm_fail(GPM_E_INVALID_ARG, "at most 32 patterns per call");
   ps->spec.npat = npat;
+  const bool enumerate_all = force == FORCE_ENUMERATE;
   for (uint32_t i = 0; i < npat; ++i) {
     const gpm_pattern *p = pats[i];
     if (!p) return gpm_fail(GPM_E_INVALID_ARG, "null pattern handle");
+    if (force == FORCE_GUIDED || (p->cls == PC_OTHER && p->k >= 6)) {
+      if (ranged) return gpm_fail(GPM_E_UNSUPPORTED, "root-range counts are not defined for the pattern-guided search");
+      GuidedPlan plan;
+      GPM_TRY(gpm_guided_plan(*p, &plan));
+      ps->guided.emplace_back(i, plan);
+      ps->spec.formula[i] = F_VERTEX;  // placeholder, replaced by the search's count
+      continue;
+    }
     if (enumerate_all || (p->cls == PC_OTHER && p->k == 5)) {
       GPM_TRY(schedule_enum(p, i, ps));  // root: the smallest vertex of the subgraph
       continue;
@@ -180,9 +192,9 @@ int schedule(const gpm_pattern_t *pats, uint32_t npat, bool ranged, Passes *ps, 
 
 // Enqueue every pass and the finalize kernel; results in out_dev[0..npat).
 int enqueue_count(gpm_graph *g, const gpm_pattern_t *pats, uint32_t npat, uint32_t lo, uint32_t hi, bool ranged,
-                  unsigned long long *out_dev, cudaStream_t st, bool enumerate_all = false) {
+                  unsigned long long *out_dev, cudaStream_t st, Force force = FORCE_NONE) {
   Passes ps;
-  GPM_TRY(schedule(pats, npat, ranged, &ps, enumerate_all));
+  GPM_TRY(schedule(pats, npat, ranged, &ps, force));
   unsigned long long *acc = acc_of(g);
   GPM_CUDA(cudaMemsetAsync(acc, 0, ACC_WORDS * sizeof(unsigned long long), st));
   GPM_CUDA(cudaMemsetAsync(status_of(g), 0, sizeof(uint64_t), st));
@@ -213,13 +225,17 @@ int enqueue_count(gpm_graph *g, const gpm_pattern_t *pats, uint32_t npat, uint32
   }
   GPM_TRY(gpm_launch_finalize(ps.spec, acc, g->n, g->m, out_dev, status_of(g), st));
   if (ps.enum_k) GPM_TRY(gpm_launch_enum_finalize(ps.espec, g->enum_counts, out_dev, status_of(g), st));
+  for (auto &gp : ps.guided) {
+    GPM_CUDA(cudaMemsetAsync(out_dev + gp.first, 0, sizeof(unsigned long long), st));
+    GPM_TRY(gpm_launch_guided(g, gp.second, out_dev + gp.first, nullptr, 0, nullptr, st));
+  }
   return GPM_OK;
 }
 
 int count_to_host(gpm_graph *g, const gpm_pattern_t *pats, uint32_t npat, uint32_t lo, uint32_t hi, bool ranged,
-                  uint64_t *counts, cudaStream_t st, bool enumerate_all = false) {
+                  uint64_t *counts, cudaStream_t st, Force force = FORCE_NONE) {
   unsigned long long *out = out_of(g);
-  GPM_TRY(enqueue_count(g, pats, npat, lo, hi, ranged, out, st, enumerate_all));
+  GPM_TRY(enqueue_count(g, pats, npat, lo, hi, ranged, out, st, force));
   uint64_t h[kMaxPatterns];
   uint64_t status = 0;
   GPM_CUDA(cudaMemcpyAsync(h, out, npat * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
@@ -533,7 +549,21 @@ int gpm_count_enumerate(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat,
   std::lock_guard<std::mutex> lk(g->mu);
   cudaStream_t st = as_stream(stream);
   GPM_TRY(prepare_locked(g, st));
-  return count_to_host(g, pats, npat, 0, g->n, false, counts, st, true);
+  return count_to_host(g, pats, npat, 0, g->n, false, counts, st, FORCE_ENUMERATE);
+}
+
+int gpm_count_guided(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uint64_t *counts, void *stream) {
+  GPM_TRY(check_graph(g));
+  if (!pats || !counts || npat == 0) return gpm_fail(GPM_E_INVALID_ARG, "null argument or no patterns");
+  for (uint32_t i = 0; i < npat; ++i) {
+    if (!pats[i]) return gpm_fail(GPM_E_INVALID_ARG, "null pattern handle");
+    if (pats[i]->k < 3)
+      return gpm_fail(GPM_E_UNSUPPORTED, "the pattern-guided search covers patterns with 3..8 vertices");
+  }
+  std::lock_guard<std::mutex> lk(g->mu);
+  cudaStream_t st = as_stream(stream);
+  GPM_TRY(prepare_locked(g, st));
+  return count_to_host(g, pats, npat, 0, g->n, false, counts, st, FORCE_GUIDED);
 }
 
 int gpm_count_roots(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uint32_t root_lo, uint32_t root_hi,
@@ -575,9 +605,9 @@ int gpm_exists(gpm_graph_t g, gpm_pattern_t p, int *found, uint32_t *witness, vo
   if (!p || !found) return gpm_fail(GPM_E_INVALID_ARG, "null argument");
   const bool clique = p->cls == PC_CLIQUE && p->k >= 3 && p->k <= 8;
   const bool sl = !p->induced && (p->cls == PC_DIAMOND || p->cls == PC_CYCLE4);
-  if (!clique && !sl)
-    return gpm_fail(GPM_E_UNSUPPORTED, "existence queries are implemented for the edge-induced diamond and 4-cycle "
-                                       "and for k-cliques with k = 3..8");
+  GuidedPlan plan{};
+  const bool guided = !clique && !sl;  // every other connected pattern of 3..8 vertices
+  if (guided) GPM_TRY(gpm_guided_plan(*p, &plan));
   std::lock_guard<std::mutex> lk(g->mu);
   cudaStream_t st = as_stream(stream);
   GPM_TRY(prepare_locked(g, st));
@@ -587,7 +617,8 @@ int gpm_exists(gpm_graph_t g, gpm_pattern_t p, int *found, uint32_t *witness, vo
   unsigned long long *counter = reinterpret_cast<unsigned long long *>(g->work + WK_MISC);
   GPM_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
   const uint32_t k = p->k;
-  if (p->cls == PC_DIAMOND) GPM_TRY(gpm_launch_list_diamond(g, dbuf, 1, counter, st));
+  if (guided) GPM_TRY(gpm_launch_guided(g, plan, nullptr, dbuf, 1, counter, st));
+  else if (p->cls == PC_DIAMOND) GPM_TRY(gpm_launch_list_diamond(g, dbuf, 1, counter, st));
   else if (p->cls == PC_CYCLE4) GPM_TRY(gpm_launch_list_cycle4(g, dbuf, 1, counter, st));
   else GPM_TRY(gpm_launch_list_cliques(g, (int)k, dbuf, 1, counter, st));
   unsigned long long c = 0;
@@ -596,8 +627,8 @@ int gpm_exists(gpm_graph_t g, gpm_pattern_t p, int *found, uint32_t *witness, vo
   GPM_CUDA(cudaMemcpyAsync(t, dbuf, k * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   GPM_CUDA(cudaStreamSynchronize(st));
   *found = c > 0 ? 1 : 0;
-  if (witness && c > 0)
-    for (uint32_t j = 0; j < k; ++j) witness[p->tmpl_to_pat[j]] = t[j];  // template order -> pattern numbering
+  if (witness && c > 0)  // template order -> pattern numbering (the guided search writes pattern order)
+    for (uint32_t j = 0; j < k; ++j) witness[guided ? j : p->tmpl_to_pat[j]] = t[j];
   return GPM_OK;
 }
 
@@ -607,9 +638,9 @@ int gpm_list(gpm_graph_t g, gpm_pattern_t p, uint32_t *buf, uint64_t cap, uint64
   if (!p || !written || !total || (cap && !buf)) return gpm_fail(GPM_E_INVALID_ARG, "null argument");
   const bool clique = p->cls == PC_CLIQUE && p->k >= 3 && p->k <= 8;
   const bool sl = !p->induced && (p->cls == PC_DIAMOND || p->cls == PC_CYCLE4);
-  if (!clique && !sl)
-    return gpm_fail(GPM_E_UNSUPPORTED, "listing is implemented for the edge-induced diamond and 4-cycle and for "
-                                       "k-cliques with k = 3..8");
+  GuidedPlan plan{};
+  const bool guided = !clique && !sl;  // every other connected pattern of 3..8 vertices
+  if (guided) GPM_TRY(gpm_guided_plan(*p, &plan));
   std::lock_guard<std::mutex> lk(g->mu);
   cudaStream_t st = as_stream(stream);
   GPM_TRY(prepare_locked(g, st));
@@ -633,7 +664,8 @@ int gpm_list(gpm_graph_t g, gpm_pattern_t p, uint32_t *buf, uint64_t cap, uint64
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) rc = gpm_cuda_fail(e, "listing");
     if (!rc) {
-      if (p->cls == PC_DIAMOND) rc = gpm_launch_list_diamond(g, dbuf, dcap, counter, st);
+      if (guided) rc = gpm_launch_guided(g, plan, nullptr, dbuf, dcap, counter, st);
+      else if (p->cls == PC_DIAMOND) rc = gpm_launch_list_diamond(g, dbuf, dcap, counter, st);
       else if (p->cls == PC_CYCLE4) rc = gpm_launch_list_cycle4(g, dbuf, dcap, counter, st);
       else rc = gpm_launch_list_cliques(g, (int)k, dbuf, dcap, counter, st);
     }
@@ -646,7 +678,7 @@ int gpm_list(gpm_graph_t g, gpm_pattern_t p, uint32_t *buf, uint64_t cap, uint64
     if (!rc) {
       nw = std::min<uint64_t>(c, dcap);
       bool ident = true;
-      for (uint32_t j = 0; j < k; ++j) ident &= (p->tmpl_to_pat[j] == j);
+      for (uint32_t j = 0; j < k && !guided; ++j) ident &= (p->tmpl_to_pat[j] == j);
       if (!ident) rc = gpm_launch_permute_tuples(dbuf, nw, (int)k, p->tmpl_to_pat, st);
     }
     if (!rc && !direct && nw) {

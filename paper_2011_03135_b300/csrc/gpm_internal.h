@@ -163,6 +163,9 @@ struct gpm_graph {
   uint32_t *enum_scratch = nullptr;
   size_t enum_scratch_bytes = 0;
   unsigned long long *enum_counts = nullptr;
+  // pattern-guided search: per-warp candidate lists
+  uint32_t *guided_scratch = nullptr;
+  size_t guided_scratch_bytes = 0;
 
   size_t device_bytes = 0;
   std::mutex mu;
@@ -306,6 +309,23 @@ struct EnumFinalize {
 };
 int gpm_launch_enum_finalize(const EnumFinalize &spec, const unsigned long long *cnt, unsigned long long *out,
                              unsigned int *status, cudaStream_t st);
+
+// Pattern-guided search for a connected pattern of 3..8 vertices, planned
+// from the pattern's matching order, symmetry-breaking pairs and degree
+// filter: level j matches pattern vertex order[j]; conn[j] bit i: adjacent in
+// the pattern to order[i]; lower[j] / upper[j] bit i: the candidate's id must
+// be above / below the vertex matched at level i; mindeg[j]: degree filter.
+struct GuidedPlan {
+  uint32_t k, induced;
+  uint32_t order[8], conn[8], lower[8], upper[8], mindeg[8];
+};
+int gpm_guided_plan(const gpm_pattern &p, GuidedPlan *plan);
+// Counting (out == nullptr): *acc += number of distinct subgraphs (acc zeroed
+// by the caller). Listing: matches written to out (tuples of k vertices in
+// pattern vertex order) while *counter < out_cap, every warp stopping at its
+// next work item once the counter reaches out_cap.
+int gpm_launch_guided(gpm_graph *g, const GuidedPlan &plan, unsigned long long *acc, uint32_t *out, uint64_t out_cap,
+                      unsigned long long *counter, cudaStream_t st);
 
 // Listing.
 int gpm_launch_list_diamond(gpm_graph *g, uint32_t *buf, uint64_t cap, unsigned long long *counter,

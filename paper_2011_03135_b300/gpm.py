@@ -97,6 +97,7 @@ _SIGS = {
     "gpm_count_async": [_vp, _vp, _u32, _vp, _vp],
     "gpm_count_roots": [_vp, _vp, _u32, _u32, _u32, _vp, _vp],
     "gpm_count_enumerate": [_vp, _vp, _u32, _vp, _vp],
+    "gpm_count_guided": [_vp, _vp, _u32, _vp, _vp],
     "gpm_count_cliques": [_vp, _u32, _u32, _u32, _vp, _vp],
     "gpm_exists": [_vp, _vp, _vp, _vp, _vp],
     "gpm_list": [_vp, _vp, _vp, _u64, _U64P, _U64P, _vp],
@@ -360,6 +361,14 @@ def count_enumerate(graph: Graph, patterns: Sequence[Pattern], stream=None) -> l
     out = np.zeros(len(patterns), dtype=np.uint64)
     _check(_lib.gpm_count_enumerate(graph.handle, _handles(patterns), len(patterns), out.ctypes.data,
                                     _stream(stream)))
+    return [int(x) for x in out]
+
+
+def count_guided(graph: Graph, patterns: Sequence[Pattern], stream=None) -> list:
+    """Counts by the pattern-guided search (any connected pattern with 3..8 vertices)."""
+    out = np.zeros(len(patterns), dtype=np.uint64)
+    _check(_lib.gpm_count_guided(graph.handle, _handles(patterns), len(patterns), out.ctypes.data,
+                                 _stream(stream)))
     return [int(x) for x in out]
 
 
