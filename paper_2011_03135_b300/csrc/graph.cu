@@ -387,109 +387,272 @@ __global__ void core_init_kernel(const uint32_t *__restrict__ deg, uint32_t n, u
   }
 }
 
-// frontier of level k among the vertices still present; cnt[0] its size,
-// cnt[1] the smallest remaining degree of the vertices left out
-__global__ void core_scan_kernel(uint32_t n, uint32_t k, uint32_t round, const uint32_t *__restrict__ cdeg,
-                                 uint32_t *__restrict__ core, uint32_t *__restrict__ order,
-                                 uint32_t *__restrict__ frontier, uint32_t *__restrict__ cnt) {
-  const uint32_t lane = threadIdx.x & 31;
-  uint32_t mn = kCoreUnset;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x; base < n; base += stride) {
-    const uint64_t v = base + threadIdx.x;
-    bool join = false;
-    if (v < n && core[v] == kCoreUnset) {
-      const uint32_t c = cdeg[v];
-      if (c <= k) {
-        core[v] = k;
-        order[v] = round;
-        join = true;
-      } else {
-        mn = min(mn, c);
+// Level-synchronous k-core peel in one cooperative launch (every block is
+// resident, so blocks may wait for one another). Phases alternate:
+//   scan at level k over the active list (vertices not yet taken when the
+//     previous scan ran): every vertex still present with remaining degree
+//     <= k is taken in the current round (frontier); the others form the next
+//     active list, and the smallest remaining degree among them is kept (to
+//     jump over empty levels);
+//   peel: the neighbours still present of every frontier vertex lose one
+//     remaining degree; a neighbour that drops to k is taken in the next round
+//     (claimed once) and forms the next frontier. A frontier vertex with at
+//     most kCoreBig neighbours is one warp's work; the lists of the larger
+//     ones are walked by the whole grid, one after the other;
+// peel rounds repeat until a frontier is empty, then k grows. Phase P counts
+// into counter slot P % 3 ({small frontier, smallest degree left, large
+// frontier, active list}); block 0 clears slot (P + 1) % 3 at the start of
+// phase P, a slot every block has finished reading one phase earlier. Phases
+// end at a grid barrier whose waits are bounded: on a timeout the kernel
+// records ST_TIMEOUT and stops.
+constexpr uint32_t kBarrierSpins = 1u << 24;
+constexpr uint32_t kCoreBig = 4096;
+
+__device__ __forceinline__ bool grid_barrier(unsigned int *bar, uint32_t nblocks, uint32_t &gen) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const uint32_t target = gen + 1;
+    __threadfence();  // this block's writes before its arrival
+    if (atomicAdd(&bar[0], 1u) == nblocks - 1) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicExch(&bar[1], target);
+    } else {
+      uint32_t it = 0;
+      while (*(volatile unsigned int *)&bar[1] != target) {
+        if (++it > kBarrierSpins) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(128);
       }
     }
-    const uint32_t m = __ballot_sync(0xffffffffu, join);
-    uint32_t at = 0;
-    if (m && lane == 0) at = atomicAdd(&cnt[0], (uint32_t)__popc(m));
-    at = __shfl_sync(0xffffffffu, at, 0);
-    if (join) frontier[at + __popc(m & ((1u << lane) - 1u))] = (uint32_t)v;
+    __threadfence();
+    gen = target;
+    s_ok = ok;
   }
-  mn = __reduce_min_sync(0xffffffffu, mn);
-  if (lane == 0 && mn != kCoreUnset) atomicMin(&cnt[1], mn);
+  __syncthreads();
+  return s_ok != 0;
 }
 
-// one warp per peeled vertex: lower the remaining degree of its neighbours
-// still present; those that drop to k join the next frontier (claimed once)
-__global__ void core_peel_kernel(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
-                                 const uint32_t *__restrict__ fin, uint32_t nin, uint32_t k, uint32_t next_round,
-                                 uint32_t *__restrict__ cdeg, uint32_t *__restrict__ core, uint32_t *__restrict__ order,
-                                 uint32_t *__restrict__ fout, uint32_t *__restrict__ nout) {
+struct CoreArgs {
+  const uint64_t *__restrict__ rowptr;
+  const uint32_t *__restrict__ col;
+  const uint32_t *__restrict__ deg;
+  uint32_t n;
+  uint32_t *cdeg, *core, *order;
+  uint32_t *fa, *fb;       // small frontiers (n words each)
+  uint32_t *ba, *bb;       // large frontiers (n words each)
+  uint32_t *act0, *act1;   // active lists (n words each; act0 = 0..n-1 at launch)
+  unsigned int *ctr;       // 3 slots x 4 words
+  unsigned int *bar;       // grid barrier {arrivals, generation}, zero at launch
+  unsigned int *status;
+  uint32_t max_phases;
+};
+
+// warp-aggregated append of v to list L with counter *c (lanes with `join`)
+__device__ __forceinline__ void warp_append(bool join, uint32_t v, uint32_t *L, unsigned int *c) {
   const uint32_t lane = threadIdx.x & 31;
-  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t i = warp; i < nin; i += nwarps) {
-    const uint32_t v = fin[i];
-    const uint64_t b = rowptr[v], e = rowptr[v + 1];
-    for (uint64_t j = b + lane; j < e; j += 32) {
-      const uint32_t w = col[j];
-      if (*(volatile uint32_t *)&core[w] != kCoreUnset) continue;
-      const uint32_t old = atomicSub(&cdeg[w], 1u);
-      if (old == k + 1 && atomicCAS(&core[w], kCoreUnset, k) == kCoreUnset) {
-        order[w] = next_round;
-        fout[atomicAdd(nout, 1u)] = w;
-      }
-    }
+  const uint32_t m = __ballot_sync(0xffffffffu, join);
+  uint32_t at = 0;
+  if (m && lane == 0) at = atomicAdd(c, (uint32_t)__popc(m));
+  at = __shfl_sync(0xffffffffu, at, 0);
+  if (join) L[at + __popc(m & ((1u << lane) - 1u))] = v;
+}
+
+// one neighbour w of a peeled vertex at level k
+__device__ __forceinline__ void core_lower(const CoreArgs &a, uint32_t w, uint32_t k, uint32_t next_round,
+                                           uint32_t *fout, uint32_t *bout, unsigned int *pc) {
+  if (*(volatile uint32_t *)&a.core[w] != kCoreUnset) return;
+  const uint32_t old = atomicSub(&a.cdeg[w], 1u);
+  if (old == k + 1 && atomicCAS(&a.core[w], kCoreUnset, k) == kCoreUnset) {
+    a.order[w] = next_round;
+    if (__ldg(a.deg + w) > kCoreBig) bout[atomicAdd(&pc[2], 1u)] = w;
+    else fout[atomicAdd(&pc[0], 1u)] = w;
   }
+}
+
+__global__ void __launch_bounds__(1024) core_peel_all_kernel(CoreArgs a) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t gtid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t first = blockIdx.x * (uint64_t)blockDim.x;  // this block's first index of a strided loop
+  const uint64_t warp = gtid >> 5, nwarps = nth >> 5;
+  uint32_t gen = 0, phase = 0, k = 0, round = 0, na = a.n;
+  uint32_t *ain = a.act0, *aout = a.act1;
+  bool ok = true;
+  auto barrier = [&]() -> bool { return grid_barrier(a.bar, gridDim.x, gen); };
+  auto clear_next = [&]() {
+    if (gtid == 0) {
+      unsigned int *nxt = a.ctr + 4 * ((phase + 1) % 3);
+      nxt[0] = 0u;
+      nxt[1] = kCoreUnset;
+      nxt[2] = 0u;
+      nxt[3] = 0u;
+    }
+  };
+  for (;;) {
+    // ---- scan phase at level k ----
+    if (phase >= a.max_phases) {
+      ok = false;
+      break;
+    }
+    unsigned int *cnt = a.ctr + 4 * (phase % 3);
+    clear_next();
+    {
+      uint32_t mn = kCoreUnset;
+      for (uint64_t base = first; base < na; base += nth) {
+        const uint64_t i = base + threadIdx.x;
+        bool take = false, keep = false;
+        uint32_t v = 0;
+        if (i < na) {
+          v = ain[i];
+          if (a.core[v] == kCoreUnset) {
+            const uint32_t c = a.cdeg[v];
+            if (c <= k) {
+              a.core[v] = k;
+              a.order[v] = round;
+              take = true;
+            } else {
+              keep = true;
+              mn = min(mn, c);
+            }
+          }
+        }
+        const bool big = take && __ldg(a.deg + v) > kCoreBig;
+        warp_append(take && !big, v, a.fa, &cnt[0]);
+        warp_append(big, v, a.ba, &cnt[2]);
+        warp_append(keep, v, aout, &cnt[3]);
+      }
+      mn = __reduce_min_sync(0xffffffffu, mn);
+      if (lane == 0 && mn != kCoreUnset) atomicMin(&cnt[1], mn);
+    }
+    if (!barrier()) {
+      ok = false;
+      break;
+    }
+    ++phase;
+    uint32_t nin = *(volatile unsigned int *)&cnt[0];
+    const uint32_t mn = *(volatile unsigned int *)&cnt[1];
+    uint32_t nbig = *(volatile unsigned int *)&cnt[2];
+    na = *(volatile unsigned int *)&cnt[3];
+    {
+      uint32_t *t = ain;
+      ain = aout;
+      aout = t;
+    }
+    if (nin + nbig == 0) {
+      if (mn == kCoreUnset) break;  // every vertex has been taken
+      if (mn <= k) {
+        ok = false;
+        break;
+      }
+      k = mn;  // no vertex left at this level: jump to the smallest remaining degree
+      continue;
+    }
+    // ---- peel rounds at level k ----
+    uint32_t *fin = a.fa, *fout = a.fb, *bin = a.ba, *bout = a.bb;
+    while (nin + nbig > 0) {
+      if (phase >= a.max_phases) {
+        ok = false;
+        break;
+      }
+      unsigned int *pc = a.ctr + 4 * (phase % 3);
+      clear_next();
+      for (uint64_t i = warp; i < nin; i += nwarps) {
+        const uint32_t v = fin[i];
+        const uint64_t b = a.rowptr[v], e = a.rowptr[v + 1];
+        for (uint64_t j = b + lane; j < e; j += 32) core_lower(a, a.col[j], k, round + 1, fout, bout, pc);
+      }
+      for (uint32_t q = 0; q < nbig; ++q) {
+        const uint32_t v = bin[q];
+        const uint64_t b = a.rowptr[v], e = a.rowptr[v + 1];
+        for (uint64_t j = b + gtid; j < e; j += nth) core_lower(a, a.col[j], k, round + 1, fout, bout, pc);
+      }
+      if (!barrier()) {
+        ok = false;
+        break;
+      }
+      ++phase;
+      nin = *(volatile unsigned int *)&pc[0];
+      nbig = *(volatile unsigned int *)&pc[2];
+      uint32_t *t = fin;
+      fin = fout;
+      fout = t;
+      t = bin;
+      bin = bout;
+      bout = t;
+      ++round;
+    }
+    if (!ok) break;
+    ++k;
+  }
+  if (!ok && gtid == 0) atomicOr(a.status, ST_TIMEOUT);
+}
+
+__global__ void core_iota_kernel(uint32_t n, uint32_t *__restrict__ act) {
+  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x)
+    act[v] = (uint32_t)v;
 }
 
 }  // namespace
 
 int gpm_core_numbers(gpm_graph *g, cudaStream_t st) {
   const uint32_t n = g->n;
-  if (!g->core) GPM_TRY(gpm_graph_alloc(g, (void **)&g->core, sizeof(uint32_t) * (size_t)std::max<uint32_t>(n, 1)));
-  if (!g->core_work)
-    GPM_TRY(gpm_graph_alloc(g, (void **)&g->core_work, sizeof(uint32_t) * 4 * (size_t)std::max<uint32_t>(n, 1)));
-  g->core_order = g->core_work + 3 * (size_t)std::max<uint32_t>(n, 1);
+  const size_t nw = std::max<uint32_t>(n, 1);
+  if (!g->core) GPM_TRY(gpm_graph_alloc(g, (void **)&g->core, sizeof(uint32_t) * nw));
+  // remaining degrees, two small and two large frontiers, two active lists,
+  // the peel round of every vertex, then counters and the grid barrier
+  if (!g->core_work) GPM_TRY(gpm_graph_alloc(g, (void **)&g->core_work, sizeof(uint32_t) * (8 * nw + 16)));
+  g->core_order = g->core_work + 7 * nw;
   if (n == 0) return GPM_OK;
-  uint32_t *cdeg = g->core_work, *fa = cdeg + n, *fb = fa + n;
-  // [0] frontier size, [1] smallest degree left out; past the two words that
-  // prepare keeps its maximum degrees in
-  uint32_t *cnt = reinterpret_cast<uint32_t *>(g->work + WK_MISC + 2);
+  uint32_t *w = g->core_work;
+  unsigned int *ctr = g->core_order + nw, *bar = ctr + 12;
+  unsigned int *status = reinterpret_cast<unsigned int *>(g->work + WK_STATUS);
   const int sms = gpm_num_sms(g->device);
-  GPM_LAUNCH("core_init_kernel", st, core_init_kernel<<<sms * 4, 256, 0, st>>>(g->deg, n, cdeg, g->core));
+  GPM_LAUNCH("core_init_kernel", st, core_init_kernel<<<sms * 4, 256, 0, st>>>(g->deg, n, w, g->core));
+  GPM_LAUNCH("core_iota_kernel", st, core_iota_kernel<<<sms * 4, 256, 0, st>>>(n, w + 5 * nw));
   GPM_CUDA(cudaGetLastError());
-  uint64_t left = n;
-  uint32_t k = 0, round = 0;
-  while (left > 0) {
-    const uint32_t init[2] = {0u, kCoreUnset};
-    GPM_CUDA(cudaMemcpyAsync(cnt, init, sizeof(init), cudaMemcpyHostToDevice, st));
-    GPM_LAUNCH("core_scan_kernel", st, core_scan_kernel<<<sms * 4, 256, 0, st>>>(n, k, round, cdeg, g->core, g->core_order, fa, cnt));
-    GPM_CUDA(cudaGetLastError());
-    uint32_t h[2];
-    GPM_CUDA(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st));
-    GPM_CUDA(cudaStreamSynchronize(st));
-    if (h[0] == 0) {
-      if (h[1] == kCoreUnset || h[1] <= k) return gpm_fail(GPM_E_DEVICE, "core peel made no progress");
-      k = h[1];  // no vertex left at this level: jump to the smallest remaining degree
-      continue;
-    }
-    uint32_t nin = h[0];
-    uint32_t *fin = fa, *fout = fb;
-    while (nin > 0) {
-      left -= nin;
-      GPM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t), st));
-      const unsigned blocks = (unsigned)std::min<uint64_t>(((uint64_t)nin + 7) / 8, (uint64_t)sms * 16);
-      GPM_LAUNCH("core_peel_kernel", st,
-                 core_peel_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, fin, nin, k, round + 1, cdeg, g->core,
-                                                          g->core_order, fout, cnt));
-      GPM_CUDA(cudaGetLastError());
-      GPM_CUDA(cudaMemcpyAsync(&nin, cnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-      GPM_CUDA(cudaStreamSynchronize(st));
-      std::swap(fin, fout);
-      ++round;
-    }
-    ++k;
-  }
+  unsigned int init[14] = {0u, kCoreUnset, 0u, 0u, 0u, kCoreUnset, 0u, 0u, 0u, kCoreUnset, 0u, 0u, 0u, 0u};
+  GPM_CUDA(cudaMemcpyAsync(ctr, init, sizeof(init), cudaMemcpyHostToDevice, st));
+  GPM_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned int), st));
+  // one 1024-thread block per SM: the grid barriers between phases cost one
+  // arrival per block
+  int per_sm = 0;
+  GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, core_peel_all_kernel, 1024, 0));
+  if (per_sm < 1) return gpm_fail(GPM_E_DEVICE, "core peel kernel does not fit an SM");
+  const unsigned blocks = (unsigned)sms;
+  CoreArgs a{};
+  a.rowptr = g->rowptr;
+  a.col = g->col;
+  a.deg = g->deg;
+  a.n = n;
+  a.cdeg = w;
+  a.fa = w + nw;
+  a.fb = w + 2 * nw;
+  a.ba = w + 3 * nw;
+  a.bb = w + 4 * nw;
+  a.act0 = w + 5 * nw;
+  a.act1 = w + 6 * nw;
+  a.core = g->core;
+  a.order = g->core_order;
+  a.ctr = ctr;
+  a.bar = bar;
+  a.status = status;
+  // every round takes at least one vertex, every scan without one raises k:
+  // at most n rounds and n + 1 scans
+  a.max_phases = (uint32_t)std::min<uint64_t>(0xffffffffull, 2ull * n + 4);
+  void *args[] = {&a};
+  GPM_LAUNCH("core_peel_all_kernel", st,
+             GPM_CUDA(cudaLaunchCooperativeKernel((const void *)core_peel_all_kernel, dim3(blocks), dim3(1024), args, 0,
+                                                  st)));
+  GPM_CUDA(cudaGetLastError());
+  unsigned int s = 0;
+  GPM_CUDA(cudaMemcpyAsync(&s, status, sizeof(s), cudaMemcpyDeviceToHost, st));
+  GPM_CUDA(cudaStreamSynchronize(st));
+  if (s & ST_TIMEOUT) return gpm_fail(GPM_E_TIMEOUT, "core peel: a grid barrier wait or the phase limit ran out");
   return GPM_OK;
 }
 

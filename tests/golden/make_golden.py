@@ -26,6 +26,13 @@ OUT = os.path.join(HERE, "fullsize_counts.json")
 _G = None
 
 
+def _largest_batch_motif4_rmat():
+    """The largest R-MAT graph among the 4-motif queries of the 512-query batch."""
+    from paper_2011_03135_b300 import graphgen as gg
+    specs = [s for s in gg.batch_query_specs(512) if s["kind"] == "rmat" and s["k"] == 4]
+    return max(specs, key=lambda s: (s["n"], s["edge_factor"]))
+
+
 def _graph(name):
     from paper_2011_03135_b300 import graphgen as gg
     return {
@@ -33,6 +40,7 @@ def _graph(name):
         "clique_rmat21": gg.workload_clique_rmat21,
         "sl_chunglu4m": gg.workload_sl_chung_lu4m,
         "clique789_chunglu1m": gg.workload_clique789_chung_lu1m,
+        "motif4_batch_rmat20": lambda: gg.graph_from_spec(_largest_batch_motif4_rmat()),
     }[name]()
 
 
@@ -56,6 +64,14 @@ def _work(args):
 def run(name, whats, procs, chunks=512):
     g = _graph(name)
     res = dict(n=g.n, nnz=g.nnz, digest=g.digest())
+    if whats == ["motifs4"]:
+        # the six induced 4-vertex motif counts are global sums (per-edge
+        # triangle terms), computed whole by the single-threaded oracle
+        import oracle as O
+        t0 = time.time()
+        res["motifs4"] = O.motifs(g, 4)
+        print(f"{name} motifs4 = {res['motifs4']}  ({time.time() - t0:.1f} s, 1 process)", flush=True)
+        return res
     bounds = [g.n * i // chunks for i in range(chunks + 1)]
     ctx = mp.get_context("spawn")
     with ctx.Pool(procs, initializer=_init, initargs=(name,)) as pool:
@@ -74,6 +90,7 @@ PLAN = {
     "clique_rmat21": ["clique3", "clique4", "clique5"],
     "sl_chunglu4m": ["diamond", "cycle4", "clique3"],
     "clique789_chunglu1m": ["clique7", "clique8", "clique9"],
+    "motif4_batch_rmat20": ["motifs4"],
 }
 
 
