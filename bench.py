@@ -249,18 +249,20 @@ def _cpu_model():
     return "unknown"
 
 
-def cpu_baseline_all_cores(g, ks, unit, single, seconds_target=4.0):
+def cpu_baseline_all_cores(g, ks, unit, single, seconds_target=6.0):
     """The same oracle code, unchanged, over root ranges on every host core
     (a spawn-started process pool: no fork after the GPU is in use). The
     sample is the prefix [0, hi) of the randomly permuted ids, sized from the
-    single-threaded rate for about `seconds_target` of wall time, cut into
-    interleaved chunks so that the heavy roots spread over the workers."""
+    single-threaded rate for about `seconds_target` of wall time, cut into two
+    ranges per process (every oracle call orients the whole graph first, so
+    few calls per process; the ids are a random permutation, so ranges of
+    equal length carry similar work)."""
     import multiprocessing as mp
     import tempfile
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     per_root_s = single["seconds"] / max(single["roots"], 1)
     hi = int(min(g.n, max(single["roots"], cores * seconds_target / max(per_root_s, 1e-9))))
-    nchunks = max(1, min(hi, cores * 64))
+    nchunks = max(1, min(hi, cores * 2))
     bounds = [hi * i // nchunks for i in range(nchunks + 1)]
     tasks = [(tuple(ks), bounds[i], bounds[i + 1]) for i in range(nchunks) if bounds[i + 1] > bounds[i]]
     with tempfile.TemporaryDirectory(prefix="gpm_cpu_") as d:
@@ -339,12 +341,50 @@ def run_batched(args, graphs=None):
     nq = len(specs)
     pq = nq / (sum(plain_t) / len(plain_t))
     bq = nq / (sum(batch_t) / len(batch_t))
+
+    def timed(fn, reps=3):
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        return min(ts)
+
+    # the queries under 1 ms of plain time alone: batched vs plain
+    small = [i for i in range(nq) if per_q[i] < 1e-3]
+    subset = None
+    if small:
+        Bs = gpm.Batch([(Gs[i], kinds[i]) for i in small])
+        assert Bs.run() == [want[i] for i in small]
+        bs = timed(Bs.run)
+        ps = timed(lambda: [gpm.count(Gs[i], pats[kinds[i]]) for i in small])
+        Bs.close()
+        subset = {"queries": len(small), "plain_queries_per_s": len(small) / ps,
+                  "batched_queries_per_s": len(small) / bs, "speedup": ps / bs}
+    # the heaviest queries alone: the persistent kernel on all their items
+    # (no plain-path fallback) against their plain launch chain
+    heavy = []
+    old = gpm.get_options()
+    try:
+        gpm.set_options(batch_direct_us=0xffffffff)
+        for i in order[:12]:
+            B1 = gpm.Batch([(Gs[i], kinds[i])])
+            assert B1.run() == [want[i]]
+            t_items = timed(B1.run)
+            B1.close()
+            t_plain = timed(lambda: gpm.count(Gs[i], pats[kinds[i]]))
+            heavy.append({"query": int(i), "kind": "3-motif" if kinds[i] == gpm.QUERY_MOTIF3 else "4-motif",
+                          "graph": graphs[i].name, "edges": int(graphs[i].m), "plain_s": t_plain,
+                          "persistent_s": t_items, "persistent_over_plain": t_items / t_plain})
+    finally:
+        gpm.set_options(**{k: v for k, v in old.items() if v})
     for G in Gs:
         G.close()
     return {"workload": BATCH_WORKLOAD, "queries": nq, "edges_total": int(sum(g.m for g in graphs)),
             "plain_queries_per_s": pq, "batched_queries_per_s": bq, "speedup": bq / pq,
             "plain_s": plain_t, "batched_s": batch_t, "autotune_s": tune_s, "setup_s": setup_s,
-            "plain_per_query": plain_profile,
+            "plain_per_query": plain_profile, "sub_1ms_subset": subset, "heaviest_alone": heavy,
             "schedule": info, "equal_counts": True}
 
 
