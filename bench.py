@@ -648,7 +648,7 @@ def run_large_k(args, workload, g, ks, case):
     for i in range(3):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        H = gpm.Graph(rp_h, col_h, g.n, validate=False, stream=stream)
+        H = gpm.Graph(rp_h, col_h, g.n, validate=True, stream=stream)
         c = [gpm.count_cliques(H, k, stream=stream) for k in ks]
         H.close()
         if i > 0:
@@ -924,14 +924,14 @@ def run_ours(args):
     units = (counts[0] + counts[1]) * world
     value = units / (ms / 1000.0)
 
-    # end to end through the C-ABI with host buffers (pinned): upload, orient, count, read back
+    # end to end through the C-ABI with host buffers (pinned): upload, validate, orient, count, read back
     rp_h = torch.from_numpy(g.rowptr.view(np.int64)).pin_memory()
     col_h = torch.from_numpy(g.col.view(np.int32)).pin_memory()
     e2e_times = []
     for i in range(max(2, min(args.steps, 5)) + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        H = gpm.Graph(rp_h, col_h, g.n, validate=False, stream=stream)
+        H = gpm.Graph(rp_h, col_h, g.n, validate=True, stream=stream)
         if args.orientation != "degree":
             H.set_orientation(args.orientation)
         c = gpm.count(H, pats, stream=stream)

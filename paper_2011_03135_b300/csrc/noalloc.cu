@@ -11,9 +11,13 @@
 // library image (kNoAllocWords 32-bit words = 64 MiB, held by every GPU that
 // loads the library until the process exits).
 //
-// The kernel is a variant of the 4-cycle pass (one CTA per root, dense wedge
-// tally per CTA, as in motif.cu) whose tallies, degree array, work queue and
-// accumulator live in that array instead of buffers owned by a graph handle.
+// The kernels are a variant of the 4-cycle pass of motif.cu whose degree
+// array, tallies, work counters and accumulator live in that array instead of
+// buffers owned by a graph handle: roots whose wedge bound is at most 512 are
+// counted first by warps with a shared-memory hash (as the small class, every
+// SM busy whatever n is); the larger roots then by CTAs with a dense wedge
+// tally of n words each (as many CTAs as tallies fit next to the degrees),
+// which pick them out of batches of 512 roots.
 #include <mutex>
 
 #include "gpm_internal.h"
@@ -23,7 +27,8 @@ namespace {
 
 constexpr uint64_t kNoAllocWords = 16ull << 20;  // 64 MiB
 constexpr uint32_t kNoAllocThreads = 512;
-constexpr uint32_t kCtrWords = 64;  // [0] queue head, [1] status, [2..3] count (uint64)
+constexpr uint32_t kCtrWords = 64;  // [0], [1] claim counters of the two kernels, [2..3] count (uint64)
+constexpr uint32_t kSmallWarps = 4;  // 8 KB of hash per warp, 32 KB of static shared memory per block
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
 
@@ -49,24 +54,75 @@ __global__ void noalloc_degree_kernel(const uint64_t *__restrict__ rowptr, uint3
     deg[v] = (uint32_t)(rowptr[v + 1] - rowptr[v]);
 }
 
-// every vertex is a candidate root (order-last vertex of its cycles); one CTA
-// per root, tally + touched list in this CTA's slot of the scratch
+// wedge bound of root v0: the degrees of its neighbours before it (degree, then id)
+__device__ __forceinline__ unsigned long long wedge_bound_thread(const uint64_t *__restrict__ rowptr,
+                                                               const uint32_t *__restrict__ col,
+                                                               const uint32_t *__restrict__ deg, uint32_t v0) {
+  const uint32_t d0 = deg[v0];
+  unsigned long long b = 0;
+  for (uint64_t e = rowptr[v0]; e < rowptr[v0 + 1]; ++e) {
+    const uint32_t x = col[e], dx = deg[x];
+    if (gpm_dev::precedes(dx, x, d0, v0)) b += dx;
+  }
+  return b;
+}
+
+// roots with wedge bound in [3, kC4SmallBound]: one warp each, shared-memory hash
+__global__ void __launch_bounds__(kSmallWarps * 32) noalloc_small_kernel(const uint64_t *__restrict__ rowptr,
+                                                                          const uint32_t *__restrict__ col,
+                                                                          const uint32_t *__restrict__ deg, uint32_t n,
+                                                                          uint32_t *ctr) {
+  __shared__ uint32_t s_hash[kSmallWarps][2 * gpm_dev::kC4HashSlots];
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t *keys = s_hash[wid], *cnt = keys + gpm_dev::kC4HashSlots;
+  unsigned long long acc = 0;
+  bool overflow = false;
+  for (;;) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&ctr[0], 32u);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= n) break;
+    // lane k finds the bound of root base + k; then the warp takes the small ones in turn
+    const uint32_t mine = base + lane;
+    const unsigned long long b = mine < n ? wedge_bound_thread(rowptr, col, deg, mine) : 0ull;
+    uint32_t small = __ballot_sync(0xffffffffu, b >= 3 && b <= gpm_dev::kC4SmallBound);
+    while (small) {
+      const uint32_t k = __ffs(small) - 1;
+      small &= small - 1;
+      acc += gpm_dev::c4_root_warp(rowptr, col, deg, nullptr, base + k, keys, cnt, overflow);
+    }
+  }
+  acc = gpm_dev::warp_sum(acc);
+  if (lane == 0 && acc) atomicAdd(reinterpret_cast<unsigned long long *>(ctr + 2), acc);
+}
+
+// roots with wedge bound above kC4SmallBound: each CTA takes batches of
+// kNoAllocThreads roots, keeps the large ones, and counts each with the whole
+// CTA on the dense tally + touched list of its slot
 __global__ void __launch_bounds__(kNoAllocThreads) noalloc_c4_kernel(const uint64_t *__restrict__ rowptr,
                                                                       const uint32_t *__restrict__ col,
                                                                       const uint32_t *__restrict__ deg, uint32_t n,
                                                                       uint32_t *slots, uint32_t *ctr) {
-  __shared__ uint32_t s_root, s_nt, s_cnt;
-  __shared__ uint32_t s_x[kNoAllocThreads];
+  __shared__ uint32_t s_base, s_nbig, s_nt, s_cnt;
+  __shared__ uint32_t s_x[kNoAllocThreads], s_big[kNoAllocThreads];
   uint32_t *tally = slots + (size_t)blockIdx.x * 2 * n;
   uint32_t *touched = tally + n;
   unsigned long long acc = 0;
   for (;;) {
-    if (threadIdx.x == 0) s_root = atomicAdd(&ctr[0], 1u);
+    if (threadIdx.x == 0) {
+      s_base = atomicAdd(&ctr[1], kNoAllocThreads);
+      s_nbig = 0;
+    }
     __syncthreads();
-    const uint32_t v0 = s_root;
+    const uint32_t base = s_base;
+    if (base >= n) break;
+    const uint32_t v = base + threadIdx.x;
+    if (v < n && wedge_bound_thread(rowptr, col, deg, v) > gpm_dev::kC4SmallBound) s_big[atomicAdd(&s_nbig, 1u)] = v;
     __syncthreads();
-    if (v0 >= n) break;
-    acc += gpm_dev::c4_root_cta(rowptr, col, deg, nullptr, v0, tally, touched, s_x, &s_cnt, &s_nt);
+    const uint32_t nbig = s_nbig;
+    for (uint32_t i = 0; i < nbig; ++i)
+      acc += gpm_dev::c4_root_cta(rowptr, col, deg, nullptr, s_big[i], tally, touched, s_x, &s_cnt, &s_nt);
+    __syncthreads();
   }
   acc = gpm_dev::warp_sum(acc);
   if ((threadIdx.x & 31) == 0 && acc) atomicAdd(reinterpret_cast<unsigned long long *>(ctr + 2), acc);
@@ -100,11 +156,17 @@ extern "C" int gpm_count_cycles4_noalloc(const uint64_t *rowptr, const uint32_t 
   uint64_t nslots = (kNoAllocWords - kCtrWords - n) / slot_words;
   nslots = std::min<uint64_t>(nslots, (uint64_t)gpm_num_sms(device));
   nslots = std::max<uint64_t>(1, std::min<uint64_t>(nslots, std::max<uint32_t>(n, 1)));
-  // the array keeps the previous call's contents: clear what must start at zero
+  // the array keeps the previous call's contents (possibly laid out for
+  // another n): clear what must start at zero -- the counters and the tally
+  // half of every slot (the touched half is written before it is read)
   GPM_CUDA(cudaMemsetAsync(ctr, 0, kCtrWords * sizeof(uint32_t), st));
-  GPM_CUDA(cudaMemsetAsync(slots, 0, nslots * slot_words * sizeof(uint32_t), st));
+  for (uint64_t s = 0; s < nslots; ++s)
+    GPM_CUDA(cudaMemsetAsync(slots + s * slot_words, 0, sizeof(uint32_t) * std::max<uint32_t>(n, 1), st));
   if (n > 0) {
-    GPM_LAUNCH("noalloc_degree_kernel", st, noalloc_degree_kernel<<<gpm_num_sms(device) * 4, 256, 0, st>>>(rowptr, n, deg));
+    const int sms = gpm_num_sms(device);
+    GPM_LAUNCH("noalloc_degree_kernel", st, noalloc_degree_kernel<<<sms * 4, 256, 0, st>>>(rowptr, n, deg));
+    GPM_LAUNCH("noalloc_small_kernel", st,
+               noalloc_small_kernel<<<(unsigned)sms * 8, kSmallWarps * 32, 0, st>>>(rowptr, col, deg, n, ctr));
     GPM_LAUNCH("noalloc_c4_kernel", st,
                noalloc_c4_kernel<<<(unsigned)nslots, kNoAllocThreads, 0, st>>>(rowptr, col, deg, n, slots, ctr));
   }

@@ -42,11 +42,30 @@ def test_noalloc_matches_regular_count_twice(env, mk):
     G = gpm.Graph.from_host(g)
     want = gpm.count(G, [gpm.Pattern.spec(O.CYCLE4, induced=False)])[0]
     G.close()
+    assert want == O.cycles4(g)
     out = torch.full((1,), -1, dtype=torch.int64, device="cuda")
     for _ in range(2):
         out.fill_(-1)
         assert _call(gpm, torch, g, out) == 0, gpm._lib.gpm_last_error()
         assert int(out.item()) == want
+
+
+def test_noalloc_near_the_size_limit(env):
+    # a ladder with m rungs (2m vertices, close to the largest n the fixed
+    # array takes, so a single tally slot): exactly m - 1 four-cycles; then a
+    # small graph again, whose slots overlap what the large call left behind
+    gpm, torch = env
+    m = 2_750_000
+    i = np.arange(m, dtype=np.int64)
+    e = np.concatenate([np.stack([2 * i, 2 * i + 1], 1), np.stack([2 * i[:-1], 2 * i[1:]], 1),
+                        np.stack([2 * i[:-1] + 1, 2 * i[1:] + 1], 1)])
+    g = gg.from_edges(2 * m, e, name="ladder")
+    out = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    assert _call(gpm, torch, g, out) == 0, gpm._lib.gpm_last_error()
+    assert int(out.item()) == m - 1
+    h = gg.rmat(12, 16.0, seed=3)
+    assert _call(gpm, torch, h, out) == 0, gpm._lib.gpm_last_error()
+    assert int(out.item()) == O.cycles4(h)
 
 
 def test_noalloc_rejects_oversize_graph(env):
