@@ -7,16 +7,23 @@ of 4- and 5-cliques counted per second of device time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+At N = 1 the same line also carries the oracle's CPU baselines (one thread,
+and the unchanged oracle over root ranges on every host core) and, under
+"legs", the subgraph-listing workload (diamonds and 4-cycles on Chung-Lu 4M,
+with the 4-cycle pass's HBM roofline and DRAM traffic) and triangle counting
+on R-MAT 14, each checked against the oracle's stored totals.
+
 Under torchrun (N > 1) every rank counts its own replica of the workload
 (weak scaling, no collective on the data path); the slowest rank's time sets
 the step time. `--impl reference` times the CPU oracle (single-threaded C) on
 a bounded root sample of the same workload.
 
-Other legs (one GPU, one JSON line each): `--workload tc` (triangles, R-MAT
-14), `sl` (diamonds and 4-cycles, Chung-Lu 4M), `clique6` (6-cliques, R-MAT
+Other legs (one GPU, one JSON line each): `--workload tc`, `sl`, `motif5`
+(the 21 five-vertex motifs, Erdos-Renyi 1M), `clique6` (6-cliques, R-MAT
 20), `clique789` (7-, 8-, 9-cliques, Chung-Lu 1M), `batched` and `served`
 (many small queries); `--orientation core` runs the headline leg under the
-core value based (degeneracy) order, k-core peel included in each step.
+core value based (degeneracy) order, k-core peel included in each step;
+`--case NAME --reps N` runs a named workload for a profiler.
 """
 from __future__ import annotations
 
