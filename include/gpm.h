@@ -14,8 +14,11 @@
  *    On error no output argument is modified and gpm_last_error() returns a
  *    message for the calling host thread.
  *  - Counts are exact unsigned 64-bit integers. A count that does not fit in
- *    64 bits is reported as GPM_E_OVERFLOW where it can be detected (motif
- *    inversion); clique/SL counts are accumulated modulo 2^64.
+ *    64 bits is reported as GPM_E_OVERFLOW: every warp's partial sum and
+ *    every addition into the device accumulators is checked for a carry out
+ *    of 64 bits (a single thread's running sum could only wrap after ~2^64
+ *    additions), and the motif inversion checks its terms. The batched and
+ *    served forms report an overflow of the motif inversion only.
  *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
  *    stream). Calls that return results in host memory synchronise that
  *    stream before returning; *_async calls do not.

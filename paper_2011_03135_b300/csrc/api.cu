@@ -596,6 +596,8 @@ int gpm_count_cliques(gpm_graph_t g, uint32_t k, uint32_t root_lo, uint32_t root
   GPM_CUDA(cudaMemcpyAsync(&status, status_of(g), sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
   GPM_CUDA(cudaStreamSynchronize(st));
   GPM_TRY(status_to_code((uint32_t)status));
+  // the high word holds one bit per accumulator slot that went past 64 bits
+  if (((status >> 32) >> slot) & 1ull) return gpm_fail(GPM_E_OVERFLOW, "the clique count does not fit in 64 bits");
   *count = h;
   return GPM_OK;
 }

@@ -56,23 +56,22 @@ struct LGArgs {
 
 __device__ __forceinline__ void flush_acc(const LGArgs &a, unsigned long long a3, unsigned long long a4,
                                           unsigned long long a5, unsigned long long a6, int kmax) {
+  bool c3 = false, c4 = false, c5 = false, c6 = false;
   if (kmax >= 7) {
     // the generic pass adds only its own clique size (a6 carries it)
-    for (int o = 16; o > 0; o >>= 1) a6 += __shfl_down_sync(0xffffffffu, a6, o);
-    if ((threadIdx.x & 31) == 0 && a6) atomicAdd(&a.acc[kmax - 7], a6);
+    a6 = warp_sum_checked(a6, c6);
+    if ((threadIdx.x & 31) == 0) acc_add_checked(&a.acc[kmax - 7], a6, c6, a.status, kmax - 7);
     return;
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    a3 += __shfl_down_sync(0xffffffffu, a3, o);
-    a4 += __shfl_down_sync(0xffffffffu, a4, o);
-    a5 += __shfl_down_sync(0xffffffffu, a5, o);
-    if (kmax >= 6) a6 += __shfl_down_sync(0xffffffffu, a6, o);
-  }
+  a3 = warp_sum_checked(a3, c3);
+  a4 = warp_sum_checked(a4, c4);
+  a5 = warp_sum_checked(a5, c5);
+  if (kmax >= 6) a6 = warp_sum_checked(a6, c6);
   if ((threadIdx.x & 31) == 0) {
-    if (a3) atomicAdd(&a.acc[3], a3);
-    if (kmax >= 4 && a4) atomicAdd(&a.acc[4], a4);
-    if (kmax >= 5 && a5) atomicAdd(&a.acc[5], a5);
-    if (kmax >= 6 && a6) atomicAdd(&a.acc[ACC_K6], a6);
+    acc_add_checked(&a.acc[3], a3, c3, a.status, ACC_T);
+    if (kmax >= 4) acc_add_checked(&a.acc[4], a4, c4, a.status, ACC_K4);
+    if (kmax >= 5) acc_add_checked(&a.acc[5], a5, c5, a.status, ACC_K5);
+    if (kmax >= 6) acc_add_checked(&a.acc[ACC_K6], a6, c6, a.status, ACC_K6);
   }
 }
 

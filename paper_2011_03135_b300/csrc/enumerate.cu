@@ -73,6 +73,7 @@ struct EnumArgs {
   uint64_t cap2, cap3;             // capacities of E2 and E3
   const uint8_t *__restrict__ cls; // class of every full code (255: none)
   unsigned long long *counts;      // per class
+  unsigned int *status;
 };
 
 // Candidates for level l + 1 after choosing w = E[i] at level l: the
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(kEnumThreads) enum_kernel(EnumArgs a) {
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < kCodes; i += blockDim.x) {
     const unsigned long long c = hist[i];
-    if (c && a.cls[i] != 255) atomicAdd(&a.counts[a.cls[i]], c);
+    if (c && a.cls[i] != 255) acc_add_checked(&a.counts[a.cls[i]], c, false, a.status, -1);
   }
 }
 
@@ -434,6 +435,7 @@ int gpm_launch_enumerate(gpm_graph *g, uint32_t k, uint32_t root_lo, uint32_t ro
   a.cap3 = cap3;
   a.cls = g->enum_cls[k];
   a.counts = counts;
+  a.status = reinterpret_cast<unsigned int *>(g->work + WK_STATUS);
   if (k == 3) GPM_LAUNCH("enum_kernel_k3", st, enum_kernel<3><<<blocks, kEnumThreads, 0, st>>>(a));
   else if (k == 4) GPM_LAUNCH("enum_kernel_k4", st, enum_kernel<4><<<blocks, kEnumThreads, 0, st>>>(a));
   else GPM_LAUNCH("enum_kernel_k5", st, enum_kernel<5><<<blocks, kEnumThreads, 0, st>>>(a));

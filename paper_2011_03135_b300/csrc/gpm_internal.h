@@ -43,6 +43,32 @@ enum : uint32_t {
   ST_CAPACITY = 128u,
 };
 
+#ifdef __CUDACC__
+// Exact 64-bit count accumulation. Per-thread sums cannot wrap in any feasible
+// run (that takes ~2^64 additions); the sums of a warp and the additions into
+// the device accumulators are checked: a carry out of 64 bits sets
+// ST_CAPACITY in *status, which the host turns into GPM_E_OVERFLOW.
+__device__ __forceinline__ unsigned long long warp_sum_checked(unsigned long long v, bool &carry) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_down_sync(0xffffffffu, v, o);
+    carry |= (v + y < v);
+    v += y;
+  }
+  return v;
+}
+// status[0]: error bits; status[1] bit s: accumulator slot s went past 64
+// bits (the finalize step turns that into ST_CAPACITY for the counts that
+// use slot s); slot < 0: report ST_CAPACITY directly
+__device__ __forceinline__ void acc_add_checked(unsigned long long *acc, unsigned long long v, bool carry,
+                                                unsigned int *status, int slot) {
+  const unsigned long long old = v ? atomicAdd(acc, v) : 0ull;
+  if ((carry || old + v < old) && status) {
+    if (slot >= 0) atomicOr(status + 1, 1u << slot);
+    else atomicOr(status, 128u);  // ST_CAPACITY
+  }
+}
+#endif
+
 // Out-degree classes of root vertices in the orientation. A root with
 // out-degree d < 2 roots no triangle and is never a task.
 enum { CLS_W32 = 0, CLS_WARP = 1, CLS_CTA = 2, CLS_XL = 3, NUM_CLS = 4 };

@@ -51,6 +51,7 @@ struct GuidedArgs {
   uint32_t *out;               // listing: tuples of k vertices in pattern order
   uint64_t out_cap;
   unsigned long long *counter; // listing: slots reserved so far
+  unsigned int *status;
 };
 
 __device__ __forceinline__ bool adjacent(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(kGuidedThreads) guided_kernel(GuidedArgs a) {
     }
   }
   cnt = __shfl_sync(0xffffffffu, cnt, 0);
-  if (lane == 0 && cnt && !a.out) atomicAdd(a.acc, cnt);
+  if (lane == 0 && !a.out) acc_add_checked(a.acc, cnt, false, a.status, -1);
 }
 
 }  // namespace
@@ -273,6 +274,7 @@ int gpm_launch_guided(gpm_graph *g, const GuidedPlan &plan, unsigned long long *
   a.out = out;
   a.out_cap = out_cap;
   a.counter = counter;
+  a.status = reinterpret_cast<unsigned int *>(g->work + WK_STATUS);
   GPM_LAUNCH("guided_kernel", st, guided_kernel<<<blocks, kGuidedThreads, 0, st>>>(a));
   GPM_CUDA(cudaGetLastError());
   return GPM_OK;

@@ -47,27 +47,29 @@ using gpm_dev::warp_sum;
 template <bool USE_T>
 __global__ void edge_terms_kernel(const uint64_t *__restrict__ drow, const uint32_t *__restrict__ dcol,
                                   const uint32_t *__restrict__ deg, uint32_t *__restrict__ t_edge, uint32_t n,
-                                  uint32_t root_lo, uint32_t root_hi, unsigned long long *__restrict__ acc) {
+                                  uint32_t root_lo, uint32_t root_hi, unsigned long long *__restrict__ acc,
+                                  unsigned int *__restrict__ status) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   gpm_dev::EdgeTerms s;
   for (uint64_t u = warp; u < n; u += nwarps)
     gpm_dev::edge_terms_vertex<USE_T, false>(drow, dcol, deg, t_edge, u, u >= root_lo && u < root_hi, s);
-  s.D = warp_sum(s.D);
-  s.P = warp_sum(s.P);
-  s.S = warp_sum(s.S);
-  s.W = warp_sum(s.W);
-  s.TT = warp_sum(s.TT);
-  s.T3 = warp_sum(s.T3);
+  bool cD = s.ovf, cP = s.ovf, cS = s.ovf, cW = s.ovf, cTT = s.ovf, cT3 = s.ovf;
+  s.D = warp_sum_checked(s.D, cD);
+  s.P = warp_sum_checked(s.P, cP);
+  s.S = warp_sum_checked(s.S, cS);
+  s.W = warp_sum_checked(s.W, cW);
+  s.TT = warp_sum_checked(s.TT, cTT);
+  s.T3 = warp_sum_checked(s.T3, cT3);
   if (lane == 0) {
-    atomicAdd(&acc[ACC_P], s.P);
-    atomicAdd(&acc[ACC_S], s.S);
-    atomicAdd(&acc[ACC_W], s.W);
+    acc_add_checked(&acc[ACC_P], s.P, cP, status, ACC_P);
+    acc_add_checked(&acc[ACC_S], s.S, cS, status, ACC_S);
+    acc_add_checked(&acc[ACC_W], s.W, cW, status, ACC_W);
     if (USE_T) {
-      atomicAdd(&acc[ACC_D], s.D);
-      atomicAdd(&acc[ACC_TT2], s.TT);
-      atomicAdd(&acc[ACC_T3], s.T3);
+      acc_add_checked(&acc[ACC_D], s.D, cD, status, ACC_D);
+      acc_add_checked(&acc[ACC_TT2], s.TT, cTT, status, ACC_TT2);
+      acc_add_checked(&acc[ACC_T3], s.T3, cT3, status, ACC_T3);
     }
   }
 }
@@ -172,8 +174,9 @@ __global__ void __launch_bounds__(256) c4_small_kernel(C4Args a) {
     if (v0 < a.root_lo || v0 >= a.root_hi) continue;
     acc += gpm_dev::c4_root_warp(a.rowptr, a.col, a.deg, a.edeg, v0, keys, cnt, overflow);
   }
-  acc = warp_sum(acc);
-  if (lane == 0 && acc) atomicAdd(&a.acc[ACC_C4], acc);
+  bool carry = false;
+  acc = warp_sum_checked(acc, carry);
+  if (lane == 0) acc_add_checked(&a.acc[ACC_C4], acc, carry, a.status, ACC_C4);
   if (__any_sync(0xffffffffu, overflow) && lane == 0) atomicOr(a.status, ST_CAPACITY);
 }
 
@@ -419,13 +422,19 @@ __global__ void __launch_bounds__(kHubThreads) c4_hub_kernel(const uint64_t *__r
     for (uint32_t b = 0; b < 2; ++b)
       if ((pending >> b) & 1u) mbar_wait(&s_bar[wid][b], (phase >> b) & 1u);
   }
-  acc = warp_sum(acc);
+  bool wcarry = false;
+  acc = warp_sum_checked(acc, wcarry);
+  if (wcarry && lane == 0) atomicOr(status + 1, 1u << ACC_C4);
   if (lane == 0) s_acc[wid] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long t = 0;
-    for (uint32_t i = 0; i < kW; ++i) t += s_acc[i];
-    if (t) atomicAdd(&acc_out[ACC_C4], t);
+    bool carry = false;
+    for (uint32_t i = 0; i < kW; ++i) {
+      carry |= (t + s_acc[i] < t);
+      t += s_acc[i];
+    }
+    acc_add_checked(&acc_out[ACC_C4], t, carry, status, ACC_C4);
   }
 }
 
@@ -451,8 +460,9 @@ __global__ void __launch_bounds__(kC4BucketThreads) c4_bucket_kernel(C4Args a, u
     acc += gpm_dev::c4_root_bucketed(a.rowptr, a.col, a.deg, a.edeg, v0, buf, buf + slot_words / 2, smem, s_x, &s_cnt,
                                      overflow, s_pre, s_rp);
   }
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(&a.acc[ACC_C4], acc);
+  bool carry = false;
+  acc = warp_sum_checked(acc, carry);
+  if ((threadIdx.x & 31) == 0) acc_add_checked(&a.acc[ACC_C4], acc, carry, a.status, ACC_C4);
   if (__syncthreads_or(overflow) && threadIdx.x == 0) atomicOr(a.status, ST_CAPACITY);
 }
 
@@ -510,6 +520,7 @@ struct C4RangeArgs {
   uint32_t root_lo, root_hi;
   unsigned int *queue;
   unsigned long long *acc;
+  unsigned int *status;
 };
 
 // C(a,2) + C(b,2) for the two 16-bit counters of a tally word
@@ -629,18 +640,47 @@ __global__ void __launch_bounds__(kRangeThreads, 1) c4_range_kernel(C4RangeArgs 
       __syncthreads();
     }
   }
-  acc = warp_sum(acc);
-  if (lane == 0 && acc) atomicAdd(&a.acc[ACC_C4], acc);
+  bool carry = false;
+  acc = warp_sum_checked(acc, carry);
+  if (lane == 0) acc_add_checked(&a.acc[ACC_C4], acc, carry, a.status, ACC_C4);
 }
 
 // ---------------------------------------------------------------------------
 // finalize: requested counts from the accumulators (one thread)
 // ---------------------------------------------------------------------------
+// accumulator slots a formula reads (their 64-bit overflow makes its count invalid)
+__device__ __forceinline__ uint32_t formula_slots(uint32_t f) {
+  const uint32_t inv = (1u << ACC_T) | (1u << ACC_K4) | (1u << ACC_D) | (1u << ACC_P) | (1u << ACC_S) |
+                       (1u << ACC_TT2) | (1u << ACC_C4);  // the 4-motif inversion reads all six terms
+  switch (f) {
+    case F_TRI: return 1u << ACC_T;
+    case F_K4: return 1u << ACC_K4;
+    case F_K5: return 1u << ACC_K5;
+    case F_K6: return 1u << ACC_K6;
+    case F_K7: return 1u << 0;
+    case F_K8: return 1u << 1;
+    case F_K9: return 1u << 2;
+    case F_WEDGE_NI: return 1u << ACC_W;
+    case F_WEDGE_I: return (1u << ACC_W) | (1u << ACC_T);
+    case F_STAR_NI: return 1u << ACC_S;
+    case F_PATH_NI: return (1u << ACC_P) | (1u << ACC_T);
+    case F_TT_NI: return 1u << ACC_TT2;
+    case F_C4_NI: return 1u << ACC_C4;
+    case F_D_NI: return 1u << ACC_D;
+    case F_STAR_I: case F_PATH_I: case F_TT_I: case F_C4_I: case F_D_I: case F_K4_I: return inv;
+    default: return 0u;
+  }
+}
+
 __global__ void finalize_kernel(FinalizeSpec spec, const unsigned long long *__restrict__ acc, uint64_t n, uint64_t m,
                                 unsigned long long *__restrict__ out, unsigned int *__restrict__ status) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   bool bad = false;
-  for (uint32_t i = 0; i < spec.npat; ++i) out[i] = gpm_dev::finalize_formula(spec.formula[i], acc, n, m, bad);
+  const uint32_t over = status[1];
+  for (uint32_t i = 0; i < spec.npat; ++i) {
+    out[i] = gpm_dev::finalize_formula(spec.formula[i], acc, n, m, bad);
+    bad |= (formula_slots(spec.formula[i]) & over) != 0;
+  }
   if (bad) atomicOr(status, ST_CAPACITY);
 }
 
@@ -650,10 +690,11 @@ int gpm_launch_edge_terms(gpm_graph *g, bool use_t_edge, uint32_t root_lo, uint3
                           unsigned long long *acc, cudaStream_t st) {
   const int blocks = gpm_num_sms(g->device) * 8;
   if (g->n == 0) return GPM_OK;
+  unsigned int *status = reinterpret_cast<unsigned int *>(g->work + WK_STATUS);
   if (use_t_edge)
-    GPM_LAUNCH("edge_terms_kernel", st, edge_terms_kernel<true><<<blocks, 256, 0, st>>>(g->drow, g->dcol, g->deg, g->t_edge, g->n, root_lo, root_hi, acc));
+    GPM_LAUNCH("edge_terms_kernel", st, edge_terms_kernel<true><<<blocks, 256, 0, st>>>(g->drow, g->dcol, g->deg, g->t_edge, g->n, root_lo, root_hi, acc, status));
   else
-    GPM_LAUNCH("edge_terms_kernel", st, edge_terms_kernel<false><<<blocks, 256, 0, st>>>(g->drow, g->dcol, g->deg, nullptr, g->n, root_lo, root_hi, acc));
+    GPM_LAUNCH("edge_terms_kernel", st, edge_terms_kernel<false><<<blocks, 256, 0, st>>>(g->drow, g->dcol, g->deg, nullptr, g->n, root_lo, root_hi, acc, status));
   GPM_CUDA(cudaGetLastError());
   return GPM_OK;
 }
@@ -1058,6 +1099,7 @@ static int launch_cycles4_range(gpm_graph *g, uint32_t root_lo, uint32_t root_hi
     r.root_hi = root_hi;
     r.queue = queues + 1;
     r.acc = acc;
+    r.status = reinterpret_cast<unsigned int *>(g->work + WK_STATUS);
     GPM_CUDA(cudaFuncSetAttribute(c4_range_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRangeSmemBytes));
     int per_sm = 0;
     GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c4_range_kernel, kRangeThreads, kRangeSmemBytes));

@@ -414,7 +414,28 @@ __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *_
 // triangle counts are read (and, with CLEAR_T, reset to zero afterwards).
 struct EdgeTerms {
   unsigned long long D = 0, P = 0, S = 0, W = 0, TT = 0, T3 = 0;
+  bool ovf = false;  // a term or a per-thread sum went past 64 bits
 };
+
+// C(d, 3) for d >= 3 without an intermediate past 64 bits: the factor
+// divisible by 2 and the one divisible by 3 are divided first; ovf is set
+// when C(d, 3) itself does not fit (d above about 4.8 million)
+__device__ __forceinline__ unsigned long long choose3(unsigned long long d, bool &ovf) {
+  unsigned long long x = d, y = d - 1, z = d - 2;
+  if (x % 2 == 0) x /= 2;
+  else y /= 2;
+  if (x % 3 == 0) x /= 3;
+  else if (y % 3 == 0) y /= 3;
+  else z /= 3;
+  const unsigned long long xy = x * y;  // d < 2^32: below 2^64
+  ovf |= __umul64hi(xy, z) != 0;
+  return xy * z;
+}
+
+__device__ __forceinline__ void add_checked(unsigned long long &s, unsigned long long v, bool &ovf) {
+  ovf |= (s + v < s);
+  s += v;
+}
 
 template <bool USE_T, bool CLEAR_T>
 __device__ __forceinline__ void edge_terms_vertex(const uint64_t *__restrict__ drow, const uint32_t *__restrict__ dcol,
@@ -423,17 +444,18 @@ __device__ __forceinline__ void edge_terms_vertex(const uint64_t *__restrict__ d
   const uint32_t lane = threadIdx.x & 31;
   const unsigned long long du = deg[u];
   if (lane == 0) {
-    if (du >= 3) s.S += du * (du - 1) * (du - 2) / 6;
-    if (du >= 2) s.W += du * (du - 1) / 2;
+    if (du >= 3) add_checked(s.S, choose3(du, s.ovf), s.ovf);
+    if (du >= 2) add_checked(s.W, du * (du - 1) / 2, s.ovf);
   }
   for (uint64_t e = drow[u] + lane; e < drow[u + 1]; e += 32) {
     const unsigned long long dv = deg[dcol[e]];
-    s.P += (du - 1) * (dv - 1);
+    add_checked(s.P, (du - 1) * (dv - 1), s.ovf);
     if (USE_T) {
       const unsigned long long t = CLEAR_T ? __ldcg(t_edge + e) : t_edge[e];
       if (t) {
-        if (in_range) s.D += t * (t - 1) / 2;
-        s.TT += t * (du + dv - 4);
+        if (in_range) add_checked(s.D, t * (t - 1) / 2, s.ovf);
+        s.ovf |= __umul64hi(t, du + dv - 4) != 0;
+        add_checked(s.TT, t * (du + dv - 4), s.ovf);
         s.T3 += t;
         if (CLEAR_T) t_edge[e] = 0;
       }

@@ -689,3 +689,25 @@ def test_core_orientation_fullsize_rmat21(gpm):
     G.set_orientation("degree")
     assert gpm.count(G, [gpm.Pattern.clique(4), gpm.Pattern.clique(5)]) == got
     G.close()
+
+
+def test_counts_past_64_bits_are_reported(gpm):
+    # K_{5, 3,000,000}: five hubs of degree 3,000,000. Each C(d, 3) fits in 64
+    # bits (d(d-1)(d-2) does not), but the edge-induced 3-star count
+    # 5 C(3e6, 3) + 3e6 C(5, 3) ~ 2.25e19 does not: the count reports
+    # GPM_E_OVERFLOW instead of a wrapped value; counts below 2^64 on the same
+    # graph stay exact (closed forms)
+    import math
+    a, b = 5, 3_000_000
+    e = np.stack([np.repeat(np.arange(a), b), a + np.tile(np.arange(b), a)], 1)
+    g = gg.from_edges(a + b, e, name="K_5_3M")
+    G = gpm.Graph.from_host(g)
+    star = gpm.Pattern.spec(O.pattern(4, [(0, 1), (0, 2), (0, 3)]), induced=False)
+    with pytest.raises(gpm.GpmError) as err:
+        gpm.count(G, [star])
+    assert err.value.name == "OVERFLOW"
+    C4 = gpm.Pattern.spec(O.CYCLE4, induced=False)
+    wedge = gpm.Pattern.spec(O.pattern(3, [(0, 1), (1, 2)]), induced=False)
+    assert gpm.count(G, [C4, wedge, gpm.Pattern.clique(3)]) == [
+        math.comb(a, 2) * math.comb(b, 2), a * math.comb(b, 2) + b * math.comb(a, 2), 0]
+    G.close()
