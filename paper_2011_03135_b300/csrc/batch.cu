@@ -113,10 +113,12 @@ struct gpm_batch {
   // queries, measured at creation), with their patterns and status words
   std::vector<uint8_t> direct;
   std::vector<gpm_pattern_t> kind_pats[8];
-  unsigned int *d_dstatus = nullptr;
+  unsigned int *d_dstatus = nullptr;  // one word per query (the direct ones use the first ndirect)
   unsigned int *h_dstatus = nullptr;
   uint32_t ndirect = 0;
   double tuned_ms = 0.0;
+  std::vector<float> qms;     // plain-path device time of every query (ms), measured at creation
+  float direct_ms = 0.0f;     // threshold in use
 };
 
 namespace {
@@ -272,16 +274,15 @@ int replay(gpm_batch *b, float *ms) {
 }
 
 // Heavy queries run their plain count path inside the captured graph: a
-// query whose plain path takes at least batch_direct_us on the device (timed
-// here; a first run also makes every lazily sized buffer) is marked direct,
-// together with every other query on the same graph. Small queries become
-// items of the persistent kernel, where they overlap instead of paying a
-// launch sequence each.
-int choose_direct(gpm_batch *b) {
-  const uint32_t direct_us = gpm_tune().batch_direct_us;
-  const float kDirectMs = direct_us == 0xffffffffu ? 3.4e38f : direct_us * 1e-3f;
+// query whose plain path takes at least the direct threshold on the device is
+// marked direct, together with every other query on the same graph (they
+// share its per-arc buffer). Small queries become items of the persistent
+// kernel, where they overlap instead of paying a launch sequence each. The
+// plain-path time of every query is measured once, when the batch is created
+// (a first run also sizes every lazily grown buffer); the autotuner then
+// tries several thresholds on these times.
+int measure_plain(gpm_batch *b) {
   const uint32_t nq = (uint32_t)b->queries.size();
-  b->direct.assign(nq, 0);
   for (uint32_t i = 0; i < nq; ++i) {
     const uint32_t kind = b->qs[i].kind;
     std::vector<gpm_pattern_t> &v = b->kind_pats[kind];
@@ -300,7 +301,7 @@ int choose_direct(gpm_batch *b) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   GPM_CUDA(cudaEventCreate(&e0));
   GPM_CUDA(cudaEventCreate(&e1));
-  std::vector<gpm_graph *> heavy_graphs;
+  b->qms.assign(nq, 0.0f);
   int rc = GPM_OK;
   for (uint32_t i = 0; i < nq && rc == GPM_OK; ++i) {
     gpm_graph *g = b->queries[i].graph;
@@ -313,24 +314,34 @@ int choose_direct(gpm_batch *b) {
       if (rc == GPM_OK && (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
                            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
         rc = gpm_fail(GPM_E_DEVICE, "timing a batched query's plain path");
-      if (rep == 0 && ms < 0.25f * kDirectMs) break;  // clearly small: no second run needed
+      if (rep == 0 && ms < 0.05f) break;  // clearly small: no second run needed
     }
-    if (rc == GPM_OK && ms >= kDirectMs) heavy_graphs.push_back(g);
+    b->qms[i] = ms;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
+  if (cudaMalloc(&b->d_dstatus, sizeof(unsigned int) * nq) != cudaSuccess ||
+      cudaMallocHost(&b->h_dstatus, sizeof(unsigned int) * nq) != cudaSuccess) {
+    cudaGetLastError();
+    return gpm_fail(GPM_E_OOM, "batch status allocation failed");
+  }
+  return GPM_OK;
+}
+
+// Direct queries for threshold `ms` (3.4e38: none); resets what the item
+// queries expect at the start of a run and drops the captured graph.
+int set_direct(gpm_batch *b, float ms) {
+  const uint32_t nq = (uint32_t)b->queries.size();
+  std::vector<gpm_graph *> heavy_graphs;
+  for (uint32_t i = 0; i < nq; ++i)
+    if (b->qms[i] >= ms) heavy_graphs.push_back(b->queries[i].graph);
+  b->direct.assign(nq, 0);
   for (uint32_t i = 0; i < nq; ++i)
     b->direct[i] = std::find(heavy_graphs.begin(), heavy_graphs.end(), b->queries[i].graph) != heavy_graphs.end();
   b->ndirect = (uint32_t)std::count(b->direct.begin(), b->direct.end(), (uint8_t)1);
-  if (b->ndirect) {
-    if (cudaMalloc(&b->d_dstatus, sizeof(unsigned int) * b->ndirect) != cudaSuccess ||
-        cudaMallocHost(&b->h_dstatus, sizeof(unsigned int) * b->ndirect) != cudaSuccess) {
-      cudaGetLastError();
-      return gpm_fail(GPM_E_OOM, "batch status allocation failed");
-    }
-  }
-  // the timing runs left per-arc triangle counts in the graphs' buffers, which
+  b->direct_ms = ms;
+  // plain runs leave per-arc triangle counts in the graphs' buffers, which
   // item queries expect zero at the start of a run; and counts in the output slots
   for (uint32_t i = 0; i < nq; ++i)
     if (!b->direct[i] && b->qs[i].t_edge)
@@ -340,25 +351,38 @@ int choose_direct(gpm_batch *b) {
   return GPM_OK;
 }
 
+// Autotuner: which queries run their plain path (threshold 1/4, 1 and 4
+// times batch_direct_us on their measured plain time) x the item schedule
+// (roots per warp item, vertices per EDGE item); each candidate is captured
+// and timed by one replay after a warm one, the fastest is kept.
 int autotune(gpm_batch *b) {
   struct Cand {
     uint32_t roots, verts;
   };
   const Cand cands[] = {{64, 8192}, {16, 4096}, {256, 32768}};
-  float best = 1e30f;
+  const uint32_t direct_us = gpm_tune().batch_direct_us;
+  std::vector<float> thresholds;
+  if (direct_us == 0xffffffffu) thresholds = {3.4e38f};
+  else thresholds = {0.25e-3f * direct_us, 1e-3f * direct_us, 4e-3f * direct_us};
+  float best = 1e30f, best_thr = thresholds[0];
   Cand bestc = cands[0];
-  for (const Cand &c : cands) {
-    b->roots_per_item = c.roots;
-    b->verts_per_item = c.verts;
-    GPM_TRY(upload_schedule(b));
-    float ms = 0.f;
-    GPM_TRY(replay(b, nullptr));  // warm
-    GPM_TRY(replay(b, &ms));
-    if (ms < best) {
-      best = ms;
-      bestc = c;
+  for (float thr : thresholds) {
+    GPM_TRY(set_direct(b, thr));
+    for (const Cand &c : cands) {
+      b->roots_per_item = c.roots;
+      b->verts_per_item = c.verts;
+      GPM_TRY(upload_schedule(b));
+      float ms = 0.f;
+      GPM_TRY(replay(b, nullptr));  // warm
+      GPM_TRY(replay(b, &ms));
+      if (ms < best) {
+        best = ms;
+        bestc = c;
+        best_thr = thr;
+      }
     }
   }
+  GPM_TRY(set_direct(b, best_thr));
   b->roots_per_item = bestc.roots;
   b->verts_per_item = bestc.verts;
   b->tuned_ms = best;
@@ -485,7 +509,12 @@ int gpm_batch_create(const gpm_query_t *queries, uint32_t nq, gpm_batch_t *out) 
     }
     cudaMemset(b->tally_pool, 0, sizeof(uint32_t) * b->tally_slot_words * b->grid);
   }
-  rc = choose_direct(b);
+  rc = measure_plain(b);
+  if (rc) return fail(rc);
+  {
+    const uint32_t direct_us = gpm_tune().batch_direct_us;
+    rc = set_direct(b, direct_us == 0xffffffffu ? 3.4e38f : 1e-3f * direct_us);
+  }
   if (rc) return fail(rc);
   rc = upload_schedule(b);
   if (rc) return fail(rc);

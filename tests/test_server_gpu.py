@@ -1,5 +1,6 @@
 """Served form: requests submitted while others run (continuous batching) give
-the same exact counts as each request alone and as the plain count path."""
+the same exact counts as each request alone, as the plain count path and as
+the oracle."""
 import time
 
 import numpy as np
@@ -46,9 +47,14 @@ def test_server_mix_equals_alone_and_plain(gpm):
     Gs = [gpm.Graph.from_host(g) for g in graphs]
     kinds = [gpm.QUERY_TC, gpm.QUERY_CLIQUE4, gpm.QUERY_CLIQUE5, gpm.QUERY_MOTIF4, gpm.QUERY_MOTIF3]
     plain = {(i, k): _plain(gpm, G, k) for i, G in enumerate(Gs) for k in kinds}
+    # every (graph, kind) against the oracle, so that alone, in the mix and
+    # plain are all compared with it
     for i, g in enumerate(graphs):
-        if g.n <= 30:
-            assert plain[(i, gpm.QUERY_MOTIF4)] == O.motifs(g, 4)
+        want = {gpm.QUERY_TC: [O.triangles(g)], gpm.QUERY_CLIQUE4: [O.cliques(g, 4)],
+                gpm.QUERY_CLIQUE5: [O.cliques(g, 5)], gpm.QUERY_MOTIF4: O.motifs(g, 4),
+                gpm.QUERY_MOTIF3: O.motifs(g, 3)}
+        for k in kinds:
+            assert plain[(i, k)] == want[k], (g.name, k)
     S = gpm.Server(Gs, max_inflight=32)
     # alone: one request at a time
     alone = {}
@@ -76,6 +82,7 @@ def test_server_admission_waits_for_memory(gpm):
     g = gg.rmat(12, 16.0, seed=105)
     G = gpm.Graph.from_host(g)
     want = _plain(gpm, G, gpm.QUERY_MOTIF4)
+    assert want == O.motifs(g, 4)
     S = gpm.Server([G], max_inflight=4, arena_bytes=4 * (g.m + 64))
     for tag in range(12):
         S.submit(0, gpm.QUERY_MOTIF4, tag)
@@ -108,6 +115,7 @@ def test_server_small_requests_overtake_blocked_large_ones(gpm):
     Gb, Gs = gpm.Graph.from_host(big), gpm.Graph.from_host(small)
     want_big = _plain(gpm, Gb, gpm.QUERY_MOTIF4)
     want_small = _plain(gpm, Gs, gpm.QUERY_TC)
+    assert want_big == O.motifs(big, 4) and want_small == [O.triangles(small)]
     S = gpm.Server([Gb, Gs], max_inflight=8, arena_bytes=4 * (big.m + 64))
     for tag in range(3):
         S.submit(0, gpm.QUERY_MOTIF4, tag)
