@@ -18,7 +18,7 @@ Under torchrun (N > 1) every rank counts its own replica of the workload
 the step time. `--impl reference` times the CPU oracle (single-threaded C) on
 a bounded root sample of the same workload.
 
-Other legs (one GPU, one JSON line each): `--workload tc`, `sl`, `motif5`
+Other legs (one GPU, one JSON line each): `--workload tc`, `sl`, `motif5`, `guided` (general patterns by the pattern-guided search, Erdos-Renyi 1M)
 (the 21 five-vertex motifs, Erdos-Renyi 1M), `clique6` (6-cliques, R-MAT
 20), `clique789` (7-, 8-, 9-cliques, Chung-Lu 1M), `batched` and `served`
 (many small queries); `--orientation core` runs the headline leg under the
@@ -173,6 +173,13 @@ NCU_COUNTERS = {
     "motif5-er1m": {
         "enum_kernel_k5": {"digest": "bb0dcc50081af389", "inst_per_launch": 226039588066,
                            "dram_bytes_per_launch": 45073920 + 975872, "ncu_ms": 267.053},
+    },
+    # three launches per step (6-path, 5-star, 6-cycle), summed;
+    # profiles/guided_er1m_counters.md; digest of guided.cu
+    "guided-er1m": {
+        "guided_kernel": {"digest": "90803c4b5ac813dc",
+                          "inst_per_step": 2031750401033 + 116953504346 + 246503983250,
+                          "dram_bytes_per_step": 49243136 + 6882816 + 48381184 + 51968 + 48180224 + 465920},
     },
     # three launches per step (k = 7, 8, 9), summed
     "clique789-cl1m": {
@@ -792,6 +799,87 @@ def run_motif5(args):
     return line
 
 
+GUIDED_WORKLOAD = ("pattern-guided search (matching order, symmetry-breaking bounds, degree filter): edge-induced "
+                   "6-vertex path, 5-star and 6-cycle on Erdos-Renyi 1,048,576 vertices, mean degree 8, seed 7")
+GUIDED_PATTERNS = {"6-path": [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5)],
+                   "5-star": [(0, 1), (0, 2), (0, 3), (0, 4), (0, 5)],
+                   "6-cycle": [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (5, 0)]}
+
+
+def guided_digest():
+    import hashlib
+    return hashlib.sha256(open(os.path.join(ROOT, "paper_2011_03135_b300", "csrc", "guided.cu"), "rb").read()
+                          ).hexdigest()[:16]
+
+
+def run_guided(args):
+    """Counts of general patterns by the pattern-guided search, one search per pattern per step."""
+    import torch
+    from paper_2011_03135_b300 import gpm
+    from paper_2011_03135_b300 import graphgen as gg
+    g = gg.workload_motif5_er1m()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    G = gpm.Graph(torch.from_numpy(g.rowptr.view(np.int64)).to(dev), torch.from_numpy(g.col.view(np.int32)).to(dev),
+                  g.n, validate=True, stream=stream)
+
+    def pat(es):
+        k = max(max(e) for e in es) + 1
+        a = np.zeros((k, k), np.uint8)
+        for u, v in es:
+            a[u, v] = a[v, u] = 1
+        return gpm.Pattern.spec(a, induced=False)
+
+    P = [pat(es) for es in GUIDED_PATTERNS.values()]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    def step():
+        G.reset()
+        return gpm.count_guided(G, P, stream=stream)
+
+    counts = None
+    for _ in range(max(args.warmup, 3)):
+        counts = step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = gpm.kernel_launches()
+    gpm.profile_reset()
+    gpm.profile_enable(True)
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev[i][0].record(stream)
+            assert step() == counts
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    gpm.profile_enable(False)
+    launches = gpm.kernel_launches() - launches0
+    prof = gpm.profile_report()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+    clk_now = clk.summary()
+    ipeak = issue_peak(clk_now["sm_mhz"] or 2032.0)
+    kms = prof.get("guided_kernel", {"ms": 0.0})["ms"] / args.steps
+    roof = {"bound": "alu", "kernel": "guided_kernel", "unit": "G warp-instructions/s", "peak": ipeak,
+            "peak_source": "148 SMs x 4 schedulers x 1 issue/clk x median SM clock under load",
+            "achieved": None, "frac": None, "traffic": None, "kernel_digest": guided_digest()}
+    cnt = NCU_COUNTERS.get("guided-er1m", {}).get("guided_kernel")
+    if cnt and cnt.get("digest") == guided_digest() and kms > 0:
+        ach = cnt["inst_per_step"] / (kms / 1000.0) / 1e9
+        roof.update(achieved=ach, frac=ach / ipeak, traffic=cnt.get("dram_bytes_per_step"))
+    total = sum(counts)
+    line = {"workload": GUIDED_WORKLOAD, "metric": "pattern embeddings (distinct subgraphs) counted per second",
+            "value": total / (ms / 1000.0), "unit": "subgraphs/s", "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": ms, "counts": dict(zip(GUIDED_PATTERNS, counts)), "dtype": "u64", "data": "synthetic",
+            "config": {"l2": "flushed between steps (512 MB write)"}, "gpu_launches": launches, "roofline": roof,
+            "clocks": clk_now,
+            "kernels": {k: {"launches": v["launches"], "ms_per_launch": v["ms"] / max(v["launches"], 1)}
+                        for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}}
+    G.close()
+    return line
+
+
 TC_WORKLOAD = "triangle counting, R-MAT scale 14 (16,384 vertices), edge factor 16, (0.57,0.19,0.19,0.05), seed 1"
 
 
@@ -1018,6 +1106,7 @@ CASES = {
     "sl-chunglu2m": ("chunglu2m", "sl"),
     "sl-chunglu4m": ("chunglu4m", "sl"),
     "motif5-er1m": ("er1m", "motif5"),
+    "guided-er1m": ("er1m", "guided"),
 }
 
 
@@ -1059,6 +1148,15 @@ def _case_patterns(gpm, name):
         return gpm.Pattern.motifs(4)
     if name == "motif5":
         return gpm.Pattern.motifs(5)
+    if name == "guided":
+        out = []
+        for es in GUIDED_PATTERNS.values():
+            k = max(max(e) for e in es) + 1
+            a = np.zeros((k, k), np.uint8)
+            for u, v in es:
+                a[u, v] = a[v, u] = 1
+            out.append(gpm.Pattern.spec(a, induced=False))
+        return out
     if name == "sl":
         d = np.zeros((4, 4), np.uint8)
         for a, b in [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3)]:
@@ -1080,7 +1178,12 @@ def run_case(args):
     out = None
     for _ in range(args.reps):
         G.reset()
-        out = [gpm.count_cliques(G, k) for k in pats] if isinstance(pats[0], int) else gpm.count(G, pats)
+        if isinstance(pats[0], int):
+            out = [gpm.count_cliques(G, k) for k in pats]
+        elif pname == "guided":
+            out = gpm.count_guided(G, pats)
+        else:
+            out = gpm.count(G, pats)
     torch.cuda.synchronize()
     print(json.dumps({"case": args.case, "n": g.n, "m": g.m, "counts": out}))
     G.close()
@@ -1097,7 +1200,8 @@ def main():
                     help="order of the orientation for the k-clique leg (core: k-core peel at prepare time)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-legs", action="store_true", help="headline leg only (no sl / tc legs in its line)")
-    ap.add_argument("--workload", choices=["cliques", "clique6", "clique789", "batched", "served", "sl", "tc", "motif5"],
+    ap.add_argument("--workload", choices=["cliques", "clique6", "clique789", "batched", "served", "sl", "tc", "motif5",
+                                           "guided"],
                     default="cliques")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -1128,6 +1232,9 @@ def main():
         return 0
     if args.workload == "motif5":
         print(json.dumps(run_motif5(args)), flush=True)
+        return 0
+    if args.workload == "guided":
+        print(json.dumps(run_guided(args)), flush=True)
         return 0
     if args.workload == "clique6":
         from paper_2011_03135_b300 import graphgen as gg

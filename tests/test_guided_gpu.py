@@ -143,3 +143,23 @@ def test_guided_rejects(gpm):
     with pytest.raises(gpm.GpmError):  # root ranges are not defined for the guided search
         gpm.count_roots(G, [gpm.Pattern.spec(_pat(PATTERNS[6]), induced=False)], 0, 3)
     G.close()
+
+
+def test_guided_fullsize_er1m(gpm):
+    # the guided bench workload (Erdos-Renyi 2^20 vertices, mean degree 8):
+    # the 5-vertex path through the guided search equals the enumeration's
+    # count (an independent path, pinned to the oracle on sampled root ranges
+    # of this graph); the 6-cycle count does not depend on the pattern's
+    # numbering (another matching order and other symmetry-breaking bounds)
+    g = gg.workload_motif5_er1m()
+    G = gpm.Graph.from_host(g)
+    p5 = gpm.Pattern.spec(_pat(PATTERNS[0]), induced=False)
+    want = gpm.count_enumerate(G, [p5])
+    assert gpm.count_guided(G, [p5]) == want and want[0] > 10 ** 9
+    c6a = gpm.Pattern.spec(_pat([(0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (5, 0)]), induced=False)
+    c6b = gpm.Pattern.spec(_pat([(3, 0), (0, 5), (5, 1), (1, 4), (4, 2), (2, 3)]), induced=False)
+    assert c6a.info()["matching_order"] != c6b.info()["matching_order"] or \
+        c6a.info()["sb_pairs"] != c6b.info()["sb_pairs"]
+    a, b = gpm.count_guided(G, [c6a, c6b])
+    assert a == b and a > 0
+    G.close()
