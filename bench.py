@@ -205,7 +205,7 @@ def kernel_digest():
 def c4_digest():
     import hashlib
     h = hashlib.sha256()
-    for f in ("motif.cu", "motif_device.cuh"):
+    for f in ("motif.cu", "motif_device.cuh", "c4_pull.cu"):
         h.update(open(os.path.join(ROOT, "paper_2011_03135_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -527,7 +527,7 @@ def run_sl(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(device=dev)
     c4opts = {k: v for k, v in dict(c4_range_bound=args.c4_range_bound, c4_range_width=args.c4_range_width,
-                                    c4_hub_bound=args.c4_hub_bound).items() if v}
+                                    c4_hub_bound=args.c4_hub_bound, c4_pull_bound=args.c4_pull_bound).items() if v}
     if c4opts:
         gpm.set_options(**c4opts)
     G = gpm.Graph(torch.from_numpy(g.rowptr.view(np.int64)).to(dev), torch.from_numpy(g.col.view(np.int32)).to(dev),
@@ -1211,6 +1211,7 @@ def main():
     ap.add_argument("--c4-range-bound", type=int, default=0, help="4-cycle tuning for the sl leg (0: library default)")
     ap.add_argument("--c4-range-width", type=int, default=0)
     ap.add_argument("--c4-hub-bound", type=int, default=0)
+    ap.add_argument("--c4-pull-bound", type=int, default=0)
     ap.add_argument("--case", choices=sorted(CASES), help="run a named workload for a profiler and exit")
     ap.add_argument("--reps", type=int, default=1)
     args = ap.parse_args()

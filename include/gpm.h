@@ -481,19 +481,23 @@ typedef struct {
   uint32_t c4_hub_bound;    /* 4-cycle roots whose wedge bound (sum of the degrees of their neighbours
                                before them) exceeds this are counted by the whole GPU a few at a time;
                                range [513, 1048576], default 1048576. The batched and served forms use it
-                               always, the plain count path only with c4_range_bound = 0xffffffff */
+                               always, the plain count path only with c4_range_bound and c4_pull_bound
+                               both 0xffffffff */
   uint32_t batch_direct_us; /* batched form: a query whose plain count path takes at least this many
                                microseconds on the device (timed when the batch is created) runs that
                                path inside the captured graph instead of as items; default 1000,
                                0xffffffff = never */
-  uint32_t c4_range_bound;  /* plain count path: 4-cycle roots whose wedge bound exceeds this are counted
-                               range by range over vertex ids with a dense shared-memory tally (graphs of
-                               maximum degree <= 65535 and fewer than 2^32 adjacency entries); roots
-                               between 512 and this bound are bucketed; range [512, 0xfffffffe], default
-                               1048576; 0xffffffff = never (then the bucketed class goes up to
-                               c4_hub_bound and the hub class takes the larger roots) */
+  uint32_t c4_range_bound;  /* plain count path (graphs of maximum degree <= 65535 and fewer than 2^32
+                               adjacency entries): 4-cycle roots whose wedge bound exceeds this, up to
+                               c4_pull_bound, are counted range by range over vertex ids with a dense
+                               shared-memory tally; roots between 512 and the smaller of the two bounds
+                               are bucketed; range [512, 0xfffffffe], default 1048576; 0xffffffff = never */
   uint32_t c4_range_width;  /* vertex ids per tally range of that path: even, in [64, 98304], default 98304 */
-  uint32_t reserved[1];
+  uint32_t c4_pull_bound;   /* plain count path: 4-cycle roots whose wedge bound exceeds this are counted
+                               128 at a time by one pass over every adjacency list with bit-sliced
+                               counters; range [512, 0xfffffffe], default 262144; 0xffffffff = never.
+                               With both bounds 0xffffffff the bucketed class goes up to c4_hub_bound and
+                               the hub class takes the larger roots */
 } gpm_options_t;
 
 int gpm_set_options(const gpm_options_t *opt);

@@ -44,7 +44,8 @@ void free_graph(gpm_graph *g) {
                   g->work,   g->t_edge, g->xl_pool, g->tally_pool, g->list_scratch, g->c4_tasks, g->c4_bucket_buf,
                   g->prep_outdeg, g->prep_tiles, g->prep_keys, g->edeg, g->c4_hub_units, g->c4_hub_tally,
                   g->c4_hub_touched, g->c4_hub_ctr, g->core, g->core_work, g->c4p_tasks, g->c4p_bval,
-                  g->c4p_items, g->c4_roff};
+                  g->c4p_items, g->c4_roff, g->c4q_ord, g->c4q_M, g->c4q_roots, g->c4q_queue,
+                  g->c4q_prow, g->c4q_pcol, g->c4q_chunks, g->c4q_cntb};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete g;
@@ -304,6 +305,10 @@ int gpm_set_options(const gpm_options_t *opt) {
       return gpm_fail(GPM_E_INVALID_ARG, "c4_range_width must be even and in [64, 98304]");
     t.c4_range_width = opt->c4_range_width;
   }
+  if (opt->c4_pull_bound) {
+    if (opt->c4_pull_bound < 512) return gpm_fail(GPM_E_INVALID_ARG, "c4_pull_bound must be >= 512");
+    t.c4_pull_bound = opt->c4_pull_bound;
+  }
   return GPM_OK;
 }
 
@@ -317,6 +322,7 @@ int gpm_get_options(gpm_options_t *opt) {
   opt->batch_direct_us = gpm_tune().batch_direct_us;
   opt->c4_range_bound = gpm_tune().c4_range_bound;
   opt->c4_range_width = gpm_tune().c4_range_width;
+  opt->c4_pull_bound = gpm_tune().c4_pull_bound;
   return GPM_OK;
 }
 

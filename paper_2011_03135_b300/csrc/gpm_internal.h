@@ -86,6 +86,10 @@ struct gpm_tuning {
   // bucketed and hub classes above take them)
   uint32_t c4_range_bound = 1048576;
   uint32_t c4_range_width = 98304;  // vertex ids per tally range (even, <= 98304)
+  // plain count path: roots whose wedge bound exceeds this (and c4_range_bound)
+  // are counted 128 at a time by a pull over every vertex with bit-sliced
+  // counters (0xffffffff: never)
+  uint32_t c4_pull_bound = 262144;
 };
 gpm_tuning &gpm_tune();
 
@@ -176,13 +180,33 @@ struct gpm_graph {
   uint32_t *c4p_bval = nullptr;
   uint32_t c4p_begin[4] = {0, 0, 0, 0};
   uint32_t c4p_bucket_maxb = 0;
-  uint32_t c4p_bound = 0, c4p_width = 0;
+  uint32_t c4p_bound = 0, c4p_pull = 0, c4p_width = 0;
   bool c4p_ready = false;
   uint32_t *c4p_items = nullptr;  // uint4 per item
   size_t c4p_items_cap = 0;
   uint32_t c4p_nitems = 0;
   uint32_t *c4_roff = nullptr;
   uint32_t c4_roff_width = 0, c4_nr1 = 0;
+  // plain count path, pull class (roots above c4_pull_bound, 128 per pass):
+  // vertices by decreasing degree (c4q_ord; the first c4q_nbig have degree
+  // > 1024, the first c4q_nact degree >= 2) and their lists in that order,
+  // membership bits of a pass's roots
+  // (c4q_M, 4 words per vertex, zero between passes), the pull roots by
+  // decreasing wedge bound (device c4q_roots, host c4q_hroots), one queue
+  // counter per pass
+  uint32_t *c4q_ord = nullptr;
+  uint32_t c4q_nbig = 0, c4q_nact = 0;
+  uint32_t *c4q_prow = nullptr;  // the lists in the order c4q_ord: c4q_pcol[prow[i] .. prow[i + 1])
+  uint32_t *c4q_pcol = nullptr;
+  uint32_t *c4q_chunks = nullptr;  // {position, first entry} of each 1024-entry chunk of the first c4q_nbig
+  uint32_t c4q_nchunks = 0;
+  uint32_t *c4q_cntb = nullptr;  // 128 counters per vertex of degree > 1024 (zero between passes)
+  uint32_t *c4q_M = nullptr;
+  uint32_t *c4q_roots = nullptr;
+  size_t c4q_roots_cap = 0;
+  std::vector<uint32_t> c4q_hroots;
+  unsigned int *c4q_queue = nullptr;
+  size_t c4q_queue_words = 0;
   // pattern-oblivious enumeration: class of every connectivity code (k = 3..5),
   // per-warp candidate lists, class counts (32 words)
   uint8_t *enum_cls[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -274,6 +298,10 @@ int gpm_c4_hub_enqueue(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigne
 // The first call per graph builds the root classes with host synchronisations;
 // gpm_c4_plain_ready tells whether they exist (later calls only enqueue).
 bool gpm_c4_plain_ready(const gpm_graph *g);
+// pull class of the plain path: roots (by decreasing wedge bound) set up once,
+// then every pass with a root in [root_lo, root_hi) enqueued
+int gpm_c4_pull_prepare(gpm_graph *g, const std::vector<uint32_t> &roots, cudaStream_t st);
+int gpm_launch_c4_pull(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigned long long *acc, cudaStream_t st);
 int gpm_launch_cycles4(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigned long long *acc, cudaStream_t st);
 
 // Per-arc and per-vertex local-count terms (ACC_D .. ACC_T3). With

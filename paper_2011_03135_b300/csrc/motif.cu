@@ -910,7 +910,9 @@ int gpm_build_c4_tasks(gpm_graph *g, cudaStream_t st) { return ensure_c4_tasks(g
 // the range tallies use 16-bit counters (a count is at most the root's
 // degree) and 32-bit positions in col
 static bool c4_use_range(const gpm_graph *g) {
-  return gpm_tune().c4_range_bound != 0xffffffffu && g->max_degree <= 0xffffu && g->nnz < (1ull << 32);
+  const gpm_tuning &t = gpm_tune();
+  return (t.c4_range_bound != 0xffffffffu || t.c4_pull_bound != 0xffffffffu) && g->max_degree <= 0xffffu &&
+         g->nnz < (1ull << 32);
 }
 
 // range offsets of every list for ranges of `width` ids, built once per graph and width
@@ -935,17 +937,19 @@ static int ensure_c4_roff(gpm_graph *g, uint32_t width, cudaStream_t st) {
   return GPM_OK;
 }
 
-// Root classes of the plain path (small, bucketed, range) and the range items:
-// one item per (root, range), roots in order of decreasing wedge bound and the
-// ranges of a root consecutive, so that the items running at the same time
-// belong to a few roots whose neighbour lists stay in L2 while every range of
-// those roots is tallied.
+// Root classes of the plain path by wedge bound B: small (B <= 512),
+// bucketed, range (c4_range_bound < B <= c4_pull_bound) and pull (B >
+// c4_pull_bound). Range items: one per (root, range), roots in order of
+// decreasing wedge bound and the ranges of a root consecutive, so that the
+// items running at the same time belong to a few roots whose neighbour lists
+// stay in L2 while every range of those roots is tallied. Pull roots: in
+// order of decreasing wedge bound, 128 per pass.
 static int ensure_c4_plain(gpm_graph *g, cudaStream_t st) {
-  const uint32_t bound = std::max<uint32_t>(gpm_tune().c4_range_bound, kSmallBound);
+  const uint32_t pull = std::max<uint32_t>(gpm_tune().c4_pull_bound, kSmallBound);
+  const uint32_t bound = std::min<uint32_t>(std::max<uint32_t>(gpm_tune().c4_range_bound, kSmallBound), pull);
   const uint32_t width = gpm_tune().c4_range_width;
-  if (g->c4p_ready && g->c4p_bound == bound && g->c4p_width == width) return GPM_OK;
+  if (g->c4p_ready && g->c4p_bound == bound && g->c4p_pull == pull && g->c4p_width == width) return GPM_OK;
   GPM_TRY(ensure_edeg(g, st));
-  GPM_TRY(ensure_c4_roff(g, width, st));
   const size_t nw = std::max<uint32_t>(g->n, 1);
   if (!g->c4p_tasks) GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4p_tasks, sizeof(uint32_t) * nw));
   if (!g->c4p_bval) GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4p_bval, sizeof(uint32_t) * nw));
@@ -987,10 +991,19 @@ static int ensure_c4_plain(gpm_graph *g, cudaStream_t st) {
   std::sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) {
     return bv[x] != bv[y] ? bv[x] > bv[y] : roots[x] < roots[y];
   });
-  const uint32_t nr = g->c4_nr1 - 1;
-  std::vector<uint32_t> items;
-  items.reserve(4 * (size_t)nbig * nr);
+  std::vector<uint32_t> pull_roots;
+  uint32_t nrange = 0;
   for (uint32_t i : ord) {
+    if (bv[i] > pull) pull_roots.push_back(roots[i]);
+    else ++nrange;
+  }
+  GPM_TRY(gpm_c4_pull_prepare(g, pull_roots, st));
+  if (nrange) GPM_TRY(ensure_c4_roff(g, width, st));
+  const uint32_t nr = nrange ? g->c4_nr1 - 1 : 0;
+  std::vector<uint32_t> items;
+  items.reserve(4 * (size_t)nrange * nr);
+  for (uint32_t i : ord) {
+    if (bv[i] > pull) continue;
     for (uint32_t r = 0; r < nr; ++r) {
       items.push_back(roots[i]);
       items.push_back(r);
@@ -1015,6 +1028,7 @@ static int ensure_c4_plain(gpm_graph *g, cudaStream_t st) {
   GPM_CUDA(cudaStreamSynchronize(st));
   g->c4p_ready = true;
   g->c4p_bound = bound;
+  g->c4p_pull = pull;
   g->c4p_width = width;
   return GPM_OK;
 }
@@ -1084,6 +1098,7 @@ static int launch_cycles4_range(gpm_graph *g, uint32_t root_lo, uint32_t root_hi
   a.acc = acc;
   a.status = reinterpret_cast<unsigned int *>(g->work + WK_STATUS);
   a.n = g->n;
+  GPM_TRY(gpm_launch_c4_pull(g, root_lo, root_hi, acc, st));
   if (g->c4p_nitems) {
     C4RangeArgs r{};
     r.rowptr = g->rowptr;

@@ -78,7 +78,7 @@ class Options(ctypes.Structure):
     _fields_ = [("warp_max_degree", ctypes.c_uint32), ("cta_max_degree", ctypes.c_uint32),
                 ("blocks_per_sm", ctypes.c_uint32), ("c4_hub_bound", ctypes.c_uint32),
                 ("batch_direct_us", ctypes.c_uint32), ("c4_range_bound", ctypes.c_uint32),
-                ("c4_range_width", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1)]
+                ("c4_range_width", ctypes.c_uint32), ("c4_pull_bound", ctypes.c_uint32)]
 
 
 _vp, _u32, _u64, _i = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
@@ -189,9 +189,9 @@ def profile_report() -> dict:
 
 
 def set_options(warp_max_degree: int = 0, cta_max_degree: int = 0, blocks_per_sm: int = 0, c4_hub_bound: int = 0,
-                batch_direct_us: int = 0, c4_range_bound: int = 0, c4_range_width: int = 0):
+                batch_direct_us: int = 0, c4_range_bound: int = 0, c4_range_width: int = 0, c4_pull_bound: int = 0):
     o = Options(warp_max_degree, cta_max_degree, blocks_per_sm, c4_hub_bound, batch_direct_us, c4_range_bound,
-                c4_range_width)
+                c4_range_width, c4_pull_bound)
     _check(_lib.gpm_set_options(ctypes.byref(o)))
 
 
@@ -200,7 +200,7 @@ def get_options() -> dict:
     _check(_lib.gpm_get_options(ctypes.byref(o)))
     return dict(warp_max_degree=o.warp_max_degree, cta_max_degree=o.cta_max_degree, blocks_per_sm=o.blocks_per_sm,
                 c4_hub_bound=o.c4_hub_bound, batch_direct_us=o.batch_direct_us, c4_range_bound=o.c4_range_bound,
-                c4_range_width=o.c4_range_width)
+                c4_range_width=o.c4_range_width, c4_pull_bound=o.c4_pull_bound)
 
 
 class Graph:

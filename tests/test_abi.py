@@ -146,8 +146,11 @@ def test_options_roundtrip(lib):
     lib.set_options(c4_range_bound=0xffffffff, c4_range_width=512)
     assert lib.get_options()["c4_range_bound"] == 0xffffffff
     assert lib.get_options()["c4_range_width"] == 512
+    assert old["c4_pull_bound"] == 262144
+    lib.set_options(c4_pull_bound=600)
+    assert lib.get_options()["c4_pull_bound"] == 600
     for bad in (dict(c4_range_bound=100), dict(c4_range_width=63), dict(c4_range_width=98306),
-                dict(c4_range_width=1001)):
+                dict(c4_range_width=1001), dict(c4_pull_bound=511)):
         with pytest.raises(lib.GpmError):
             lib.set_options(**bad)
     lib.set_options(**{k: v for k, v in old.items() if v})

@@ -125,16 +125,24 @@ def _multi_hub_graph(hubs=(1500, 2200, 3100), nl=3200, nm=120, per=3, seed=6):
     return gg.from_edges(nh + nl + nm, e, name="multihub")
 
 
-@pytest.mark.parametrize("width,bound", [(98304, 1048576), (98304, 512), (512, 512), (64, 2000), (1000, 4000)])
-def test_cycles4_range_path(gpm, width, bound):
+NEVER = 0xffffffff
+
+
+@pytest.mark.parametrize("width,bound,pull", [(98304, 1048576, 262144), (98304, 512, NEVER), (512, 512, NEVER),
+                                              (64, 2000, NEVER), (1000, 4000, NEVER), (98304, 512, 512),
+                                              (512, 512, 4000), (98304, 4000, 600), (98304, NEVER, 2000)])
+def test_cycles4_range_path(gpm, width, bound, pull):
     # large roots counted range by range over vertex ids with a dense
-    # shared-memory tally: narrow ranges make many ranges per root, a low bound
-    # sends most roots there, and the multi-hub graph has roots whose lists
-    # span several 1024-entry chunks; totals, root ranges and the motif
-    # inversion against the oracle
+    # shared-memory tally, or 128 at a time by the pull over every list with
+    # bit-sliced counters: narrow ranges make many ranges per root, low bounds
+    # send most roots there (several pull passes, the last one partial), and
+    # the multi-hub graph has roots whose lists span several 1024-entry chunks
+    # and vertices of degree > 1024 that precede some roots of a pass and not
+    # others; totals, root ranges (passes with no root in the range skipped)
+    # and the motif inversion against the oracle
     old = gpm.get_options()
     try:
-        gpm.set_options(c4_range_width=width, c4_range_bound=bound)
+        gpm.set_options(c4_range_width=width, c4_range_bound=bound, c4_pull_bound=pull)
         C = gpm.Pattern.spec(O.CYCLE4, induced=False)
         for g in _medium() + [gg.rmat(12, 16.0, seed=31), _multi_hub_graph()]:
             G = gpm.Graph.from_host(g)
@@ -155,10 +163,10 @@ def test_cycles4_hub_path(gpm, hub_bound):
     # a low hub threshold sends many roots of medium graphs through the
     # whole-grid tally path (groups of roots per launch, tally reset by the
     # next launch); totals, root ranges and the motif inversion must not change.
-    # The plain path takes the hub class only with the range tallies switched off.
+    # The plain path takes the hub class only with the range and pull classes switched off.
     old = gpm.get_options()
     try:
-        gpm.set_options(c4_hub_bound=hub_bound, c4_range_bound=0xffffffff)
+        gpm.set_options(c4_hub_bound=hub_bound, c4_range_bound=NEVER, c4_pull_bound=NEVER)
         C = gpm.Pattern.spec(O.CYCLE4, induced=False)
         for g in _medium():
             G = gpm.Graph.from_host(g)
