@@ -163,11 +163,12 @@ NCU_COUNTERS = {
         "lg_cta_hi": {"digest": "2b577df7558f17b7", "inst_per_step": 1638151502659,
                       "dram_bytes_per_step": 13073920, "ncu_ms": 1688.935},
     },
-    # every 4-cycle kernel launch of one step (c4_bound x 2, c4_range,
-    # c4_bucket, c4_small; the per-graph c4_edeg and c4_roff tables excluded),
-    # summed; profiles/c4_sl_chunglu4m_dram.md; digest of motif.cu + motif_device.cuh
+    # every 4-cycle kernel launch of one step (c4_bound x 2, 42 pull passes of
+    # c4_pull_mark x 2, c4_pull, c4_pull_tiny, c4_pull_rows; c4_bucket,
+    # c4_small; the per-graph tables excluded), summed;
+    # profiles/c4_sl_chunglu4m_dram.md; digest of motif.cu + motif_device.cuh + c4_pull.cu
     "sl-chunglu4m": {
-        "c4": {"digest": "91324121aec85ca0", "dram_bytes_per_step": 134.73e9},
+        "c4": {"digest": "94edd33fa40de13a", "dram_bytes_per_step": 85433498624},
     },
     # profiles/enum_k5_er1m_counters.md; digest of enumerate.cu
     "motif5-er1m": {

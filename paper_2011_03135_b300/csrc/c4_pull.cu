@@ -25,12 +25,13 @@
 // roots up to 128), where the wedge walk reads every list of every root's
 // neighbours. The lists are read from a copy of the CSR in order of
 // decreasing degree (built once per graph, 32-bit offsets), so that the
-// vertices a warp holds have similar degrees. Work items are taken 8 per warp
-// claim, one per group of 4 lanes (lane l of a group owns roots
-// 32l..32l+31): a vertex of degree <= kPullChunk is one item, whose counts
-// are finished in registers; a larger vertex is cut into items of kPullChunk
-// entries, whose per-root counts are added into a counter row of that vertex
-// (128 words in global memory), finished by a second kernel.
+// vertices a warp holds have similar degrees. Vertices of degree <= kTinyMax
+// take one lane each (a kernel of their own); for the others, work items are
+// taken 8 per warp claim, one per group of 4 lanes (lane l of a group owns
+// roots 32l..32l+31): a vertex of degree <= kPullChunk is one item, whose
+// counts are finished in registers; a larger vertex is cut into items of
+// kPullChunk entries, whose per-root counts are added into a counter row of
+// that vertex (128 words in global memory), finished by a third kernel.
 #include <algorithm>
 #include <vector>
 
@@ -45,7 +46,10 @@ constexpr int kPullThreads = 256;
 constexpr uint32_t kPullRoots = 128;   // roots per pass (4 words of M per vertex)
 constexpr uint32_t kPullChunk = 1024;  // entries per item
 constexpr int kPlanes = 11;            // counters up to 2047 >= kPullChunk
-constexpr int kBatch = 8;              // entries loaded together by a lane
+constexpr int kBatch = 8;              // entries summed by one carry-save tree
+constexpr int kLoad = 16;              // entries loaded together by a lane (main kernel)
+constexpr int kPad = 16;               // entries of padding after the last list
+constexpr uint32_t kTinyMax = 15;      // vertices of degree <= 15: one per lane, all 128 roots
 
 struct C4PullArgs {
   const uint32_t *__restrict__ deg;
@@ -55,6 +59,7 @@ struct C4PullArgs {
   const uint2 *__restrict__ chunks;    // items of the large vertices: {position, first entry}
   uint32_t nchunks;                    // ord[0, n_big) are cut into chunks
   uint32_t n_big, n_act;               // ord[0, n_act): degree >= 2
+  uint32_t n_tiny;                     // ord[n_tiny, n_act): degree <= kTinyMax
   const uint32_t *__restrict__ M;      // 4 words per vertex
   uint32_t *__restrict__ cntb;         // kPullRoots counters per large vertex (zero)
   const uint32_t *__restrict__ roots;  // the pass's roots
@@ -157,7 +162,7 @@ __device__ __forceinline__ uint32_t ld_once(const uint32_t *p, uint64_t pol) {
   return v;
 }
 
-__global__ void __launch_bounds__(kPullThreads, 6) c4_pull_kernel(C4PullArgs a) {
+__global__ void __launch_bounds__(kPullThreads, 4) c4_pull_kernel(C4PullArgs a) {
   __shared__ unsigned long long s_key[kPullRoots];
   __shared__ unsigned long long s_min;
   const uint32_t tid = threadIdx.x, lane = tid & 31;
@@ -173,7 +178,7 @@ __global__ void __launch_bounds__(kPullThreads, 6) c4_pull_kernel(C4PullArgs a) 
   }
   __syncthreads();
   const unsigned long long minkey = s_min;
-  const uint32_t nitems = a.nchunks + (a.n_act - a.n_big);
+  const uint32_t nitems = a.nchunks + (a.n_tiny - a.n_big);
   unsigned long long acc = 0;
   bool carry = false;
   for (;;) {
@@ -203,17 +208,29 @@ __global__ void __launch_bounds__(kPullThreads, 6) c4_pull_kernel(C4PullArgs a) 
     uint32_t p[kPlanes];
 #pragma unroll
     for (int j = 0; j < kPlanes; ++j) p[j] = 0;
-    // batches of kBatch entries; pcol has kBatch entries of padding, so the
+    // batches of kLoad entries; pcol has kPad entries of padding, so the
     // loads past e1 stay in bounds and only their membership words are skipped
-    for (uint32_t e = e0; e < e1; e += kBatch) {
-      const uint32_t *src = a.pcol + e;
-      const uint32_t left = e1 - e;
-      uint32_t y[kBatch], m[kBatch];
+    // the next batch's entries are loaded before this batch's words are
+    // gathered (software pipelining over the batches of a long list)
+    uint32_t yn[kLoad];
 #pragma unroll
-      for (int i = 0; i < kBatch; ++i) y[i] = ld_once(src + i, pol);
+    for (int i = 0; i < kLoad; ++i) yn[i] = ld_once(a.pcol + e0 + i, pol);
+    for (uint32_t e = e0; e < e1; e += kLoad) {
+      const uint32_t left = e1 - e;
+      uint32_t y[kLoad], m[kBatch], m2[kBatch];
+#pragma unroll
+      for (int i = 0; i < kLoad; ++i) y[i] = yn[i];
+      if (left > kLoad) {
+#pragma unroll
+        for (int i = 0; i < kLoad; ++i) yn[i] = ld_once(a.pcol + e + kLoad + i, pol);
+      }
 #pragma unroll
       for (int i = 0; i < kBatch; ++i) m[i] = (uint32_t)i < left ? __ldg(a.M + 4ull * y[i] + lw) : 0u;
+#pragma unroll
+      for (int i = 0; i < kBatch; ++i)
+        m2[i] = (uint32_t)(i + kBatch) < left ? __ldg(a.M + 4ull * y[i + kBatch] + lw) : 0u;
       plane_add8(p, m, mask);
+      plane_add8(p, m2, mask);
     }
     if (item >= a.nchunks) {
       acc += plane_pairs(p, e1 - e0);
@@ -230,6 +247,115 @@ __global__ void __launch_bounds__(kPullThreads, 6) c4_pull_kernel(C4PullArgs a) 
   }
   // per-thread sums are far below 2^64; the warp sums and the accumulator
   // additions are checked
+  acc = warp_sum_checked(acc, carry);
+  if (lane == 0) acc_add_checked(&a.acc[ACC_C4], acc, carry, a.status, ACC_C4);
+}
+
+// 4-bit counters (at most 15 additions): the carry-save sum of 8 inputs added into 4 planes
+__device__ __forceinline__ void plane_add8_4(uint32_t (&p)[4], const uint32_t (&x)[8], uint32_t mask) {
+  uint32_t s1, c1, s2, c2, s3, c3, s5, d1;
+  fadd(x[0], x[1], x[2], s1, c1);
+  fadd(x[3], x[4], x[5], s2, c2);
+  fadd(s1, s2, x[6], s3, c3);
+  const uint32_t b0 = (s3 ^ x[7]) & mask, c4 = s3 & x[7];
+  fadd(c1, c2, c3, s5, d1);
+  const uint32_t b1 = (s5 ^ c4) & mask, d2 = s5 & c4;
+  const uint32_t b2 = (d1 ^ d2) & mask, b3 = d1 & d2 & mask;
+  uint32_t c = p[0] & b0, t;
+  p[0] ^= b0;
+  fadd(p[1], b1, c, t, c);
+  p[1] = t;
+  fadd(p[2], b2, c, t, c);
+  p[2] = t;
+  p[3] ^= b3 ^ c;  // no carry out of plane 3: every counter stays <= 15
+}
+
+__device__ __forceinline__ unsigned long long pairs4(const uint32_t (&p)[4], uint32_t walked) {
+  // plane_pairs_t over 4 planes, read through an 11-plane view
+  uint32_t q[kPlanes];
+#pragma unroll
+  for (int j = 0; j < kPlanes; ++j) q[j] = j < 4 ? p[j] : 0u;
+  switch (32 - __clz(walked)) {
+    case 0:
+    case 1: return 0;
+    case 2: return plane_pairs_t<2>(q);
+    case 3: return plane_pairs_t<3>(q);
+    default: return plane_pairs_t<4>(q);
+  }
+}
+
+// Vertices of degree 2..kTinyMax (ord[n_tiny, n_act)), one per lane: a warp
+// claims 32 consecutive positions (adjacent lists of similar length), each
+// lane gathers the whole 16-byte membership word of its entries and keeps
+// 4 x 4 planes (all 128 roots); the latency of each vertex's dependent loads
+// is shared by 32 vertices instead of 8.
+__global__ void __launch_bounds__(kPullThreads, 3) c4_pull_tiny_kernel(C4PullArgs a) {
+  __shared__ unsigned long long s_key[kPullRoots];
+  __shared__ unsigned long long s_min;
+  const uint32_t tid = threadIdx.x, lane = tid & 31;
+  const uint64_t pol = evict_first_policy();
+  for (uint32_t r = tid; r < kPullRoots; r += kPullThreads)
+    s_key[r] = r < a.nb ? ((unsigned long long)a.deg[a.roots[r]] << 32) | a.roots[r] : ~0ull;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long mk = ~0ull;
+    for (uint32_t r = 0; r < a.nb; ++r) mk = s_key[r] < mk ? s_key[r] : mk;
+    s_min = mk;
+  }
+  __syncthreads();
+  const unsigned long long minkey = s_min;
+  const uint32_t ntiny = a.n_act - a.n_tiny;
+  const uint4 *M4 = reinterpret_cast<const uint4 *>(a.M);
+  unsigned long long acc = 0;
+  bool carry = false;
+  for (;;) {
+    uint32_t first = 0;
+    if (lane == 0) first = atomicAdd(a.queue + 1, 32u);
+    first = __shfl_sync(0xffffffffu, first, 0);
+    if (first >= ntiny) break;
+    if (first + lane >= ntiny) continue;
+    const uint32_t pos = a.n_tiny + first + lane;
+    const uint32_t e0 = ld_once(a.prow + pos, pol), e1 = ld_once(a.prow + pos + 1, pol);
+    const uint32_t dw = e1 - e0;
+    uint32_t mk[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};
+    if (((unsigned long long)dw << 32 | 0xffffffffull) >= minkey) {
+      // w may follow some roots of the pass: exact key comparisons
+      const unsigned long long kw = ((unsigned long long)dw << 32) | ld_once(a.ord + pos, pol);
+#pragma unroll
+      for (uint32_t k = 0; k < 4; ++k) mk[k] = before_mask(s_key, minkey, a.nb, kw, k);
+      if (!(mk[0] | mk[1] | mk[2] | mk[3])) continue;
+    }
+    uint32_t p[4][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) p[k][j] = 0;
+    for (uint32_t e = e0; e < e1; e += kBatch) {
+      const uint32_t *src = a.pcol + e;
+      const uint32_t left = e1 - e;
+      uint32_t y[kBatch];
+      uint4 m[kBatch];
+#pragma unroll
+      for (int i = 0; i < kBatch; ++i) y[i] = ld_once(src + i, pol);
+#pragma unroll
+      for (int i = 0; i < kBatch; ++i) m[i] = (uint32_t)i < left ? __ldg(M4 + y[i]) : make_uint4(0, 0, 0, 0);
+      uint32_t x[kBatch];
+#pragma unroll
+      for (int i = 0; i < kBatch; ++i) x[i] = m[i].x;
+      plane_add8_4(p[0], x, mk[0]);
+#pragma unroll
+      for (int i = 0; i < kBatch; ++i) x[i] = m[i].y;
+      plane_add8_4(p[1], x, mk[1]);
+#pragma unroll
+      for (int i = 0; i < kBatch; ++i) x[i] = m[i].z;
+      plane_add8_4(p[2], x, mk[2]);
+#pragma unroll
+      for (int i = 0; i < kBatch; ++i) x[i] = m[i].w;
+      plane_add8_4(p[3], x, mk[3]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc += pairs4(p[k], dw);
+  }
   acc = warp_sum_checked(acc, carry);
   if (lane == 0) acc_add_checked(&a.acc[ACC_C4], acc, carry, a.status, ACC_C4);
 }
@@ -357,6 +483,7 @@ static int ensure_c4_pull(gpm_graph *g, uint32_t npass, cudaStream_t st) {
     }
     g->c4q_nbig = nbin > kPullChunk + 1 ? cur[kPullChunk] : 0;
     g->c4q_nact = nbin > 2 ? cur[1] : 0;
+    g->c4q_ntiny = nbin > kTinyMax ? cur[kTinyMax] : 0;
     const uint64_t pnnz = nbin > 2 ? base[1] : 0;
     // chunks of the vertices of degree > kPullChunk, in position order
     std::vector<uint2> chunks;
@@ -377,8 +504,8 @@ static int ensure_c4_pull(gpm_graph *g, uint32_t npass, cudaStream_t st) {
     // positions: reload the first positions
     GPM_CUDA(cudaMemcpyAsync(hist, cur.data(), sizeof(uint32_t) * nbin, cudaMemcpyHostToDevice, st));
     GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4q_prow, sizeof(uint32_t) * ((size_t)g->c4q_nact + 1)));
-    GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4q_pcol, sizeof(uint32_t) * (pnnz + kBatch)));
-    GPM_CUDA(cudaMemsetAsync(g->c4q_pcol + pnnz, 0, sizeof(uint32_t) * kBatch, st));
+    GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4q_pcol, sizeof(uint32_t) * (pnnz + kPad)));
+    GPM_CUDA(cudaMemsetAsync(g->c4q_pcol + pnnz, 0, sizeof(uint32_t) * kPad, st));
     GPM_CUDA(cudaMemsetAsync(g->c4q_prow, 0, sizeof(uint32_t), st));
     if (g->c4q_nact) {
       GPM_LAUNCH("c4_pull_csr_kernel", st,
@@ -403,15 +530,15 @@ static int ensure_c4_pull(gpm_graph *g, uint32_t npass, cudaStream_t st) {
     GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4q_M, 4 * sizeof(uint32_t) * nw));
     GPM_CUDA(cudaMemsetAsync(g->c4q_M, 0, 4 * sizeof(uint32_t) * nw, st));
   }
-  if (g->c4q_queue_words < npass) {
+  if (g->c4q_queue_words < 2 * npass) {
     if (g->c4q_queue) {
       cudaFree(g->c4q_queue);
       g->device_bytes -= sizeof(unsigned int) * g->c4q_queue_words;
       g->c4q_queue = nullptr;
       g->c4q_queue_words = 0;
     }
-    GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4q_queue, sizeof(unsigned int) * npass));
-    g->c4q_queue_words = npass;
+    GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4q_queue, sizeof(unsigned int) * 2 * npass));
+    g->c4q_queue_words = 2 * npass;
   }
   return GPM_OK;
 }
@@ -440,11 +567,13 @@ int gpm_launch_c4_pull(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigne
   const std::vector<uint32_t> &hr = g->c4q_hroots;
   if (hr.empty()) return GPM_OK;
   const uint32_t npass = (uint32_t)((hr.size() + kPullRoots - 1) / kPullRoots);
-  GPM_CUDA(cudaMemsetAsync(g->c4q_queue, 0, sizeof(unsigned int) * npass, st));
-  int per_sm = 0;
+  GPM_CUDA(cudaMemsetAsync(g->c4q_queue, 0, sizeof(unsigned int) * 2 * npass, st));
+  int per_sm = 0, per_sm_tiny = 0;
   GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c4_pull_kernel, kPullThreads, 0));
+  GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_tiny, c4_pull_tiny_kernel, kPullThreads, 0));
   const int sms = gpm_num_sms(g->device);
   const unsigned blocks = (unsigned)sms * (unsigned)std::max(per_sm, 1);
+  const unsigned blocks_tiny = (unsigned)sms * (unsigned)std::max(per_sm_tiny, 1);
   unsigned int *status = reinterpret_cast<unsigned int *>(g->work + WK_STATUS);
   for (uint32_t p = 0; p < npass; ++p) {
     const uint32_t r0 = p * kPullRoots;
@@ -466,15 +595,22 @@ int gpm_launch_c4_pull(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigne
     a.nchunks = g->c4q_nchunks;
     a.n_big = g->c4q_nbig;
     a.n_act = g->c4q_nact;
+    a.n_tiny = g->c4q_ntiny;
     a.M = g->c4q_M;
     a.cntb = g->c4q_cntb;
     a.roots = roots;
     a.nb = nb;
-    a.queue = g->c4q_queue + p;
+    a.queue = g->c4q_queue + 2 * p;
     a.acc = acc;
     a.status = status;
-    GPM_LAUNCH("c4_pull_kernel", st, c4_pull_kernel<<<blocks, kPullThreads, 0, st>>>(a));
-    GPM_CUDA(cudaGetLastError());
+    if (a.nchunks + (a.n_tiny - a.n_big)) {
+      GPM_LAUNCH("c4_pull_kernel", st, c4_pull_kernel<<<blocks, kPullThreads, 0, st>>>(a));
+      GPM_CUDA(cudaGetLastError());
+    }
+    if (a.n_act > a.n_tiny) {
+      GPM_LAUNCH("c4_pull_tiny_kernel", st, c4_pull_tiny_kernel<<<blocks_tiny, kPullThreads, 0, st>>>(a));
+      GPM_CUDA(cudaGetLastError());
+    }
     if (g->c4q_nbig) {
       const uint64_t nwords = (uint64_t)g->c4q_nbig * kPullRoots;
       const unsigned rb = (unsigned)std::min<uint64_t>((nwords + 255) / 256, (uint64_t)sms * 8);

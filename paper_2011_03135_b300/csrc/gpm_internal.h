@@ -195,7 +195,7 @@ struct gpm_graph {
   // decreasing wedge bound (device c4q_roots, host c4q_hroots), one queue
   // counter per pass
   uint32_t *c4q_ord = nullptr;
-  uint32_t c4q_nbig = 0, c4q_nact = 0;
+  uint32_t c4q_nbig = 0, c4q_nact = 0, c4q_ntiny = 0;  // ord[c4q_ntiny, c4q_nact): degree 2..15
   uint32_t *c4q_prow = nullptr;  // the lists in the order c4q_ord: c4q_pcol[prow[i] .. prow[i + 1])
   uint32_t *c4q_pcol = nullptr;
   uint32_t *c4q_chunks = nullptr;  // {position, first entry} of each 1024-entry chunk of the first c4q_nbig

@@ -438,8 +438,13 @@ __global__ void __launch_bounds__(kHubThreads) c4_hub_kernel(const uint64_t *__r
   }
 }
 
-// one CTA per large root, bucketed aggregation (buffer slot per CTA)
+// one CTA per large root, bucketed aggregation (buffer slot per CTA); roots
+// whose wedge bound is at most 3/4 of kC4DirectSlots are counted in one
+// shared-memory table instead (the space of the bucket tables)
 constexpr int kC4BucketThreads = 512;
+constexpr uint32_t kC4DirectSlots =
+    (gpm_dev::c4_bucket_smem_words(kC4BucketThreads / 32) - (2 * gpm_dev::kC4MaxBuckets + 4)) / 2;
+static_assert((kC4DirectSlots & (kC4DirectSlots - 1)) == 0, "direct table slots: a power of two");
 __global__ void __launch_bounds__(kC4BucketThreads) c4_bucket_kernel(C4Args a, uint64_t slot_words) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint32_t s_task, s_cnt;
@@ -458,7 +463,7 @@ __global__ void __launch_bounds__(kC4BucketThreads) c4_bucket_kernel(C4Args a, u
     const uint32_t v0 = a.tasks[task];
     if (v0 < a.root_lo || v0 >= a.root_hi) continue;
     acc += gpm_dev::c4_root_bucketed(a.rowptr, a.col, a.deg, a.edeg, v0, buf, buf + slot_words / 2, smem, s_x, &s_cnt,
-                                     overflow, s_pre, s_rp);
+                                     overflow, s_pre, s_rp, kC4DirectSlots);
   }
   bool carry = false;
   acc = warp_sum_checked(acc, carry);

@@ -180,11 +180,13 @@ __device__ __forceinline__ uint32_t c4_row_of(const uint32_t *pre, uint32_t n, u
 // consecutive entries per lane (one row search for the first), so short
 // lists do not leave lanes idle. s_pre holds blockDim.x + 33 words, s_rp
 // blockDim.x entries. Every thread calls it; the caller synchronises after.
+// sink(w, v) is called by every lane for every slot of the walk (v: w is
+// a wedge end before v0), warp-synchronously.
+template <class Sink>
 __device__ __forceinline__ void c4_walk_flat(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
                                              const uint32_t *__restrict__ deg, const uint32_t *__restrict__ edeg,
                                              uint32_t v0, uint32_t d0, const uint32_t *s_x, uint32_t cnt,
-                                             uint32_t *s_pre, uint64_t *s_rp, uint32_t *bcnt, uint32_t pmask,
-                                             uint32_t *ctl, uint32_t *lin) {
+                                             uint32_t *s_pre, uint64_t *s_rp, Sink &&sink) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   uint32_t *s_wsum = s_pre + nt + 1;
   uint32_t len = 0;
@@ -231,15 +233,26 @@ __device__ __forceinline__ void c4_walk_flat(const uint64_t *__restrict__ rowptr
         w = col[e];
         v = precedes(nbr_deg(edeg, deg, e, w), w, d0, v0);
       }
-      if (v) atomicAdd(&bcnt[c4_bucket_hash(w) & pmask], 1u);
-      const uint32_t m = __ballot_sync(0xffffffffu, v);
-      if (m) {
-        const int leader = __ffs(m) - 1;
-        uint32_t pos = 0;
-        if ((int)lane == leader) pos = atomicAdd(&ctl[2], (uint32_t)__popc(m));
-        pos = __shfl_sync(0xffffffffu, pos, leader);
-        if (v) lin[pos + __popc(m & ((1u << lane) - 1u))] = w;
-      }
+      sink(w, v);
+    }
+  }
+}
+
+// counts wedge end w in a shared-memory table of tmask + 1 slots (linear
+// probing); a full table sets overflow
+__device__ __forceinline__ void c4_table_add(uint32_t *keys, uint32_t *vals, uint32_t tmask, uint32_t bits,
+                                             uint32_t w, bool &overflow) {
+  uint32_t h = c4_slot_hash(w, bits);
+  for (uint32_t probes = 0;; ++probes) {
+    const uint32_t k = atomicCAS(&keys[h], kC4Empty, w);
+    if (k == kC4Empty || k == w) {
+      atomicAdd(&vals[h], 1u);
+      return;
+    }
+    h = (h + 1) & tmask;
+    if (probes >= tmask) {
+      overflow = true;
+      return;
     }
   }
 }
@@ -256,7 +269,8 @@ __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *_
                                                                const uint32_t *__restrict__ edeg, uint32_t v0,
                                                                uint32_t *lin, uint32_t *buf, uint32_t *sm,
                                                                uint32_t *s_x, uint32_t *s_cnt, bool &overflow,
-                                                               uint32_t *s_pre = nullptr, uint64_t *s_rp = nullptr) {
+                                                               uint32_t *s_pre = nullptr, uint64_t *s_rp = nullptr,
+                                                               uint32_t direct_slots = 0) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   uint32_t *bcnt = sm;                       // [kC4MaxBuckets]: counts, then write cursors
   uint32_t *boff = sm + kC4MaxBuckets;       // [kC4MaxBuckets + 1]
@@ -283,6 +297,39 @@ __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *_
   }
   __syncthreads();
   const uint32_t bound = ctl[0];
+  if (direct_slots && s_pre && 4ull * bound <= 3ull * direct_slots) {
+    // every wedge end fits a table of direct_slots slots (at most 3/4 full):
+    // counted there directly, no bucket buffers
+    uint32_t bits = 6;
+    while ((1u << bits) < 2 * bound && (1u << bits) < direct_slots) ++bits;
+    const uint32_t tmask = (1u << bits) - 1;
+    uint32_t *dkeys = sm + 2 * kC4MaxBuckets + 4, *dvals = dkeys + direct_slots;
+    for (uint32_t i = tid; i <= tmask; i += nt) {
+      dkeys[i] = kC4Empty;
+      dvals[i] = 0;
+    }
+    for (uint64_t cb = b0; cb < e0; cb += nt) {
+      if (tid == 0) *s_cnt = 0;
+      __syncthreads();
+      const uint64_t ex = cb + tid;
+      if (ex < e0) {
+        const uint32_t x = col[ex];
+        if (precedes(nbr_deg(edeg, deg, ex, x), x, d0, v0)) s_x[atomicAdd(s_cnt, 1u)] = x;
+      }
+      __syncthreads();
+      c4_walk_flat(rowptr, col, deg, edeg, v0, d0, s_x, *s_cnt, s_pre, s_rp, [&](uint32_t w, bool v) {
+        if (v) c4_table_add(dkeys, dvals, tmask, bits, w, overflow);
+      });
+      __syncthreads();
+    }
+    unsigned long long acc = 0;
+    for (uint32_t i = tid; i <= tmask; i += nt) {
+      const unsigned long long c = dvals[i];
+      acc += c * (c - (c > 0)) / 2;
+    }
+    __syncthreads();
+    return acc;
+  }
   uint32_t P = 1;
   while (P < kC4MaxBuckets && (unsigned long long)P * kC4BucketTarget < bound) P <<= 1;
   const uint32_t pmask = P - 1;
@@ -301,7 +348,17 @@ __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *_
     __syncthreads();
     const uint32_t cnt = *s_cnt;
     if (s_pre) {
-      c4_walk_flat(rowptr, col, deg, edeg, v0, d0, s_x, cnt, s_pre, s_rp, bcnt, pmask, ctl, lin);
+      c4_walk_flat(rowptr, col, deg, edeg, v0, d0, s_x, cnt, s_pre, s_rp, [&](uint32_t w, bool v) {
+        if (v) atomicAdd(&bcnt[c4_bucket_hash(w) & pmask], 1u);
+        const uint32_t m = __ballot_sync(0xffffffffu, v);
+        if (m) {
+          const int leader = __ffs(m) - 1;
+          uint32_t pos = 0;
+          if ((int)lane == leader) pos = atomicAdd(&ctl[2], (uint32_t)__popc(m));
+          pos = __shfl_sync(0xffffffffu, pos, leader);
+          if (v) lin[pos + __popc(m & ((1u << lane) - 1u))] = w;
+        }
+      });
       __syncthreads();
       continue;
     }
