@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256) lg_warp_kernel(LGArgs a) {
 // one CTA per root; bitmap in shared memory (GLOBAL = false) or in this
 // CTA's global-memory slot (GLOBAL = true)
 // ---------------------------------------------------------------------------
-template <int G, int KMAX, bool SCATTER, bool GLOBAL, int THREADS>
+template <int G, int KMAX, bool SCATTER, bool GLOBAL, int THREADS, int NWLG = 4>
 __global__ void __launch_bounds__(THREADS) lg_cta_kernel(LGArgs a, uint32_t maxd, uint32_t big_cap, uint32_t wcap) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint32_t s_task;
@@ -118,10 +118,12 @@ __global__ void __launch_bounds__(THREADS) lg_cta_kernel(LGArgs a, uint32_t maxd
   // nested local graphs for the 5-clique level live after the bitmap (shared memory only)
   uint32_t *nest = (!GLOBAL && KMAX >= 5 && big_cap) ? smem + gpm_dev::cta_words(maxd, a.W) : nullptr;
   // k >= 7 with global-memory bitmaps: the generic search's counter and
-  // per-warp scratch in static shared memory (rows of up to 128 words)
-  constexpr int kNwl = (GLOBAL && KMAX >= 7) ? 4 : 1;
-  __shared__ uint32_t gen_s[(GLOBAL && KMAX >= 7) ? 4 + (THREADS / 32) * gpm_dev::gen_warp_words(4) : 1];
-  uint32_t *gen = (GLOBAL && KMAX >= 7) ? gen_s : nullptr;
+  // per-warp scratch, for rows of up to 32 NWLG words: in static shared memory
+  // (NWLG = 4), or in the dynamic shared memory, which global-memory bitmaps
+  // leave unused (NWLG = 16)
+  constexpr int kNwl = (GLOBAL && KMAX >= 7) ? NWLG : 1;
+  __shared__ uint32_t gen_s[(GLOBAL && KMAX >= 7 && NWLG <= 4) ? 4 + (THREADS / 32) * gpm_dev::gen_warp_words(4) : 1];
+  uint32_t *gen = (GLOBAL && KMAX >= 7) ? (NWLG <= 4 ? gen_s : smem) : nullptr;
   unsigned long long a3 = 0, a4 = 0, a5 = 0, a6 = 0;
   for (;;) {
     if (threadIdx.x == 0) s_task = atomicAdd(a.queue, 1u);
@@ -178,10 +180,11 @@ int max_smem_optin(int device) {
 // roots with the nested 5-clique search: 32 warp buffers for rows of up to
 // 128 candidates fit beside a bitmap of up to 1024 rows, and the big-row
 // groups reuse the same pool afterwards.
-template <int G, int KMAX, bool SCATTER, bool GLOBAL, int THREADS>
+template <int G, int KMAX, bool SCATTER, bool GLOBAL, int THREADS, int NWLG = 4>
 int launch_cta_t(const LGArgs &a, uint32_t maxd, int blocks_cap, int device, cudaStream_t st, size_t smem_limit,
                  const char *name) {
   size_t smem = GLOBAL ? 0 : (size_t)cta_words(maxd, a.W) * 4;
+  if (GLOBAL && KMAX >= 7 && NWLG > 4) smem = (4 + (size_t)(THREADS / 32) * gpm_dev::gen_warp_words(NWLG)) * 4;
   const size_t limit = smem_limit ? smem_limit : (size_t)max_smem_optin(device);
   // one-warp rows of up to 128 candidates when their buffers fit, else 64
   uint32_t wcap = gpm_dev::kNestWarpC;
@@ -198,8 +201,8 @@ int launch_cta_t(const LGArgs &a, uint32_t maxd, int blocks_cap, int device, cud
   if (KMAX >= 7 && !GLOBAL &&
       (big_cap == 0 || gpm_dev::nest_warp_words(wcap) < gpm_dev::gen_warp_words(1) + 4))
     return gpm_fail(GPM_E_UNSUPPORTED, "no shared memory left for the generic clique search's scratch");
-  auto kern = lg_cta_kernel<G, KMAX, SCATTER, GLOBAL, THREADS>;
-  if (!GLOBAL) GPM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  auto kern = lg_cta_kernel<G, KMAX, SCATTER, GLOBAL, THREADS, NWLG>;
+  if (smem) GPM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem));
   if (per_sm < 1) per_sm = 1;
@@ -212,12 +215,12 @@ int launch_cta_t(const LGArgs &a, uint32_t maxd, int blocks_cap, int device, cud
   return GPM_OK;
 }
 
-template <int G, int KMAX, bool SCATTER, bool GLOBAL>
+template <int G, int KMAX, bool SCATTER, bool GLOBAL, int NWLG = 4>
 int launch_cta(const LGArgs &a, uint32_t maxd, int blocks_cap, int device, cudaStream_t st,
                size_t smem_limit = 0, const char *name = nullptr, bool wide = false) {
   if (KMAX >= 5 && !GLOBAL && wide)
     return launch_cta_t<G, KMAX, SCATTER, GLOBAL, 1024>(a, maxd, blocks_cap, device, st, smem_limit, name);
-  return launch_cta_t<G, KMAX, SCATTER, GLOBAL, 512>(a, maxd, blocks_cap, device, st, smem_limit, name);
+  return launch_cta_t<G, KMAX, SCATTER, GLOBAL, 512, NWLG>(a, maxd, blocks_cap, device, st, smem_limit, name);
 }
 
 template <int KMAX, bool SCATTER>
@@ -242,6 +245,7 @@ int launch_all(gpm_graph *g, LGArgs base, unsigned int *queues, cudaStream_t st)
       // the generic search spreads a root over a CTA (a heavy local graph in
       // one warp would be the last to finish)
       a.W = (md + 31) / 32;
+      a.slices = 2;  // lighter roots than the CTA class: two CTAs each (measured best of 2, 4, 8, 16)
       GPM_TRY((launch_cta<32, KMAX, SCATTER, false>(a, md, 0, dev, st, (size_t)(max_smem_optin(dev) / 2 - 1024),
                                                     "lg_cta_mid")));
     } else if (a.ntasks) {
@@ -284,8 +288,8 @@ int launch_all(gpm_graph *g, LGArgs base, unsigned int *queues, cudaStream_t st)
     const uint32_t md = g->cls_maxdeg[CLS_XL];
     if (a.ntasks) {
       a.W = (md + 31) / 32;
-      if (KMAX >= 7 && a.W > 128)
-        return gpm_fail(GPM_E_UNSUPPORTED, "k-clique counting for k >= 7 supports root out-degrees up to 4096 "
+      if (KMAX >= 7 && a.W > 512)
+        return gpm_fail(GPM_E_UNSUPPORTED, "k-clique counting for k >= 7 supports root out-degrees up to 16384 "
                                            "(this graph has " + std::to_string(md) + ")");
       a.slot_words = (cta_words(md, a.W) + 63) & ~63ull;
       const size_t slot_bytes = a.slot_words * 4;
@@ -307,7 +311,8 @@ int launch_all(gpm_graph *g, LGArgs base, unsigned int *queues, cudaStream_t st)
       }
       a.pool = g->xl_pool;
       if constexpr (KMAX >= 7) {
-        GPM_TRY((launch_cta<32, KMAX, SCATTER, true>(a, md, slots, dev, st)));
+        if (a.W > 128) GPM_TRY((launch_cta<32, KMAX, SCATTER, true, 16>(a, md, slots, dev, st)));
+        else GPM_TRY((launch_cta<32, KMAX, SCATTER, true>(a, md, slots, dev, st)));
       } else {
         if (a.W <= 8) GPM_TRY((launch_cta<8, KMAX, SCATTER, true>(a, md, slots, dev, st)));
         else if (a.W <= 16) GPM_TRY((launch_cta<16, KMAX, SCATTER, true>(a, md, slots, dev, st)));

@@ -705,6 +705,78 @@ __device__ __forceinline__ uint32_t reg_cliques_warp(uint32_t m, uint32_t dl, co
   }
 }
 
+// position of the j-th (from 0) set bit of v (j < popc(v)), by halving
+__device__ __forceinline__ uint32_t select_bit(uint32_t v, uint32_t j) {
+  uint32_t pos = 0, c = __popc(v & 0xffffu);
+  if (j >= c) { j -= c; v >>= 16; pos += 16; }
+  c = __popc(v & 0xffu);
+  if (j >= c) { j -= c; v >>= 8; pos += 8; }
+  c = __popc(v & 0xfu);
+  if (j >= c) { j -= c; v >>= 4; pos += 4; }
+  c = __popc(v & 0x3u);
+  if (j >= c) { j -= c; v >>= 2; pos += 2; }
+  if (j >= (v & 1u)) pos += 1;
+  return pos;
+}
+
+// r-cliques (r >= 1) of the register graph among the members c, counted by
+// one lane on its own (rows Ds in shared memory)
+template <int r>
+__device__ __forceinline__ uint32_t seq_cliques(uint32_t c, const uint32_t *Ds) {
+  if constexpr (r == 1) {
+    return __popc(c);
+  } else {
+    uint32_t s = 0, rest = c;
+    while (rest) {
+      const uint32_t z = __ffs(rest) - 1;
+      rest &= rest - 1;
+      const uint32_t c2 = c & Ds[z];
+      if constexpr (r == 2) s += __popc(c2);
+      else if (__popc(c2) >= (uint32_t)(r - 1)) s += seq_cliques<r - 1>(c2, Ds);
+    }
+    return s;
+  }
+}
+
+// r-cliques (r >= 4) among the members m of the register graph, with the
+// pairs (x, y) of a member and one of its successors spread over the lanes:
+// an inclusive scan of the successor counts numbers the pairs, lane p takes
+// pairs p, p + 32, ... (x by a binary search of the scan, y by bit selection)
+// and counts the (r - 2)-cliques among the common successors of x and y on
+// its own. All lanes work as long as there are 32 pairs, where walking the
+// first levels warp-uniformly leaves every lane outside the current set idle.
+// tmp: 64 words of the warp's scratch. Returns this lane's share.
+template <int r>
+__device__ __forceinline__ uint32_t reg_cliques_pairs(uint32_t m, const uint32_t *Ds, uint32_t *tmp) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t *succ = tmp, *upto = tmp + 32;
+  const uint32_t mx = ((m >> lane) & 1u) ? (m & Ds[lane]) : 0u;
+  uint32_t incl = __popc(mx);
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= (uint32_t)o) incl += y;
+  }
+  succ[lane] = mx;
+  upto[lane] = incl;
+  __syncwarp();
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  uint32_t s = 0;
+  for (uint32_t p = lane; p < total; p += 32) {
+    uint32_t lo = 0, hi = 31;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (upto[mid] > p) hi = mid;
+      else lo = mid + 1;
+    }
+    const uint32_t sx = succ[lo];
+    const uint32_t y = select_bit(sx, p - (upto[lo] - __popc(sx)));
+    const uint32_t c = sx & Ds[y];
+    if (__popc(c) >= (uint32_t)(r - 2)) s += seq_cliques<r - 2>(c, Ds);
+  }
+  __syncwarp();
+  return s;
+}
+
 // Q-cliques (Q >= 1) among the members of the set m (NWL words per lane) of
 // the local-graph DAG R (W words per row, stride rs). Called by a whole warp
 // with warp-uniform arguments; returns this lane's share (the warp sum is the
@@ -757,7 +829,10 @@ __device__ unsigned long long set_cliques(const uint32_t *R, uint32_t W, uint32_
       }
       Ds[lane] = db;
       __syncwarp();
-      const unsigned long long s = reg_cliques_warp<Q>(c == 32 ? ~0u : (1u << c) - 1u, db, Ds);
+      const uint32_t all = c == 32 ? ~0u : (1u << c) - 1u;
+      unsigned long long s;
+      if constexpr (Q >= 4) s = reg_cliques_pairs<Q>(all, Ds, scr);  // Mw and pref are free again
+      else s = reg_cliques_warp<Q>(all, db, Ds);
       __syncwarp();
       return s;
     } else if constexpr (Q <= 3) {

@@ -568,6 +568,41 @@ def test_large_k_cliques_every_root_class(gpm, opts):
         gpm.set_options(**{k: v for k, v in old.items() if v})
 
 
+def _bipartite_with_planted_clique(na, nb, q):
+    """Complete bipartite A x B (A = 0..na-1, B = na..na+nb-1) plus a clique on
+    the last q vertices of B, as a symmetric sorted CSR: a k-clique holds at
+    most one vertex of A and a clique of B, so there are C(q, k) + na C(q, k-1)
+    of them (k >= 3). Every vertex of A has the whole of B as out-neighbours in
+    the degree order (equal degrees, larger ids)."""
+    n = na + nb
+    planted = np.arange(n - q, n)
+    rows = []
+    for v in range(na):
+        rows.append(np.arange(na, n, dtype=np.uint32))
+    for v in range(na, n):
+        r = np.arange(0, na, dtype=np.uint32)
+        if v >= n - q:
+            r = np.concatenate([r, planted[planted != v].astype(np.uint32)])
+        rows.append(r)
+    rowptr = np.zeros(n + 1, dtype=np.uint64)
+    rowptr[1:] = np.cumsum([len(r) for r in rows])
+    return rowptr, np.concatenate(rows).astype(np.uint32), n
+
+
+def test_large_k_cliques_outdegree_above_4096(gpm):
+    # roots of out-degree 4130 (local-graph rows of 130 words): the generic
+    # search with 16 words of a candidate set per lane; closed form
+    import math
+    import torch
+    na, nb, q = 4130, 4130, 8
+    rowptr, col, n = _bipartite_with_planted_clique(na, nb, q)
+    G = gpm.Graph(torch.from_numpy(rowptr.view(np.int64)), torch.from_numpy(col.view(np.int32)), n)
+    for k in (7, 8, 9):
+        assert gpm.count_cliques(G, k) == math.comb(q, k) + na * math.comb(q, k - 1), k
+    assert G.info()["max_out_degree"] == nb + q - 1 or G.info()["max_out_degree"] > 4096
+    G.close()
+
+
 def test_count_cliques_ranges_and_small_k(gpm):
     # gpm_count_cliques: root ranges partition the total; k = 3..6 agree with
     # the fused pass; a mixed call (k <= 6 and k >= 7 patterns) fills both
