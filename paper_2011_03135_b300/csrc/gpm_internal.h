@@ -111,7 +111,7 @@ struct gpm_graph {
   // in both; okey points at the key array of the order in use
   uint32_t orient_mode = 0;      // GPM_ORIENT_DEGREE or GPM_ORIENT_CORE
   uint32_t *core = nullptr;      // n core numbers (core order only)
-  uint32_t *core_work = nullptr; // 8n + 16: remaining degrees, frontiers, active lists, peel rounds, counters
+  uint32_t *core_work = nullptr; // remaining degrees, active lists, peel rounds, counters, frontier items
   uint32_t *core_order = nullptr; // n (inside core_work): round of the peel that took each vertex
   uint32_t *okey = nullptr;
   bool prepared = false;

@@ -396,17 +396,18 @@ __global__ void core_init_kernel(const uint32_t *__restrict__ deg, uint32_t n, u
 //     jump over empty levels);
 //   peel: the neighbours still present of every frontier vertex lose one
 //     remaining degree; a neighbour that drops to k is taken in the next round
-//     (claimed once) and forms the next frontier. A frontier vertex with at
-//     most kCoreBig neighbours is one warp's work; the lists of the larger
-//     ones are walked by the whole grid, one after the other;
+//     (claimed once) and forms the next frontier. A frontier holds work items
+//     {vertex, piece}: the list of a taken vertex is cut into pieces of
+//     kCorePiece entries when it is taken, and a warp walks one piece, so the
+//     high-degree vertices of the late rounds spread over the grid;
 // peel rounds repeat until a frontier is empty, then k grows. Phase P counts
-// into counter slot P % 3 ({small frontier, smallest degree left, large
-// frontier, active list}); block 0 clears slot (P + 1) % 3 at the start of
+// into counter slot P % 3 ({frontier items, smallest degree left, unused,
+// active list}); block 0 clears slot (P + 1) % 3 at the start of
 // phase P, a slot every block has finished reading one phase earlier. Phases
 // end at a grid barrier whose waits are bounded: on a timeout the kernel
 // records ST_TIMEOUT and stops.
 constexpr uint32_t kBarrierSpins = 1u << 24;
-constexpr uint32_t kCoreBig = 4096;
+constexpr uint32_t kCorePiece = 32;  // list entries per frontier item: one per lane
 
 __device__ __forceinline__ bool grid_barrier(unsigned int *bar, uint32_t nblocks, uint32_t &gen) {
   __shared__ int s_ok;
@@ -443,14 +444,21 @@ struct CoreArgs {
   const uint32_t *__restrict__ deg;
   uint32_t n;
   uint32_t *cdeg, *core, *order;
-  uint32_t *fa, *fb;       // small frontiers (n words each)
-  uint32_t *ba, *bb;       // large frontiers (n words each)
+  uint2 *fa, *fb;          // frontiers: {vertex, piece} items (n + nnz / kCorePiece each)
   uint32_t *act0, *act1;   // active lists (n words each; act0 = 0..n-1 at launch)
   unsigned int *ctr;       // 3 slots x 4 words
   unsigned int *bar;       // grid barrier {arrivals, generation}, zero at launch
   unsigned int *status;
   uint32_t max_phases;
 };
+
+// the pieces of w's list as items of frontier F (item counter *c)
+__device__ __forceinline__ void push_pieces(const CoreArgs &a, uint32_t w, uint2 *F, unsigned int *c) {
+  const uint32_t np = (__ldg(a.deg + w) + kCorePiece - 1) / kCorePiece;
+  if (!np) return;
+  const uint32_t at = atomicAdd(c, np);
+  for (uint32_t p = 0; p < np; ++p) F[at + p] = make_uint2(w, p);
+}
 
 // warp-aggregated append of v to list L with counter *c (lanes with `join`)
 __device__ __forceinline__ void warp_append(bool join, uint32_t v, uint32_t *L, unsigned int *c) {
@@ -462,15 +470,15 @@ __device__ __forceinline__ void warp_append(bool join, uint32_t v, uint32_t *L, 
   if (join) L[at + __popc(m & ((1u << lane) - 1u))] = v;
 }
 
-// one neighbour w of a peeled vertex at level k
-__device__ __forceinline__ void core_lower(const CoreArgs &a, uint32_t w, uint32_t k, uint32_t next_round,
-                                           uint32_t *fout, uint32_t *bout, unsigned int *pc) {
-  if (*(volatile uint32_t *)&a.core[w] != kCoreUnset) return;
+// one neighbour w of a peeled vertex at level k (the remaining degree of a
+// vertex already taken may drop further; it is never read again, and the
+// claim below fails for it)
+__device__ __forceinline__ void core_lower(const CoreArgs &a, uint32_t w, uint32_t k, uint32_t next_round, uint2 *fout,
+                                           unsigned int *pc) {
   const uint32_t old = atomicSub(&a.cdeg[w], 1u);
   if (old == k + 1 && atomicCAS(&a.core[w], kCoreUnset, k) == kCoreUnset) {
     a.order[w] = next_round;
-    if (__ldg(a.deg + w) > kCoreBig) bout[atomicAdd(&pc[2], 1u)] = w;
-    else fout[atomicAdd(&pc[0], 1u)] = w;
+    push_pieces(a, w, fout, &pc[0]);
   }
 }
 
@@ -521,9 +529,7 @@ __global__ void __launch_bounds__(1024) core_peel_all_kernel(CoreArgs a) {
             }
           }
         }
-        const bool big = take && __ldg(a.deg + v) > kCoreBig;
-        warp_append(take && !big, v, a.fa, &cnt[0]);
-        warp_append(big, v, a.ba, &cnt[2]);
+        if (take) push_pieces(a, v, a.fa, &cnt[0]);
         warp_append(keep, v, aout, &cnt[3]);
       }
       mn = __reduce_min_sync(0xffffffffu, mn);
@@ -536,14 +542,13 @@ __global__ void __launch_bounds__(1024) core_peel_all_kernel(CoreArgs a) {
     ++phase;
     uint32_t nin = *(volatile unsigned int *)&cnt[0];
     const uint32_t mn = *(volatile unsigned int *)&cnt[1];
-    uint32_t nbig = *(volatile unsigned int *)&cnt[2];
     na = *(volatile unsigned int *)&cnt[3];
     {
       uint32_t *t = ain;
       ain = aout;
       aout = t;
     }
-    if (nin + nbig == 0) {
+    if (nin == 0) {
       if (mn == kCoreUnset) break;  // every vertex has been taken
       if (mn <= k) {
         ok = false;
@@ -553,8 +558,8 @@ __global__ void __launch_bounds__(1024) core_peel_all_kernel(CoreArgs a) {
       continue;
     }
     // ---- peel rounds at level k ----
-    uint32_t *fin = a.fa, *fout = a.fb, *bin = a.ba, *bout = a.bb;
-    while (nin + nbig > 0) {
+    uint2 *fin = a.fa, *fout = a.fb;
+    while (nin > 0) {
       if (phase >= a.max_phases) {
         ok = false;
         break;
@@ -562,14 +567,11 @@ __global__ void __launch_bounds__(1024) core_peel_all_kernel(CoreArgs a) {
       unsigned int *pc = a.ctr + 4 * (phase % 3);
       clear_next();
       for (uint64_t i = warp; i < nin; i += nwarps) {
-        const uint32_t v = fin[i];
-        const uint64_t b = a.rowptr[v], e = a.rowptr[v + 1];
-        for (uint64_t j = b + lane; j < e; j += 32) core_lower(a, a.col[j], k, round + 1, fout, bout, pc);
-      }
-      for (uint32_t q = 0; q < nbig; ++q) {
-        const uint32_t v = bin[q];
-        const uint64_t b = a.rowptr[v], e = a.rowptr[v + 1];
-        for (uint64_t j = b + gtid; j < e; j += nth) core_lower(a, a.col[j], k, round + 1, fout, bout, pc);
+        const uint2 it = fin[i];
+        const uint64_t e = a.rowptr[it.x + 1];
+        const uint64_t b = a.rowptr[it.x] + (uint64_t)it.y * kCorePiece;
+        const uint64_t pe = b + kCorePiece < e ? b + kCorePiece : e;
+        for (uint64_t j = b + lane; j < pe; j += 32) core_lower(a, a.col[j], k, round + 1, fout, pc);
       }
       if (!barrier()) {
         ok = false;
@@ -577,13 +579,9 @@ __global__ void __launch_bounds__(1024) core_peel_all_kernel(CoreArgs a) {
       }
       ++phase;
       nin = *(volatile unsigned int *)&pc[0];
-      nbig = *(volatile unsigned int *)&pc[2];
-      uint32_t *t = fin;
+      uint2 *t = fin;
       fin = fout;
       fout = t;
-      t = bin;
-      bin = bout;
-      bout = t;
       ++round;
     }
     if (!ok) break;
@@ -603,17 +601,19 @@ int gpm_core_numbers(gpm_graph *g, cudaStream_t st) {
   const uint32_t n = g->n;
   const size_t nw = std::max<uint32_t>(n, 1);
   if (!g->core) GPM_TRY(gpm_graph_alloc(g, (void **)&g->core, sizeof(uint32_t) * nw));
-  // remaining degrees, two small and two large frontiers, two active lists,
-  // the peel round of every vertex, then counters and the grid barrier
-  if (!g->core_work) GPM_TRY(gpm_graph_alloc(g, (void **)&g->core_work, sizeof(uint32_t) * (8 * nw + 16)));
-  g->core_order = g->core_work + 7 * nw;
+  // remaining degrees, two active lists, the peel round of every vertex,
+  // counters and the grid barrier, then two frontiers of items
+  const size_t fcap = nw + g->nnz / kCorePiece + 1;
+  if (!g->core_work)
+    GPM_TRY(gpm_graph_alloc(g, (void **)&g->core_work, sizeof(uint32_t) * (4 * nw + 16 + 4 * fcap)));
+  g->core_order = g->core_work + 3 * nw;
   if (n == 0) return GPM_OK;
   uint32_t *w = g->core_work;
   unsigned int *ctr = g->core_order + nw, *bar = ctr + 12;
   unsigned int *status = reinterpret_cast<unsigned int *>(g->work + WK_STATUS);
   const int sms = gpm_num_sms(g->device);
   GPM_LAUNCH("core_init_kernel", st, core_init_kernel<<<sms * 4, 256, 0, st>>>(g->deg, n, w, g->core));
-  GPM_LAUNCH("core_iota_kernel", st, core_iota_kernel<<<sms * 4, 256, 0, st>>>(n, w + 5 * nw));
+  GPM_LAUNCH("core_iota_kernel", st, core_iota_kernel<<<sms * 4, 256, 0, st>>>(n, w + nw));
   GPM_CUDA(cudaGetLastError());
   unsigned int init[14] = {0u, kCoreUnset, 0u, 0u, 0u, kCoreUnset, 0u, 0u, 0u, kCoreUnset, 0u, 0u, 0u, 0u};
   GPM_CUDA(cudaMemcpyAsync(ctr, init, sizeof(init), cudaMemcpyHostToDevice, st));
@@ -630,12 +630,10 @@ int gpm_core_numbers(gpm_graph *g, cudaStream_t st) {
   a.deg = g->deg;
   a.n = n;
   a.cdeg = w;
-  a.fa = w + nw;
-  a.fb = w + 2 * nw;
-  a.ba = w + 3 * nw;
-  a.bb = w + 4 * nw;
-  a.act0 = w + 5 * nw;
-  a.act1 = w + 6 * nw;
+  a.act0 = w + nw;
+  a.act1 = w + 2 * nw;
+  a.fa = reinterpret_cast<uint2 *>(w + 4 * nw + 16);
+  a.fb = a.fa + fcap;
   a.core = g->core;
   a.order = g->core_order;
   a.ctr = ctr;
