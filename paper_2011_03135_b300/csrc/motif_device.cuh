@@ -45,34 +45,59 @@ __device__ __forceinline__ unsigned long long c4_root_warp(const uint64_t *__res
   const uint32_t d0 = deg[v0];
   const uint64_t b0 = rowptr[v0], e0 = rowptr[v0 + 1];
   for (uint64_t cb = b0; cb < e0; cb += 32) {
+    // up to 32 neighbours x of v0 at a time; the lists of those before v0
+    // are walked as one concatenated run, 32 entries per step, each lane
+    // finding its entry's list by a binary search (over the lanes, by
+    // shuffles) of the inclusive scan of the list lengths
     const uint64_t ex = cb + lane;
-    uint32_t x = 0;
-    bool ok = false;
+    uint32_t len = 0;
+    uint64_t xs = 0;
     if (ex < e0) {
-      x = col[ex];
-      ok = precedes(nbr_deg(edeg, deg, ex, x), x, d0, v0);
+      const uint32_t x = col[ex];
+      if (precedes(nbr_deg(edeg, deg, ex, x), x, d0, v0)) {
+        xs = rowptr[x];
+        len = (uint32_t)(rowptr[x + 1] - xs);
+      }
     }
-    uint32_t mask = __ballot_sync(0xffffffffu, ok);
-    while (mask) {
-      const int src = __ffs(mask) - 1;
-      mask &= mask - 1;
-      const uint32_t xx = __shfl_sync(0xffffffffu, x, src);
-      for (uint64_t f = rowptr[xx] + lane; f < rowptr[xx + 1]; f += 32) {
-        const uint32_t w = col[f];
-        if (!precedes(nbr_deg(edeg, deg, f, w), w, d0, v0)) continue;
-        uint32_t h = (w * 2654435761u) >> 22;  // 10 bits
-        uint32_t probes = 0;
-        for (;;) {
-          const uint32_t k = atomicCAS(&keys[h], kC4Empty, w);
-          if (k == kC4Empty || k == w) {
-            atomicAdd(&cnt[h], 1u);
-            break;
-          }
-          h = (h + 1) & (kC4HashSlots - 1);
-          if (++probes >= kC4HashSlots) {
-            overflow = true;
-            break;
-          }
+    uint32_t incl = len;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (uint32_t)o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    for (uint32_t fb = 0; fb < total; fb += 32) {
+      const uint32_t f = fb + lane;
+      // first lane whose inclusive sum exceeds f (lane 31 for every f < total:
+      // five halvings of [0, 31])
+      uint32_t lo = 0, hi = 31;
+#pragma unroll
+      for (int step = 0; step < 5; ++step) {
+        const uint32_t mid = (lo + hi) >> 1;
+        const uint32_t v = __shfl_sync(0xffffffffu, incl, mid);
+        if (lo < hi) {
+          if (v <= f) lo = mid + 1;
+          else hi = mid;
+        }
+      }
+      const uint32_t src = lo;
+      const uint64_t st = __shfl_sync(0xffffffffu, xs, src);
+      const uint32_t before = __shfl_sync(0xffffffffu, incl - len, src);
+      if (f >= total) continue;
+      const uint64_t e = st + (f - before);
+      const uint32_t w = col[e];
+      if (!precedes(nbr_deg(edeg, deg, e, w), w, d0, v0)) continue;
+      uint32_t h = (w * 2654435761u) >> 22;  // 10 bits
+      uint32_t probes = 0;
+      for (;;) {
+        const uint32_t k = atomicCAS(&keys[h], kC4Empty, w);
+        if (k == kC4Empty || k == w) {
+          atomicAdd(&cnt[h], 1u);
+          break;
+        }
+        h = (h + 1) & (kC4HashSlots - 1);
+        if (++probes >= kC4HashSlots) {
+          overflow = true;
+          break;
         }
       }
     }
