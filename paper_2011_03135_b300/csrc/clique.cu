@@ -51,6 +51,7 @@ struct LGArgs {
   uint32_t *pool;           // global-memory slots (XL class)
   uint64_t slot_words;
   uint32_t slices;          // CTAs per root (k >= 7: a root's units are split over them)
+  unsigned int *ucount;     // k >= 7: per-task unit counters shared by a root's CTAs (zero at launch)
   unsigned int *status;
 };
 
@@ -136,7 +137,8 @@ __global__ void __launch_bounds__(THREADS) lg_cta_kernel(LGArgs a, uint32_t maxd
     const uint32_t d = (uint32_t)(a.drow[u + 1] - a.drow[u]);
     if (d < 2 || d > maxd) continue;
     gpm_dev::lg_root_cta<G, KMAX, SCATTER, kNwl>(a.drow, a.dcol, a.t_edge, u, maxd, a.W, base, a3, a4, a5, a6,
-                                                 nest, big_cap, a.deg, wcap, gen, task % a.slices, a.slices);
+                                                 nest, big_cap, a.deg, wcap, gen, task % a.slices, a.slices,
+                                                 a.ucount ? a.ucount + task / a.slices : nullptr);
   }
   flush_acc(a, a3, a4, a5, a6, KMAX);
 }
@@ -246,6 +248,7 @@ int launch_all(gpm_graph *g, LGArgs base, unsigned int *queues, cudaStream_t st)
       // one warp would be the last to finish)
       a.W = (md + 31) / 32;
       a.slices = 2;  // lighter roots than the CTA class: two CTAs each (measured best of 2, 4, 8, 16)
+      if (base.ucount) a.ucount = base.ucount + g->cls_begin[CLS_WARP];
       GPM_TRY((launch_cta<32, KMAX, SCATTER, false>(a, md, 0, dev, st, (size_t)(max_smem_optin(dev) / 2 - 1024),
                                                     "lg_cta_mid")));
     } else if (a.ntasks) {
@@ -263,6 +266,7 @@ int launch_all(gpm_graph *g, LGArgs base, unsigned int *queues, cudaStream_t st)
     a.tasks = g->tasks + b0;
     a.ntasks = b1 - b0;
     a.queue = queues + (part == 0 ? 2 : 6);
+    if (base.ucount) a.ucount = base.ucount + b0;
     const uint32_t md = part == 0 ? g->cls_maxdeg[CLS_CTA] : g->cta_lo_maxd;
     a.W = (md + 31) / 32;
     const size_t limit = part == 0 ? 0 : (size_t)(max_smem_optin(dev) / 2 - 1024);
@@ -285,6 +289,7 @@ int launch_all(gpm_graph *g, LGArgs base, unsigned int *queues, cudaStream_t st)
     a.tasks = g->tasks + g->cls_begin[CLS_XL];
     a.ntasks = g->cls_begin[CLS_XL + 1] - g->cls_begin[CLS_XL];
     a.queue = queues + 3;
+    if (base.ucount) a.ucount = base.ucount + g->cls_begin[CLS_XL];
     const uint32_t md = g->cls_maxdeg[CLS_XL];
     if (a.ntasks) {
       a.W = (md + 31) / 32;
@@ -333,6 +338,13 @@ int gpm_launch_cliques(gpm_graph *g, int kmax, bool scatter, uint32_t root_lo, u
   GPM_CUDA(cudaMemsetAsync(queues, 0, 8 * sizeof(unsigned int), st));
   LGArgs a{};
   a.slices = kmax >= 7 ? 4u : 1u;
+  if (kmax >= 7) {
+    // one unit counter per root task of the CTA classes, shared by the root's CTAs
+    const size_t words = std::max<uint32_t>(g->n, 1);
+    if (!g->gen_ucount) GPM_TRY(gpm_graph_alloc(g, (void **)&g->gen_ucount, sizeof(unsigned int) * words));
+    GPM_CUDA(cudaMemsetAsync(g->gen_ucount, 0, sizeof(unsigned int) * words, st));
+    a.ucount = g->gen_ucount;
+  }
   a.drow = g->drow;
   a.dcol = g->dcol;
   a.deg = g->okey ? g->okey : g->deg;  // the key of the orientation order

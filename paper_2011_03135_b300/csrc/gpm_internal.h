@@ -141,6 +141,7 @@ struct gpm_graph {
   // scratch pools, grown on demand
   uint32_t *t_edge = nullptr;   // per-arc triangle counts (m)
   uint32_t *xl_pool = nullptr;  // global-memory bitmaps for CLS_XL roots
+  unsigned int *gen_ucount = nullptr;  // k >= 7: unit counter per root task (n words)
   size_t xl_pool_bytes = 0;
   uint32_t *tally_pool = nullptr;  // 4-cycle wedge tallies, n words per slot
   size_t tally_slots = 0;

@@ -900,25 +900,27 @@ __device__ unsigned long long set_cliques(const uint32_t *R, uint32_t W, uint32_
 }
 
 // k-cliques (KMAX = k >= 7) through the root of the CTA's local graph. The
-// work is cut into (row i, word w) units, claimed dynamically by warps (ctr: a
-// shared counter) in word-major order, so that the rows of a heavy local
-// graph spread over the CTA: a unit takes each member a in word w of R_i and
-// counts the (k-3)-cliques among R_i & R_a. A root may be split over nslices
-// CTAs (each builds the local graph and takes the units congruent to its
-// slice). Every thread of the CTA calls it.
+// work is cut into (row i, word w) units, claimed dynamically by warps in
+// word-major order, so that the rows of a heavy local graph spread over the
+// CTA: a unit takes each member a in word w of R_i and counts the
+// (k-3)-cliques among R_i & R_a. A root may be split over nslices CTAs, each
+// building the local graph: with a global counter gctr (zero before the
+// launch) their warps claim the root's units from it, so the CTAs of a root
+// finish together; without it (ctr: a shared counter) each takes the units
+// congruent to its slice. Every thread of the CTA calls it.
 template <int KMAX, int NWL>
 __device__ __forceinline__ void rows_generic_cta(const uint32_t *R, uint32_t d, uint32_t W, uint32_t rs,
                                                  uint32_t *ctr, uint32_t *scr, bool tri, unsigned long long &ak,
-                                                 uint32_t slice, uint32_t nslices) {
+                                                 uint32_t slice, uint32_t nslices, unsigned int *gctr = nullptr) {
   const uint32_t lane = threadIdx.x & 31;
   if (threadIdx.x == 0) *ctr = 0;
   __syncthreads();
   const uint32_t units = d * W;
   for (;;) {
     uint32_t q = 0;
-    if (lane == 0) q = atomicAdd(ctr, 1u);
+    if (lane == 0) q = atomicAdd(gctr ? gctr : ctr, 1u);
     q = __shfl_sync(0xffffffffu, q, 0);
-    const uint32_t u = q * nslices + slice;  // this CTA's share of the root: units = slice mod nslices
+    const uint32_t u = gctr ? q : q * nslices + slice;
     if (u >= units) break;
     const uint32_t i = u % d, w = u / d;
     const uint32_t *ri = R + (size_t)i * rs;
@@ -1011,7 +1013,8 @@ __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, c
                                             unsigned long long &a3, unsigned long long &a4, unsigned long long &a5,
                                             unsigned long long &a6, uint32_t *nest = nullptr, uint32_t big_cap = 0,
                                             const uint32_t *__restrict__ deg = nullptr, uint32_t wcap = kNestWarpC,
-                                            uint32_t *gen = nullptr, uint32_t slice = 0, uint32_t nslices = 1) {
+                                            uint32_t *gen = nullptr, uint32_t slice = 0, uint32_t nslices = 1,
+                                            unsigned int *gctr = nullptr) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
   uint64_t *xb = reinterpret_cast<uint64_t *>(base);
   uint32_t *L = base + 2 * (size_t)maxd;
@@ -1081,7 +1084,7 @@ __device__ __forceinline__ void lg_root_cta(const uint64_t *__restrict__ drow, c
     // is free again once the rows are built); a6 carries the k-clique count
     uint32_t *g = gen ? gen : nest + 4 + 2 * (size_t)maxd;
     rows_generic_cta<KMAX, NWL>(R, d, w_used, rs, g, g + 4 + (size_t)(tid >> 5) * gen_warp_words(NWL), tri, a6,
-                                slice, nslices);
+                                slice, nslices, gctr);
   } else if (KMAX >= 5 && nest != nullptr && w_used <= 32) {
     enumerate_nested_cta<(KMAX >= 6)>(R, d, w_used, rs, nest, maxd, big_cap, a4, a5, a6, tri, wcap);
   } else if (KMAX >= 4) {
