@@ -156,12 +156,12 @@ def clique_pass_bytes(g, opts):
 # csrc/lg_device.cuh + csrc/clique.cu); a stale entry is ignored.
 NCU_COUNTERS = {
     "clique-rmat21": {
-        "lg_cta_hi": {"digest": "50d2c1b44237a19b", "inst_per_launch": 151171049978,
-                      "dram_bytes_per_launch": 28339712 + 1536, "ncu_ms": 184.577},
+        "lg_cta_hi": {"digest": "f9ad6174a8f66f41", "inst_per_launch": 151170570623,
+                      "dram_bytes_per_launch": 28330752 + 2048, "ncu_ms": 184.623},
     },
     "clique6-rmat20": {
-        "lg_cta_hi": {"digest": "50d2c1b44237a19b", "inst_per_step": 1638179278559,
-                      "dram_bytes_per_step": 13067008, "ncu_ms": 1675.990},
+        "lg_cta_hi": {"digest": "f9ad6174a8f66f41", "inst_per_step": 1638179812823,
+                      "dram_bytes_per_step": 13044480, "ncu_ms": 1678.119},
     },
     # every 4-cycle kernel launch of one step (c4_bound x 2, 42 pull passes of
     # c4_pull_mark x 2, c4_pull, c4_pull_tiny, c4_pull_rows; c4_bucket,
@@ -184,8 +184,8 @@ NCU_COUNTERS = {
     },
     # three launches per step (k = 7, 8, 9), summed
     "clique789-cl1m": {
-        "lg_cta_lo": {"digest": "50d2c1b44237a19b", "inst_per_step": 17979133968 + 36071962599 + 85406719515,
-                      "dram_bytes_per_step": 6542848 + 7029248 + 6898432, "ncu_ms": 27.420 + 66.192 + 185.470},
+        "lg_cta_lo": {"digest": "f9ad6174a8f66f41", "inst_per_step": 18020016326 + 36222245783 + 85370439759,
+                      "dram_bytes_per_step": 6797312 + 6560256 + 6670592, "ncu_ms": 27.433 + 64.626 + 179.485},
     },
 }
 
