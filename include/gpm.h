@@ -275,8 +275,10 @@ int gpm_count_roots(gpm_graph_t g, const gpm_pattern_t *pats, uint32_t npat, uin
  * search of Section 5 ("search on local graph"): for k <= 6 the fused pass of
  * gpm_count; for k >= 7 the generic search, which keeps the shrinking
  * candidate set as a bitmap over the root's out-neighbours and switches to
- * per-lane register graphs once it has at most 32 members. k >= 7 needs root
- * out-degrees <= 4096 (GPM_E_UNSUPPORTED otherwise).
+ * register graphs once it has at most 32 members (their (member, successor)
+ * pairs spread over the lanes). k >= 7 needs root out-degrees <= 16384
+ * (GPM_E_UNSUPPORTED otherwise; every out-degree of the degree order is at
+ * most sqrt(2m), so graphs of up to 134 M edges always qualify).
  *   *count : host uint64
  * Errors: GPM_E_INVALID_ARG for k outside 3..9, a bad range or a null
  * pointer. The count is accumulated in uint64 (exact below 2^64).
