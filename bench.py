@@ -168,7 +168,7 @@ NCU_COUNTERS = {
     # c4_small; the per-graph tables excluded), summed;
     # profiles/c4_sl_chunglu4m_dram.md; digest of motif.cu + motif_device.cuh + c4_pull.cu
     "sl-chunglu4m": {
-        "c4": {"digest": "ff57838d2bec4ac7", "dram_bytes_per_step": 85433207296},
+        "c4": {"digest": "6dc525e7bef88559", "dram_bytes_per_step": 85421231872},
     },
     # profiles/enum_k5_er1m_counters.md; digest of enumerate.cu
     "motif5-er1m": {

@@ -87,18 +87,44 @@ __global__ void c4_bound_kernel(const uint64_t *__restrict__ rowptr, const uint3
                                 uint32_t hub_bound, uint32_t *__restrict__ counts, uint32_t *__restrict__ tasks,
                                 uint32_t *__restrict__ cursors, int fill, uint32_t *__restrict__ bvals = nullptr,
                                 uint32_t begin2 = 0) {
-  // a warp takes 32 consecutive vertices, one at a time (lanes over the
+  // a warp takes 32 consecutive vertices: lane k sums the list of vertex k
+  // on its own when it has at most kBoundLane entries (four loads in flight),
+  // and the warp then walks the longer lists one at a time (lanes over the
   // neighbours); lane k keeps vertex k's class, and the 32 outcomes are
   // counted / placed with one atomic per class
+  constexpr uint32_t kBoundLane = 64;
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t g0 = warp * 32; g0 < n; g0 += nwarps * 32) {
     int my_c = -1;
     uint32_t my_b = 0;
-    for (uint32_t k = 0; k < 32 && g0 + k < n; ++k) {
+    const uint64_t vl = g0 + lane;
+    const bool on = vl < n;
+    const uint32_t dl = on ? deg[vl] : 0u;
+    unsigned long long bl = 0;
+    if (on && dl <= kBoundLane) {
+      const uint64_t rb = rowptr[vl];
+      uint32_t i = 0;
+      for (; i + 4 <= dl; i += 4) {
+        const uint32_t x0 = col[rb + i], x1 = col[rb + i + 1], x2 = col[rb + i + 2], x3 = col[rb + i + 3];
+        const uint32_t d0 = edeg[rb + i], d1 = edeg[rb + i + 1], d2 = edeg[rb + i + 2], d3 = edeg[rb + i + 3];
+        if (precedes(d0, x0, dl, (uint32_t)vl)) bl += d0;
+        if (precedes(d1, x1, dl, (uint32_t)vl)) bl += d1;
+        if (precedes(d2, x2, dl, (uint32_t)vl)) bl += d2;
+        if (precedes(d3, x3, dl, (uint32_t)vl)) bl += d3;
+      }
+      for (; i < dl; ++i) {
+        const uint32_t x = col[rb + i], dx = edeg[rb + i];
+        if (precedes(dx, x, dl, (uint32_t)vl)) bl += dx;
+      }
+    }
+    uint32_t longm = __ballot_sync(0xffffffffu, on && dl > kBoundLane);
+    while (longm) {
+      const uint32_t k = __ffs(longm) - 1;
+      longm &= longm - 1;
       const uint64_t v = g0 + k;
-      const uint32_t dv = deg[v];
+      const uint32_t dv = __shfl_sync(0xffffffffu, dl, k);
       unsigned long long b = 0;
       for (uint64_t e = rowptr[v] + lane; e < rowptr[v + 1]; e += 32) {
         const uint32_t x = col[e];
@@ -106,10 +132,11 @@ __global__ void c4_bound_kernel(const uint64_t *__restrict__ rowptr, const uint3
         if (precedes(dx, x, dv, (uint32_t)v)) b += dx;
       }
       b = __shfl_sync(0xffffffffu, warp_sum(b), 0);
-      if (lane == k && b >= 3) {  // a cycle needs two wedges, each scanning v0 itself plus w
-        my_c = (b <= kSmallBound) ? 0 : (b <= hub_bound ? 1 : 2);
-        my_b = (uint32_t)(b > 0xffffffffull ? 0xffffffffull : b);
-      }
+      if (lane == k) bl = b;
+    }
+    if (on && bl >= 3) {  // a cycle needs two wedges, each scanning v0 itself plus w
+      my_c = (bl <= kSmallBound) ? 0 : (bl <= hub_bound ? 1 : 2);
+      my_b = (uint32_t)(bl > 0xffffffffull ? 0xffffffffull : bl);
     }
     for (int c = 0; c < 3; ++c) {
       const uint32_t m = __ballot_sync(0xffffffffu, my_c == c);
