@@ -168,7 +168,7 @@ NCU_COUNTERS = {
     # c4_small; the per-graph tables excluded), summed;
     # profiles/c4_sl_chunglu4m_dram.md; digest of motif.cu + motif_device.cuh + c4_pull.cu
     "sl-chunglu4m": {
-        "c4": {"digest": "6dc525e7bef88559", "dram_bytes_per_step": 85421231872},
+        "c4": {"digest": "639b5648dd4e8f72", "dram_bytes_per_step": 89739834880},
     },
     # profiles/enum_k5_er1m_counters.md; digest of enumerate.cu
     "motif5-er1m": {

@@ -92,17 +92,24 @@ __global__ void __launch_bounds__(256) lg_warp_kernel(LGArgs a) {
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t *base = smem + (size_t)wid * kStride;
   unsigned long long a3 = 0, a4 = 0, a5 = 0, a6 = 0;
+  // roots are claimed kClaim at a time: the warp classes hold most of the
+  // vertices, and one atomic per root on a single counter would serialise
+  // the warps
+  constexpr uint32_t kClaim = 4;
   for (;;) {
-    uint32_t task = 0;
-    if (lane == 0) task = atomicAdd(a.queue, 1u);
-    task = __shfl_sync(0xffffffffu, task, 0);
-    if (task >= a.ntasks) break;
-    const uint32_t u = a.tasks[task];
-    if (u < a.root_lo || u >= a.root_hi) continue;
-    const uint32_t d = (uint32_t)(a.drow[u + 1] - a.drow[u]);
-    if (d < 2 || d > MAXD) continue;
-    gpm_dev::lg_root_warp<MAXD, G, KMAX, SCATTER>(a.drow, a.dcol, a.t_edge, u, base, a3, a4, a5, a6,
-                                                  base + gpm_dev::warp_words(MAXD, SCATTER));
+    uint32_t first = 0;
+    if (lane == 0) first = atomicAdd(a.queue, kClaim);
+    first = __shfl_sync(0xffffffffu, first, 0);
+    if (first >= a.ntasks) break;
+    const uint32_t last = first + kClaim < a.ntasks ? first + kClaim : a.ntasks;
+    for (uint32_t task = first; task < last; ++task) {
+      const uint32_t u = a.tasks[task];
+      if (u < a.root_lo || u >= a.root_hi) continue;
+      const uint32_t d = (uint32_t)(a.drow[u + 1] - a.drow[u]);
+      if (d < 2 || d > MAXD) continue;
+      gpm_dev::lg_root_warp<MAXD, G, KMAX, SCATTER>(a.drow, a.dcol, a.t_edge, u, base, a3, a4, a5, a6,
+                                                    base + gpm_dev::warp_words(MAXD, SCATTER));
+    }
   }
   flush_acc(a, a3, a4, a5, a6, KMAX);
 }

@@ -192,14 +192,21 @@ __global__ void __launch_bounds__(256) c4_small_kernel(C4Args a) {
   uint32_t *cnt = keys + kHashSlots;
   unsigned long long acc = 0;
   bool overflow = false;
+  // roots are claimed 8 at a time: most roots of this class are a few
+  // microseconds of work, and one atomic per root on a single counter would
+  // serialise the warps
+  constexpr uint32_t kClaim = 8;
   for (;;) {
-    uint32_t task = 0;
-    if (lane == 0) task = atomicAdd(a.queue, 1u);
-    task = __shfl_sync(0xffffffffu, task, 0);
-    if (task >= a.ntasks) break;
-    const uint32_t v0 = a.tasks[task];
-    if (v0 < a.root_lo || v0 >= a.root_hi) continue;
-    acc += gpm_dev::c4_root_warp(a.rowptr, a.col, a.deg, a.edeg, v0, keys, cnt, overflow);
+    uint32_t first = 0;
+    if (lane == 0) first = atomicAdd(a.queue, kClaim);
+    first = __shfl_sync(0xffffffffu, first, 0);
+    if (first >= a.ntasks) break;
+    const uint32_t last = first + kClaim < a.ntasks ? first + kClaim : a.ntasks;
+    for (uint32_t task = first; task < last; ++task) {
+      const uint32_t v0 = a.tasks[task];
+      if (v0 < a.root_lo || v0 >= a.root_hi) continue;
+      acc += gpm_dev::c4_root_warp(a.rowptr, a.col, a.deg, a.edeg, v0, keys, cnt, overflow);
+    }
   }
   bool carry = false;
   acc = warp_sum_checked(acc, carry);
@@ -465,12 +472,16 @@ __global__ void __launch_bounds__(kHubThreads) c4_hub_kernel(const uint64_t *__r
   }
 }
 
-// one CTA per large root, bucketed aggregation (buffer slot per CTA); roots
-// whose wedge bound is at most 3/4 of kC4DirectSlots are counted in one
-// shared-memory table instead (the space of the bucket tables)
+// one CTA per large root, bucketed aggregation (buffer slot per CTA) with
+// tables of kC4PlainTable slots per warp, so that three CTAs fit an SM
+// (roots above c4_bucket_narrow_bound<kC4PlainTable>() take wider tables in
+// half of the warps); roots whose wedge bound is at most 3/4 of
+// kC4DirectSlots are counted in one shared-memory table instead (the space of
+// the bucket tables)
 constexpr int kC4BucketThreads = 512;
+constexpr uint32_t kC4PlainTable = 256;
 constexpr uint32_t kC4DirectSlots =
-    (gpm_dev::c4_bucket_smem_words(kC4BucketThreads / 32) - (2 * gpm_dev::kC4MaxBuckets + 4)) / 2;
+    (gpm_dev::c4_bucket_smem_words<kC4PlainTable>(kC4BucketThreads / 32) - (2 * gpm_dev::kC4MaxBuckets + 4)) / 2;
 static_assert((kC4DirectSlots & (kC4DirectSlots - 1)) == 0, "direct table slots: a power of two");
 __global__ void __launch_bounds__(kC4BucketThreads) c4_bucket_kernel(C4Args a, uint64_t slot_words) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -489,8 +500,8 @@ __global__ void __launch_bounds__(kC4BucketThreads) c4_bucket_kernel(C4Args a, u
     if (task >= a.ntasks) break;
     const uint32_t v0 = a.tasks[task];
     if (v0 < a.root_lo || v0 >= a.root_hi) continue;
-    acc += gpm_dev::c4_root_bucketed(a.rowptr, a.col, a.deg, a.edeg, v0, buf, buf + slot_words / 2, smem, s_x, &s_cnt,
-                                     overflow, s_pre, s_rp, kC4DirectSlots);
+    acc += gpm_dev::c4_root_bucketed<kC4PlainTable>(a.rowptr, a.col, a.deg, a.edeg, v0, buf, buf + slot_words / 2,
+                                                    smem, s_x, &s_cnt, overflow, s_pre, s_rp, kC4DirectSlots);
   }
   bool carry = false;
   acc = warp_sum_checked(acc, carry);
@@ -978,7 +989,10 @@ static int ensure_c4_roff(gpm_graph *g, uint32_t width, cudaStream_t st) {
 // order of decreasing wedge bound, 128 per pass.
 static int ensure_c4_plain(gpm_graph *g, cudaStream_t st) {
   const uint32_t pull = std::max<uint32_t>(gpm_tune().c4_pull_bound, kSmallBound);
-  const uint32_t bound = std::min<uint32_t>(std::max<uint32_t>(gpm_tune().c4_range_bound, kSmallBound), pull);
+  // the bucketed class takes bounds up to kC4BucketMaxBound; larger roots
+  // below the pull bound become range items
+  const uint32_t bound = std::min<uint32_t>(
+      std::min<uint32_t>(std::max<uint32_t>(gpm_tune().c4_range_bound, kSmallBound), pull), gpm_dev::kC4BucketMaxBound);
   const uint32_t width = gpm_tune().c4_range_width;
   if (g->c4p_ready && g->c4p_bound == bound && g->c4p_pull == pull && g->c4p_width == width) return GPM_OK;
   GPM_TRY(ensure_edeg(g, st));
@@ -1074,7 +1088,7 @@ static int launch_c4_bucketed(gpm_graph *g, const C4Args &a, const uint32_t *tas
   b.tasks = tasks;
   b.ntasks = ntasks;
   b.queue = queue;
-  const size_t smem = (size_t)gpm_dev::c4_bucket_smem_words(kC4BucketThreads / 32) * 4;
+  const size_t smem = (size_t)gpm_dev::c4_bucket_smem_words<kC4PlainTable>(kC4BucketThreads / 32) * 4;
   GPM_CUDA(cudaFuncSetAttribute(c4_bucket_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   GPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c4_bucket_kernel, kC4BucketThreads, smem));

@@ -37,13 +37,22 @@ __device__ __forceinline__ unsigned long long c4_root_warp(const uint64_t *__res
                                                            const uint32_t *__restrict__ edeg, uint32_t v0,
                                                            uint32_t *keys, uint32_t *cnt, bool &overflow) {
   const uint32_t lane = threadIdx.x & 31;
-  for (uint32_t i = lane; i < kC4HashSlots; i += 32) {
-    keys[i] = kC4Empty;
-    cnt[i] = 0;
-  }
-  __syncwarp();
   const uint32_t d0 = deg[v0];
   const uint64_t b0 = rowptr[v0], e0 = rowptr[v0 + 1];
+  // a root with at most 32 neighbours has at most its one chunk's total of
+  // wedge ends: its table is the smallest power of two >= twice that (32 ..
+  // kC4HashSlots slots), cleared and summed at that size; larger roots use
+  // every slot
+  uint32_t bits = 10;  // log2(kC4HashSlots)
+  bool cleared = false;
+  if (e0 - b0 > 32) {
+    for (uint32_t i = lane; i < kC4HashSlots; i += 32) {
+      keys[i] = kC4Empty;
+      cnt[i] = 0;
+    }
+    __syncwarp();
+    cleared = true;
+  }
   for (uint64_t cb = b0; cb < e0; cb += 32) {
     // up to 32 neighbours x of v0 at a time; the lists of those before v0
     // are walked as one concatenated run, 32 entries per step, each lane
@@ -65,6 +74,17 @@ __device__ __forceinline__ unsigned long long c4_root_warp(const uint64_t *__res
       if (lane >= (uint32_t)o) incl += y;
     }
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (!cleared) {
+      bits = 5;
+      while (bits < 10 && (1u << bits) < 2 * total) ++bits;
+      for (uint32_t i = lane; i < (1u << bits); i += 32) {
+        keys[i] = kC4Empty;
+        cnt[i] = 0;
+      }
+      __syncwarp();
+      cleared = true;
+    }
+    const uint32_t tmask = (1u << bits) - 1;
     for (uint32_t fb = 0; fb < total; fb += 32) {
       const uint32_t f = fb + lane;
       // first lane whose inclusive sum exceeds f (lane 31 for every f < total:
@@ -86,7 +106,7 @@ __device__ __forceinline__ unsigned long long c4_root_warp(const uint64_t *__res
       const uint64_t e = st + (f - before);
       const uint32_t w = col[e];
       if (!precedes(nbr_deg(edeg, deg, e, w), w, d0, v0)) continue;
-      uint32_t h = (w * 2654435761u) >> 22;  // 10 bits
+      uint32_t h = (w * 2654435761u) >> (32 - bits);
       uint32_t probes = 0;
       for (;;) {
         const uint32_t k = atomicCAS(&keys[h], kC4Empty, w);
@@ -94,8 +114,8 @@ __device__ __forceinline__ unsigned long long c4_root_warp(const uint64_t *__res
           atomicAdd(&cnt[h], 1u);
           break;
         }
-        h = (h + 1) & (kC4HashSlots - 1);
-        if (++probes >= kC4HashSlots) {
+        h = (h + 1) & tmask;
+        if (++probes > tmask) {
           overflow = true;
           break;
         }
@@ -104,9 +124,11 @@ __device__ __forceinline__ unsigned long long c4_root_warp(const uint64_t *__res
   }
   __syncwarp();
   unsigned long long acc = 0;
-  for (uint32_t i = lane; i < kC4HashSlots; i += 32) {
-    const unsigned long long c = cnt[i];
-    acc += c * (c - 1) / 2;
+  if (cleared) {
+    for (uint32_t i = lane; i < (1u << bits); i += 32) {
+      const unsigned long long c = cnt[i];
+      acc += c * (c - (c > 0)) / 2;
+    }
   }
   __syncwarp();
   return acc;
@@ -179,9 +201,16 @@ __device__ __forceinline__ uint32_t c4_bucket_hash(uint32_t w) { return (w * 0x9
 // slot of w in a table of 2^bits slots
 __device__ __forceinline__ uint32_t c4_slot_hash(uint32_t w, uint32_t bits) { return (w * 0x85EBCA77u) >> (32 - bits); }
 
-// shared memory words for c4_root_bucketed with nwarps warps
+// shared memory words for c4_root_bucketed<TABLE> with nwarps warps
+template <uint32_t TABLE = kC4BucketTable>
 __host__ __device__ constexpr uint32_t c4_bucket_smem_words(uint32_t nwarps) {
-  return 2 * kC4MaxBuckets + 4 + nwarps * 2 * kC4BucketTable;
+  return 2 * kC4MaxBuckets + 4 + nwarps * 2 * TABLE;
+}
+// largest wedge bound c4_root_bucketed<TABLE> takes with one table of TABLE
+// slots per warp (buckets of TABLE / 4 entries on average, at most 2x that)
+template <uint32_t TABLE>
+__host__ __device__ constexpr uint32_t c4_bucket_narrow_bound() {
+  return kC4MaxBuckets * 2 * (TABLE / 4);
 }
 
 // words of one CTA's bucket buffer (lin, then buf) for wedge bounds <= maxb
@@ -286,8 +315,14 @@ __device__ __forceinline__ void c4_table_add(uint32_t *keys, uint32_t *vals, uin
 // v0 - x - w appends every wedge end to `lin` (warp-aggregated) and counts it
 // in its hash bucket; a streaming pass then scatters `lin` into `buf` by
 // bucket. lin and buf hold at least the root's wedge bound entries each;
-// sm = c4_bucket_smem_words(blockDim.x / 32) words of shared memory; s_x holds
-// blockDim.x words. Every thread must call it; returns this thread's part.
+// sm = c4_bucket_smem_words<TABLE>(blockDim.x / 32) words of shared memory;
+// s_x holds blockDim.x words. Each warp aggregates buckets in a table of
+// TABLE slots; a root whose bound exceeds c4_bucket_narrow_bound<TABLE>() uses
+// tables of 2 TABLE slots (two warps' space) in half of the warps, so every
+// TABLE takes bounds up to c4_bucket_narrow_bound<2 TABLE>() (up to
+// kC4BucketMaxBound for TABLE >= kC4BucketTable / 2). Every thread must call
+// it; returns this thread's part.
+template <uint32_t TABLE = kC4BucketTable>
 __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *__restrict__ rowptr,
                                                                const uint32_t *__restrict__ col,
                                                                const uint32_t *__restrict__ deg,
@@ -300,8 +335,7 @@ __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *_
   uint32_t *bcnt = sm;                       // [kC4MaxBuckets]: counts, then write cursors
   uint32_t *boff = sm + kC4MaxBuckets;       // [kC4MaxBuckets + 1]
   uint32_t *ctl = boff + kC4MaxBuckets + 1;  // [0] bound, [1] next bucket, [2] wedges in lin
-  uint32_t *keys = sm + 2 * kC4MaxBuckets + 4 + (size_t)wid * 2 * kC4BucketTable;
-  uint32_t *vals = keys + kC4BucketTable;
+  uint32_t *const tables = sm + 2 * kC4MaxBuckets + 4;
   const uint32_t d0 = deg[v0];
   const uint64_t b0 = rowptr[v0], e0 = rowptr[v0 + 1];
   // wedge bound -> bucket count P (a power of two)
@@ -355,8 +389,13 @@ __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *_
     __syncthreads();
     return acc;
   }
+  // table slots per aggregating warp, buckets of a quarter of that on average
+  const bool wide = bound > c4_bucket_narrow_bound<TABLE>();
+  const uint32_t tslots = wide ? 2 * TABLE : TABLE;
+  uint32_t *keys = tables + (size_t)wid * 2 * tslots;
+  uint32_t *vals = keys + tslots;
   uint32_t P = 1;
-  while (P < kC4MaxBuckets && (unsigned long long)P * kC4BucketTarget < bound) P <<= 1;
+  while (P < kC4MaxBuckets && (unsigned long long)P * (tslots / 4) < bound) P <<= 1;
   const uint32_t pmask = P - 1;
   for (uint32_t b = tid; b < P; b += nt) bcnt[b] = 0;
   __syncthreads();
@@ -442,13 +481,18 @@ __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *_
   }
   // the buffer is read below by other warps of this CTA (plain loads, CTA scope)
   __syncthreads();
-  // each warp aggregates whole buckets in its hash table
-  for (uint32_t i = lane; i < kC4BucketTable; i += 32) {
+  // each warp aggregates whole buckets in its hash table (with wide tables,
+  // the warps of the first half only)
+  unsigned long long acc = 0;
+  if (wide && wid >= nw / 2) {
+    __syncthreads();
+    return acc;
+  }
+  for (uint32_t i = lane; i < tslots; i += 32) {
     keys[i] = kC4Empty;
     vals[i] = 0;
   }
   __syncwarp();
-  unsigned long long acc = 0;
   for (;;) {
     uint32_t b = 0;
     if (lane == 0) b = atomicAdd(&ctl[1], 1u);
@@ -456,10 +500,10 @@ __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *_
     if (b >= P) break;
     const uint32_t e0 = boff[b], e1 = boff[b + 1];
     if (e1 - e0 < 2) continue;  // a single wedge closes no cycle
-    // table of the smallest power of two >= 2 x entries (32 .. kC4BucketTable
+    // table of the smallest power of two >= 2 x entries (32 .. tslots
     // slots): clearing and summing it costs at most twice the bucket
     uint32_t bits = 5;
-    while (bits < 31 && (1u << bits) < 2 * (e1 - e0) && (1u << bits) < kC4BucketTable) ++bits;
+    while (bits < 31 && (1u << bits) < 2 * (e1 - e0) && (1u << bits) < tslots) ++bits;
     const uint32_t tmask = (1u << bits) - 1;
     for (uint32_t e = e0 + lane; e < e1; e += 32) {
       const uint32_t w = buf[e];

@@ -128,9 +128,22 @@ def _multi_hub_graph(hubs=(1500, 2200, 3100), nl=3200, nm=120, per=3, seed=6):
 NEVER = 0xffffffff
 
 
+def _wide_root_graph(nl=2000, per=300, nm=50000, seed=8):
+    """One hub joined to nl vertices, each joined to `per` random vertices of
+    a set of nm: the hub's wedge bound is about nl (per + 1) = 602,000, above
+    the bucketed kernel's narrow-table bound (524,288)."""
+    rng = np.random.default_rng(seed)
+    L0, M0 = 1, 1 + nl
+    e = [(0, L0 + i) for i in range(nl)]
+    for i in range(nl):
+        e += [(L0 + i, M0 + int(w)) for w in rng.choice(nm, size=per, replace=False)]
+    return gg.from_edges(1 + nl + nm, e, name="wide-root")
+
+
 @pytest.mark.parametrize("width,bound,pull", [(98304, 1048576, 262144), (98304, 512, NEVER), (512, 512, NEVER),
                                               (64, 2000, NEVER), (1000, 4000, NEVER), (98304, 512, 512),
-                                              (512, 512, 4000), (98304, 4000, 600), (98304, NEVER, 2000)])
+                                              (512, 512, 4000), (98304, 4000, 600), (98304, NEVER, 2000),
+                                              (98304, 0xfffffffe, 0xfffffffe)])
 def test_cycles4_range_path(gpm, width, bound, pull):
     # large roots counted range by range over vertex ids with a dense
     # shared-memory tally, or 128 at a time by the pull over every list with
@@ -138,13 +151,16 @@ def test_cycles4_range_path(gpm, width, bound, pull):
     # send most roots there (several pull passes, the last one partial), and
     # the multi-hub graph has roots whose lists span several 1024-entry chunks
     # and vertices of degree > 1024 that precede some roots of a pass and not
-    # others; totals, root ranges (passes with no root in the range skipped)
+    # others; with both bounds at their largest the bucketed class takes roots
+    # up to 2^20 (the wide-root graph's hub with wider tables in half of the
+    # warps); totals, root ranges (passes with no root in the range skipped)
     # and the motif inversion against the oracle
     old = gpm.get_options()
     try:
         gpm.set_options(c4_range_width=width, c4_range_bound=bound, c4_pull_bound=pull)
         C = gpm.Pattern.spec(O.CYCLE4, induced=False)
-        for g in _medium() + [gg.rmat(12, 16.0, seed=31), _multi_hub_graph()]:
+        extra = [_wide_root_graph()] if bound == 0xfffffffe else []
+        for g in _medium() + [gg.rmat(12, 16.0, seed=31), _multi_hub_graph()] + extra:
             G = gpm.Graph.from_host(g)
             want = O.cycles4(g)
             assert gpm.count(G, [C]) == [want], g.name
