@@ -156,19 +156,19 @@ def clique_pass_bytes(g, opts):
 # csrc/lg_device.cuh + csrc/clique.cu); a stale entry is ignored.
 NCU_COUNTERS = {
     "clique-rmat21": {
-        "lg_cta_hi": {"digest": "f9ad6174a8f66f41", "inst_per_launch": 151170570623,
-                      "dram_bytes_per_launch": 28330752 + 2048, "ncu_ms": 184.623},
+        "lg_cta_hi": {"digest": "88c1037f49f64430", "inst_per_launch": 151170055324,
+                      "dram_bytes_per_launch": 28273152 + 3584, "ncu_ms": 184.272},
     },
     "clique6-rmat20": {
-        "lg_cta_hi": {"digest": "f9ad6174a8f66f41", "inst_per_step": 1638179812823,
-                      "dram_bytes_per_step": 13044480, "ncu_ms": 1678.119},
+        "lg_cta_hi": {"digest": "88c1037f49f64430", "inst_per_step": 1638179347992,
+                      "dram_bytes_per_step": 13086464, "ncu_ms": 1676.139},
     },
     # every 4-cycle kernel launch of one step (c4_bound x 2, 42 pull passes of
     # c4_pull_mark x 2, c4_pull, c4_pull_tiny, c4_pull_rows; c4_bucket,
     # c4_small; the per-graph tables excluded), summed;
     # profiles/c4_sl_chunglu4m_dram.md; digest of motif.cu + motif_device.cuh + c4_pull.cu
     "sl-chunglu4m": {
-        "c4": {"digest": "639b5648dd4e8f72", "dram_bytes_per_step": 89739834880},
+        "c4": {"digest": "a53d75e409a2207c", "dram_bytes_per_step": 89361425664},
     },
     # profiles/enum_k5_er1m_counters.md; digest of enumerate.cu
     "motif5-er1m": {
@@ -184,8 +184,8 @@ NCU_COUNTERS = {
     },
     # three launches per step (k = 7, 8, 9), summed
     "clique789-cl1m": {
-        "lg_cta_lo": {"digest": "f9ad6174a8f66f41", "inst_per_step": 18020016326 + 36222245783 + 85370439759,
-                      "dram_bytes_per_step": 6797312 + 6560256 + 6670592, "ncu_ms": 27.433 + 64.626 + 179.485},
+        "lg_cta_lo": {"digest": "88c1037f49f64430", "inst_per_step": 18019851342 + 36222280753 + 85370485547,
+                      "dram_bytes_per_step": 6813952 + 6629632 + 6719744, "ncu_ms": 27.188 + 64.375 + 179.117},
     },
 }
 

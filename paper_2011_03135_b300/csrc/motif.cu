@@ -85,8 +85,7 @@ constexpr uint32_t kHashSlots = gpm_dev::kC4HashSlots;
 __global__ void c4_bound_kernel(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
                                 const uint32_t *__restrict__ deg, const uint32_t *__restrict__ edeg, uint32_t n,
                                 uint32_t hub_bound, uint32_t *__restrict__ counts, uint32_t *__restrict__ tasks,
-                                uint32_t *__restrict__ cursors, int fill, uint32_t *__restrict__ bvals = nullptr,
-                                uint32_t begin2 = 0) {
+                                uint32_t *__restrict__ cursors, int fill, uint32_t *__restrict__ bvals = nullptr) {
   // a warp takes 32 consecutive vertices: lane k sums the list of vertex k
   // on its own when it has at most kBoundLane entries (four loads in flight),
   // and the warp then walks the longer lists one at a time (lanes over the
@@ -149,7 +148,7 @@ __global__ void c4_bound_kernel(const uint64_t *__restrict__ rowptr, const uint3
         if (my_c == c) {
           const uint32_t at = pos + __popc(m & ((1u << lane) - 1u));
           tasks[at] = (uint32_t)(g0 + lane);
-          if (c == 2 && bvals) bvals[at - begin2] = my_b;
+          if (c >= 1 && bvals) bvals[at] = my_b;
         }
       } else {
         const uint32_t mb = __reduce_max_sync(0xffffffffu, my_c == 1 ? my_b : 0u);
@@ -181,6 +180,7 @@ struct C4Args {
   unsigned long long *acc;
   unsigned int *status;
   uint32_t *pool;  // bucketed class: per-CTA bucket buffers
+  const uint32_t *bvals;  // wedge bound of every task (plain path), or null
   uint32_t n;
 };
 
@@ -476,12 +476,12 @@ __global__ void __launch_bounds__(kHubThreads) c4_hub_kernel(const uint64_t *__r
 // tables of kC4PlainTable slots per warp, so that three CTAs fit an SM
 // (roots above c4_bucket_narrow_bound<kC4PlainTable>() take wider tables in
 // half of the warps); roots whose wedge bound is at most 3/4 of
-// kC4DirectSlots are counted in one shared-memory table instead (the space of
-// the bucket tables)
+// kC4DirectSlots are counted in one shared-memory table instead (the whole
+// dynamic shared memory)
 constexpr int kC4BucketThreads = 512;
 constexpr uint32_t kC4PlainTable = 256;
-constexpr uint32_t kC4DirectSlots =
-    (gpm_dev::c4_bucket_smem_words<kC4PlainTable>(kC4BucketThreads / 32) - (2 * gpm_dev::kC4MaxBuckets + 4)) / 2;
+constexpr uint32_t kC4DirectSlots = 1u << (31 - __builtin_clz(gpm_dev::c4_bucket_smem_words<kC4PlainTable>(
+                                                              kC4BucketThreads / 32) / 2));
 static_assert((kC4DirectSlots & (kC4DirectSlots - 1)) == 0, "direct table slots: a power of two");
 __global__ void __launch_bounds__(kC4BucketThreads) c4_bucket_kernel(C4Args a, uint64_t slot_words) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -501,7 +501,8 @@ __global__ void __launch_bounds__(kC4BucketThreads) c4_bucket_kernel(C4Args a, u
     const uint32_t v0 = a.tasks[task];
     if (v0 < a.root_lo || v0 >= a.root_hi) continue;
     acc += gpm_dev::c4_root_bucketed<kC4PlainTable>(a.rowptr, a.col, a.deg, a.edeg, v0, buf, buf + slot_words / 2,
-                                                    smem, s_x, &s_cnt, overflow, s_pre, s_rp, kC4DirectSlots);
+                                                    smem, s_x, &s_cnt, overflow, s_pre, s_rp, kC4DirectSlots,
+                                                    a.bvals ? a.bvals[task] : 0u);
   }
   bool carry = false;
   acc = warp_sum_checked(acc, carry);
@@ -1021,7 +1022,7 @@ static int ensure_c4_plain(gpm_graph *g, cudaStream_t st) {
   if (g->n) {
     GPM_LAUNCH("c4_bound_kernel", st,
                c4_bound_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->edeg, g->n, bound, nullptr,
-                                                        g->c4p_tasks, tmp + 4, 1, g->c4p_bval, g->c4p_begin[2]));
+                                                        g->c4p_tasks, tmp + 4, 1, g->c4p_bval));
     GPM_CUDA(cudaGetLastError());
   }
   const uint32_t nbig = h[2];
@@ -1029,7 +1030,8 @@ static int ensure_c4_plain(gpm_graph *g, cudaStream_t st) {
   if (nbig) {
     GPM_CUDA(cudaMemcpyAsync(roots.data(), g->c4p_tasks + g->c4p_begin[2], sizeof(uint32_t) * nbig,
                              cudaMemcpyDeviceToHost, st));
-    GPM_CUDA(cudaMemcpyAsync(bv.data(), g->c4p_bval, sizeof(uint32_t) * nbig, cudaMemcpyDeviceToHost, st));
+    GPM_CUDA(cudaMemcpyAsync(bv.data(), g->c4p_bval + g->c4p_begin[2], sizeof(uint32_t) * nbig,
+                             cudaMemcpyDeviceToHost, st));
   }
   GPM_CUDA(cudaStreamSynchronize(st));
   std::vector<uint32_t> ord(nbig);
@@ -1170,8 +1172,11 @@ static int launch_cycles4_range(gpm_graph *g, uint32_t root_lo, uint32_t root_hi
     GPM_CUDA(cudaGetLastError());
   }
   const uint32_t nsmall = g->c4p_begin[1], nbucket = g->c4p_begin[2] - g->c4p_begin[1];
-  if (nbucket)
-    GPM_TRY(launch_c4_bucketed(g, a, g->c4p_tasks + g->c4p_begin[1], nbucket, g->c4p_bucket_maxb, queues + 2, st));
+  if (nbucket) {
+    C4Args ab = a;
+    ab.bvals = g->c4p_bval + g->c4p_begin[1];  // the bounds computed when the classes were built
+    GPM_TRY(launch_c4_bucketed(g, ab, g->c4p_tasks + g->c4p_begin[1], nbucket, g->c4p_bucket_maxb, queues + 2, st));
+  }
   if (nsmall) GPM_TRY(launch_c4_small(g, a, g->c4p_tasks, nsmall, queues, st));
   return GPM_OK;
 }

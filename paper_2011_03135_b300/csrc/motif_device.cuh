@@ -330,7 +330,7 @@ __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *_
                                                                uint32_t *lin, uint32_t *buf, uint32_t *sm,
                                                                uint32_t *s_x, uint32_t *s_cnt, bool &overflow,
                                                                uint32_t *s_pre = nullptr, uint64_t *s_rp = nullptr,
-                                                               uint32_t direct_slots = 0) {
+                                                               uint32_t direct_slots = 0, uint32_t known_bound = 0) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   uint32_t *bcnt = sm;                       // [kC4MaxBuckets]: counts, then write cursors
   uint32_t *boff = sm + kC4MaxBuckets;       // [kC4MaxBuckets + 1]
@@ -338,13 +338,15 @@ __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *_
   uint32_t *const tables = sm + 2 * kC4MaxBuckets + 4;
   const uint32_t d0 = deg[v0];
   const uint64_t b0 = rowptr[v0], e0 = rowptr[v0 + 1];
-  // wedge bound -> bucket count P (a power of two)
+  // wedge bound (known from the class split, else summed here) -> bucket
+  // count P (a power of two)
   if (tid == 0) {
     ctl[0] = 0;
     ctl[2] = 0;
   }
   __syncthreads();
-  {
+  uint32_t bound = known_bound;
+  if (!bound) {
     unsigned long long b = 0;
     for (uint64_t e = b0 + tid; e < e0; e += nt) {
       const uint32_t x = col[e];
@@ -353,16 +355,18 @@ __device__ __forceinline__ unsigned long long c4_root_bucketed(const uint64_t *_
     }
     b = warp_sum(b);
     if (lane == 0 && b) atomicAdd(&ctl[0], (uint32_t)(b > 0xffffffffull ? 0xffffffffull : b));
+    __syncthreads();
+    bound = ctl[0];
   }
-  __syncthreads();
-  const uint32_t bound = ctl[0];
   if (direct_slots && s_pre && 4ull * bound <= 3ull * direct_slots) {
-    // every wedge end fits a table of direct_slots slots (at most 3/4 full):
-    // counted there directly, no bucket buffers
+    // every wedge end fits a table of direct_slots slots (at most 3/4 full)
+    // in the whole shared-memory region: counted there directly, no bucket
+    // buffers (every thread has read the bound before the region is reused)
+    __syncthreads();
     uint32_t bits = 6;
     while ((1u << bits) < 2 * bound && (1u << bits) < direct_slots) ++bits;
     const uint32_t tmask = (1u << bits) - 1;
-    uint32_t *dkeys = sm + 2 * kC4MaxBuckets + 4, *dvals = dkeys + direct_slots;
+    uint32_t *dkeys = sm, *dvals = dkeys + direct_slots;
     for (uint32_t i = tid; i <= tmask; i += nt) {
       dkeys[i] = kC4Empty;
       dvals[i] = 0;
