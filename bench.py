@@ -172,8 +172,8 @@ NCU_COUNTERS = {
     },
     # profiles/enum_k5_er1m_counters.md; digest of enumerate.cu
     "motif5-er1m": {
-        "enum_kernel_k5": {"digest": "bb0dcc50081af389", "inst_per_launch": 226039588066,
-                           "dram_bytes_per_launch": 45073920 + 975872, "ncu_ms": 267.053},
+        "enum_kernel_k5": {"digest": "8422a055c7d075f6", "inst_per_launch": 226039644786,
+                           "dram_bytes_per_launch": 44991232 + 972544, "ncu_ms": 266.830},
     },
     # three launches per step (6-path, 5-star, 6-cycle), summed;
     # profiles/guided_er1m_counters.md; digest of guided.cu
