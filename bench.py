@@ -168,7 +168,7 @@ NCU_COUNTERS = {
     # c4_small; the per-graph tables excluded), summed;
     # profiles/c4_sl_chunglu4m_dram.md; digest of motif.cu + motif_device.cuh + c4_pull.cu
     "sl-chunglu4m": {
-        "c4": {"digest": "a53d75e409a2207c", "dram_bytes_per_step": 89361425664},
+        "c4": {"digest": "ae36e12d04121df9", "dram_bytes_per_step": 84845894144},
     },
     # profiles/enum_k5_er1m_counters.md; digest of enumerate.cu
     "motif5-er1m": {

@@ -45,7 +45,8 @@ void free_graph(gpm_graph *g) {
                   g->prep_outdeg, g->prep_tiles, g->prep_keys, g->edeg, g->c4_hub_units, g->c4_hub_tally,
                   g->c4_hub_touched, g->c4_hub_ctr, g->core, g->core_work, g->c4p_tasks, g->c4p_bval,
                   g->c4p_items, g->c4_roff, g->c4q_ord, g->c4q_M, g->c4q_roots, g->c4q_queue,
-                  g->c4q_prow, g->c4q_pcol, g->c4q_chunks, g->c4q_cntb, g->gen_ucount};
+                  g->c4q_prow, g->c4q_pcol, g->c4q_chunks, g->c4q_cntb, g->gen_ucount,
+                  g->c4q_inv};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete g;

@@ -383,8 +383,8 @@ __global__ void c4_pull_rows_kernel(uint32_t *__restrict__ cntb, uint64_t nwords
 // [root_lo, root_hi) left out
 __global__ void c4_pull_mark_kernel(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
                                     const uint32_t *__restrict__ deg, const uint32_t *__restrict__ edeg,
-                                    const uint32_t *__restrict__ roots, uint32_t root_lo, uint32_t root_hi,
-                                    uint32_t *__restrict__ M, int set) {
+                                    const uint32_t *__restrict__ inv, const uint32_t *__restrict__ roots,
+                                    uint32_t root_lo, uint32_t root_hi, uint32_t *__restrict__ M, int set) {
   const uint32_t r = blockIdx.x;
   const uint32_t v0 = roots[r];
   if (v0 < root_lo || v0 >= root_hi) return;
@@ -393,9 +393,16 @@ __global__ void c4_pull_mark_kernel(const uint64_t *__restrict__ rowptr, const u
   for (uint64_t e = rowptr[v0] + threadIdx.x; e < rowptr[v0 + 1]; e += blockDim.x) {
     const uint32_t y = col[e];
     if (!precedes(edeg[e], y, d0, v0)) continue;
-    if (set) atomicOr(&M[4ull * y + word], bit);
-    else M[4ull * y + word] = 0u;
+    const uint32_t q = inv[y];
+    if (set) atomicOr(&M[4ull * q + word], bit);
+    else M[4ull * q + word] = 0u;
   }
+}
+
+// position of every vertex in the order ord
+__global__ void c4_pull_inv_kernel(const uint32_t *__restrict__ ord, uint32_t n, uint32_t *__restrict__ inv) {
+  const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += nth) inv[ord[i]] = (uint32_t)i;
 }
 
 // vertices by decreasing degree: a histogram of the degrees, then a scatter
@@ -428,7 +435,7 @@ __global__ void c4_deg_scatter_kernel(const uint32_t *__restrict__ deg, uint32_t
 // per position
 __global__ void c4_pull_csr_kernel(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
                                    const uint32_t *__restrict__ deg, const uint32_t *__restrict__ ord,
-                                   uint32_t n_act, const uint32_t *__restrict__ first,
+                                   const uint32_t *__restrict__ inv, uint32_t n_act, const uint32_t *__restrict__ first,
                                    const uint64_t *__restrict__ base, uint32_t *__restrict__ prow,
                                    uint32_t *__restrict__ pcol) {
   const uint32_t lane = threadIdx.x & 31;
@@ -443,7 +450,7 @@ __global__ void c4_pull_csr_kernel(const uint64_t *__restrict__ rowptr, const ui
       if (i + 1 == n_act) prow[n_act] = (uint32_t)(at + d);
     }
     const uint64_t src = rowptr[w];
-    for (uint32_t k = lane; k < d; k += 32) pcol[at + k] = col[src + k];
+    for (uint32_t k = lane; k < d; k += 32) pcol[at + k] = inv[col[src + k]];
   }
 }
 
@@ -503,14 +510,19 @@ static int ensure_c4_pull(gpm_graph *g, uint32_t npass, cudaStream_t st) {
     // the scatter advanced every cursor to the end of its degree's
     // positions: reload the first positions
     GPM_CUDA(cudaMemcpyAsync(hist, cur.data(), sizeof(uint32_t) * nbin, cudaMemcpyHostToDevice, st));
+    GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4q_inv, sizeof(uint32_t) * nw));
+    if (g->n) {
+      GPM_LAUNCH("c4_pull_inv_kernel", st, c4_pull_inv_kernel<<<blocks, 256, 0, st>>>(g->c4q_ord, g->n, g->c4q_inv));
+      GPM_CUDA(cudaGetLastError());
+    }
     GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4q_prow, sizeof(uint32_t) * ((size_t)g->c4q_nact + 1)));
     GPM_TRY(gpm_graph_alloc(g, (void **)&g->c4q_pcol, sizeof(uint32_t) * (pnnz + kPad)));
     GPM_CUDA(cudaMemsetAsync(g->c4q_pcol + pnnz, 0, sizeof(uint32_t) * kPad, st));
     GPM_CUDA(cudaMemsetAsync(g->c4q_prow, 0, sizeof(uint32_t), st));
     if (g->c4q_nact) {
       GPM_LAUNCH("c4_pull_csr_kernel", st,
-                 c4_pull_csr_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->c4q_ord, g->c4q_nact, hist,
-                                                            dbase, g->c4q_prow, g->c4q_pcol));
+                 c4_pull_csr_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->c4q_ord, g->c4q_inv,
+                                                            g->c4q_nact, hist, dbase, g->c4q_prow, g->c4q_pcol));
       GPM_CUDA(cudaGetLastError());
     }
     g->c4q_nchunks = (uint32_t)chunks.size();
@@ -583,8 +595,8 @@ int gpm_launch_c4_pull(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigne
     if (!any) continue;  // no root of this pass in the requested range
     const uint32_t *roots = g->c4q_roots + r0;
     GPM_LAUNCH("c4_pull_mark_kernel", st,
-               c4_pull_mark_kernel<<<nb, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->edeg, roots, root_lo, root_hi,
-                                                       g->c4q_M, 1));
+               c4_pull_mark_kernel<<<nb, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->edeg, g->c4q_inv, roots,
+                                                       root_lo, root_hi, g->c4q_M, 1));
     GPM_CUDA(cudaGetLastError());
     C4PullArgs a{};
     a.deg = g->deg;
@@ -619,8 +631,8 @@ int gpm_launch_c4_pull(gpm_graph *g, uint32_t root_lo, uint32_t root_hi, unsigne
       GPM_CUDA(cudaGetLastError());
     }
     GPM_LAUNCH("c4_pull_mark_kernel", st,
-               c4_pull_mark_kernel<<<nb, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->edeg, roots, root_lo, root_hi,
-                                                       g->c4q_M, 0));
+               c4_pull_mark_kernel<<<nb, 256, 0, st>>>(g->rowptr, g->col, g->deg, g->edeg, g->c4q_inv, roots,
+                                                       root_lo, root_hi, g->c4q_M, 0));
     GPM_CUDA(cudaGetLastError());
   }
   return GPM_OK;

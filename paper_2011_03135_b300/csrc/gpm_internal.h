@@ -202,6 +202,7 @@ struct gpm_graph {
   uint32_t *c4q_chunks = nullptr;  // {position, first entry} of each 1024-entry chunk of the first c4q_nbig
   uint32_t c4q_nchunks = 0;
   uint32_t *c4q_cntb = nullptr;  // 128 counters per vertex of degree > 1024 (zero between passes)
+  uint32_t *c4q_inv = nullptr;   // position of every vertex in c4q_ord (c4q_pcol and c4q_M use positions)
   uint32_t *c4q_M = nullptr;
   uint32_t *c4q_roots = nullptr;
   size_t c4q_roots_cap = 0;
