@@ -179,6 +179,7 @@ int gpm_pattern_destroy(gpm_pattern_t p);
 #define GPM_STRATEGY_LOCAL_COUNT 2   /* local counting (Section 5) for 3/4-vertex patterns */
 #define GPM_STRATEGY_EDGE 3          /* single edge / vertex: closed form */
 #define GPM_STRATEGY_ENUMERATE 4     /* pattern-oblivious enumeration with connectivity codes (5 vertices) */
+#define GPM_STRATEGY_GUIDED 5        /* pattern-guided search from the matching order (6..8 vertices) */
 
 typedef struct {
   uint32_t k;

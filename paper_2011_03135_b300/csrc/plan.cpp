@@ -206,7 +206,7 @@ int gpm_plan_pattern(gpm_pattern *p) {
     case PC_VERTEX:
     case PC_EDGE: info.strategy = GPM_STRATEGY_EDGE; break;
     case PC_CLIQUE: info.strategy = GPM_STRATEGY_CLIQUE_DAG; break;
-    case PC_OTHER: info.strategy = (k == 5) ? GPM_STRATEGY_ENUMERATE : 0; break;
+    case PC_OTHER: info.strategy = (k == 5) ? GPM_STRATEGY_ENUMERATE : GPM_STRATEGY_GUIDED; break;
     default: info.strategy = GPM_STRATEGY_LOCAL_COUNT; break;
   }
   if (k == 3) info.motif_index = (p->cls == PC_WEDGE) ? 0u : 1u;

@@ -30,7 +30,7 @@ ERRORS = {
 }
 GRAPH_VALIDATE = 1
 GRAPH_DEVICE_INPUT = 2
-STRATEGY_CLIQUE_DAG, STRATEGY_LOCAL_COUNT, STRATEGY_EDGE = 1, 2, 3
+STRATEGY_CLIQUE_DAG, STRATEGY_LOCAL_COUNT, STRATEGY_EDGE, STRATEGY_ENUMERATE, STRATEGY_GUIDED = 1, 2, 3, 4, 5
 MOTIF4_NAMES = ("3-star", "4-path", "tailed-triangle", "4-cycle", "diamond", "4-clique")
 MOTIF3_NAMES = ("wedge", "triangle")
 

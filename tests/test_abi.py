@@ -119,12 +119,65 @@ def test_planner_other_numberings(lib):
 
 
 def test_planner_five_vertex_pattern(lib):
-    # a 5-vertex house: planned, but no GPU kernel (strategy 0)
+    # a 5-vertex house: counted by the pattern-oblivious enumeration
     house = O.pattern(5, [(0, 1), (1, 2), (2, 3), (3, 0), (0, 4), (1, 4)])
     info = lib.Pattern.spec(house).info()
     assert info["automorphisms"] == O.automorphisms(house)
     assert O.orders_satisfying(5, info["sb_pairs"]) * info["automorphisms"] == 120
-    assert info["strategy"] == 4 and info["motif_index"] < 21  # pattern-oblivious enumeration
+    assert info["strategy"] == lib.STRATEGY_ENUMERATE and info["motif_index"] < 21
+
+
+def _connected_patterns(kmin, kmax):
+    import networkx as nx
+    for G in nx.graph_atlas_g():
+        k = G.number_of_nodes()
+        if kmin <= k <= kmax and nx.is_connected(G):
+            yield k, G.number_of_edges(), nx.to_numpy_array(G, dtype=np.uint8)
+
+
+def test_planner_every_connected_pattern_up_to_7_vertices(lib):
+    # appendix "Symmetry Breaking (Partial Order)" and "Pattern-Guided Search
+    # (Matching Order)", Section 4.3: over all 994 connected patterns of 3..7
+    # vertices (the networkx graph atlas), |Aut| equals the brute-force count,
+    # the partial order leaves exactly one of the |Aut| equivalent vertex
+    # orders, every vertex of the matching order after the first has a matched
+    # neighbour before it, and the degree filter is the pattern degree
+    seen = 0
+    for k, m, a in _connected_patterns(3, 7):
+        aut = O.automorphisms(a)
+        for induced in (True, False):
+            info = lib.Pattern.spec(a, induced=induced).info()
+            assert info["automorphisms"] == aut
+            assert O.orders_satisfying(k, info["sb_pairs"]) * aut == math.factorial(k)
+            mo = info["matching_order"]
+            assert sorted(mo) == list(range(k))
+            assert all(any(a[mo[j], mo[i]] for i in range(j)) for j in range(1, k))
+            assert info["min_degree"] == [int(x) for x in a.sum(axis=1)]
+            clique = m == k * (k - 1) // 2
+            want = (lib.STRATEGY_CLIQUE_DAG if clique else lib.STRATEGY_LOCAL_COUNT if k <= 4
+                    else lib.STRATEGY_ENUMERATE if k == 5 else lib.STRATEGY_GUIDED)
+            assert info["strategy"] == want
+        seen += 1
+    assert seen == 2 + 6 + 21 + 112 + 853
+
+
+def test_planner_random_eight_vertex_patterns(lib):
+    import networkx as nx
+    rng = np.random.default_rng(8)
+    seen = 0
+    while seen < 60:
+        G = nx.gnp_random_graph(8, float(rng.uniform(0.25, 0.8)), seed=int(rng.integers(1 << 30)))
+        if not nx.is_connected(G):
+            continue
+        a = nx.to_numpy_array(G, dtype=np.uint8)
+        info = lib.Pattern.spec(a, induced=False).info()
+        aut = O.automorphisms(a)
+        assert info["automorphisms"] == aut
+        assert O.orders_satisfying(8, info["sb_pairs"]) * aut == 40320
+        mo = info["matching_order"]
+        assert sorted(mo) == list(range(8))
+        assert all(any(a[mo[j], mo[i]] for i in range(j)) for j in range(1, 8))
+        seen += 1
 
 
 def test_options_roundtrip(lib):
