@@ -361,7 +361,9 @@ int gpm_graph_create(const uint64_t *rowptr, const uint32_t *col, uint32_t n, ui
   if (e != cudaSuccess) return fail(gpm_cuda_fail(e, "graph upload"));
   if (flags & GPM_GRAPH_VALIDATE) {
     uint32_t *dst = reinterpret_cast<uint32_t *>(g->work + WK_STATUS);
-    if ((rc = gpm_launch_validate(g, st, dst))) return fail(rc);
+    // the degree array (filled only when the graph is prepared) lists the
+    // long rows; WK_MISC (cleared above) counts them
+    if ((rc = gpm_launch_validate(g, st, dst, g->deg, reinterpret_cast<uint32_t *>(g->work + WK_MISC)))) return fail(rc);
     uint32_t s = 0;
     e = cudaMemcpyAsync(&s, dst, sizeof(s), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

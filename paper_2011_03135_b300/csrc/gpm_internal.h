@@ -269,7 +269,11 @@ int gpm_plan_pattern(gpm_pattern *p);  // fills cls, info, tmpl_to_pat
 // ---------------------------------------------------------------------------
 // device entry points (launchers), all asynchronous on `st`
 // ---------------------------------------------------------------------------
-int gpm_launch_validate(gpm_graph *g, cudaStream_t st, uint32_t *d_status);
+// CSR checks into *d_status; d_longv (room for n ids, e.g. the not yet
+// filled degree array) and d_nlong (zero) let rows above 2048 entries be
+// checked one CTA per row
+int gpm_launch_validate(gpm_graph *g, cudaStream_t st, uint32_t *d_status, uint32_t *d_longv = nullptr,
+                        uint32_t *d_nlong = nullptr);
 int gpm_prepare_graph(gpm_graph *g, cudaStream_t st);
 int gpm_ensure_classes(gpm_graph *g, cudaStream_t st);
 // core numbers of every vertex into g->core and the peel round of every

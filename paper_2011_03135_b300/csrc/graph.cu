@@ -18,10 +18,45 @@ __device__ __forceinline__ bool precedes(uint32_t du, uint32_t u, uint32_t dv, u
 }
 
 // ---------------------------------------------------------------------------
-// validation: one warp per vertex
+// validation: one warp per vertex; rows longer than kValidateSplit entries
+// are listed and checked by validate_long_kernel, one CTA per row, so that a
+// hub's row does not leave one warp working after all others are done
 // ---------------------------------------------------------------------------
+constexpr uint32_t kValidateSplit = 2048;
+
+// the checks of entry i of the row [b, e) of v (b <= i < e <= nnz, checked by
+// the caller): id range, loop, ascending order, mirror arc
+__device__ __forceinline__ uint32_t validate_entry(const uint64_t *__restrict__ rowptr,
+                                                   const uint32_t *__restrict__ col, uint32_t n, uint64_t nnz,
+                                                   uint64_t v, uint64_t b, uint64_t i) {
+  uint32_t bad = 0;
+  const uint32_t c = col[i];
+  if (c >= n) return ST_OUT_OF_RANGE;
+  if (c == v) bad |= ST_SELF_LOOP;
+  if (i > b) {
+    const uint32_t p = col[i - 1];
+    if (p == c) bad |= ST_DUPLICATE;
+    else if (p > c) bad |= ST_NOT_SORTED;
+  }
+  // symmetric: v must be in N(c) (binary search; rows may be unsorted if
+  // the input is bad, in which case NOT_SORTED is reported as well)
+  uint64_t lo = rowptr[c], hi = rowptr[c + 1];
+  if (hi < lo || hi > nnz) return bad | ST_BAD_ROWPTR;
+  const uint64_t end = hi;
+  while (lo < hi) {
+    uint64_t mid = lo + ((hi - lo) >> 1);
+    if (col[mid] < (uint32_t)v) lo = mid + 1;
+    else hi = mid;
+  }
+  if (lo >= end || col[lo] != (uint32_t)v) bad |= ST_ASYMMETRIC;
+  return bad;
+}
+
+// longv (room for n ids) and *nlong (zero at launch) collect the rows longer
+// than kValidateSplit; with longv null every row is checked here
 __global__ void validate_kernel(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col, uint32_t n,
-                                uint64_t nnz, uint32_t *__restrict__ status) {
+                                uint64_t nnz, uint32_t *__restrict__ status, uint32_t *__restrict__ longv,
+                                uint32_t *__restrict__ nlong) {
   const int lane = threadIdx.x & 31;
   const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -35,36 +70,30 @@ __global__ void validate_kernel(const uint64_t *__restrict__ rowptr, const uint3
       bad |= ST_BAD_ROWPTR;
       continue;
     }
-    for (uint64_t i = b + lane; i < e; i += 32) {
-      const uint32_t c = col[i];
-      if (c >= n) {
-        bad |= ST_OUT_OF_RANGE;
-        continue;
-      }
-      if (c == v) bad |= ST_SELF_LOOP;
-      if (i > b) {
-        const uint32_t p = col[i - 1];
-        if (p == c) bad |= ST_DUPLICATE;
-        else if (p > c) bad |= ST_NOT_SORTED;
-      }
-      // symmetric: v must be in N(c) (binary search; rows may be unsorted if
-      // the input is bad, in which case NOT_SORTED is reported as well)
-      uint64_t lo = rowptr[c], hi = rowptr[c + 1];
-      if (hi < lo || hi > nnz) {
-        bad |= ST_BAD_ROWPTR;
-        continue;
-      }
-      const uint64_t end = hi;
-      while (lo < hi) {
-        uint64_t mid = lo + ((hi - lo) >> 1);
-        if (col[mid] < (uint32_t)v) lo = mid + 1;
-        else hi = mid;
-      }
-      if (lo >= end || col[lo] != (uint32_t)v) bad |= ST_ASYMMETRIC;
+    if (longv && e - b > kValidateSplit) {
+      if (lane == 0) longv[atomicAdd(nlong, 1u)] = (uint32_t)v;
+      continue;
     }
+    for (uint64_t i = b + lane; i < e; i += 32) bad |= validate_entry(rowptr, col, n, nnz, v, b, i);
   }
   bad = __reduce_or_sync(0xffffffffu, bad);
   if (lane == 0 && bad) atomicOr(status, bad);
+}
+
+// the rows listed by validate_kernel (whose offsets it has checked), one CTA
+// per row at a time
+__global__ void validate_long_kernel(const uint64_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
+                                     uint32_t n, uint64_t nnz, uint32_t *__restrict__ status,
+                                     const uint32_t *__restrict__ longv, const uint32_t *__restrict__ nlong) {
+  const uint32_t count = *nlong;
+  uint32_t bad = 0;
+  for (uint32_t l = blockIdx.x; l < count; l += gridDim.x) {
+    const uint32_t v = longv[l];
+    const uint64_t b = rowptr[v], e = rowptr[v + 1];
+    for (uint64_t i = b + threadIdx.x; i < e; i += blockDim.x) bad |= validate_entry(rowptr, col, n, nnz, v, b, i);
+  }
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31) == 0 && bad) atomicOr(status, bad);
 }
 
 // degrees and the largest degree
@@ -284,10 +313,17 @@ int gpm_num_sms(int device) {
   return cached[device];
 }
 
-int gpm_launch_validate(gpm_graph *g, cudaStream_t st, uint32_t *d_status) {
-  int blocks = gpm_num_sms(g->device) * 8;
-  GPM_LAUNCH("validate_kernel", st, validate_kernel<<<blocks, 256, 0, st>>>(g->rowptr, g->col, g->n, g->nnz, d_status));
+int gpm_launch_validate(gpm_graph *g, cudaStream_t st, uint32_t *d_status, uint32_t *d_longv, uint32_t *d_nlong) {
+  const int sms = gpm_num_sms(g->device);
+  GPM_LAUNCH("validate_kernel", st,
+             validate_kernel<<<sms * 8, 256, 0, st>>>(g->rowptr, g->col, g->n, g->nnz, d_status, d_longv, d_nlong));
   GPM_CUDA(cudaGetLastError());
+  if (d_longv) {
+    GPM_LAUNCH("validate_long_kernel", st,
+               validate_long_kernel<<<sms * 2, 1024, 0, st>>>(g->rowptr, g->col, g->n, g->nnz, d_status, d_longv,
+                                                              d_nlong));
+    GPM_CUDA(cudaGetLastError());
+  }
   return GPM_OK;
 }
 

@@ -342,6 +342,47 @@ def test_validation_rejects_malformed_csr(gpm, rows, code):
     assert e.value.name == code
 
 
+def _hub_rows(h):
+    # hubs 0 and 1 each joined to leaves 2..h+1: rows of h entries
+    return [list(range(2, h + 2)), list(range(2, h + 2))] + [[0, 1] for _ in range(h)]
+
+
+def _long_row_cases(h=3000):
+    swapped = _hub_rows(h)
+    swapped[0][100], swapped[0][101] = swapped[0][101], swapped[0][100]
+    unmirrored = _hub_rows(h)
+    unmirrored[h + 1] = []  # 0 -> h+1 and 1 -> h+1 have no mirror; nnz stays even
+    outside = _hub_rows(h)
+    outside[0][-1] = outside[1][-1] = h + 2
+    outside[h + 1] = []
+    doubled = _hub_rows(h)
+    doubled[0][50] = doubled[0][49]
+    return [(swapped, "NOT_SORTED"), (unmirrored, "ASYMMETRIC"), (outside, "OUT_OF_RANGE"),
+            (doubled, "DUPLICATE")]
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_validation_rejects_malformed_long_rows(gpm, case):
+    # rows above 2048 entries are checked by their own kernel: every fault
+    # planted here lies in the two hub rows only
+    rows, code = _long_row_cases()[case]
+    rp, col = _bad(len(rows), rows)
+    with pytest.raises(gpm.GpmError) as e:
+        gpm.Graph(rp, col, len(rp) - 1)
+    assert e.value.name == code
+
+
+def test_validation_accepts_rows_at_and_above_the_split(gpm):
+    # hub 0 has 2048 neighbours (warp-per-vertex check), hub 1 2049 (long-row
+    # check), the leaves form a path
+    edges = [(0, k) for k in range(2, 2050)] + [(1, k) for k in range(2, 2051)] + [(k, k + 1) for k in range(2, 2050)]
+    g = gg.from_edges(2051, edges)
+    assert np.diff(g.rowptr.astype(np.int64))[:2].tolist() == [2048, 2049]
+    G = gpm.Graph.from_host(g)
+    assert gpm.count(G, [gpm.Pattern.clique(3), gpm.Pattern.clique(4)]) == [O.triangles(g), O.cliques(g, 4)]
+    G.close()
+
+
 def test_degenerate_graphs(gpm):
     for g in (gg.empty(1), gg.empty(100), gg.from_edges(2, [(0, 1)])):
         G = gpm.Graph.from_host(g)
