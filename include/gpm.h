@@ -77,7 +77,12 @@ typedef struct gpm_pattern *gpm_pattern_t;
  * The library copies both arrays; the caller keeps ownership of its buffers.
  * With GPM_GRAPH_VALIDATE, a malformed CSR returns GPM_E_NOT_SORTED,
  * GPM_E_SELF_LOOP, GPM_E_DUPLICATE, GPM_E_ASYMMETRIC or GPM_E_OUT_OF_RANGE and
- * no handle is created. Without it the input is trusted.
+ * no handle is created; an input with several faults reports the first of
+ * GPM_E_INVALID_ARG (offsets that decrease or run past nnz),
+ * GPM_E_OUT_OF_RANGE, GPM_E_NOT_SORTED, GPM_E_DUPLICATE, GPM_E_SELF_LOOP,
+ * GPM_E_ASYMMETRIC. Without the flag the input is trusted. In both cases an
+ * odd nnz (GPM_E_ASYMMETRIC) and, for host input, rowptr[0] != 0 or
+ * rowptr[n] != nnz (GPM_E_INVALID_ARG) are rejected before any device work.
  * Synchronises `stream`.
  */
 int gpm_graph_create(const uint64_t *rowptr, const uint32_t *col, uint32_t n, uint64_t nnz, uint32_t flags,
