@@ -141,6 +141,8 @@ typedef struct {
   uint64_t device_bytes;    /* device memory held by the handle */
 } gpm_graph_info_t;
 
+/* Facts of a graph handle into *info (host memory, written only on success);
+ * GPM_E_INVALID_ARG for a null handle or output. No device work. */
 int gpm_graph_info(gpm_graph_t g, gpm_graph_info_t *info);
 
 /* ---------------- patterns ---------------- */
@@ -177,6 +179,7 @@ int gpm_pattern_clique(uint32_t k, gpm_pattern_t *out);
  */
 int gpm_pattern_motifs(uint32_t k, gpm_pattern_t *out, uint32_t *npat);
 
+/* Release a pattern handle (host memory only); GPM_E_INVALID_ARG for null. */
 int gpm_pattern_destroy(gpm_pattern_t p);
 
 /* strategy chosen by the planner */
@@ -200,6 +203,8 @@ typedef struct {
   uint32_t min_degree[8];      /* degree filter per pattern vertex (its pattern degree) */
 } gpm_pattern_info_t;
 
+/* The planner's facts of a pattern into *info (host memory, written only on
+ * success); GPM_E_INVALID_ARG for a null handle or output. No device work. */
 int gpm_pattern_info(gpm_pattern_t p, gpm_pattern_info_t *info);
 
 /* ---------------- counting ---------------- */
@@ -372,6 +377,8 @@ int gpm_batch_info(gpm_batch_t b, uint32_t *nitems, uint32_t *roots_per_item, ui
  * kernels one replay launches. */
 int gpm_batch_direct(gpm_batch_t b, uint32_t *ndirect, uint64_t *graph_kernels);
 
+/* Release a batch and its captured graph and device buffers (synchronises
+ * the batch's stream); the graphs it counts stay owned by the caller. */
 int gpm_batch_destroy(gpm_batch_t b);
 
 /* create + run + destroy. */
@@ -508,6 +515,10 @@ typedef struct {
                                the hub class takes the larger roots */
 } gpm_options_t;
 
+/* Process-wide: gpm_set_options applies every non-zero field (GPM_E_INVALID_ARG,
+ * and nothing applied, when a field is outside its range); graphs rebuild the
+ * task classes that depend on a changed field at their next count.
+ * gpm_get_options writes the values in force. */
 int gpm_set_options(const gpm_options_t *opt);
 int gpm_get_options(gpm_options_t *opt);
 

@@ -279,7 +279,8 @@ const char *gpm_version(void) { return "gpm-b300 0.1 (sm_103a)"; }
 
 int gpm_set_options(const gpm_options_t *opt) {
   if (!opt) return gpm_fail(GPM_E_INVALID_ARG, "null options");
-  gpm_tuning &t = gpm_tune();
+  // checked and applied on a copy: an invalid field leaves every option as it was
+  gpm_tuning t = gpm_tune();
   if (opt->warp_max_degree) {
     if (opt->warp_max_degree < 32 || opt->warp_max_degree > 256)
       return gpm_fail(GPM_E_INVALID_ARG, "warp_max_degree must be in [32, 256]");
@@ -310,6 +311,7 @@ int gpm_set_options(const gpm_options_t *opt) {
     if (opt->c4_pull_bound < 512) return gpm_fail(GPM_E_INVALID_ARG, "c4_pull_bound must be >= 512");
     t.c4_pull_bound = opt->c4_pull_bound;
   }
+  gpm_tune() = t;
   return GPM_OK;
 }
 

@@ -206,4 +206,9 @@ def test_options_roundtrip(lib):
                 dict(c4_range_width=1001), dict(c4_pull_bound=511)):
         with pytest.raises(lib.GpmError):
             lib.set_options(**bad)
+    # a call with one invalid field applies none of its fields
+    before = lib.get_options()
+    with pytest.raises(lib.GpmError):
+        lib.set_options(warp_max_degree=96, c4_hub_bound=2000, c4_pull_bound=511)
+    assert lib.get_options() == before
     lib.set_options(**{k: v for k, v in old.items() if v})
