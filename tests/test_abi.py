@@ -212,3 +212,29 @@ def test_options_roundtrip(lib):
         lib.set_options(warp_max_degree=96, c4_hub_bound=2000, c4_pull_bound=511)
     assert lib.get_options() == before
     lib.set_options(**{k: v for k, v in old.items() if v})
+
+
+def test_binding_structs_match_the_header(lib, tmp_path):
+    # every struct the binding passes through the ABI has the header's size
+    # and field offsets (compiled here with the host C compiler)
+    import subprocess
+    pairs = {"gpm_graph_info_t": lib.GraphInfo, "gpm_pattern_info_t": lib.PatternInfo, "gpm_query_t": lib.Query,
+             "gpm_server_opts_t": lib.ServerOpts, "gpm_completion_t": lib.Completion, "gpm_options_t": lib.Options}
+    lines = ['#include <stdio.h>', '#include "gpm.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, field, value = line.split()
+        got[(cname, field)] = int(value)
+    for cname, py in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
