@@ -238,3 +238,22 @@ def test_binding_structs_match_the_header(lib, tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for field, _ in py._fields_:
             assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
+
+
+def test_binding_declares_every_call_with_the_header_arity(lib):
+    # each call of include/gpm.h is declared in the binding with as many
+    # arguments as its prototype has
+    txt = ""
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt += open(os.path.join(ROOT, "include", h)).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    protos = re.findall(r"^\s*(?:int|uint64_t|const char\s*\*)\s*(gpm_\w+)\s*\(([^;]*?)\)\s*;", txt,
+                        flags=re.M | re.S)
+    assert len(protos) == len(_declared())
+    for name, args in protos:
+        args = args.strip()
+        arity = 0 if args in ("", "void") else args.count(",") + 1
+        declared = getattr(lib._lib, name).argtypes
+        assert declared is not None, name
+        assert len(declared) == arity, (name, arity, len(declared))
