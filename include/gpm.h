@@ -52,7 +52,7 @@ extern "C" {
 #define GPM_E_DEVICE (-9)            /* a CUDA call failed */
 #define GPM_E_TIMEOUT (-10)          /* a bounded device-side wait gave up */
 #define GPM_E_BUSY (-11)             /* admission refused (server) */
-#define GPM_E_UNSUPPORTED (-12)      /* pattern class has no GPU kernel yet */
+#define GPM_E_UNSUPPORTED (-12)      /* outside a kernel's limits (pattern size, root out-degree, root ranges) */
 #define GPM_E_OVERFLOW (-13)         /* a result does not fit in 64 bits */
 #define GPM_E_OUT_OF_RANGE (-14)     /* vertex id >= n in the CSR */
 

@@ -257,3 +257,14 @@ def test_binding_declares_every_call_with_the_header_arity(lib):
         declared = getattr(lib._lib, name).argtypes
         assert declared is not None, name
         assert len(declared) == arity, (name, arity, len(declared))
+
+
+def test_binding_constants_match_the_header(lib):
+    txt = open(os.path.join(ROOT, "include", "gpm.h")).read()
+    codes = {name: int(v) for name, v in re.findall(r"#define GPM_E_(\w+) \((-\d+)\)", txt)}
+    assert codes == {name: code for code, name in lib.ERRORS.items()}
+    defs = {name: int(v) for name, v in re.findall(r"#define GPM_(\w+) (\d+)u?\b", txt)}
+    for name in ("GRAPH_VALIDATE", "GRAPH_DEVICE_INPUT", "STRATEGY_CLIQUE_DAG", "STRATEGY_LOCAL_COUNT",
+                 "STRATEGY_EDGE", "STRATEGY_ENUMERATE", "STRATEGY_GUIDED", "QUERY_MOTIF3", "QUERY_MOTIF4",
+                 "QUERY_TC", "QUERY_CLIQUE4", "QUERY_CLIQUE5"):
+        assert getattr(lib, name) == defs[name], name
