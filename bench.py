@@ -18,10 +18,11 @@ Under torchrun (N > 1) every rank counts its own replica of the workload
 the step time. `--impl reference` times the CPU oracle (single-threaded C) on
 a bounded root sample of the same workload.
 
-Other legs (one GPU, one JSON line each): `--workload tc`, `sl`, `motif5`, `guided` (general patterns by the pattern-guided search, Erdos-Renyi 1M)
-(the 21 five-vertex motifs, Erdos-Renyi 1M), `clique6` (6-cliques, R-MAT
-20), `clique789` (7-, 8-, 9-cliques, Chung-Lu 1M), `batched` and `served`
-(many small queries); `--orientation core` runs the headline leg under the
+Other legs (one GPU, one JSON line each): `--workload tc`, `sl`, `motif5`
+(the 21 five-vertex motifs, Erdos-Renyi 1M), `guided` (general patterns by
+the pattern-guided search, Erdos-Renyi 1M), `clique6` (6-cliques, R-MAT 20),
+`clique789` (7-, 8-, 9-cliques, Chung-Lu 1M), `batched` and `served` (many
+small queries); `--orientation core` runs the headline leg under the
 core value based (degeneracy) order, k-core peel included in each step;
 `--case NAME --reps N` runs a named workload for a profiler.
 """
